@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Throughput of the dense-indirect EM (VOLDOR+, Sec. III-A) on one GPU per rank.
+
+One step = one whole window of EM on the KITTI-like driving workload
+(1216 x 368, N = 6 flows, K = 128 hypotheses, 8 EM iterations, S = 64 P3P
+samples per frame): the monocular bootstrap plus 8 iterations of depth
+M-step, rigidness E-step and pose M-step.  Inputs are synthetic
+(synth.make_window("driving1216", seed 2000 + rank)) and resident in HBM;
+L2 is flushed before every timed step.
+
+value  = pixel*frame*iterations per second over all ranks (W*H*N*8 per window)
+e2e    = the same metric through the C ABI with host buffers: flows pushed from
+         pinned host memory, inverse depth and poses read back, every step.
+roofline = the depth-sampling kernel (the dominant kernel), FP32-issue bound:
+         algorithmic FP32 instructions per launch / its CUDA-event time.
+cpu_baseline = the float64 oracle on a bounded crop of the same window.
+
+--impl reference times the oracle (the CPU definition of the method) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] \
+    if os.path.exists(os.path.join(ROOT, "BASELINE.json")) else "EM pixel*frame*iters/s"
+UNIT = "pixel*frame*iter/s"
+WORK = dict(name="driving1216", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2000)
+
+# Algorithmic FP32 instructions of one hypothesis evaluation against one flow
+# (projection 3 FMA + 2 MUL, residual 4 ADD + 2 FMA/MUL, energy 5, view tests 1
+# for t = 1; plus 12 for the bilinear sample and 4 bound tests for t >= 2) and
+# MUFU operations (one reciprocal, one log2).
+FP32_T1, FP32_TN, MUFU_PER_EVAL = 17, 33, 2
+SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_per_pixel_hyp(N):
+    return FP32_T1 + (N - 1) * FP32_TN
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n > 1 else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x, device):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(seconds_hint=20.0):
+    """Time the float64 oracle on a centred 304 x 92 crop of the same window
+    (1/16 of the pixels, same N, K, S): one EM iteration from a mid-EM state."""
+    import synth
+    from oracle import em as oem
+    from oracle import model as omodel
+    win = synth.make_window(WORK["name"], WORK["seed"])
+    cw, ch = WORK["W"] // 4, WORK["H"] // 4
+    u0, v0 = (WORK["W"] - cw) // 2, (WORK["H"] - ch) // 2
+    fx, fy, cx, cy = win.intrinsics
+    P = omodel.Problem(cw, ch, WORK["N"], (fx, fy, cx - u0, cy - v0),
+                       np.ascontiguousarray(win.flow[:, v0:v0 + ch, u0:u0 + cw]))
+    pr = win.params
+    p = omodel.Params(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"], rho_max=pr["rho_max"],
+                      n_hyp=WORK["K"], n_pose_samples=WORK["S"])
+    s = pr["scale"]
+    G = win.G.copy()
+    G[:, :, 3] /= s
+    rho = (s / win.depth0[v0:v0 + ch, u0:u0 + cw]).astype(np.float32)
+    S = omodel.State(rho=rho, q=np.ones((P.N, ch, cw), np.float32),
+                     qhat=np.zeros((ch, cw), np.float32), G=G)
+    t0 = time.perf_counter()
+    oem.iteration(P, S, 0, p)
+    dt = time.perf_counter() - t0
+    units = cw * ch * WORK["N"] * 1
+    return units / dt, dt, f"one EM iteration of the float64 oracle on a centred {cw}x{ch} crop " \
+                           f"(N={WORK['N']}, K={WORK['K']}, S={WORK['S']}), {dt:.1f} s"
+
+
+def cpu_cores_used():
+    return 1
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local, pg):
+    import torch
+    from paper_2104_06800_gb300 import build as B
+    from paper_2104_06800_gb300 import voldor as V
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    V.load()
+    stream = torch.cuda.current_stream(dev)
+    win = synth.make_window(WORK["name"], WORK["seed"] + rank)
+    pr = win.params
+    params = V.vd_params_default(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"],
+                                 rho_max=pr["rho_max"], n_hyp=WORK["K"],
+                                 n_pose_samples=WORK["S"], seed=WORK["seed"] + rank)
+    W, H, N, iters = win.W, win.H, win.N, WORK["iters"]
+    ctx = V.vd_create(W, H, N, win.intrinsics, params, V.C.c_void_p(stream.cuda_stream))
+    flows_dev = torch.from_numpy(win.flow).to(dev)
+    for t in range(1, N + 1):
+        V.vd_push_flow(ctx, t, flows_dev[t - 1])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        V.vd_bootstrap(ctx)
+        V.vd_run_em(ctx, iters, stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = Clocks(local)
+    clocks.start()
+    V.vd_profile_enable(ctx, True)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    prof = V.vd_get_profile(ctx)
+    V.vd_profile_enable(ctx, False)
+    clk = clocks.stop()
+    barrier(pg)
+    total_ms = sum(times)
+    total_ms = max_over_ranks(pg, total_ms, dev)
+    units_per_window = W * H * N * iters
+    value = units_per_window * args.steps * world / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the depth-sampling kernel
+    smp = prof["depth_sample"]
+    launch_ms = smp["ms"] / max(smp["calls"], 1)
+    evals = W * H * N * WORK["K"]
+    fp32 = W * H * WORK["K"] * fp32_per_pixel_hyp(N)
+    achieved = fp32 / (launch_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_depth_sample", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "launch_ms": round(launch_ms, 4),
+                "evals_per_s": round(evals / (launch_ms / 1e3), 1),
+                "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)"}
+    stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
+
+    e2e = None
+    if not args.no_e2e:
+        host_flows = [torch.from_numpy(win.flow[t]).pin_memory() for t in range(N)]
+        host_rho = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        n_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for t in range(N):
+                V.vd_push_flow(ctx, t + 1, host_flows[t].numpy())
+            V.vd_run_em(ctx, iters, stats=False)
+            V.vd_get_inv_depth(ctx, host_rho.numpy())
+            V.vd_get_poses(ctx, N)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(pg, time.perf_counter() - t0, dev)
+        e2e = {"value": round(units_per_window * n_e2e * world / dt, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(win.flow.nbytes),
+               "d2h_bytes_per_step": int(W * H * 4 + (N + 1) * 12 * 8), "steps": n_e2e}
+
+    V.vd_destroy(ctx)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "driving1216: 1216x368, N=6 flows, K=128 hypotheses, 8 EM "
+                                   "iterations, S=64 P3P samples, monocular bootstrap",
+                       "windows_per_step_per_gpu": 1, "l2": "flushed (256 MB write) before "
+                                                            "every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "windows_per_s": round(args.steps * world / (total_ms / 1e3), 3),
+            "roofline": roofline, "stage_ms_per_window": stages,
+            "gpu_launches": int(prof["total_launches"]), "clocks": clk, "e2e": e2e}
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        units_s = []
+        samples = []
+        for _ in range(max(args.warmup, 0) and 0):
+            pass
+        for _ in range(args.steps):
+            v, dt, desc = oracle_sample()
+            units_s.append(v)
+            samples.append(dt)
+        value = statistics.median(units_s)
+        line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * statistics.median(samples), 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "driving1216 crop (oracle sample)"},
+                "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cpu_cores_used(),
+                                 "kind": "oracle", "sample": desc},
+                "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+    line = run_ours(args, rank, world, local, pg)
+    if rank == 0:
+        if not args.no_cpu:
+            v, dt, desc = oracle_sample()
+            line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cpu_cores_used(),
+                                    "kind": "oracle", "sample": desc}
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * voldor_em.h -- C ABI of the GB300 (sm_103a) dense-indirect EM library.
+ *
+ * The library estimates, for one window of N dense optical-flow fields, the
+ * inverse-depth map of the reference frame, per-flow rigidness maps and the
+ * camera poses, by the generalised EM of VOLDOR+ (Min & Dunn, "VOLDOR+SLAM:
+ * For the times when feature-based or direct methods are not good enough",
+ * 2021, Sec. III-A, Eq. 1-7):
+ *   depth M-step      -- sample inverse-depth hypotheses per pixel, keep the
+ *                        argmin of flow energy + prior energy (Eq. 5, Eq. 4),
+ *                        propagate along alternately directed 1-D chains;
+ *   rigidness E-step  -- forward-backward smoothing of two-state chains;
+ *   pose M-step       -- Monte-Carlo P3P samples scored against every rigid
+ *                        pixel, mean-shift mode in se(3) (Eq. 7).
+ *
+ * Conventions used by every call
+ *   - Pixel (u, v): u = column in [0, W), v = row in [0, H); maps are row-major
+ *     [H][W] float32 (rigidness [N][H][W]).
+ *   - Flow X_t (t = 1..N) lives on frame t-1's pixel grid and holds (dx, dy) in
+ *     pixels, interleaved: uv[2 * (v * row_pitch + u) + {0, 1}].
+ *   - Poses are float64 3x4 row-major [R | tau].  ABSOLUTE pose G_t maps
+ *     reference-frame (frame 0) coordinates to frame t: X_t = R X_0 + tau.
+ *     RELATIVE pose T_t = G_t G_{t-1}^-1 maps frame t-1 to frame t.
+ *   - Host pointers (VD_MEM_HOST) may be pageable or pinned; device pointers
+ *     (VD_MEM_DEVICE) must be device memory of the context's GPU.  The library
+ *     copies inputs when they are pushed and never keeps a caller pointer.
+ *     All buffers belong to the caller; the context owns its internal state.
+ *   - Work is issued on the context's CUDA stream.  Calls that return data to
+ *     host memory, and vd_run_em, synchronise that stream before returning.
+ *   - No call aborts or throws.  Every call returns a vd_status; on
+ *     VD_ERR_CUDA the CUDA error string is available from vd_last_error().
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef VOLDOR_EM_H
+#define VOLDOR_EM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vd_ctx vd_ctx;
+
+typedef enum {
+  VD_OK = 0,
+  VD_WARN_DEGENERATE = 1,  /* a pose M-step had < 3 rigid pixels or no valid
+                              P3P sample; that pose was kept unchanged        */
+  VD_ERR_ARG = -1,         /* invalid argument (null, size, range, NaN flow) */
+  VD_ERR_CUDA = -2,        /* a CUDA call failed, see vd_last_error()         */
+  VD_ERR_OOM = -3,         /* device allocation failed                        */
+  VD_ERR_STATE = -4,       /* call out of order (e.g. EM before every flow)   */
+  VD_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up         */
+  VD_ERR_NUMERIC = -6      /* non-finite value detected in the state          */
+} vd_status;
+
+typedef enum { VD_MEM_HOST = 0, VD_MEM_DEVICE = 1 } vd_mem;
+typedef enum { VD_POSE_ABSOLUTE = 0, VD_POSE_RELATIVE = 1 } vd_pose_kind;
+
+/* Window geometry: image size, number of flow fields N (1..8), pinhole K. */
+typedef struct {
+  int width, height, n_flows;
+  double fx, fy, cx, cy;
+} vd_window_desc;
+
+/* Hyper-parameters of the hot path.  The paper names several of them without
+ * values (Sigma of Eq. 7, the chain schedule, the hierarchical scale and
+ * window of Sec. III-A); vd_params_default() fills the library's choices. */
+typedef struct {
+  float fisk_alpha0;        /* Fisk scale of the end-point error, px            */
+  float fisk_alpha1;        /* scale growth per px of observed flow magnitude   */
+  float fisk_beta;          /* Fisk shape (2 selects the fast closed form)      */
+  float outlier_density;    /* P0, density of an outlier residual, 1/px^2       */
+  float gamma_stay;         /* rigidness chain: probability to keep the state   */
+  float rho_min, rho_max;   /* inverse-depth search range (same units as tau)   */
+  int n_hyp;                /* K hypotheses per pixel per iteration (1..1024)   */
+  int n_pose_samples;       /* S P3P samples per frame (1..256)                 */
+  double pose_sigma_rot;        /* mean-shift kernel, rad                      */
+  double pose_sigma_trans_rel;  /* mean-shift kernel, fraction of |tau|        */
+  double pose_sigma_trans_abs;  /* mean-shift kernel, absolute translation     */
+  int sample_share;         /* pixels of an aligned row segment sharing draws   */
+  int hierarchical;         /* 1: hierarchical propagation (Sec. III-A)        */
+  int hier_scale;           /* coarse grid step of the global pass, px          */
+  int hier_window;          /* length of the local full-resolution windows, px  */
+  float prior_c_sigma;      /* RGB-D prior: sigma = c_sigma * rho_hat (Eq. 3)   */
+  float prior_w_uniform;    /* RGB-D prior: uniform density 1/(w rho_hat)       */
+  unsigned long long seed;  /* key of every Philox4x32-10 draw                  */
+} vd_params;
+
+/* Statistics of the last vd_run_em. */
+typedef struct {
+  int iterations;           /* EM iterations run by the call                     */
+  int bootstrapped;         /* 1 if the call ran the bootstrap                   */
+  int degenerate_frames;    /* pose M-steps that kept their pose                 */
+  double mean_energy;       /* mean per-pixel energy after the last depth step   */
+  double rigid_fraction;    /* mean rigidness over all flows after the E-step    */
+} vd_stats;
+
+/* Fill *out with the default hyper-parameters.  Never fails for non-null out. */
+vd_status vd_params_default(vd_params* out);
+
+/* Create a context for windows of the given geometry; allocates all device
+ * state (about 4 + 2N float32 maps plus pose scratch).  cuda_stream may be
+ * NULL (the legacy default stream).  Errors: VD_ERR_ARG for sizes outside
+ * 2..16384 px, N outside 1..8, non-positive focal lengths or parameters out of
+ * range; VD_ERR_OOM / VD_ERR_CUDA. */
+vd_status vd_create(const vd_window_desc* desc, const vd_params* params, void* cuda_stream,
+                    vd_ctx** out);
+vd_status vd_destroy(vd_ctx* ctx);
+vd_status vd_set_stream(vd_ctx* ctx, void* cuda_stream);
+vd_status vd_set_params(vd_ctx* ctx, const vd_params* params);
+
+/* Push flow field t (1..N).  row_pitch_floats >= 2W is the distance between
+ * rows in floats (2W for a dense array).  Non-finite values are rejected with
+ * VD_ERR_ARG (the check synchronises the stream).  Pushing a flow invalidates
+ * the EM state: the next vd_run_em bootstraps again. */
+vd_status vd_push_flow(vd_ctx* ctx, int t, const float* uv, long row_pitch_floats, vd_mem mem);
+
+/* Stereo prior of the reference frame (Sec. III-A "Geometric Priors", last
+ * paragraph; Sec. IV): disparity in px of a rectified pair with the given
+ * baseline, so rho_hat = d / (fx b).  NaN or d <= 0 marks a hole. */
+vd_status vd_push_stereo_prior(vd_ctx* ctx, const float* disparity, double baseline_m, vd_mem mem);
+
+/* RGB-D prior (Eq. 3): depth in the units of tau (0 or NaN = hole), optional
+ * per-pixel confidence in [0, 1] (NULL = 1) that multiplies the prior's
+ * rigidness weight (Eq. 6 paragraph).  T_hat (12 doubles) must be NULL or the
+ * identity: the prior is given on the reference frame's grid. */
+vd_status vd_push_depth_prior(vd_ctx* ctx, const float* depth, const float* confidence,
+                              const double* T_hat, vd_mem mem);
+vd_status vd_clear_prior(vd_ctx* ctx);
+
+/* Poses G (N+1 x 12, kind ABSOLUTE, G_0 must be the identity) or T (N x 12,
+ * kind RELATIVE).  Setting poses skips the pose part of the bootstrap. */
+vd_status vd_set_poses(vd_ctx* ctx, const double* poses, vd_pose_kind kind);
+vd_status vd_get_poses(vd_ctx* ctx, double* poses_out, vd_pose_kind kind);
+
+/* Set the EM state: inverse depth rho (H*W, > 0), rigidness q (N*H*W, NULL =
+ * all 1) and prior rigidness q_hat (H*W, NULL = all 1).  Marks the context as
+ * bootstrapped. */
+vd_status vd_set_state(vd_ctx* ctx, const float* rho, const float* q, const float* q_hat,
+                       vd_mem mem);
+
+/* Bootstrap (Sec. I, III-A): with a prior, rho from the prior and one pose
+ * M-step; monocular, 8-point G_1 (|tau_1| = 1), random rho, a depth M-step on
+ * X_1 and one pose M-step.  Poses set with vd_set_poses are kept. */
+vd_status vd_bootstrap(vd_ctx* ctx);
+
+/* Run n_iters EM iterations (bootstrapping first if needed).  Iteration i of
+ * the context (counted across calls) sweeps chain direction i mod 4
+ * (0 L->R, 1 T->B, 2 R->L, 3 B->T).  Synchronises; returns VD_WARN_DEGENERATE
+ * if any pose step kept its pose.  stats may be NULL. */
+vd_status vd_run_em(vd_ctx* ctx, int n_iters, vd_stats* stats);
+
+/* Single steps (for staged use and testing).  `iter` selects the random
+ * streams (-1 = the bootstrap streams) and `direction` the chains. */
+vd_status vd_depth_mstep(vd_ctx* ctx, int iter, int direction);
+vd_status vd_rigidness_estep(vd_ctx* ctx, int direction);
+/* Pose M-step of frame t (1..N), or of every frame in order for t = 0. */
+vd_status vd_pose_mstep(vd_ctx* ctx, int iter, int t);
+
+/* Results.  Host outputs are written after a stream synchronisation. */
+vd_status vd_get_inv_depth(vd_ctx* ctx, float* out, vd_mem mem);
+vd_status vd_get_rigidness(vd_ctx* ctx, float* out, vd_mem mem);          /* N*H*W */
+vd_status vd_get_prior_rigidness(vd_ctx* ctx, float* out, vd_mem mem);    /* H*W   */
+vd_status vd_get_confidence(vd_ctx* ctx, float* out, vd_mem mem);         /* Eq. 6 */
+/* rho* and E* of the last depth M-step before propagation (H*W each). */
+vd_status vd_get_depth_candidates(vd_ctx* ctx, float* rho_star, float* e_star, vd_mem mem);
+/* Energy E_j(rho_j) of every pixel for the given inverse-depth map under the
+ * current state (Eq. 5 criterion; H*W in, H*W out). */
+vd_status vd_eval_energy(vd_ctx* ctx, const float* rho, float* energy_out, vd_mem mem);
+
+/* Per-sample results of the last single-frame pose M-step: the kept root of
+ * every sample (S x 12, absolute), its energy (S; +inf for a void sample) and
+ * the rigid-set size.  Host memory. */
+vd_status vd_get_pose_samples(vd_ctx* ctx, double* poses, double* energies, int* n_rigid);
+
+/* Dense pose scoring (Eq. 7 scoring step) as a standalone call on device
+ * buffers: for every pose m (poses: m x 12 float64, absolute) computes
+ *   E_m = sum_i w_i l(| obs_i - pi(K (R_m X_i + tau_m)) |)
+ * with points[i] = (X, Y, Z, w) and obs[i] = (x, y, alpha, unused) as float4,
+ * l the Fisk maximum-inlier energy with shape beta and outlier density p0,
+ * and a large constant for points behind the camera.  energies: m float64.
+ * Allocates its own scratch for the block partial sums; runs on cuda_stream
+ * and synchronises it.  n >= 0, 1 <= m <= 1024. */
+vd_status vd_score_poses(const float* points, const float* obs, int n, const double* poses, int m,
+                         const double* intrinsics, float beta, float p0, double* energies,
+                         void* cuda_stream);
+
+/* Stage profiling (tracing): CUDA events recorded on the context stream
+ * around every stage, and kernel launch counters.  Stages: 0 depth sampling
+ * (hypotheses + argmin), 1 depth propagation, 2 rigidness E-step, 3 rigid-set
+ * compaction, 4 P3P sampling, 5 dense pose scoring, 6 sample selection and
+ * mean-shift, 7 bootstrap and other work.  Enabling resets the counters;
+ * vd_get_profile synchronises the stream. */
+#define VD_N_STAGES 8
+typedef struct {
+  double ms[VD_N_STAGES];           /* summed event time per stage           */
+  long long calls[VD_N_STAGES];     /* stage executions                      */
+  long long launches[VD_N_STAGES];  /* kernel launches per stage             */
+  long long total_launches;
+} vd_profile;
+vd_status vd_profile_enable(vd_ctx* ctx, int enable);
+vd_status vd_get_profile(vd_ctx* ctx, vd_profile* out);
+
+/* State export/import for checkpoint and resume: a self-describing blob with
+ * rho, q, q_hat, C, the poses, the iteration counter and the bootstrap flag.
+ * Call export with blob = NULL to learn the size. */
+vd_status vd_export_state(vd_ctx* ctx, void* blob, size_t* bytes);
+vd_status vd_import_state(vd_ctx* ctx, const void* blob, size_t bytes);
+
+const char* vd_status_str(vd_status s);
+const char* vd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOLDOR_EM_H */

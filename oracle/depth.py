@@ -46,20 +46,24 @@ def iter_code(it):
     return philox.ITER_BOOT if it < 0 else int(it)
 
 
-def hypotheses(P: model.Problem, rho_cur, it, p: model.Params):
-    """Candidate inverse depths, float32 [K, H, W]."""
+def hypotheses(P: model.Problem, rho_cur, it, p: model.Params, iu=None, iv=None):
+    """Candidate inverse depths, float32 [K, H, W] (or [K, n] for the pixels
+    (iu, iv) when given; rho_cur is then the [n] current values)."""
     K = p.n_hyp
-    H, W = P.H, P.W
-    iv, iu = np.mgrid[0:H, 0:W]
-    j = (iv * W + iu).astype(np.uint64)
+    if iu is None:
+        iv, iu = np.mgrid[0:P.H, 0:P.W]
+    iu = np.asarray(iu)
+    iv = np.asarray(iv)
+    rho_cur = np.asarray(rho_cur, np.float32)
+    j = (iv.astype(np.int64) * P.W + iu).astype(np.uint64)
     c0 = j - (iu % p.sample_share).astype(np.uint64)
     k0, k1 = philox.seed_key(p.seed)
     rmin, rmax = p.f32("rho_min"), p.f32("rho_max")
     rng = np.float32(rmax - rmin)
     s = perturb_scale(it)
     n_unif = (K - 1) // 2
-    cands = np.empty((K, H, W), np.float32)
-    cands[0] = np.clip(rho_cur.astype(np.float32), rmin, rmax)
+    cands = np.empty((K,) + iu.shape, np.float32)
+    cands[0] = np.clip(rho_cur, rmin, rmax)
     words = None
     for k in range(1, K):
         w = k - 1
@@ -70,12 +74,13 @@ def hypotheses(P: model.Problem, rho_cur, it, p: model.Params):
             c = rmin + np.float32(u * rng)
         else:
             a = np.float32(np.float32(2.0) * u) - np.float32(1.0)
-            c = rho_cur.astype(np.float32) * np.float32(np.float32(1.0) + np.float32(s * a))
+            c = rho_cur * np.float32(np.float32(1.0) + np.float32(s * a))
         cands[k] = np.clip(c.astype(np.float32), rmin, rmax)
     prho = P.prior_rho()
     if prho is not None and K > 1:
-        ok = np.isfinite(prho)
-        cands[1] = np.where(ok, np.clip(prho, rmin, rmax), cands[1])
+        pr = prho[iv, iu]
+        ok = np.isfinite(pr)
+        cands[1] = np.where(ok, np.clip(pr, rmin, rmax), cands[1])
     return cands
 
 

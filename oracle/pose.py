@@ -117,7 +117,7 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
     it_code = philox.ITER_BOOT if it < 0 else int(it)
     rs = rigid_set(P, S, t, p)
     n = len(rs["j"])
-    out = dict(n_rigid=n, degenerate=False, samples=[], scores=[], roots=[])
+    out = dict(n_rigid=n, degenerate=False, samples=[], scores=[], roots=[], root_scores=[])
     if n < 3:
         out["degenerate"] = True
         return out
@@ -127,6 +127,7 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
         tri = draw_triplet(n, g, t, it_code, p)
         if tri is None:
             out["roots"].append([])
+            out["root_scores"].append([])
             continue
         X3 = rs["X"][tri]
         xo = rs["xobs"][tri]
@@ -134,9 +135,11 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
         roots = sorted(p3p.solve(bear, X3), key=root_key)
         if detail:
             out["roots"].append(roots)
+        Es = [score(P, G, rs, p) for G in roots]
+        if detail:
+            out["root_scores"].append(Es)
         if not roots:
             continue
-        Es = [score(P, G, rs, p) for G in roots]
         k = int(np.argmin(Es))
         samples.append(roots[k])
         sample_E.append(Es[k])

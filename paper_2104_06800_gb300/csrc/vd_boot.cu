@@ -1,0 +1,393 @@
+// Bootstrap of the EM (VOLDOR+ bootstraps from priors where it has them and
+// from monocular flow otherwise, Sec. I and III-A) and small utility kernels.
+// Monocular: the first relative pose from the epipolar constraint of X_1 by
+// the linear 8-point method on calibrated rays (Longuet-Higgins 1981), made
+// robust to the heavy-tailed Fisk noise by iterative re-weighting with the
+// weight 1 / (1 + (d / alpha0)^2) of the Sampson distance d.
+#include "vd_device.cuh"
+#include "vd_geom64.cuh"
+
+#define EP_THREADS 256
+
+// ---------------------------------------------------------------------------
+// Initial inverse depth: Philox word 0 of (j, ITER_BOOT, TAG_INIT, 0) mapped
+// uniformly to [rho_min, rho_max]; the clamped prior where it is valid.
+// ---------------------------------------------------------------------------
+__global__ void k_initial_rho(DevParams P, const float* __restrict__ prior_rho,
+                              float* __restrict__ rho) {
+  const size_t npix = (size_t)P.W * P.H;
+  const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= npix) return;
+  const uint4 w = vd_philox(make_uint4((uint32_t)j, VD_ITER_BOOT, VD_TAG_INIT, 0u), P.key0, P.key1);
+  float r = vd_cand_uniform(w.x, P.rho_min, __fsub_rn(P.rho_max, P.rho_min));
+  if (P.prior_kind != VD_PRIOR_NONE) {
+    const float pr = prior_rho[j];
+    if (isfinite(pr)) r = vd_clamp(pr, P.rho_min, P.rho_max);
+  }
+  rho[j] = r;
+}
+
+cudaError_t launch_initial_rho(vd_ctx* c) {
+  k_initial_rho<<<(unsigned)((c->npix + 255) / 256), 256, 0, c->stream>>>(c->dp, c->prior_rho,
+                                                                          c->rho);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Weighted normal matrix M = sum_j w_j r_j r_j^T, r_j = b (x) a, upper
+// triangle (45 entries), per-block partial sums in float64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double vd_sampson_px(const double* E, const double* a, const double* b,
+                                                double f) {
+  double Ea[3], Etb[3];
+  for (int i = 0; i < 3; ++i) {
+    Ea[i] = E[3 * i] * a[0] + E[3 * i + 1] * a[1] + E[3 * i + 2] * a[2];
+    Etb[i] = E[i] * b[0] + E[3 + i] * b[1] + E[6 + i] * b[2];
+  }
+  const double num = b[0] * Ea[0] + b[1] * Ea[1] + b[2] * Ea[2];
+  const double den = Ea[0] * Ea[0] + Ea[1] * Ea[1] + Etb[0] * Etb[0] + Etb[1] * Etb[1];
+  return f * fabs(num) / sqrt(fmax(den, 1e-300));
+}
+
+__global__ void __launch_bounds__(EP_THREADS)
+k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restrict__ Eprev,
+            int weighted, double* __restrict__ partial) {
+  __shared__ double sW[EP_THREADS / 32][45];
+  double acc[45];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) acc[i] = 0.0;
+  double E[9];
+  for (int i = 0; i < 9; ++i) E[i] = weighted ? Eprev[i] : 0.0;
+  const double f = sqrt(P.fx_d * P.fy_d);
+  const double ia = 1.0 / (double)P.alpha0;
+  const size_t npix = (size_t)P.W * P.H;
+  for (size_t j = (size_t)blockIdx.x * EP_THREADS + threadIdx.x; j < npix;
+       j += (size_t)gridDim.x * EP_THREADS) {
+    const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
+    const float2 F = flow[j];
+    const double a[3] = {((double)u - P.cx_d) / P.fx_d, ((double)v - P.cy_d) / P.fy_d, 1.0};
+    const double b[3] = {((double)u + (double)F.x - P.cx_d) / P.fx_d,
+                         ((double)v + (double)F.y - P.cy_d) / P.fy_d, 1.0};
+    double w = 1.0;
+    if (weighted) {
+      const double d = vd_sampson_px(E, a, b, f) * ia;
+      w = 1.0 / (1.0 + d * d);
+    }
+    double r[9];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = 0; n < 3; ++n) r[3 * m + n] = b[m] * a[n];
+    int k = 0;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const double wr = w * r[p];
+#pragma unroll
+      for (int q = p; q < 9; ++q) acc[k++] += wr * r[q];
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 45; ++i) {
+    double x = acc[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sW[wid][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 45) {
+    double s = 0.0;
+    for (int w = 0; w < EP_THREADS / 32; ++w) s += sW[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * 45 + threadIdx.x] = s;
+  }
+}
+
+// Sum the partials (fixed order) and take the eigenvector of the smallest
+// eigenvalue as E (unit Frobenius norm).
+__global__ void k_ep_solve(const double* __restrict__ partial, int nblk, double* __restrict__ Mout,
+                           double* __restrict__ Eout) {
+  __shared__ double sM[45];
+  if (threadIdx.x < 45) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * 45 + threadIdx.x];
+    sM[threadIdx.x] = s;
+    Mout[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double A[81], w[9], V[81];
+  int k = 0;
+  for (int p = 0; p < 9; ++p)
+    for (int q = p; q < 9; ++q) {
+      A[9 * p + q] = sM[k];
+      A[9 * q + p] = sM[k];
+      ++k;
+    }
+  vd_jacobi_eig<9>(A, w, V);
+  int mi = 0;
+  for (int i = 1; i < 9; ++i)
+    if (w[i] < w[mi]) mi = i;
+  double n = 0.0;
+  for (int i = 0; i < 9; ++i) n += V[9 * i + mi] * V[9 * i + mi];
+  n = sqrt(n);
+  for (int i = 0; i < 9; ++i) Eout[i] = V[9 * i + mi] / n;
+}
+
+// E = U diag(s) V^T with det U = det V = +1: the two rotations U W V^T and
+// U W^T V^T with translation +-U[:, 2] give the four candidate motions.
+__global__ void k_ep_decompose(const double* __restrict__ Ein, double* __restrict__ cand,
+                               int* __restrict__ counts) {
+  if (threadIdx.x != 0) return;
+  double E[9];
+  for (int i = 0; i < 9; ++i) E[i] = Ein[i];
+  double A[9], w[3], V[9];
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q)
+      A[3 * p + q] = E[p] * E[q] + E[3 + p] * E[3 + q] + E[6 + p] * E[6 + q];   // E^T E
+  vd_jacobi_eig<3>(A, w, V);
+  // order the eigenvalues descending
+  int o[3] = {0, 1, 2};
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b)
+      if (w[o[b]] > w[o[a]]) {
+        const int tmp = o[a];
+        o[a] = o[b];
+        o[b] = tmp;
+      }
+  double v[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int i = 0; i < 3; ++i) v[c][i] = V[3 * i + o[c]];
+  double cr[3];
+  vd_cross3(v[0], v[1], cr);
+  if (cr[0] * v[2][0] + cr[1] * v[2][1] + cr[2] * v[2][2] < 0.0)
+    for (int i = 0; i < 3; ++i) v[2][i] = -v[2][i];
+  double U[3][3];
+  for (int c = 0; c < 2; ++c) {
+    for (int i = 0; i < 3; ++i) U[c][i] = E[3 * i] * v[c][0] + E[3 * i + 1] * v[c][1] + E[3 * i + 2] * v[c][2];
+    vd_normalize3(U[c]);
+  }
+  vd_cross3(U[0], U[1], U[2]);
+  // R = U W V^T with W = [[0,-1,0],[1,0,0],[0,0,1]]: R = u2 v1^T - u1 v2^T + u3 v3^T
+  for (int s = 0; s < 2; ++s) {
+    double R[9];
+    const double sg = s == 0 ? 1.0 : -1.0;   // W or W^T
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k)
+        R[3 * i + k] = sg * (U[1][i] * v[0][k] - U[0][i] * v[1][k]) + U[2][i] * v[2][k];
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      double* T = cand + 12 * (2 * s + sgn);
+      for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) T[4 * i + k] = R[3 * i + k];
+        T[4 * i + 3] = (sgn == 0 ? 1.0 : -1.0) * U[2][i];
+      }
+    }
+  }
+  for (int i = 0; i < 4; ++i) counts[i] = 0;
+}
+
+// Pixels whose least-squares triangulation lam_b b = lam_a R a + t has both
+// depths positive, for each of the four candidate motions.
+__global__ void __launch_bounds__(EP_THREADS)
+k_ep_cheirality(DevParams P, const float2* __restrict__ flow, const double* __restrict__ cand,
+                int* __restrict__ counts) {
+  __shared__ double sC[48];
+  if (threadIdx.x < 48) sC[threadIdx.x] = cand[threadIdx.x];
+  __syncthreads();
+  int cnt[4] = {0, 0, 0, 0};
+  const size_t npix = (size_t)P.W * P.H;
+  for (size_t j = (size_t)blockIdx.x * EP_THREADS + threadIdx.x; j < npix;
+       j += (size_t)gridDim.x * EP_THREADS) {
+    const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
+    const float2 F = flow[j];
+    const double a[3] = {((double)u - P.cx_d) / P.fx_d, ((double)v - P.cy_d) / P.fy_d, 1.0};
+    const double b[3] = {((double)u + (double)F.x - P.cx_d) / P.fx_d,
+                         ((double)v + (double)F.y - P.cy_d) / P.fy_d, 1.0};
+    for (int k = 0; k < 4; ++k) {
+      const double* T = sC + 12 * k;
+      const double Ra[3] = {T[0] * a[0] + T[1] * a[1] + T[2] * a[2],
+                            T[4] * a[0] + T[5] * a[1] + T[6] * a[2],
+                            T[8] * a[0] + T[9] * a[1] + T[10] * a[2]};
+      const double t[3] = {T[3], T[7], T[11]};
+      const double m11 = Ra[0] * Ra[0] + Ra[1] * Ra[1] + Ra[2] * Ra[2];
+      const double m12 = -(Ra[0] * b[0] + Ra[1] * b[1] + Ra[2] * b[2]);
+      const double m22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+      const double r1 = -(Ra[0] * t[0] + Ra[1] * t[1] + Ra[2] * t[2]);
+      const double r2 = b[0] * t[0] + b[1] * t[1] + b[2] * t[2];
+      const double det = m11 * m22 - m12 * m12;
+      const double la = (m22 * r1 - m12 * r2) / det;
+      const double lb = (m11 * r2 - m12 * r1) / det;
+      cnt[k] += (la > 0.0 && lb > 0.0) ? 1 : 0;
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    int x = cnt[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(counts + k, x);
+  }
+}
+
+// Keep the motion with most positive depths (first on ties), |tau_1| = 1,
+// and constant-velocity guesses G_t = G_1 o G_{t-1}.
+__global__ void k_ep_finalize(DevParams P, const double* __restrict__ cand,
+                              const int* __restrict__ counts, double* __restrict__ G,
+                              float* __restrict__ posef) {
+  if (threadIdx.x != 0) return;
+  int best = 0;
+  for (int k = 1; k < 4; ++k)
+    if (counts[k] > counts[best]) best = k;
+  double G1[12];
+  for (int i = 0; i < 12; ++i) G1[i] = cand[12 * best + i];
+  const double n = sqrt(G1[3] * G1[3] + G1[7] * G1[7] + G1[11] * G1[11]);
+  G1[3] /= n;
+  G1[7] /= n;
+  G1[11] /= n;
+  double prev[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  for (int i = 0; i < 12; ++i) G[i] = prev[i];
+  for (int t = 1; t <= P.N; ++t) {
+    double cur[12];
+    vd_compose(G1, prev, cur);
+    for (int i = 0; i < 12; ++i) {
+      G[12 * t + i] = cur[i];
+      prev[i] = cur[i];
+    }
+  }
+  for (int t = 0; t <= P.N; ++t) {
+    const double* g = G + 12 * t;
+    float* o = posef + 12 * t;
+    for (int i = 0; i < 4; ++i) {
+      o[i < 3 ? i : 9] = (float)(P.fx_d * g[i] + P.cx_d * g[8 + i]);
+      o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
+      o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
+    }
+  }
+}
+
+cudaError_t launch_eight_point(vd_ctx* c) {
+  for (int r = 0; r < VD_IRLS_ITERS; ++r) {
+    k_ep_normal<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_E, r > 0 ? 1 : 0,
+                                                            c->ep_partial);
+    k_ep_solve<<<1, 64, 0, c->stream>>>(c->ep_partial, c->ep_blocks, c->ep_M, c->ep_E);
+  }
+  k_ep_decompose<<<1, 32, 0, c->stream>>>(c->ep_E, c->ep_cand, c->ep_count);
+  k_ep_cheirality<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_cand,
+                                                              c->ep_count);
+  k_ep_finalize<<<1, 32, 0, c->stream>>>(c->dp, c->ep_cand, c->ep_count, c->G, c->posef);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// utilities
+// ---------------------------------------------------------------------------
+__global__ void k_fill(float* __restrict__ p, float v, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, v, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_check_finite(const float* __restrict__ p, size_t n, int* __restrict__ flag) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(p[i])) atomicOr(flag, 1);
+}
+
+cudaError_t launch_check_finite(const float* p, size_t n, int* flag, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_check_finite<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, flag);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_flow(const float* __restrict__ src, long pitch, int W, int H,
+                            float2* __restrict__ dst) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (u >= W || v >= H) return;
+  const float* s = src + (size_t)v * pitch + 2 * (size_t)u;
+  dst[(size_t)v * W + u] = make_float2(s[0], s[1]);
+}
+
+cudaError_t launch_copy_flow(vd_ctx* c, int t, const float* src, long pitch) {
+  k_copy_flow<<<dim3((c->W + 127) / 128, c->H), 128, 0, c->stream>>>(
+      src, pitch, c->W, c->H, c->flow + (size_t)(t - 1) * c->npix);
+  return cudaGetLastError();
+}
+
+// Prior maps: stereo disparity d -> value d, inverse depth d / (fx b);
+// RGB-D depth z -> value and inverse depth 1 / z; holes -> NaN.
+__global__ void k_prior_prepare(DevParams P, int kind, const float* __restrict__ raw,
+                                const float* __restrict__ conf_in, float* __restrict__ val,
+                                float* __restrict__ prho, float* __restrict__ conf) {
+  const size_t npix = (size_t)P.W * P.H;
+  const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= npix) return;
+  const float x = raw[j];
+  const bool ok = isfinite(x) && x > 0.0f;
+  float r = nanf("");
+  float v = nanf("");
+  if (ok) {
+    if (kind == VD_PRIOR_STEREO) {
+      r = __fdiv_rn(x, P.fxb);
+      v = x;
+    } else {
+      r = __fdiv_rn(1.0f, x);
+      v = r;
+    }
+  }
+  val[j] = v;
+  prho[j] = r;
+  conf[j] = conf_in ? conf_in[j] : 1.0f;
+}
+
+cudaError_t launch_prior_prepare(vd_ctx* c, const float* raw, const float* conf) {
+  k_prior_prepare<<<(unsigned)((c->npix + 255) / 256), 256, 0, c->stream>>>(
+      c->dp, c->prior_kind, raw, conf, c->prior_val, c->prior_rho, c->prior_conf);
+  return cudaGetLastError();
+}
+
+// Mean energy (of e_star after propagation is not kept; the energy of the new
+// depth map is recomputed by the caller into e_mid) and mean rigidness.
+__global__ void k_stats(const float* __restrict__ e, size_t npix, const float* __restrict__ q,
+                        size_t nq, double* __restrict__ partial) {
+  __shared__ double s0[256], s1[256];
+  double a = 0.0, b = 0.0;
+  for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < nq; i += (size_t)gridDim.x * 256) {
+    if (i < npix) a += (double)e[i];
+    b += (double)q[i];
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s0[threadIdx.x] += s0[threadIdx.x + o];
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0[0];
+    partial[2 * blockIdx.x + 1] = s1[0];
+  }
+}
+
+__global__ void k_stats_final(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    a += partial[2 * i];
+    b += partial[2 * i + 1];
+  }
+  out[0] = a;
+  out[1] = b;
+}
+
+cudaError_t launch_stats(vd_ctx* c, double* out2) {
+  cudaError_t e = launch_eval_energy(c, c->rho, c->e_mid);
+  if (e != cudaSuccess) return e;
+  k_stats<<<c->stat_blocks, 256, 0, c->stream>>>(c->e_mid, c->npix, c->q, c->npix * c->N,
+                                                 c->stat_partial);
+  k_stats_final<<<1, 32, 0, c->stream>>>(c->stat_partial, c->stat_blocks, out2);
+  return cudaGetLastError();
+}

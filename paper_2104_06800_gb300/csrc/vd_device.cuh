@@ -1,0 +1,218 @@
+// Device-side building blocks of the dense-indirect EM: the Philox counter
+// RNG, the Fisk residual energy, bilinear flow sampling and the per-pixel
+// energy E_j(rho) of the depth M-step (Eq. 5 of VOLDOR+, Sec. III-A).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "vd_internal.h"
+
+#define VD_LN2 0.69314718055994530942f
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 bit
+// multiplies, mixing with the key, key advanced by the Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 vd_philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t vd_word(const uint4& w, int i) {
+  return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// (x >> 8) * 2^-24 as float (exact).
+__device__ __forceinline__ float vd_u24(uint32_t x) {
+  return __fmul_rn(__uint2float_rn(x >> 8), 5.9604644775390625e-8f);
+}
+
+// Hypothesis values, each operation rounded once (no contraction), so the
+// float32 values are reproducible bit for bit.
+__device__ __forceinline__ float vd_cand_uniform(uint32_t x, float rmin, float range) {
+  return __fadd_rn(rmin, __fmul_rn(vd_u24(x), range));
+}
+__device__ __forceinline__ float vd_cand_perturb(uint32_t x, float rho, float s) {
+  const float a = __fsub_rn(__fmul_rn(2.0f, vd_u24(x)), 1.0f);
+  return __fmul_rn(rho, __fadd_rn(1.0f, __fmul_rn(s, a)));
+}
+__device__ __forceinline__ float vd_clamp(float c, float lo, float hi) {
+  return fminf(fmaxf(c, lo), hi);
+}
+
+// ---------------------------------------------------------------------------
+// Residual energy l = log(1 + P0 / p1(r)), p1 = density of a 2-D residual
+// vector whose length is Fisk(alpha, beta) distributed and whose direction is
+// uniform.  Returned in log2 units (multiply by ln 2).  Also returns
+// y = P0 / p1 (the outlier-to-rigid likelihood ratio) for the E-step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vd_ratio_general(const DevParams& P, float r2, float alpha) {
+  float r = sqrtf(r2);
+  if (P.beta != 2.0f) r = fmaxf(r, VD_R_FLOOR);
+  const float s = r / alpha;
+  const float ls = __log2f(s);
+  const float sb = exp2f(P.beta * ls);
+  const float s2b = exp2f((2.0f - P.beta) * ls);
+  const float one = 1.0f + sb;
+  return P.cgen * alpha * alpha * s2b * one * one;
+}
+
+__device__ __forceinline__ float vd_ratio_y(const DevParams& P, float r2, float fmag2) {
+  if (P.fast_beta2) {
+    // beta = 2: P0 / p1 = P0 pi alpha^2 (1 + r^2 / alpha^2)^2
+    const float s = fmaf(r2, P.inv_a2, 1.0f);
+    return P.c0 * s * s;
+  }
+  return vd_ratio_general(P, r2, fmaf(P.alpha1, sqrtf(fmag2), P.alpha0));
+}
+
+__device__ __forceinline__ float vd_ell2(float y) { return __log2f(1.0f + y); }
+
+// ---------------------------------------------------------------------------
+// Bilinear sample of one flow field at (x, y), which must be inside the image.
+// Taps (x0, y0)..(x0+1, y0+1) with x0 = min(floor(x), W-2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 vd_bilinear(const float2* __restrict__ F, int W, int H, float x,
+                                              float y) {
+  const int x0 = min(__float2int_rd(x), W - 2);
+  const int y0 = min(__float2int_rd(y), H - 2);
+  const float ax = x - (float)x0;
+  const float ay = y - (float)y0;
+  const float2* p = F + (size_t)y0 * W + x0;
+  const float2 f00 = __ldg(p), f01 = __ldg(p + 1);
+  const float2 f10 = __ldg(p + W), f11 = __ldg(p + W + 1);
+  const float tx = fmaf(ax, f01.x - f00.x, f00.x), ty = fmaf(ax, f01.y - f00.y, f00.y);
+  const float bx = fmaf(ax, f11.x - f10.x, f10.x), by = fmaf(ax, f11.y - f10.y, f10.y);
+  return make_float2(fmaf(ay, bx - tx, tx), fmaf(ay, by - ty, ty));
+}
+
+__device__ __forceinline__ bool vd_inside(float x, float y, int W, int H) {
+  return x >= 0.0f && x <= (float)(W - 1) && y >= 0.0f && y <= (float)(H - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel constant part of the energy.  A_t = K R_t r_j (homogeneous image
+// point of the ray), B_t = K tau_t is shared by all pixels (shared memory).
+// ---------------------------------------------------------------------------
+template <int NF>
+struct VdPixel {
+  float ax[NF], ay[NF], az[NF];
+  float wl[NF];           // q_t * ln 2
+  float f1x, f1y;         // X_1 at the pixel (x_0 = j exactly)
+  float u, v;
+  float pv;               // prior value (disparity or rho_hat)
+  float pw;               // prior weight q_hat * conf (0 at holes / no prior)
+};
+
+// posef layout per frame t (0..N): 9 floats K R_t (row-major), 3 floats K tau_t.
+template <int NF>
+__device__ __forceinline__ void vd_pixel_setup(VdPixel<NF>& px, const DevParams& P,
+                                               const float* __restrict__ sPose, int u, int v,
+                                               const float* __restrict__ q, size_t npix, size_t j,
+                                               const float2* __restrict__ flow,
+                                               const float* __restrict__ prior_val,
+                                               const float* __restrict__ qhat,
+                                               const float* __restrict__ pconf) {
+  const float rx = ((float)u - P.cx) / P.fx;
+  const float ry = ((float)v - P.cy) / P.fy;
+#pragma unroll
+  for (int t = 0; t < NF; ++t) {
+    const float* M = sPose + 12 * (t + 1);
+    px.ax[t] = fmaf(M[0], rx, fmaf(M[1], ry, M[2]));
+    px.ay[t] = fmaf(M[3], rx, fmaf(M[4], ry, M[5]));
+    px.az[t] = fmaf(M[6], rx, fmaf(M[7], ry, M[8]));
+    px.wl[t] = __ldg(q + (size_t)t * npix + j) * VD_LN2;
+  }
+  const float2 f1 = __ldg(flow + j);
+  px.f1x = f1.x;
+  px.f1y = f1.y;
+  px.u = (float)u;
+  px.v = (float)v;
+  px.pw = 0.0f;
+  px.pv = 0.0f;
+  if (P.prior_kind != VD_PRIOR_NONE) {
+    const float pvv = __ldg(prior_val + j);
+    if (isfinite(pvv)) {
+      px.pv = pvv;
+      px.pw = __ldg(qhat + j) * __ldg(pconf + j);
+    }
+  }
+}
+
+// E_j(c): sum_t q_t l_t(c) + w_hat l_hat(c) in natural-log units.
+template <int NF>
+__device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParams& P,
+                                           const float* __restrict__ sPose,
+                                           const float2* __restrict__ flow, size_t npix,
+                                           float c) {
+  float E = 0.0f;
+  float xp = px.u, yp = px.v;
+  bool front_prev = true;
+#pragma unroll
+  for (int t = 0; t < NF; ++t) {
+    const float* M = sPose + 12 * (t + 1);
+    const float hx = fmaf(c, M[9], px.ax[t]);
+    const float hy = fmaf(c, M[10], px.ay[t]);
+    const float hz = fmaf(c, M[11], px.az[t]);
+    const bool front = hz > VD_Z_EPS;
+    const float iz = __fdividef(1.0f, hz);
+    const float x = hx * iz, y = hy * iz;
+    bool obs;
+    float Fx, Fy;
+    if (t == 0) {
+      obs = true;
+      Fx = px.f1x;
+      Fy = px.f1y;
+    } else {
+      obs = front_prev && vd_inside(xp, yp, P.W, P.H);
+      float2 F = make_float2(0.0f, 0.0f);
+      if (obs) F = vd_bilinear(flow + (size_t)t * npix, P.W, P.H, xp, yp);
+      Fx = F.x;
+      Fy = F.y;
+    }
+    float l2;
+    if (obs && front) {
+      const float dx = Fx - (x - xp);
+      const float dy = Fy - (y - yp);
+      const float r2 = fmaf(dx, dx, dy * dy);
+      l2 = vd_ell2(vd_ratio_y(P, r2, fmaf(Fx, Fx, Fy * Fy)));
+    } else {
+      l2 = obs ? (VD_L_BEHIND / VD_LN2) : 0.0f;
+    }
+    E = fmaf(px.wl[t], l2, E);
+    xp = x;
+    yp = y;
+    front_prev = front;
+  }
+  if (px.pw > 0.0f) {
+    if (P.prior_kind == VD_PRIOR_STEREO) {
+      const float d = px.pv - P.fxb * c;
+      float y;
+      if (P.beta == 2.0f) {
+        const float s = fmaf(d * d, P.inv_a2, 1.0f);
+        y = P.c0 * s * s;
+      } else {
+        y = vd_ratio_general(P, d * d, P.alpha0);
+      }
+      E = fmaf(px.pw * VD_LN2, vd_ell2(y), E);
+    } else {
+      const float res = px.pv - c;
+      const float sig = P.c_sigma * px.pv;
+      const float z = fmaf(res * res, 0.5f / (sig * sig), P.logk);
+      const float l = z > 20.0f ? z : __logf(1.0f + __expf(z));
+      E = fmaf(px.pw, l, E);
+    }
+  }
+  return E;
+}

@@ -1,0 +1,145 @@
+// Internal definitions shared by the library's translation units: the device
+// parameter block, the context and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "voldor_em.h"
+
+#define VD_MAX_FLOWS 8
+#define VD_MAX_SAMPLES 256
+#define VD_MAX_ROOTS (4 * VD_MAX_SAMPLES)
+
+// Constants of the model that both hosts and kernels use.
+#define VD_Z_EPS 1e-6f
+#define VD_L_BEHIND 64.0f           // energy of an observation the rigid model cannot explain
+#define VD_R_FLOOR 1e-6f
+#define VD_ITER_BOOT 0xFFFFFFFFu
+#define VD_TAG_DEPTH 0u
+#define VD_TAG_POSE 1u
+#define VD_TAG_INIT 2u
+#define VD_MS_MAX_ITERS 100
+#define VD_MS_TOL 1e-12
+#define VD_MAX_ATTEMPTS 8
+#define VD_IRLS_ITERS 8
+
+enum { VD_PRIOR_NONE = 0, VD_PRIOR_STEREO = 1, VD_PRIOR_RGBD = 2 };
+
+// Everything a kernel needs to know about the window and the parameters,
+// passed by value.
+struct DevParams {
+  int W, H, N, K, S;
+  float fx, fy, cx, cy;
+  float alpha0, alpha1, beta, p0;
+  int fast_beta2;          // beta == 2 and alpha1 == 0: closed-form energy
+  float c0;                // P0 * pi * alpha0^2
+  float inv_a2;            // 1 / alpha0^2
+  float cgen;              // P0 * 2 pi / beta (general path factor, times alpha^2)
+  float gamma;
+  float rho_min, rho_max;
+  int share;
+  uint32_t key0, key1;
+  int prior_kind;
+  float fxb;               // fx * baseline (stereo)
+  float c_sigma, w_unif, logk;   // RGB-D prior: logk = log(sqrt(2 pi) c_sigma / w)
+  double fx_d, fy_d, cx_d, cy_d;
+  double ms_sig_rot, ms_sig_rel, ms_sig_abs;
+};
+
+struct vd_ctx {
+  vd_window_desc desc;
+  vd_params prm;
+  DevParams dp;
+  cudaStream_t stream;
+  int W, H, N;
+  size_t npix;
+
+  // inputs
+  float2* flow;            // [N][H][W]
+  unsigned flow_pushed;    // bit t-1 set once X_t was pushed
+  int prior_kind;
+  float fxb;               // fx * stereo baseline
+  float* prior_val;        // stereo: disparity; rgbd: inverse depth (NaN = hole)
+  float* prior_rho;        // inverse depth of the prior (NaN = hole)
+  float* prior_conf;       // confidence (1 if none given)
+
+  // EM state
+  float* rho;              // [H][W]
+  float* q;                // [N][H][W]
+  float* qhat;             // [H][W]
+  float* conf;             // [H][W] Eq. 6
+  double* G;               // [N+1][12] absolute poses
+  float* posef;            // [N+1][12] float K R | K tau
+  int bootstrapped;
+  int poses_set;
+  int iter;                // next EM iteration index
+
+  // depth step scratch
+  float* rho_star;
+  float* e_star;
+  float* rho_mid;
+  float* e_mid;
+  float* coarse;           // hierarchical coarse map
+  float* lam;              // [N][H][W] rigid / outlier likelihood ratio
+
+  // pose step scratch
+  unsigned char* flags;    // [H*W]
+  int* blk_counts;         // [nblk_scan]
+  int* blk_offsets;        // [nblk_scan]
+  int* n_rigid;            // [1]
+  int* rigid_idx;          // [H*W]
+  float4* rpts;            // [H*W] (X, Y, Z, w)
+  float4* robs;            // [H*W] (x_obs, y_obs, alpha, 0)
+  double* roots;           // [S][4][12]
+  int* root_count;         // [S]
+  float* rootsf;           // [S*4][12]
+  float* partial;          // [S*4][score blocks]
+  double* root_energy;     // [S*4]
+  double* sample_pose;     // [S][12]
+  double* sample_energy;   // [S]
+  int* degenerate;         // [1] counter of kept poses
+  int nblk_scan;
+  int nblk_score;
+
+  // bootstrap scratch
+  double* ep_partial;      // [blocks][45]
+  double* ep_M;            // [45]
+  double* ep_E;            // [9] current essential matrix (row-major)
+  double* ep_cand;         // [4][12]
+  int* ep_count;           // [4]
+  int ep_blocks;
+
+  // profiling: event pairs per recorded stage execution, launch counters
+  int prof_on;
+  void* prof;              // ProfState (vd_api.cu)
+  long long launches[VD_N_STAGES];
+
+  // reductions for stats
+  double* stat_partial;    // [blocks][2]
+  double* stat_out;        // [2]
+  int stat_blocks;
+};
+
+// ---- launchers (one per translation unit family) --------------------------
+cudaError_t launch_posef(vd_ctx* c);
+cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, const float* q_override);
+cudaError_t launch_depth_propagate(vd_ctx* c, int direction);
+cudaError_t launch_eval_energy(vd_ctx* c, const float* rho_in, float* e_out);
+cudaError_t launch_estep(vd_ctx* c, int direction);
+cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t);
+cudaError_t launch_initial_rho(vd_ctx* c);
+cudaError_t launch_eight_point(vd_ctx* c);
+cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t s);
+cudaError_t launch_stats(vd_ctx* c, double* out2);
+cudaError_t launch_prior_prepare(vd_ctx* c, const float* raw, const float* conf);
+cudaError_t launch_check_finite(const float* p, size_t n, int* flag, cudaStream_t s);
+cudaError_t launch_copy_flow(vd_ctx* c, int t, const float* src, long pitch);
+
+void vd_set_error(const char* msg);
+// stage profiling hooks (no-ops unless enabled); `n_launch` kernels are counted
+void vd_prof_begin(vd_ctx* c, int stage);
+void vd_prof_end(vd_ctx* c, int stage, int n_launch);
+
+enum { VD_ST_SAMPLE = 0, VD_ST_PROPAGATE = 1, VD_ST_ESTEP = 2, VD_ST_RIGID = 3, VD_ST_P3P = 4,
+       VD_ST_SCORE = 5, VD_ST_SELECT = 6, VD_ST_OTHER = 7 };

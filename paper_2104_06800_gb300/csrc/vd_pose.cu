@@ -1,0 +1,573 @@
+// Pose M-step of VOLDOR+ (Sec. III-A, Eq. 7): the posterior of each camera
+// pose is approximated by S P3P samples drawn from the rigid pixels; every
+// root is scored against all rigid pixels, each sample keeps its best root,
+// and the pose is the mean-shift mode of the samples in se(3).
+#include "vd_device.cuh"
+#include "vd_geom64.cuh"
+
+#define SCAN_BLOCK 256
+#define SCORE_THREADS 256
+#define SCORE_PPT 4
+
+// ---------------------------------------------------------------------------
+// Float64 track position x_{t-1} of pixel j at inverse depth rho (t >= 2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool vd_track64(const DevParams& P, const double* g, int u, int v,
+                                           double rho, double* x, double* y) {
+  const double rx = ((double)u - P.cx_d) / P.fx_d, ry = ((double)v - P.cy_d) / P.fy_d;
+  const double X = g[0] * rx + g[1] * ry + g[2] + rho * g[3];
+  const double Y = g[4] * rx + g[5] * ry + g[6] + rho * g[7];
+  const double Z = g[8] * rx + g[9] * ry + g[10] + rho * g[11];
+  const double hx = P.fx_d * X + P.cx_d * Z, hy = P.fy_d * Y + P.cy_d * Z;
+  if (!(Z > (double)VD_Z_EPS)) return false;
+  *x = hx / Z;
+  *y = hy / Z;
+  return true;
+}
+
+__device__ __forceinline__ bool vd_front64(const DevParams& P, const double* g, int u, int v,
+                                           double rho) {
+  const double rx = ((double)u - P.cx_d) / P.fx_d, ry = ((double)v - P.cy_d) / P.fy_d;
+  return g[8] * rx + g[9] * ry + g[10] + rho * g[11] > (double)VD_Z_EPS;
+}
+
+__device__ __forceinline__ void vd_bilinear64(const float2* __restrict__ F, int W, int H, double x,
+                                              double y, double* fx, double* fy) {
+  const int x0 = min((int)floor(x), W - 2), y0 = min((int)floor(y), H - 2);
+  const double ax = x - x0, ay = y - y0;
+  const float2* p = F + (size_t)y0 * W + x0;
+  const float2 a = p[0], b = p[1], c = p[W], d = p[W + 1];
+  *fx = (1 - ay) * ((1 - ax) * a.x + ax * b.x) + ay * ((1 - ax) * c.x + ax * d.x);
+  *fy = (1 - ay) * ((1 - ax) * a.y + ax * b.y) + ay * ((1 - ax) * c.y + ax * d.y);
+}
+
+// Membership of the rigid set (decisions in float64; a float32 test decides
+// directly when it is far from every threshold, the float64 one otherwise).
+__device__ bool vd_is_rigid(const DevParams& P, const double* __restrict__ G,
+                            const float* __restrict__ posef, const float* __restrict__ rho,
+                            const float* __restrict__ q, int t, int u, int v, size_t j) {
+  const size_t npix = (size_t)P.W * P.H;
+  if (!(q[(size_t)(t - 1) * npix + j] > 0.5f)) return false;
+  const float c = rho[j];
+  const float rx = ((float)u - P.cx) / P.fx, ry = ((float)v - P.cy) / P.fy;
+  if (t >= 2) {
+    const float* M = posef + 12 * (t - 1);
+    const float hx = fmaf(c, M[9], fmaf(M[0], rx, fmaf(M[1], ry, M[2])));
+    const float hy = fmaf(c, M[10], fmaf(M[3], rx, fmaf(M[4], ry, M[5])));
+    const float hz = fmaf(c, M[11], fmaf(M[6], rx, fmaf(M[7], ry, M[8])));
+    const float x = hx / hz, y = hy / hz;
+    const float mg = 1e-2f;
+    const bool clear = fabsf(hz - VD_Z_EPS) > 1e-3f && fabsf(x) > mg && fabsf(x - (P.W - 1)) > mg &&
+                       fabsf(y) > mg && fabsf(y - (P.H - 1)) > mg && isfinite(x) && isfinite(y);
+    bool ok;
+    if (clear) {
+      ok = hz > VD_Z_EPS && vd_inside(x, y, P.W, P.H);
+    } else {
+      double xd, yd;
+      ok = vd_track64(P, G + 12 * (t - 1), u, v, (double)c, &xd, &yd) && xd >= 0.0 &&
+           xd <= (double)(P.W - 1) && yd >= 0.0 && yd <= (double)(P.H - 1);
+    }
+    if (!ok) return false;
+  }
+  const float* M = posef + 12 * t;
+  const float hz = fmaf(c, M[11], fmaf(M[6], rx, fmaf(M[7], ry, M[8])));
+  if (fabsf(hz - VD_Z_EPS) > 1e-3f) return hz > VD_Z_EPS;
+  return vd_front64(P, G + 12 * t, u, v, (double)c);
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK)
+k_rigid_flags(DevParams P, const double* __restrict__ G, const float* __restrict__ posef,
+              const float* __restrict__ rho, const float* __restrict__ q, int t,
+              unsigned char* __restrict__ flags, int* __restrict__ blk_counts) {
+  const size_t npix = (size_t)P.W * P.H;
+  const size_t j = (size_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  int f = 0;
+  if (j < npix) {
+    const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
+    f = vd_is_rigid(P, G, posef, rho, q, t, u, v, j) ? 1 : 0;
+    flags[j] = (unsigned char)f;
+  }
+  const int cnt = __syncthreads_count(f);
+  if (threadIdx.x == 0) blk_counts[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the block counts by one block; total into n_out.
+__global__ void k_scan_counts(const int* __restrict__ counts, int nblk, int* __restrict__ offsets,
+                              int* __restrict__ n_out) {
+  __shared__ int s[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblk; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int x = i < nblk ? counts[i] : 0;
+    s[threadIdx.x] = x;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int y = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < nblk) offsets[i] = carry + s[threadIdx.x] - x;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_out = carry;
+}
+
+// Scatter the rigid pixels in row-major order with their float32 scoring data:
+// X = r_j / rho_j (reference frame), x_obs = x_{t-1} + X_t(x_{t-1}), w = q_t.
+__global__ void __launch_bounds__(SCAN_BLOCK)
+k_rigid_scatter(DevParams P, const float* __restrict__ posef, const float2* __restrict__ flow,
+                const float* __restrict__ rho, const float* __restrict__ q, int t,
+                const unsigned char* __restrict__ flags, const int* __restrict__ offsets,
+                int* __restrict__ idx, float4* __restrict__ rpts, float4* __restrict__ robs) {
+  __shared__ int warp_tot[SCAN_BLOCK / 32];
+  const size_t npix = (size_t)P.W * P.H;
+  const size_t j = (size_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+  const int f = (j < npix) ? flags[j] : 0;
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) warp_tot[wid] = __popc(bal);
+  __syncthreads();
+  int before = 0;
+  for (unsigned w = 0; w < wid; ++w) before += warp_tot[w];
+  before += __popc(bal & ((1u << lane) - 1u));
+  if (!f) return;
+  const int pos = offsets[blockIdx.x] + before;
+  const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
+  const float c = rho[j];
+  const float rx = ((float)u - P.cx) / P.fx, ry = ((float)v - P.cy) / P.fy;
+  const float th = 1.0f / c;
+  float xp = (float)u, yp = (float)v;
+  float2 F;
+  if (t == 1) {
+    F = flow[j];
+  } else {
+    const float* M = posef + 12 * (t - 1);
+    const float hx = fmaf(c, M[9], fmaf(M[0], rx, fmaf(M[1], ry, M[2])));
+    const float hy = fmaf(c, M[10], fmaf(M[3], rx, fmaf(M[4], ry, M[5])));
+    const float hz = fmaf(c, M[11], fmaf(M[6], rx, fmaf(M[7], ry, M[8])));
+    xp = hx / hz;
+    yp = hy / hz;
+    // the float64 membership test may accept a point the float32 position
+    // puts a hair outside: clamp the sampling position
+    xp = fminf(fmaxf(xp, 0.0f), (float)(P.W - 1));
+    yp = fminf(fmaxf(yp, 0.0f), (float)(P.H - 1));
+    F = vd_bilinear(flow + (size_t)(t - 1) * npix, P.W, P.H, xp, yp);
+  }
+  const float alpha = fmaf(P.alpha1, sqrtf(fmaf(F.x, F.x, F.y * F.y)), P.alpha0);
+  idx[pos] = (int)j;
+  rpts[pos] = make_float4(rx * th, ry * th, th, q[(size_t)(t - 1) * npix + j]);
+  robs[pos] = make_float4(xp + F.x, yp + F.y, alpha, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// One thread per sample: three distinct indices into the rigid set, float64
+// correspondences, P3P, roots ordered by (rotation vector, translation).
+// ---------------------------------------------------------------------------
+__device__ void vd_correspondence64(const DevParams& P, const double* __restrict__ G,
+                                    const float2* __restrict__ flow, const float* __restrict__ rho,
+                                    int t, int j, double* X, double* bearing) {
+  const int v = j / P.W, u = j - v * P.W;
+  const double c = (double)rho[j];
+  const double rx = ((double)u - P.cx_d) / P.fx_d, ry = ((double)v - P.cy_d) / P.fy_d;
+  X[0] = rx / c;
+  X[1] = ry / c;
+  X[2] = 1.0 / c;
+  const size_t npix = (size_t)P.W * P.H;
+  double xp, yp, fx, fy;
+  if (t == 1) {
+    xp = u;
+    yp = v;
+    const float2 F = flow[j];
+    fx = F.x;
+    fy = F.y;
+  } else {
+    xp = 0.0;
+    yp = 0.0;
+    vd_track64(P, G + 12 * (t - 1), u, v, c, &xp, &yp);
+    // members of the rigid set are inside the image; the clamp only guards
+    // the gather against a non-finite position
+    xp = fmin(fmax(xp, 0.0), (double)(P.W - 1));
+    yp = fmin(fmax(yp, 0.0), (double)(P.H - 1));
+    if (!(xp == xp)) xp = 0.0;
+    if (!(yp == yp)) yp = 0.0;
+    vd_bilinear64(flow + (size_t)(t - 1) * npix, P.W, P.H, xp, yp, &fx, &fy);
+  }
+  const double xo = xp + fx, yo = yp + fy;
+  bearing[0] = (xo - P.cx_d) / P.fx_d;
+  bearing[1] = (yo - P.cy_d) / P.fy_d;
+  bearing[2] = 1.0;
+}
+
+__device__ __forceinline__ bool vd_key_less(const double* a, const double* b) {
+  double ka[6], kb[6];
+  vd_so3_log(a, ka);
+  vd_so3_log(b, kb);
+  ka[3] = a[3]; ka[4] = a[7]; ka[5] = a[11];
+  kb[3] = b[3]; kb[4] = b[7]; kb[5] = b[11];
+  for (int i = 0; i < 6; ++i) {
+    if (ka[i] < kb[i]) return true;
+    if (ka[i] > kb[i]) return false;
+  }
+  return false;
+}
+
+__global__ void k_p3p_samples(DevParams P, const double* __restrict__ G,
+                              const float2* __restrict__ flow, const float* __restrict__ rho,
+                              const int* __restrict__ idx, const int* __restrict__ n_rigid, int t,
+                              uint32_t itcode, double* __restrict__ roots,
+                              int* __restrict__ root_count) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.S) return;
+  const int n = *n_rigid;
+  root_count[g] = 0;
+  if (n < 3) return;
+  int pick[3];
+  bool ok = false;
+  for (uint32_t b = 0; b < VD_MAX_ATTEMPTS && !ok; ++b) {
+    const uint4 w = vd_philox(make_uint4((uint32_t)g + 65536u * (uint32_t)t, itcode, VD_TAG_POSE, b),
+                              P.key0, P.key1);
+    pick[0] = (int)(((unsigned long long)w.x * (unsigned long long)n) >> 32);
+    pick[1] = (int)(((unsigned long long)w.y * (unsigned long long)n) >> 32);
+    pick[2] = (int)(((unsigned long long)w.z * (unsigned long long)n) >> 32);
+    ok = pick[0] != pick[1] && pick[0] != pick[2] && pick[1] != pick[2];
+  }
+  if (!ok) return;
+  double X[9], f[9];
+  for (int k = 0; k < 3; ++k) vd_correspondence64(P, G, flow, rho, t, idx[pick[k]], X + 3 * k, f + 3 * k);
+  double* out = roots + (size_t)g * 48;
+  const int nr = vd_p3p(f, X, out);
+  // insertion sort by (rotation vector, translation)
+  for (int a = 1; a < nr; ++a) {
+    for (int b = a; b > 0 && vd_key_less(out + 12 * b, out + 12 * (b - 1)); --b) {
+      for (int i = 0; i < 12; ++i) {
+        const double tmp = out[12 * b + i];
+        out[12 * b + i] = out[12 * (b - 1) + i];
+        out[12 * (b - 1) + i] = tmp;
+      }
+    }
+  }
+  root_count[g] = nr;
+}
+
+// float K R | K tau of every root slot (invalid slots: zero).
+__global__ void k_roots_float(DevParams P, const double* __restrict__ roots,
+                              const int* __restrict__ root_count, float* __restrict__ rootsf) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= 4 * P.S) return;
+  float* o = rootsf + 12 * r;
+  if ((r & 3) >= root_count[r >> 2]) {
+    for (int i = 0; i < 12; ++i) o[i] = 0.0f;
+    return;
+  }
+  const double* g = roots + 12 * r;
+  for (int i = 0; i < 4; ++i) {
+    o[i < 3 ? i : 9] = (float)(P.fx_d * g[i] + P.cx_d * g[8 + i]);
+    o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
+    o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense scoring: every root against every rigid pixel.  Each block owns a
+// contiguous range of rigid pixels, keeps SCORE_PPT of them per thread in
+// registers and loops over the roots (broadcast from shared memory); warp
+// sums go to per-warp shared slots, summed in fixed order at the end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vd_score_term(const DevParams& P, const float* Mr, float4 pt,
+                                               float4 ob) {
+  const float hx = fmaf(Mr[0], pt.x, fmaf(Mr[1], pt.y, fmaf(Mr[2], pt.z, Mr[9])));
+  const float hy = fmaf(Mr[3], pt.x, fmaf(Mr[4], pt.y, fmaf(Mr[5], pt.z, Mr[10])));
+  const float hz = fmaf(Mr[6], pt.x, fmaf(Mr[7], pt.y, fmaf(Mr[8], pt.z, Mr[11])));
+  if (!(hz > VD_Z_EPS)) return pt.w * VD_L_BEHIND;
+  const float iz = __fdividef(1.0f, hz);
+  const float dx = ob.x - hx * iz, dy = ob.y - hy * iz;
+  const float r2 = fmaf(dx, dx, dy * dy);
+  float y;
+  if (P.fast_beta2) {
+    const float s = fmaf(r2, P.inv_a2, 1.0f);
+    y = P.c0 * s * s;
+  } else {
+    y = vd_ratio_general(P, r2, ob.z);
+  }
+  return pt.w * VD_LN2 * vd_ell2(y);
+}
+
+__global__ void __launch_bounds__(SCORE_THREADS)
+k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restrict__ robs,
+             const int* __restrict__ n_ptr, int n_host, const float* __restrict__ rootsf,
+             const int* __restrict__ root_count, int M, float* __restrict__ partial) {
+  extern __shared__ float smem[];
+  float* sRoot = smem;                       // M * 12
+  float* sAcc = smem + 12 * M;               // (SCORE_THREADS / 32) * M
+  const int nwarp = SCORE_THREADS / 32;
+  for (int i = threadIdx.x; i < 12 * M; i += SCORE_THREADS) sRoot[i] = rootsf[i];
+  for (int i = threadIdx.x; i < nwarp * M; i += SCORE_THREADS) sAcc[i] = 0.0f;
+  __syncthreads();
+  const int n = n_ptr ? *n_ptr : n_host;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int beg = blockIdx.x * per;
+  const int end = min(n, beg + per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = beg; base < end; base += SCORE_THREADS * SCORE_PPT) {
+    float4 pt[SCORE_PPT], ob[SCORE_PPT];
+#pragma unroll
+    for (int k = 0; k < SCORE_PPT; ++k) {
+      const int i = base + k * SCORE_THREADS + threadIdx.x;
+      if (i < end) {
+        pt[k] = rpts[i];
+        ob[k] = robs[i];
+      } else {
+        pt[k] = make_float4(0.f, 0.f, 1.f, 0.f);
+        ob[k] = make_float4(0.f, 0.f, 1.f, 0.f);
+      }
+    }
+    for (int r = 0; r < M; ++r) {
+      if (root_count && (r & 3) >= root_count[r >> 2]) continue;
+      const float* Mr = sRoot + 12 * r;
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < SCORE_PPT; ++k) acc += vd_score_term(P, Mr, pt[k], ob[k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) sAcc[wid * M + r] += acc;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < M; r += SCORE_THREADS) {
+    float s = 0.0f;
+    for (int w = 0; w < nwarp; ++w) s += sAcc[w * M + r];
+    partial[(size_t)r * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_root_energy(const float* __restrict__ partial, int nblk, int M,
+                              const int* __restrict__ root_count, double* __restrict__ energy) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  if (root_count && (r & 3) >= root_count[r >> 2]) {
+    energy[r] = INFINITY;
+    return;
+  }
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += (double)partial[(size_t)r * nblk + b];
+  energy[r] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Per sample: the lowest-energy root; then mean-shift from the best sample:
+// x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
+// w_g = exp(-d^T Sigma^-1 d / 2), until |step| < 1e-12 or 100 steps.
+// One block of 256 threads, one sample per thread.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __restrict__ root_count,
+                   const double* __restrict__ root_energy, int t, double* __restrict__ G,
+                   float* __restrict__ posef, double* __restrict__ sample_pose,
+                   double* __restrict__ sample_energy, int* __restrict__ degenerate) {
+  __shared__ double sRed[256 * 7];
+  __shared__ int sIdx[256];
+  __shared__ double sX[12];
+  __shared__ int sDone;
+  const int g = threadIdx.x;
+  double Tg[12];
+  double Eg = INFINITY;
+  if (g < P.S) {
+    const int nr = root_count[g];
+    int best = -1;
+    for (int r = 0; r < nr; ++r) {
+      const double e = root_energy[4 * g + r];
+      if (best < 0 || e < Eg) {
+        Eg = e;
+        best = r;
+      }
+    }
+    if (best >= 0) {
+      for (int i = 0; i < 12; ++i) Tg[i] = roots[(size_t)48 * g + 12 * best + i];
+    } else {
+      Eg = INFINITY;
+    }
+    for (int i = 0; i < 12; ++i) sample_pose[12 * g + i] = best >= 0 ? Tg[i] : 0.0;
+    sample_energy[g] = Eg;
+  }
+  const bool valid = g < P.S && Eg < INFINITY;
+  // argmin over samples (lowest energy, then lowest index)
+  sRed[g] = valid ? Eg : INFINITY;
+  sIdx[g] = g;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (g < off) {
+      const double a = sRed[g], b = sRed[g + off];
+      const int ia = sIdx[g], ib = sIdx[g + off];
+      if (b < a || (b == a && ib < ia)) {
+        sRed[g] = b;
+        sIdx[g] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  const int start = sIdx[0];
+  const bool any = sRed[0] < INFINITY;
+  __syncthreads();
+  if (!any) {
+    if (g == 0) atomicAdd(degenerate, 1);
+    return;
+  }
+  if (g == start)
+    for (int i = 0; i < 12; ++i) sX[i] = Tg[i];
+  __syncthreads();
+  const double st_ = P.ms_sig_rel * sqrt(sX[3] * sX[3] + sX[7] * sX[7] + sX[11] * sX[11]) + P.ms_sig_abs;
+  const double ivr = 1.0 / (P.ms_sig_rot * P.ms_sig_rot), ivt = 1.0 / (st_ * st_);
+  if (g == 0) sDone = 0;
+  __syncthreads();
+  for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
+    double d[6] = {0, 0, 0, 0, 0, 0};
+    double w = 0.0;
+    if (valid) {
+      double xi[12], rel[12];
+      double xl[12];
+      for (int i = 0; i < 12; ++i) xl[i] = sX[i];
+      vd_inverse(xl, xi);
+      vd_compose(xi, Tg, rel);
+      vd_se3_log(rel, d);
+      const double m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
+                       (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
+      w = exp(-0.5 * m);
+    }
+    sRed[g * 7] = w;
+    for (int i = 0; i < 6; ++i) sRed[g * 7 + 1 + i] = w * d[i];
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if (g < off)
+        for (int i = 0; i < 7; ++i) sRed[g * 7 + i] += sRed[(g + off) * 7 + i];
+      __syncthreads();
+    }
+    if (g == 0) {
+      double step[6];
+      double nrm = 0.0;
+      for (int i = 0; i < 6; ++i) {
+        step[i] = sRed[1 + i] / sRed[0];
+        nrm += step[i] * step[i];
+      }
+      double E[12], xn[12], xo[12];
+      for (int i = 0; i < 12; ++i) xo[i] = sX[i];
+      vd_se3_exp(step, E);
+      vd_compose(xo, E, xn);
+      for (int i = 0; i < 12; ++i) sX[i] = xn[i];
+      if (sqrt(nrm) < VD_MS_TOL) sDone = 1;
+    }
+    __syncthreads();
+    if (sDone) break;
+  }
+  if (g < 12) G[12 * t + g] = sX[g];
+  if (g == 0) {
+    // float K R | K tau of the updated pose
+    float* o = posef + 12 * t;
+    for (int i = 0; i < 4; ++i) {
+      o[i < 3 ? i : 9] = (float)(P.fx_d * sX[i] + P.cx_d * sX[8 + i]);
+      o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * sX[4 + i] + P.cy_d * sX[8 + i]);
+      o[i < 3 ? 6 + i : 11] = (float)sX[8 + i];
+    }
+  }
+}
+
+cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
+  const DevParams& P = c->dp;
+  vd_prof_begin(c, VD_ST_RIGID);
+  k_rigid_flags<<<c->nblk_scan, SCAN_BLOCK, 0, c->stream>>>(P, c->G, c->posef, c->rho, c->q, t,
+                                                            c->flags, c->blk_counts);
+  k_scan_counts<<<1, 1024, 0, c->stream>>>(c->blk_counts, c->nblk_scan, c->blk_offsets, c->n_rigid);
+  k_rigid_scatter<<<c->nblk_scan, SCAN_BLOCK, 0, c->stream>>>(P, c->posef, c->flow, c->rho, c->q, t,
+                                                              c->flags, c->blk_offsets,
+                                                              c->rigid_idx, c->rpts, c->robs);
+  vd_prof_end(c, VD_ST_RIGID, 3);
+  vd_prof_begin(c, VD_ST_P3P);
+  k_p3p_samples<<<(P.S + 31) / 32, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
+                                                       c->n_rigid, t, itcode, c->roots,
+                                                       c->root_count);
+  const int M = 4 * P.S;
+  k_roots_float<<<(M + 127) / 128, 128, 0, c->stream>>>(P, c->roots, c->root_count, c->rootsf);
+  vd_prof_end(c, VD_ST_P3P, 2);
+  vd_prof_begin(c, VD_ST_SCORE);
+  const size_t smem = sizeof(float) * (size_t)M * (12 + SCORE_THREADS / 32);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pose_score<<<c->nblk_score, SCORE_THREADS, smem, c->stream>>>(
+      P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
+  k_root_energy<<<(M + 127) / 128, 128, 0, c->stream>>>(c->partial, c->nblk_score, M,
+                                                        c->root_count, c->root_energy);
+  vd_prof_end(c, VD_ST_SCORE, 2);
+  vd_prof_begin(c, VD_ST_SELECT);
+  k_select_meanshift<<<1, 256, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
+                                               c->posef, c->sample_pose, c->sample_energy,
+                                               c->degenerate);
+  vd_prof_end(c, VD_ST_SELECT, 1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Standalone dense scoring on caller buffers (allocates its partial sums).
+// ---------------------------------------------------------------------------
+__global__ void k_poses_float(DevParams P, const double* __restrict__ poses, int m,
+                              float* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  const double* g = poses + 12 * r;
+  float* o = out + 12 * r;
+  for (int i = 0; i < 4; ++i) {
+    o[i < 3 ? i : 9] = (float)(P.fx_d * g[i] + P.cx_d * g[8 + i]);
+    o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
+    o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
+  }
+}
+
+extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n, const double* poses,
+                                    int m, const double* intrinsics, float beta, float p0,
+                                    double* energies, void* cuda_stream) {
+  if (!points || !obs || !poses || !intrinsics || !energies || n < 0 || m < 1 || m > 1024 ||
+      !(beta > 0.0f) || !(p0 > 0.0f))
+    return VD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double K[4];
+  if (cudaMemcpy(K, intrinsics, sizeof K, cudaMemcpyDefault) != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(cudaGetLastError()));
+    return VD_ERR_CUDA;
+  }
+  DevParams P{};
+  P.fx_d = K[0]; P.fy_d = K[1]; P.cx_d = K[2]; P.cy_d = K[3];
+  P.beta = beta;
+  P.p0 = p0;
+  P.fast_beta2 = 0;           // the per-point scale rides in obs.z
+  P.cgen = p0 * 2.0f * 3.14159265358979f / beta;
+  const int nblk = 2 * 152;
+  float* rootsf = nullptr;
+  float* partial = nullptr;
+  cudaError_t e = cudaMallocAsync(&rootsf, sizeof(float) * 12 * m, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&partial, sizeof(float) * (size_t)m * nblk, s);
+  if (e != cudaSuccess) {
+    if (rootsf) cudaFreeAsync(rootsf, s);
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_OOM;
+  }
+  k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
+  const size_t smem = sizeof(float) * (size_t)m * (12 + SCORE_THREADS / 32);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pose_score<<<nblk, SCORE_THREADS, smem, s>>>(P, (const float4*)points, (const float4*)obs,
+                                                 nullptr, n, rootsf, nullptr, m, partial);
+  k_root_energy<<<(m + 127) / 128, 128, 0, s>>>(partial, nblk, m, nullptr, energies);
+  e = cudaGetLastError();
+  cudaFreeAsync(rootsf, s);
+  cudaFreeAsync(partial, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  return VD_OK;
+}

@@ -1,0 +1,348 @@
+"""ctypes binding of libvoldor_em.so (the C ABI in include/voldor_em.h).
+
+Argument marshalling only: every function below converts Python arguments to
+the C types and calls the entry point of the same name; all computation runs
+in the library's CUDA kernels.  Buffers may be numpy arrays (host memory,
+VD_MEM_HOST) or CUDA torch tensors (device memory, VD_MEM_DEVICE).
+
+The library must have been built (``paper_2104_06800_gb300.build.build()``);
+there is no fallback: a missing library raises at load time.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvoldor_em.so")
+
+VD_OK, VD_WARN_DEGENERATE = 0, 1
+VD_ERR_ARG, VD_ERR_CUDA, VD_ERR_OOM, VD_ERR_STATE, VD_ERR_TIMEOUT, VD_ERR_NUMERIC = -1, -2, -3, -4, -5, -6
+VD_MEM_HOST, VD_MEM_DEVICE = 0, 1
+VD_POSE_ABSOLUTE, VD_POSE_RELATIVE = 0, 1
+
+
+class vd_window_desc(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("n_flows", C.c_int),
+                ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double)]
+
+
+class vd_params(C.Structure):
+    _fields_ = [("fisk_alpha0", C.c_float), ("fisk_alpha1", C.c_float), ("fisk_beta", C.c_float),
+                ("outlier_density", C.c_float), ("gamma_stay", C.c_float),
+                ("rho_min", C.c_float), ("rho_max", C.c_float),
+                ("n_hyp", C.c_int), ("n_pose_samples", C.c_int),
+                ("pose_sigma_rot", C.c_double), ("pose_sigma_trans_rel", C.c_double),
+                ("pose_sigma_trans_abs", C.c_double),
+                ("sample_share", C.c_int), ("hierarchical", C.c_int), ("hier_scale", C.c_int),
+                ("hier_window", C.c_int), ("prior_c_sigma", C.c_float),
+                ("prior_w_uniform", C.c_float), ("seed", C.c_ulonglong)]
+
+
+class vd_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("bootstrapped", C.c_int), ("degenerate_frames", C.c_int),
+                ("mean_energy", C.c_double), ("rigid_fraction", C.c_double)]
+
+
+VD_N_STAGES = 8
+STAGE_NAMES = ("depth_sample", "depth_propagate", "rigidness_estep", "pose_rigid_set",
+               "pose_p3p", "pose_score", "pose_select_meanshift", "bootstrap_other")
+
+
+class vd_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * VD_N_STAGES), ("calls", C.c_longlong * VD_N_STAGES),
+                ("launches", C.c_longlong * VD_N_STAGES), ("total_launches", C.c_longlong)]
+
+
+class VoldorError(RuntimeError):
+    def __init__(self, fn, status, lib):
+        msg = lib.vd_status_str(status).decode()
+        last = lib.vd_last_error().decode()
+        super().__init__(f"{fn} -> {status} ({msg}){': ' + last if last else ''}")
+        self.status = status
+
+
+_P = C.c_void_p
+_SIGS = {
+    "vd_params_default": [C.POINTER(vd_params)],
+    "vd_create": [C.POINTER(vd_window_desc), C.POINTER(vd_params), _P, C.POINTER(_P)],
+    "vd_destroy": [_P],
+    "vd_set_stream": [_P, _P],
+    "vd_set_params": [_P, C.POINTER(vd_params)],
+    "vd_push_flow": [_P, C.c_int, _P, C.c_long, C.c_int],
+    "vd_push_stereo_prior": [_P, _P, C.c_double, C.c_int],
+    "vd_push_depth_prior": [_P, _P, _P, _P, C.c_int],
+    "vd_clear_prior": [_P],
+    "vd_set_poses": [_P, _P, C.c_int],
+    "vd_get_poses": [_P, _P, C.c_int],
+    "vd_set_state": [_P, _P, _P, _P, C.c_int],
+    "vd_bootstrap": [_P],
+    "vd_run_em": [_P, C.c_int, C.POINTER(vd_stats)],
+    "vd_depth_mstep": [_P, C.c_int, C.c_int],
+    "vd_rigidness_estep": [_P, C.c_int],
+    "vd_pose_mstep": [_P, C.c_int, C.c_int],
+    "vd_get_inv_depth": [_P, _P, C.c_int],
+    "vd_get_rigidness": [_P, _P, C.c_int],
+    "vd_get_prior_rigidness": [_P, _P, C.c_int],
+    "vd_get_confidence": [_P, _P, C.c_int],
+    "vd_get_depth_candidates": [_P, _P, _P, C.c_int],
+    "vd_eval_energy": [_P, _P, _P, C.c_int],
+    "vd_get_pose_samples": [_P, _P, _P, _P],
+    "vd_score_poses": [_P, _P, C.c_int, _P, C.c_int, _P, C.c_float, C.c_float, _P, _P],
+    "vd_profile_enable": [_P, C.c_int],
+    "vd_get_profile": [_P, C.POINTER(vd_profile)],
+    "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
+    "vd_import_state": [_P, _P, C.c_size_t],
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the shared library (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"{p} not found: build it with paper_2104_06800_gb300.build.build()")
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.vd_status_str.argtypes = [C.c_int]
+    lib.vd_status_str.restype = C.c_char_p
+    lib.vd_last_error.argtypes = []
+    lib.vd_last_error.restype = C.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(name, st, allow_warn=True):
+    if st == VD_OK or (allow_warn and st == VD_WARN_DEGENERATE):
+        return st
+    raise VoldorError(name, st, load())
+
+
+def _call(name, *args, allow_warn=True):
+    return _check(name, getattr(load(), name)(*args), allow_warn)
+
+
+# ------------------------------------------------------------------ buffers
+def _is_tensor(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype=np.float32):
+    """(pointer, mem kind, keep-alive) of a numpy array or CUDA tensor."""
+    if x is None:
+        return None, VD_MEM_HOST, None
+    if _is_tensor(x):
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            if not x.is_contiguous():
+                raise ValueError("device tensors must be contiguous")
+            return C.c_void_p(x.data_ptr()), VD_MEM_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), VD_MEM_HOST, a
+
+
+def current_stream():
+    """The torch current CUDA stream handle (0 when torch has no CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+# ------------------------------------------------------------------ entry points
+def vd_params_default(**overrides):
+    p = vd_params()
+    _call("vd_params_default", C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def vd_create(W, H, N, K, params=None, stream=None):
+    d = vd_window_desc(int(W), int(H), int(N), *[float(v) for v in K])
+    h = C.c_void_p()
+    _call("vd_create", C.byref(d), C.byref(params) if params is not None else None,
+          stream if stream is not None else current_stream(), C.byref(h))
+    return h
+
+
+def vd_destroy(ctx):
+    _call("vd_destroy", ctx)
+
+
+def vd_set_stream(ctx, stream):
+    _call("vd_set_stream", ctx, stream)
+
+
+def vd_set_params(ctx, params):
+    _call("vd_set_params", ctx, C.byref(params))
+
+
+def vd_push_flow(ctx, t, uv, row_pitch_floats=None):
+    ptr, mem, keep = _buf(uv)
+    W = uv.shape[-2]
+    _call("vd_push_flow", ctx, int(t), ptr, int(row_pitch_floats or 2 * W), mem)
+
+
+def vd_push_stereo_prior(ctx, disparity, baseline):
+    ptr, mem, keep = _buf(disparity)
+    _call("vd_push_stereo_prior", ctx, ptr, float(baseline), mem)
+
+
+def vd_push_depth_prior(ctx, depth, confidence=None, T_hat=None):
+    ptr, mem, keep = _buf(depth)
+    cptr, cmem, ckeep = _buf(confidence)
+    if confidence is not None and cmem != mem:
+        raise ValueError("depth and confidence must live in the same memory")
+    tptr = None
+    if T_hat is not None:
+        T_hat = np.ascontiguousarray(T_hat, np.float64).reshape(12)
+        tptr = T_hat.ctypes.data_as(C.c_void_p)
+    _call("vd_push_depth_prior", ctx, ptr, cptr, tptr, mem)
+
+
+def vd_clear_prior(ctx):
+    _call("vd_clear_prior", ctx)
+
+
+def vd_set_poses(ctx, poses, kind=VD_POSE_ABSOLUTE):
+    a = np.ascontiguousarray(poses, np.float64)
+    _call("vd_set_poses", ctx, a.ctypes.data_as(C.c_void_p), int(kind))
+
+
+def vd_get_poses(ctx, N, kind=VD_POSE_ABSOLUTE):
+    n = N + 1 if kind == VD_POSE_ABSOLUTE else N
+    out = np.zeros((n, 3, 4), np.float64)
+    _call("vd_get_poses", ctx, out.ctypes.data_as(C.c_void_p), int(kind))
+    return out
+
+
+def vd_set_state(ctx, rho, q=None, q_hat=None):
+    p1, m1, k1 = _buf(rho)
+    p2, m2, k2 = _buf(q)
+    p3, m3, k3 = _buf(q_hat)
+    for x, m in ((q, m2), (q_hat, m3)):
+        if x is not None and m != m1:
+            raise ValueError("state buffers must live in the same memory")
+    _call("vd_set_state", ctx, p1, p2, p3, m1)
+
+
+def vd_bootstrap(ctx):
+    return _call("vd_bootstrap", ctx)
+
+
+def vd_run_em(ctx, n_iters, stats=True):
+    s = vd_stats()
+    st = _call("vd_run_em", ctx, int(n_iters), C.byref(s) if stats else None)
+    return st, s
+
+
+def vd_depth_mstep(ctx, iter, direction):
+    _call("vd_depth_mstep", ctx, int(iter), int(direction))
+
+
+def vd_rigidness_estep(ctx, direction):
+    _call("vd_rigidness_estep", ctx, int(direction))
+
+
+def vd_pose_mstep(ctx, iter, t):
+    return _call("vd_pose_mstep", ctx, int(iter), int(t))
+
+
+def _get(name, ctx, out):
+    ptr, mem, keep = _buf(out)
+    if mem == VD_MEM_HOST and keep is not out:
+        raise ValueError("host outputs must be contiguous float32 numpy arrays")
+    _call(name, ctx, ptr, mem)
+    return out
+
+
+def vd_get_inv_depth(ctx, out):
+    return _get("vd_get_inv_depth", ctx, out)
+
+
+def vd_get_rigidness(ctx, out):
+    return _get("vd_get_rigidness", ctx, out)
+
+
+def vd_get_prior_rigidness(ctx, out):
+    return _get("vd_get_prior_rigidness", ctx, out)
+
+
+def vd_get_confidence(ctx, out):
+    return _get("vd_get_confidence", ctx, out)
+
+
+def vd_get_depth_candidates(ctx, rho_star, e_star):
+    p1, m1, k1 = _buf(rho_star)
+    p2, m2, k2 = _buf(e_star)
+    _call("vd_get_depth_candidates", ctx, p1, p2, m1)
+    return rho_star, e_star
+
+
+def vd_eval_energy(ctx, rho, out):
+    p1, m1, k1 = _buf(rho)
+    p2, m2, k2 = _buf(out)
+    if m1 != m2:
+        raise ValueError("rho and out must live in the same memory")
+    _call("vd_eval_energy", ctx, p1, p2, m1)
+    return out
+
+
+def vd_get_pose_samples(ctx, S):
+    poses = np.zeros((S, 3, 4), np.float64)
+    en = np.zeros(S, np.float64)
+    n = C.c_int(0)
+    _call("vd_get_pose_samples", ctx, poses.ctypes.data_as(C.c_void_p),
+          en.ctypes.data_as(C.c_void_p), C.byref(n))
+    return poses, en, int(n.value)
+
+
+def vd_score_poses(points, obs, poses, intrinsics, beta, p0, energies, stream=None):
+    """All arguments except beta, p0 and stream are CUDA tensors."""
+    n = points.shape[0]
+    m = poses.shape[0]
+    _call("vd_score_poses", C.c_void_p(points.data_ptr()), C.c_void_p(obs.data_ptr()), int(n),
+          C.c_void_p(poses.data_ptr()), int(m), C.c_void_p(intrinsics.data_ptr()), float(beta),
+          float(p0), C.c_void_p(energies.data_ptr()), stream if stream is not None else current_stream())
+    return energies
+
+
+def vd_profile_enable(ctx, enable=True):
+    _call("vd_profile_enable", ctx, 1 if enable else 0)
+
+
+def vd_get_profile(ctx):
+    p = vd_profile()
+    _call("vd_get_profile", ctx, C.byref(p))
+    return {name: dict(ms=p.ms[i], calls=p.calls[i], launches=p.launches[i])
+            for i, name in enumerate(STAGE_NAMES)} | {"total_launches": p.total_launches}
+
+
+def vd_export_state(ctx):
+    n = C.c_size_t(0)
+    _call("vd_export_state", ctx, None, C.byref(n))
+    blob = (C.c_char * n.value)()
+    _call("vd_export_state", ctx, C.cast(blob, C.c_void_p), C.byref(n))
+    return bytes(blob)
+
+
+def vd_import_state(ctx, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _call("vd_import_state", ctx, C.cast(buf, C.c_void_p), len(blob))

@@ -1,0 +1,69 @@
+"""The shared library builds, loads, and exports every symbol of the header.
+
+No compute calls here (no GPU on this host)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(vd_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_06800_gb300 import build, voldor
+    build.build()
+    return voldor.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 25
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    from paper_2104_06800_gb300 import voldor
+    for n in _declared():
+        assert n in voldor._SIGS or n in ("vd_status_str", "vd_last_error"), n
+        assert hasattr(voldor, n) or n in ("vd_status_str", "vd_last_error"), n
+
+
+def test_host_only_calls(lib):
+    from paper_2104_06800_gb300 import voldor as V
+    p = V.vd_params_default()
+    assert p.n_hyp == 64 and abs(p.fisk_alpha0 - 0.5) < 1e-7 and p.sample_share == 1
+    assert lib.vd_status_str(V.VD_ERR_STATE) == b"call out of order"
+    assert lib.vd_params_default(None) == V.VD_ERR_ARG
+    # argument validation happens before any CUDA call
+    h = V.C.c_void_p()
+    bad = V.vd_window_desc(1, 10, 3, 100.0, 100.0, 0.0, 0.0)
+    assert lib.vd_create(V.C.byref(bad), None, None, V.C.byref(h)) == V.VD_ERR_ARG
+    bad = V.vd_window_desc(10, 10, 9, 100.0, 100.0, 0.0, 0.0)
+    assert lib.vd_create(V.C.byref(bad), None, None, V.C.byref(h)) == V.VD_ERR_ARG
+    good = V.vd_window_desc(10, 10, 3, 100.0, 100.0, 0.0, 0.0)
+    pp = V.vd_params_default(rho_min=1.0, rho_max=0.5)
+    assert lib.vd_create(V.C.byref(good), V.C.byref(pp), None, V.C.byref(h)) == V.VD_ERR_ARG
+    assert lib.vd_run_em(None, 1, None) == V.VD_ERR_ARG
+
+
+def test_struct_layouts_match_the_header():
+    """ctypes structures mirror the C declarations field by field."""
+    from paper_2104_06800_gb300 import voldor as V
+    src = open(os.path.join(ROOT, "include", "voldor_em.h")).read()
+    body = src[src.index("typedef struct {\n  float fisk_alpha0"):]
+    body = body[:body.index("} vd_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b([a-z_0-9]+)\s*[,;]", body.replace("typedef struct {", ""))
+    assert [f for f, _ in V.vd_params._fields_] == fields

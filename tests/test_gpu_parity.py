@@ -1,0 +1,385 @@
+"""Parity of the CUDA path with the FP64 oracle, stage by stage, through the C ABI.
+
+Each stage gets the same input state on both sides (set through
+vd_set_state / vd_set_poses) and is compared element by element:
+  * hypotheses: bit-exact (every GPU choice is one of the oracle's float32
+    candidates of that pixel);
+  * argmin / propagation: identical choice, or a choice whose float64 energy
+    is within the tie band of the oracle's (a float32 near-tie);
+  * rigidness: 1e-4 absolute;
+  * poses: 1e-4 rad / 1e-4 relative translation.
+"""
+import numpy as np
+import pytest
+
+from oracle import depth as odepth
+from oracle import em as oem
+from oracle import geometry as ogeo
+from oracle import hmm as ohmm
+from oracle import model as omodel
+from oracle import pose as opose
+
+from gpu_common import (POSE_ROT_TOL, POSE_TRANS_TOL, RIGID_TOL, make_ctx, noisy_state,
+                        push_state, tie_band, window)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_06800_gb300 import build, voldor
+    build.build()
+    voldor.load()
+    return voldor
+
+
+def _get(V, fn, ctx, shape):
+    out = np.zeros(shape, np.float32)
+    fn(ctx, out)
+    return out
+
+
+def _pose_err(A, B):
+    d = ogeo.se3_log(ogeo.compose(ogeo.inverse(A), B))
+    rot = float(np.linalg.norm(d[:3]))
+    trans = float(np.linalg.norm(A[:, 3] - B[:, 3]) / max(np.linalg.norm(A[:, 3]), 1e-9))
+    return rot, trans
+
+
+# ------------------------------------------------------------------ depth step
+CASES = [
+    ("planes160", dict(), "none"),
+    ("planes160", dict(sample_share=32, n_hyp=33), "none"),
+    ("boxes640_stereo", dict(size=(97, 61), N=4), "stereo"),
+    ("rgbd_batch", dict(size=(83, 45), N=5), "rgbd"),
+]
+
+
+@pytest.mark.parametrize("name,kw,prior", CASES)
+def test_depth_sample_parity(V, name, kw, prior):
+    wkw = {k: v for k, v in kw.items() if k in ("size", "N")}
+    pkw = {k: v for k, v in kw.items() if k not in ("size", "N")}
+    win = window(name, 3, **wkw)
+    ctx, P, p = make_ctx(V, win, prior=prior, **pkw)
+    try:
+        assert P.prior_kind == prior
+        S = noisy_state(win, P, np.random.default_rng(1))
+        push_state(V, ctx, S)
+        it = 2
+        V.vd_depth_mstep(ctx, it, 0)
+        rs = np.zeros((P.H, P.W), np.float32)
+        es = np.zeros((P.H, P.W), np.float32)
+        V.vd_get_depth_candidates(ctx, rs, es)
+        cands = odepth.hypotheses(P, S.rho, it, p)
+        # candidate sets are bit-identical: the GPU's choice is one of them
+        assert np.all((cands == rs[None]).any(0))
+        ro, eo, _ = odepth.argmin_candidates(P, S, cands, p)
+        iu, iv = omodel.pixel_grid(P)
+        e_gpu_choice = omodel.energy(P, S, iu, iv, rs, p)
+        # float32 energy of the chosen candidate vs float64
+        band = tie_band(P, eo)
+        assert np.all(np.abs(es - e_gpu_choice) <= band)
+        same = rs == ro
+        ok = same | (e_gpu_choice - eo <= band)
+        assert ok.all(), f"{(~ok).sum()} pixels outside the tie band"
+        assert same.mean() > 0.99
+    finally:
+        V.vd_destroy(ctx)
+
+
+@pytest.mark.parametrize("direction", [0, 1, 2, 3])
+def test_propagation_parity(V, direction):
+    win = window("planes160", 5)
+    ctx, P, p = make_ctx(V, win, n_hyp=24)
+    try:
+        S = noisy_state(win, P, np.random.default_rng(direction))
+        push_state(V, ctx, S)
+        V.vd_depth_mstep(ctx, 1, direction)
+        rs = np.zeros((P.H, P.W), np.float32)
+        es = np.zeros((P.H, P.W), np.float32)
+        V.vd_get_depth_candidates(ctx, rs, es)
+        new = _get(V, V.vd_get_inv_depth, ctx, (P.H, P.W))
+        iu, iv = omodel.pixel_grid(P)
+        E_own = omodel.energy(P, S, iu, iv, rs, p)
+        # replay of the oracle from the GPU's rho*
+        ro, _ = odepth.propagate(P, S, rs, E_own, direction, p)
+        assert (new == ro).mean() > 0.99
+        # every GPU step is a valid propagation step within the tie band
+        cu, cv = odepth.chain_coords(P, direction)
+        band = tie_band(P, E_own)
+        prev = new[cv[0], cu[0]]
+        assert np.array_equal(prev, rs[cv[0], cu[0]])
+        for m in range(1, cu.shape[0]):
+            u, v = cu[m], cv[m]
+            g = new[v, u]
+            assert np.all((g == rs[v, u]) | (g == prev))
+            Ep = omodel.energy(P, S, u, v, prev, p)
+            took = (g == prev) & (g != rs[v, u])
+            kept = (g == rs[v, u]) & (g != prev)
+            assert np.all(Ep[took] < E_own[v, u][took] + band[v, u][took])
+            assert np.all(Ep[kept] >= E_own[v, u][kept] - band[v, u][kept])
+            prev = g
+    finally:
+        V.vd_destroy(ctx)
+
+
+@pytest.mark.parametrize("direction", [0, 3])
+def test_hierarchical_propagation_parity(V, direction):
+    win = window("planes160", 6)
+    ctx, P, p = make_ctx(V, win, n_hyp=16, hierarchical=1, hier_scale=4, hier_window=16)
+    try:
+        S = noisy_state(win, P, np.random.default_rng(9))
+        push_state(V, ctx, S)
+        V.vd_depth_mstep(ctx, 0, direction)
+        rs = np.zeros((P.H, P.W), np.float32)
+        es = np.zeros((P.H, P.W), np.float32)
+        V.vd_get_depth_candidates(ctx, rs, es)
+        new = _get(V, V.vd_get_inv_depth, ctx, (P.H, P.W))
+        iu, iv = omodel.pixel_grid(P)
+        E_own = omodel.energy(P, S, iu, iv, rs, p)
+        ro, _ = odepth.hierarchical(P, S, rs, E_own, direction, p)
+        assert (new == ro).mean() > 0.99
+        # every value comes from the pixel's own candidate, its window or its coarse cell
+        assert np.all(np.isin(new, rs))
+    finally:
+        V.vd_destroy(ctx)
+
+
+def test_energy_eval_matches_oracle(V):
+    win = window("boxes640_stereo", 4, size=(128, 96), N=3)
+    ctx, P, p = make_ctx(V, win)
+    try:
+        S = noisy_state(win, P, np.random.default_rng(3))
+        push_state(V, ctx, S)
+        rho = (S.rho * np.float32(1.03)).astype(np.float32)
+        eg = np.zeros_like(rho)
+        V.vd_eval_energy(ctx, rho, eg)
+        iu, iv = omodel.pixel_grid(P)
+        eo = omodel.energy(P, S, iu, iv, rho, p)
+        assert np.all(np.abs(eg - eo) <= tie_band(P, eo))
+    finally:
+        V.vd_destroy(ctx)
+
+
+# ------------------------------------------------------------------ E-step
+@pytest.mark.parametrize("name,kw,direction", [("planes160", {}, 0), ("planes160", {}, 1),
+                                               ("boxes640_stereo", dict(size=(90, 70), N=3), 2),
+                                               ("rgbd_batch", dict(size=(77, 41), N=4), 3)])
+def test_estep_parity(V, name, kw, direction):
+    win = window(name, 7, **kw)
+    ctx, P, p = make_ctx(V, win)
+    try:
+        S = noisy_state(win, P, np.random.default_rng(4), rel=0.01)
+        push_state(V, ctx, S)
+        V.vd_rigidness_estep(ctx, direction)
+        q = _get(V, V.vd_get_rigidness, ctx, (P.N, P.H, P.W))
+        qh = _get(V, V.vd_get_prior_rigidness, ctx, (P.H, P.W))
+        C = _get(V, V.vd_get_confidence, ctx, (P.H, P.W))
+        qo, qho, Co = ohmm.rigidness_estep(P, S, S.rho, direction, p)
+        err = np.abs(q - qo)
+        assert np.mean(err <= RIGID_TOL) > 0.999, f"max err {err.max()}"
+        assert np.quantile(err, 0.99) < RIGID_TOL
+        if P.prior_kind != "none":
+            assert np.abs(qh - qho).max() < RIGID_TOL
+        assert np.mean(np.abs(C - Co) <= RIGID_TOL) > 0.999
+    finally:
+        V.vd_destroy(ctx)
+
+
+# ------------------------------------------------------------------ pose step
+@pytest.mark.parametrize("name,kw", [("planes160", {}), ("boxes640_stereo", dict(size=(160, 120), N=3))])
+def test_pose_step_parity(V, name, kw):
+    win = window(name, 8, **kw)
+    ctx, P, p = make_ctx(V, win, prior="none")
+    try:
+        rng = np.random.default_rng(5)
+        S = noisy_state(win, P, rng, rel=0.002, qmode="random")
+        S.q = (S.q * 0.5 + 0.45).astype(np.float32)      # most pixels rigid
+        push_state(V, ctx, S)
+        for t in range(1, P.N + 1):
+            So = S.copy()
+            out = opose.pose_mstep_frame(P, So, t, 3, p, detail=True)
+            st = V.vd_pose_mstep(ctx, 3, t)
+            assert st == V.VD_OK
+            poses, en, n = V.vd_get_pose_samples(ctx, p.n_pose_samples)
+            assert n == out["n_rigid"]
+            # every GPU sample is the oracle's lowest-energy root of the same draw
+            for g in range(p.n_pose_samples):
+                roots, Es = out["roots"][g], out["root_scores"][g]
+                if not roots:
+                    assert not np.isfinite(en[g])
+                    continue
+                k = int(np.argmin(Es))
+                srt = np.sort(Es)
+                if len(Es) > 1 and srt[1] - srt[0] < 1e-4 * abs(srt[0]):
+                    continue        # float32 near-tie between roots: either is correct
+                assert np.abs(poses[g] - roots[k]).max() < 1e-7
+                assert abs(en[g] - Es[k]) <= 2e-5 * abs(Es[k])
+            assert np.allclose(np.sort(en[np.isfinite(en)]), np.sort(out["scores"]), rtol=2e-5)
+            Gg = V.vd_get_poses(ctx, P.N)
+            rot, trans = _pose_err(So.G[t], Gg[t])
+            assert rot < POSE_ROT_TOL and trans < POSE_TRANS_TOL, (t, rot, trans)
+            # continue both sides from the oracle's pose (stage-wise)
+            S.G[t] = So.G[t]
+            V.vd_set_poses(ctx, S.G.reshape(-1, 12))
+    finally:
+        V.vd_destroy(ctx)
+
+
+def test_pose_step_degenerate_frame_keeps_pose(V):
+    win = window("planes160", 2)
+    ctx, P, p = make_ctx(V, win)
+    try:
+        S = noisy_state(win, P, np.random.default_rng(0))
+        S.q[:] = 0.0
+        push_state(V, ctx, S)
+        G0 = V.vd_get_poses(ctx, P.N)
+        st = V.vd_pose_mstep(ctx, 0, 2)
+        assert st == V.VD_WARN_DEGENERATE
+        assert np.array_equal(V.vd_get_poses(ctx, P.N), G0)
+    finally:
+        V.vd_destroy(ctx)
+
+
+def test_score_poses_standalone(V):
+    import torch
+    rng = np.random.default_rng(2)
+    n, m = 5000, 37
+    X = rng.uniform(-3, 3, size=(n, 3))
+    X[:, 2] = rng.uniform(2, 20, size=n)
+    w = rng.uniform(0, 1, size=n)
+    K = (300.0, 310.0, 160.0, 120.0)
+    poses = np.stack([ogeo.se3_exp(rng.normal(size=6) * 0.05) for _ in range(m)])
+    xobs = np.stack([K[0] * X[:, 0] / X[:, 2] + K[2], K[1] * X[:, 1] / X[:, 2] + K[3]], 1)
+    xobs += rng.normal(size=xobs.shape)
+    alpha = rng.uniform(0.4, 1.2, size=n)
+    pts = np.concatenate([X, w[:, None]], 1).astype(np.float32)
+    obs = np.concatenate([xobs, alpha[:, None], np.zeros((n, 1))], 1).astype(np.float32)
+    dev = torch.device("cuda")
+    e = torch.zeros(m, dtype=torch.float64, device=dev)
+    V.vd_score_poses(torch.from_numpy(pts).to(dev), torch.from_numpy(obs).to(dev),
+                     torch.from_numpy(poses.reshape(m, 12)).to(dev),
+                     torch.tensor(K, dtype=torch.float64, device=dev), 2.0, 1e-3, e)
+    P = omodel.Problem(10, 10, 1, K, np.zeros((1, 10, 10, 2), np.float32))
+    p = omodel.Params(fisk_beta=2.0, outlier_density=1e-3)
+    rs = dict(X=pts[:, :3].astype(np.float64), xobs=obs[:, :2].astype(np.float64),
+              w=pts[:, 3].astype(np.float64), alpha=obs[:, 2].astype(np.float64))
+    want = np.array([opose.score(P, G, rs, p) for G in poses])
+    assert np.allclose(e.cpu().numpy(), want, rtol=1e-4)
+
+
+# ------------------------------------------------------------------ bootstrap and whole EM
+def test_bootstrap_mono_parity(V):
+    win = window("boxes640_stereo", 2, size=(160, 120), N=3, noisy=False)
+    ctx, P, p = make_ctx(V, win, prior="none", n_hyp=16)
+    try:
+        V.vd_bootstrap(ctx)
+        So, _ = oem.bootstrap(P, p)
+        Gg = V.vd_get_poses(ctx, P.N)
+        for t in range(1, P.N + 1):
+            rot, trans = _pose_err(So.G[t], Gg[t])
+            assert rot < POSE_ROT_TOL and trans < POSE_TRANS_TOL, (t, rot, trans)
+        rho = _get(V, V.vd_get_inv_depth, ctx, (P.H, P.W))
+        rel = np.abs(rho - So.rho) / So.rho
+        assert np.mean(rel < 1e-4) > 0.99
+    finally:
+        V.vd_destroy(ctx)
+
+
+def test_whole_em_noise_free_parity(V):
+    win = window("planes160", 0, noisy=False)
+    ctx, P, p = make_ctx(V, win)
+    try:
+        st, stats = V.vd_run_em(ctx, 4)
+        So, _ = oem.run(P, p, 4)
+        rho = _get(V, V.vd_get_inv_depth, ctx, (P.H, P.W))
+        q = _get(V, V.vd_get_rigidness, ctx, (P.N, P.H, P.W))
+        Gg = V.vd_get_poses(ctx, P.N)
+        for t in range(1, P.N + 1):
+            rot, trans = _pose_err(So.G[t], Gg[t])
+            assert rot < POSE_ROT_TOL and trans < POSE_TRANS_TOL, (t, rot, trans)
+        rigid = So.q.min(0) > 0.5
+        rel = np.abs(rho - So.rho) / So.rho
+        assert np.mean(rel[rigid] <= 1e-4) > 0.999
+        assert np.mean(np.abs(q - So.q) <= RIGID_TOL) > 0.999
+        assert stats.iterations == 4 and stats.bootstrapped == 1
+    finally:
+        V.vd_destroy(ctx)
+
+
+def test_export_import_resume_is_exact(V):
+    win = window("planes160", 1)
+    ctx, P, p = make_ctx(V, win, n_hyp=16)
+    ctx2, _, _ = make_ctx(V, win, n_hyp=16)
+    try:
+        V.vd_run_em(ctx, 2)
+        blob = V.vd_export_state(ctx)
+        V.vd_run_em(ctx, 2)
+        V.vd_import_state(ctx2, blob)
+        V.vd_run_em(ctx2, 2)
+        a = _get(V, V.vd_get_inv_depth, ctx, (P.H, P.W))
+        b = _get(V, V.vd_get_inv_depth, ctx2, (P.H, P.W))
+        assert np.array_equal(a, b)
+        assert np.array_equal(V.vd_get_poses(ctx, P.N), V.vd_get_poses(ctx2, P.N))
+    finally:
+        V.vd_destroy(ctx)
+        V.vd_destroy(ctx2)
+
+
+def test_errors_and_state_machine(V):
+    win = window("planes160", 0)
+    params = V.vd_params_default()
+    ctx = V.vd_create(win.W, win.H, win.N, win.intrinsics, params)
+    try:
+        with pytest.raises(V.VoldorError) as e:
+            V.vd_run_em(ctx, 1)
+        assert e.value.status == V.VD_ERR_STATE
+        bad = win.flow[0].copy()
+        bad[3, 4, 0] = np.nan
+        with pytest.raises(V.VoldorError) as e:
+            V.vd_push_flow(ctx, 1, bad)
+        assert e.value.status == V.VD_ERR_ARG
+        with pytest.raises(V.VoldorError):
+            V.vd_push_flow(ctx, 4, win.flow[0])
+        with pytest.raises(V.VoldorError):
+            V.vd_push_depth_prior(ctx, np.ones((win.H, win.W), np.float32),
+                                  T_hat=np.eye(3, 4) * 2)
+    finally:
+        V.vd_destroy(ctx)
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_full_size_depth_step_sampled(V):
+    """1216 x 368, N = 6, K = 128 (the driving workload), in the launch
+    configuration the benchmark uses; oracle on a sample of pixels."""
+    win = window("driving1216", 0)
+    ctx, P, p = make_ctx(V, win)
+    try:
+        rng = np.random.default_rng(11)
+        S = noisy_state(win, P, rng, rel=0.02)
+        push_state(V, ctx, S)
+        it = 1
+        V.vd_depth_mstep(ctx, it, 0)
+        rs = np.zeros((P.H, P.W), np.float32)
+        es = np.zeros((P.H, P.W), np.float32)
+        V.vd_get_depth_candidates(ctx, rs, es)
+        idx = rng.choice(P.W * P.H, size=1500, replace=False)
+        iv, iu = np.divmod(idx, P.W)
+        # include the image corners and the last row / column
+        iu = np.concatenate([iu, [0, P.W - 1, 0, P.W - 1]])
+        iv = np.concatenate([iv, [0, 0, P.H - 1, P.H - 1]])
+        cands = odepth.hypotheses(P, S.rho[iv, iu], it, p, iu, iv)
+        g = rs[iv, iu]
+        assert np.all((cands == g[None]).any(0))
+        E = np.stack([omodel.energy(P, S, iu, iv, cands[k], p) for k in range(p.n_hyp)])
+        eo = E.min(0)
+        e_g = omodel.energy(P, S, iu, iv, g, p)
+        band = tie_band(P, eo)
+        assert np.all(e_g - eo <= band)
+        assert np.all(np.abs(es[iv, iu] - e_g) <= band)
+        assert np.mean(g == cands[np.argmin(E, 0), np.arange(len(iu))]) > 0.98
+    finally:
+        V.vd_destroy(ctx)
