@@ -6,8 +6,12 @@
 
 #include <math.h>
 
+#ifndef VD_HD
+#define VD_HD __host__ __device__
+#endif
+
 // ---------------------------------------------------------------- small algebra
-__device__ __forceinline__ void vd_compose(const double* A, const double* B, double* O) {
+VD_HD __forceinline__ void vd_compose(const double* A, const double* B, double* O) {
   // O = A o B (apply B first)
   for (int r = 0; r < 3; ++r) {
     for (int c = 0; c < 3; ++c)
@@ -16,7 +20,7 @@ __device__ __forceinline__ void vd_compose(const double* A, const double* B, dou
   }
 }
 
-__device__ __forceinline__ void vd_inverse(const double* T, double* O) {
+VD_HD __forceinline__ void vd_inverse(const double* T, double* O) {
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) O[4 * r + c] = T[4 * c + r];
   for (int r = 0; r < 3; ++r)
@@ -24,7 +28,7 @@ __device__ __forceinline__ void vd_inverse(const double* T, double* O) {
 }
 
 // Rodrigues: R = I + a [w]x + b [w]x^2 with a = sin(th)/th, b = (1-cos th)/th^2.
-__device__ __forceinline__ void vd_so3_coeffs(double th2, double* a, double* b, double* cc) {
+VD_HD __forceinline__ void vd_so3_coeffs(double th2, double* a, double* b, double* cc) {
   // cc = (th - sin th) / th^3 (for the left Jacobian V)
   if (th2 < 1e-12) {
     *a = 1.0 - th2 / 6.0;
@@ -39,7 +43,7 @@ __device__ __forceinline__ void vd_so3_coeffs(double th2, double* a, double* b, 
   }
 }
 
-__device__ __forceinline__ void vd_se3_exp(const double* xi, double* T) {
+VD_HD __forceinline__ void vd_se3_exp(const double* xi, double* T) {
   const double wx = xi[0], wy = xi[1], wz = xi[2];
   const double th2 = wx * wx + wy * wy + wz * wz;
   double a, b, cc;
@@ -60,7 +64,7 @@ __device__ __forceinline__ void vd_se3_exp(const double* xi, double* T) {
 }
 
 // so(3) logarithm (rotation vector) of a rotation given as the 3x3 part of T.
-__device__ __forceinline__ void vd_so3_log(const double* T, double* w) {
+VD_HD __forceinline__ void vd_so3_log(const double* T, double* w) {
   const double tr = T[0] + T[5] + T[10];
   const double c = 0.5 * (tr - 1.0);
   const double vx = 0.5 * (T[9] - T[6]), vy = 0.5 * (T[2] - T[8]), vz = 0.5 * (T[4] - T[1]);
@@ -97,7 +101,7 @@ __device__ __forceinline__ void vd_so3_log(const double* T, double* w) {
 
 // se(3) logarithm: w = log R, v = V(w)^-1 tau with the closed-form inverse
 // V^-1 = I - [w]x / 2 + (1/th^2) (1 - a / (2 b)) [w]x^2.
-__device__ __forceinline__ void vd_se3_log(const double* T, double* xi) {
+VD_HD __forceinline__ void vd_se3_log(const double* T, double* xi) {
   vd_so3_log(T, xi);
   const double wx = xi[0], wy = xi[1], wz = xi[2];
   const double th2 = wx * wx + wy * wy + wz * wz;
@@ -123,14 +127,14 @@ __device__ __forceinline__ void vd_se3_log(const double* T, double* xi) {
 
 // ---------------------------------------------------------------- polynomials
 // Value of sum_i c[i] x^i.
-__device__ __forceinline__ double vd_poly_eval(const double* c, int deg, double x) {
+VD_HD __forceinline__ double vd_poly_eval(const double* c, int deg, double x) {
   double r = c[deg];
   for (int i = deg - 1; i >= 0; --i) r = r * x + c[i];
   return r;
 }
 
 // Root of a polynomial known to change sign on [lo, hi]: safeguarded Newton.
-static __device__ double vd_poly_bracketed_root(const double* c, int deg, double lo, double hi) {
+static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, double hi) {
   double d[4];
   for (int i = 1; i <= deg; ++i) d[i - 1] = c[i] * i;
   double flo = vd_poly_eval(c, deg, lo);
@@ -154,9 +158,37 @@ static __device__ double vd_poly_bracketed_root(const double* c, int deg, double
   return x;
 }
 
-// All real roots of sum_{i<=deg} c[i] x^i (deg <= 4), ascending.  Real roots
-// are isolated between consecutive real roots of the derivative.
-static __device__ int vd_poly_real_roots(const double* cin, int deg, double* out) {
+// Real roots of a polynomial of exact degree `deg` (leading coefficient
+// non-zero) on the intervals cut by the sorted split points `crit` (the real
+// roots of its derivative): one root per interval with a sign change.
+// Writes at most ncrit + 1 roots.
+VD_HD __forceinline__ int vd_roots_between(const double* c, int deg, const double* crit,
+                                                int ncrit, double* out) {
+  double bound = 0.0;
+  for (int i = 0; i < deg; ++i) bound = fmax(bound, fabs(c[i] / c[deg]));
+  bound += 1.0;  // Cauchy bound on the magnitude of every root
+  double lo = -bound;
+  double flo = vd_poly_eval(c, deg, lo);
+  int n = 0;
+  for (int i = 0; i <= ncrit; ++i) {
+    double hi = i < ncrit ? fmin(fmax(crit[i], -bound), bound) : bound;
+    if (!(hi > lo)) continue;
+    const double fhi = vd_poly_eval(c, deg, hi);
+    if (flo == 0.0) {
+      out[n++] = lo;
+    } else if ((flo < 0.0) != (fhi < 0.0) && fhi != 0.0) {
+      out[n++] = vd_poly_bracketed_root(c, deg, lo, hi);
+    }
+    lo = hi;
+    flo = fhi;
+  }
+  return n;
+}
+
+// All real roots of sum_{i<=deg} c[i] x^i for deg <= 4, ascending.  Real
+// roots are isolated between consecutive real roots of the derivative; the
+// degrees are handled one by one without recursion (no dynamic stack).
+static VD_HD int vd_poly_real_roots(const double* cin, int deg, double* out) {
   double c[5];
   double mx = 0.0;
   for (int i = 0; i <= deg; ++i) {
@@ -170,37 +202,36 @@ static __device__ int vd_poly_real_roots(const double* cin, int deg, double* out
     out[0] = -c[0] / c[1];
     return 1;
   }
-  // Cauchy bound on the magnitude of the roots
-  double bound = 0.0;
-  for (int i = 0; i < deg; ++i) bound = fmax(bound, fabs(c[i] / c[deg]));
-  bound += 1.0;
-  double pts[6];
-  int np = 0;
-  pts[np++] = -bound;
-  if (deg == 2) {
-    pts[np++] = -c[1] / (2.0 * c[2]);
-  } else {
-    double d[4];
-    for (int i = 1; i <= deg; ++i) d[i - 1] = c[i] * i;
-    double crit[4];
-    const int nc = vd_poly_real_roots(d, deg - 1, crit);
-    for (int i = 0; i < nc; ++i)
-      if (crit[i] > -bound && crit[i] < bound) pts[np++] = crit[i];
-  }
-  pts[np++] = bound;
-  int n = 0;
-  for (int i = 0; i + 1 < np; ++i) {
-    const double a = pts[i], b = pts[i + 1];
-    if (!(b > a)) continue;
-    const double fa = vd_poly_eval(c, deg, a), fb = vd_poly_eval(c, deg, b);
-    if (fa == 0.0) {
-      if (n == 0 || out[n - 1] != a) out[n++] = a;
-      continue;
+  // quadratic: split at the vertex
+  double r2[2];
+  int n2;
+  {
+    const int dq = deg - 2;      // the (deg-2)-th derivative is a quadratic
+    double q[3];
+    // coefficients of the (deg-2)-th derivative of c
+    for (int i = 0; i <= 2; ++i) {
+      double f = 1.0;
+      for (int k = 1; k <= dq; ++k) f *= (double)(i + k);
+      q[i] = c[i + dq] * f;
     }
-    if ((fa < 0.0) != (fb < 0.0) && fb != 0.0) out[n++] = vd_poly_bracketed_root(c, deg, a, b);
-    else if (fb == 0.0 && i + 2 == np) out[n++] = b;
+    if (deg == 2) {
+      const double split = -q[1] / (2.0 * q[2]);
+      return vd_roots_between(q, 2, &split, 1, out);
+    }
+    const double split = -q[1] / (2.0 * q[2]);
+    n2 = vd_roots_between(q, 2, &split, 1, r2);
   }
-  return n;
+  // cubic (the derivative of c when deg == 4, else c itself)
+  double r3[3];
+  int n3;
+  {
+    const int dc = deg - 3;
+    double cc[4];
+    for (int i = 0; i <= 3; ++i) cc[i] = dc ? c[i + 1] * (double)(i + 1) : c[i];
+    if (deg == 3) return vd_roots_between(cc, 3, r2, n2, out);
+    n3 = vd_roots_between(cc, 3, r2, n2, r3);
+  }
+  return vd_roots_between(c, 4, r3, n3, out);
 }
 
 // ---------------------------------------------------------------- P3P
@@ -211,45 +242,70 @@ static __device__ int vd_poly_real_roots(const double* cin, int deg, double* out
 // Their resultant in u, (p2 q0 - p0 q2)^2 - (p2 q1 - p1 q2)(p1 q0 - p0 q1), is a
 // quartic in v; each real positive root gives the camera-frame triangle, and
 // the rigid motion follows from the two point triads.
-__device__ __forceinline__ void vd_pmul(const double* a, int da, const double* b, int db, double* o) {
+VD_HD __forceinline__ void vd_pmul(const double* a, int da, const double* b, int db, double* o) {
   for (int i = 0; i <= da + db; ++i) o[i] = 0.0;
   for (int i = 0; i <= da; ++i)
     for (int k = 0; k <= db; ++k) o[i + k] += a[i] * b[k];
 }
 
-__device__ __forceinline__ void vd_normalize3(double* v) {
+VD_HD __forceinline__ void vd_normalize3(double* v) {
   const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   v[0] /= n;
   v[1] /= n;
   v[2] /= n;
 }
 
-__device__ __forceinline__ void vd_cross3(const double* a, const double* b, double* o) {
+VD_HD __forceinline__ void vd_cross3(const double* a, const double* b, double* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Orthonormal frame of a triangle: e1 along p1->p2, e3 normal, e2 = e3 x e1.
-__device__ __forceinline__ void vd_triad(const double* p1, const double* p2, const double* p3,
-                                         double* F) {
-  double e1[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
-  double d[3] = {p3[0] - p1[0], p3[1] - p1[1], p3[2] - p1[2]};
-  double e3[3];
-  vd_cross3(e1, d, e3);
-  vd_normalize3(e1);
-  vd_normalize3(e3);
-  double e2[3];
-  vd_cross3(e3, e1, e2);
-  for (int i = 0; i < 3; ++i) {  // columns e1, e2, e3
-    F[3 * i + 0] = e1[i];
-    F[3 * i + 1] = e2[i];
-    F[3 * i + 2] = e3[i];
+template <int NN>
+static VD_HD void vd_jacobi_eig(double* A, double* w, double* V);
+
+// Least-squares rigid motion Q_i ~ R X_i + tau of three point pairs by Horn's
+// closed form with unit quaternions (J. Opt. Soc. Am. A 4, 1987): the rotation
+// is the eigenvector of the largest eigenvalue of the symmetric 4x4 matrix
+// built from the cross-covariance of the centred points.
+static VD_HD void vd_absolute_orientation(const double* X, const double* Q, double* T) {
+  double px[3] = {0, 0, 0}, qx[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) {
+      px[a] += X[3 * i + a] / 3.0;
+      qx[a] += Q[3 * i + a] / 3.0;
+    }
+  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // S_ab = sum (X - mx)_a (Q - mq)_b
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[3 * a + b] += (X[3 * i + a] - px[a]) * (Q[3 * i + b] - qx[b]);
+  const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5];
+  const double Szx = S[6], Szy = S[7], Szz = S[8];
+  double N[16] = {Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx,
+                  Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz,
+                  Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy,
+                  Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz};
+  double w[4], V[16];
+  vd_jacobi_eig<4>(N, w, V);
+  int k = 0;
+  for (int i = 1; i < 4; ++i)
+    if (w[i] > w[k]) k = i;
+  const double q0 = V[k], q1 = V[4 + k], q2 = V[8 + k], q3 = V[12 + k];
+  const double R[9] = {q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3),
+                       2 * (q1 * q3 + q0 * q2),
+                       2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3,
+                       2 * (q2 * q3 - q0 * q1),
+                       2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1),
+                       q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3};
+  const double nq = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+  for (int i = 0; i < 3; ++i) {
+    for (int a = 0; a < 3; ++a) T[4 * i + a] = R[3 * i + a] / nq;
+    T[4 * i + 3] = qx[i] - (T[4 * i] * px[0] + T[4 * i + 1] * px[1] + T[4 * i + 2] * px[2]);
   }
 }
 
 // bearings f[3][3] (any length), world points X[3][3]; writes up to 4 poses.
-static __device__ int vd_p3p(const double* fin, const double* X, double* poses) {
+static VD_HD int vd_p3p(const double* fin, const double* X, double* poses) {
   double f[9];
   for (int i = 0; i < 9; ++i) f[i] = fin[i];
   vd_normalize3(f);
@@ -302,15 +358,7 @@ static __device__ int vd_p3p(const double* fin, const double* X, double* poses) 
     const double Q[9] = {s1 * f[0], s1 * f[1], s1 * f[2],
                          u * s1 * f[3], u * s1 * f[4], u * s1 * f[5],
                          v * s1 * f[6], v * s1 * f[7], v * s1 * f[8]};
-    double Fp[9], Fq[9];
-    vd_triad(X, X + 3, X + 6, Fp);
-    vd_triad(Q, Q + 3, Q + 6, Fq);
-    double* T = poses + 12 * ns;
-    for (int i = 0; i < 3; ++i)
-      for (int k = 0; k < 3; ++k)
-        T[4 * i + k] = Fq[3 * i] * Fp[3 * k] + Fq[3 * i + 1] * Fp[3 * k + 1] + Fq[3 * i + 2] * Fp[3 * k + 2];
-    for (int i = 0; i < 3; ++i)
-      T[4 * i + 3] = Q[i] - (T[4 * i] * X[0] + T[4 * i + 1] * X[1] + T[4 * i + 2] * X[2]);
+    vd_absolute_orientation(X, Q, poses + 12 * ns);
     ++ns;
   }
   return ns;
@@ -320,7 +368,7 @@ static __device__ int vd_p3p(const double* fin, const double* X, double* poses) 
 // Cyclic Jacobi on a symmetric n x n matrix A (row-major, destroyed); writes
 // eigenvalues to w and eigenvectors to the columns of V.
 template <int NN>
-static __device__ void vd_jacobi_eig(double* A, double* w, double* V) {
+static VD_HD void vd_jacobi_eig(double* A, double* w, double* V) {
   for (int i = 0; i < NN * NN; ++i) V[i] = (i % (NN + 1) == 0) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0.0, tot = 0.0;

@@ -1,0 +1,127 @@
+"""The library's float64 device geometry, compiled for the host, against the
+oracle and against closed forms (no GPU needed)."""
+import ctypes as C
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import geometry, p3p
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hc():
+    from paper_2104_06800_gb300.build import nvcc_path
+    out = os.path.join(tempfile.mkdtemp(), "libvd_hostcheck.so")
+    src = os.path.join(ROOT, "tests", "native", "vd_hostcheck.cu")
+    cmd = [nvcc_path(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", os.path.join(ROOT, "paper_2104_06800_gb300", "csrc"), src, "-o", out]
+    subprocess.run(cmd, check=True, capture_output=True)
+    lib = C.CDLL(out)
+    P = C.POINTER(C.c_double)
+    lib.hc_p3p.argtypes = [P, P, P]
+    lib.hc_real_roots.argtypes = [P, C.c_int, P]
+    for n in ("hc_se3_exp", "hc_se3_log"):
+        getattr(lib, n).argtypes = [P, P]
+    for n in ("hc_jacobi9", "hc_jacobi3"):
+        getattr(lib, n).argtypes = [P, P, P]
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def test_real_roots_of_products_and_random_polynomials(hc):
+    rng = np.random.default_rng(0)
+    out = np.zeros(4)
+    for _ in range(300):
+        r = np.sort(rng.uniform(-5, 5, size=4))
+        c = np.polynomial.polynomial.polyfromroots(r) * rng.uniform(0.1, 10)
+        n = hc.hc_real_roots(_p(c), 4, _p(out))
+        assert n == 4 and np.allclose(out[:n], r, atol=1e-9)
+    for _ in range(300):
+        c = rng.normal(size=5)
+        n = hc.hc_real_roots(_p(c), 4, _p(out))
+        ref = np.roots(c[::-1])
+        real = np.sort(ref[np.abs(ref.imag) < 1e-9].real)
+        assert n == len(real) and np.allclose(out[:n], real, atol=1e-8)
+    # degenerate leading coefficients fall back to lower degrees
+    c = np.array([-6.0, 11.0, -6.0, 1.0, 0.0])
+    assert hc.hc_real_roots(_p(c), 4, _p(out)) == 3 and np.allclose(out[:3], [1, 2, 3])
+    c = np.array([2.0, 0.0, 1.0, 0.0, 0.0])      # no real root
+    assert hc.hc_real_roots(_p(c), 4, _p(out)) == 0
+
+
+def _reproj(G, X, f):
+    Y = X @ G[:, :3].T + G[:, 3]
+    return np.abs(Y / np.linalg.norm(Y, axis=1, keepdims=True)
+                  - f / np.linalg.norm(f, axis=1, keepdims=True)).max()
+
+
+def test_p3p_matches_oracle_and_is_exact(hc):
+    rng = np.random.default_rng(11)
+    errs = []
+    illcond = 0
+    poses = np.zeros(48)
+    for _ in range(300):
+        R = geometry.so3_exp(rng.normal(size=3) * 0.5)
+        X = rng.normal(size=(3, 3))
+        tau = rng.normal(size=3)
+        tau[2] += 5 - (X @ R.T + tau)[:, 2].min()
+        Xc = X @ R.T + tau
+        f = np.ascontiguousarray(Xc / Xc[:, 2:3])      # bearings as (x, y, 1)
+        n = hc.hc_p3p(_p(f), _p(np.ascontiguousarray(X)), _p(poses))
+        got = [poses[12 * k:12 * k + 12].reshape(3, 4) for k in range(n)]
+        ref = p3p.solve(f, X)
+        assert 1 <= n <= 4
+        G = np.concatenate([R, tau[:, None]], 1)
+        errs.append(min(np.abs(g - G).max() for g in got))
+        # the same solution set as the oracle (up to order); on an
+        # ill-conditioned quartic (clustered roots) the two roundings may
+        # differ, then both must still reproject the three bearings
+        if len(ref) == n:
+            for r in ref:
+                g = min(got, key=lambda g: np.abs(g - r).max())
+                if np.abs(g - r).max() >= 1e-6:
+                    illcond += 1
+                    assert _reproj(g, X, f) < 1e-6 and _reproj(r, X, f) < 1e-6
+        else:
+            illcond += 1
+    errs = np.array(errs)
+    assert illcond <= 3
+    assert np.percentile(errs, 90) < 1e-9 and errs.max() < 1e-5
+
+
+def test_se3_maps_match_oracle(hc):
+    rng = np.random.default_rng(5)
+    T = np.zeros(12)
+    xi2 = np.zeros(6)
+    for _ in range(200):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        xi = np.concatenate([ax * rng.choice([1e-9, 1e-4, 0.3, 3.0]), rng.normal(size=3)])
+        hc.hc_se3_exp(_p(xi), _p(T))
+        assert np.allclose(T.reshape(3, 4), geometry.se3_exp(xi), atol=1e-13)
+        hc.hc_se3_log(_p(T), _p(xi2))
+        assert np.allclose(xi2, xi, atol=1e-9)
+
+
+def test_jacobi_eigen_matches_numpy(hc):
+    rng = np.random.default_rng(2)
+    for n, fn in ((9, hc.hc_jacobi9), (3, hc.hc_jacobi3)):
+        for _ in range(50):
+            B = rng.normal(size=(n, n))
+            A = B @ B.T
+            w = np.zeros(n)
+            V = np.zeros(n * n)
+            a = np.ascontiguousarray(A.copy().ravel())
+            fn(_p(a), _p(w), _p(V))
+            V = V.reshape(n, n)
+            assert np.allclose(np.sort(w), np.linalg.eigvalsh(A), rtol=1e-10, atol=1e-10)
+            assert np.allclose(A @ V, V * w, atol=1e-9)
