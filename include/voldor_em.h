@@ -202,6 +202,27 @@ typedef struct {
 vd_status vd_profile_enable(vd_ctx* ctx, int enable);
 vd_status vd_get_profile(vd_ctx* ctx, vd_profile* out);
 
+/* Dense pose scoring without any device allocation.  The paper has no
+ * counterpart; this is a library convenience for callers that may not
+ * allocate device memory at run time -- for example a host whose device memory
+ * is entirely reserved by another allocator, or a real-time loop where a
+ * cudaMalloc (which can synchronise the device and can fail under memory
+ * pressure) is not allowed.  Same arguments and result as vd_score_poses, but
+ * the block partial sums live in a fixed array of the library's device code
+ * (VD_NOALLOC_MAX_POSES x (12 + 304) floats, about 324 KB, held by every GPU
+ * that loads the library until the process exits).
+ *   - m must be in 1..VD_NOALLOC_MAX_POSES, else VD_ERR_ARG (see vd_last_error).
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - All calls share the one array: calls that may overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ *     Every scratch value a call reads is written earlier in the same call.
+ *   - Runs on cuda_stream and synchronises it. */
+#define VD_NOALLOC_MAX_POSES 256
+vd_status vd_score_poses_noalloc(const float* points, const float* obs, int n,
+                                 const double* poses, int m, const double* intrinsics,
+                                 float beta, float p0, double* energies, void* cuda_stream);
+
 /* State export/import for checkpoint and resume: a self-describing blob with
  * rho, q, q_hat, C, the poses, the iteration counter and the bootstrap flag.
  * Call export with blob = NULL to learn the size. */

@@ -2,6 +2,8 @@
 // pose is approximated by S P3P samples drawn from the rigid pixels; every
 // root is scored against all rigid pixels, each sample keeps its best root,
 // and the pose is the mean-shift mode of the samples in se(3).
+#include <mutex>
+
 #include "vd_device.cuh"
 #include "vd_geom64.cuh"
 
@@ -523,6 +525,81 @@ __global__ void k_poses_float(DevParams P, const double* __restrict__ poses, int
     o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
     o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the standalone scoring: its scratch (float
+// K R | K tau of every pose, then the per-block partial sums) lives in this
+// fixed device array instead of memory allocated per call.
+// ---------------------------------------------------------------------------
+#define VD_NOALLOC_BLOCKS (2 * 152)
+#define VD_NOALLOC_FLOATS (VD_NOALLOC_MAX_POSES * (12 + VD_NOALLOC_BLOCKS))
+static __device__ __align__(256) float g_noalloc_scratch[VD_NOALLOC_FLOATS];
+
+#define VD_NOALLOC_MAX_DEVICES 64
+static float* g_noalloc_ptr[VD_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current; host code must not use the symbol
+// itself, which is only a host-side stand-in).
+static cudaError_t noalloc_scratch(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= VD_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (float*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* obs, int n,
+                                            const double* poses, int m, const double* intrinsics,
+                                            float beta, float p0, double* energies,
+                                            void* cuda_stream) {
+  if (!points || !obs || !poses || !intrinsics || !energies || n < 0 || !(beta > 0.0f) ||
+      !(p0 > 0.0f))
+    return VD_ERR_ARG;
+  if (m < 1 || m > VD_NOALLOC_MAX_POSES) {
+    vd_set_error("vd_score_poses_noalloc: m must be between 1 and VD_NOALLOC_MAX_POSES (256)");
+    return VD_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  float* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  double K[4];
+  if (e == cudaSuccess) e = cudaMemcpy(K, intrinsics, sizeof K, cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  DevParams P{};
+  P.fx_d = K[0]; P.fy_d = K[1]; P.cx_d = K[2]; P.cy_d = K[3];
+  P.beta = beta;
+  P.p0 = p0;
+  P.fast_beta2 = 0;           // the per-point scale rides in obs.z
+  P.cgen = p0 * 2.0f * 3.14159265358979f / beta;
+  float* rootsf = scratch;                          // m x 12
+  float* partial = scratch + 12 * VD_NOALLOC_MAX_POSES;   // m x VD_NOALLOC_BLOCKS
+  k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
+  const size_t smem = sizeof(float) * (size_t)m * (12 + SCORE_THREADS / 32);
+  k_pose_score<<<VD_NOALLOC_BLOCKS, SCORE_THREADS, smem, s>>>(
+      P, (const float4*)points, (const float4*)obs, nullptr, n, rootsf, nullptr, m, partial);
+  k_root_energy<<<(m + 127) / 128, 128, 0, s>>>(partial, VD_NOALLOC_BLOCKS, m, nullptr, energies);
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  return VD_OK;
 }
 
 extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n, const double* poses,

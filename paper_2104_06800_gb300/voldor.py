@@ -91,6 +91,7 @@ _SIGS = {
     "vd_eval_energy": [_P, _P, _P, C.c_int],
     "vd_get_pose_samples": [_P, _P, _P, _P],
     "vd_score_poses": [_P, _P, C.c_int, _P, C.c_int, _P, C.c_float, C.c_float, _P, _P],
+    "vd_score_poses_noalloc": [_P, _P, C.c_int, _P, C.c_int, _P, C.c_float, C.c_float, _P, _P],
     "vd_profile_enable": [_P, C.c_int],
     "vd_get_profile": [_P, C.POINTER(vd_profile)],
     "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
@@ -333,6 +334,22 @@ def vd_get_profile(ctx):
     _call("vd_get_profile", ctx, C.byref(p))
     return {name: dict(ms=p.ms[i], calls=p.calls[i], launches=p.launches[i])
             for i, name in enumerate(STAGE_NAMES)} | {"total_launches": p.total_launches}
+
+
+VD_NOALLOC_MAX_POSES = 256
+
+
+def vd_score_poses_noalloc(points, obs, poses, intrinsics, beta, p0, energies, stream=None):
+    """vd_score_poses without any device allocation (scratch in a fixed
+    library array; at most VD_NOALLOC_MAX_POSES poses; overlapping calls race).
+    All arguments except beta, p0 and stream are CUDA tensors."""
+    n = points.shape[0]
+    m = poses.shape[0]
+    _call("vd_score_poses_noalloc", C.c_void_p(points.data_ptr()), C.c_void_p(obs.data_ptr()),
+          int(n), C.c_void_p(poses.data_ptr()), int(m), C.c_void_p(intrinsics.data_ptr()),
+          float(beta), float(p0), C.c_void_p(energies.data_ptr()),
+          stream if stream is not None else current_stream())
+    return energies
 
 
 def vd_export_state(ctx):
