@@ -102,9 +102,12 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
 }
 
 // Sum the partials (fixed order) and take the eigenvector of the smallest
-// eigenvalue as E (unit Frobenius norm).
+// eigenvalue as E (unit Frobenius norm), by inverse iteration on the
+// symmetric positive semi-definite M shifted by 1e-14 trace(M): Cholesky once,
+// then x <- (M + d I)^-1 x / |.| until the iterate stops moving.  `warm`
+// starts from the previous round's E, else from (1, ..., 1) / 3.
 __global__ void k_ep_solve(const double* __restrict__ partial, int nblk, double* __restrict__ Mout,
-                           double* __restrict__ Eout) {
+                           double* __restrict__ Eio, int warm) {
   __shared__ double sM[45];
   if (threadIdx.x < 45) {
     double s = 0.0;
@@ -114,22 +117,70 @@ __global__ void k_ep_solve(const double* __restrict__ partial, int nblk, double*
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double A[81], w[9], V[81];
+  double A[81];
   int k = 0;
+  double tr = 0.0;
   for (int p = 0; p < 9; ++p)
     for (int q = p; q < 9; ++q) {
       A[9 * p + q] = sM[k];
       A[9 * q + p] = sM[k];
+      if (p == q) tr += sM[k];
       ++k;
     }
-  vd_jacobi_eig<9>(A, w, V);
-  int mi = 0;
-  for (int i = 1; i < 9; ++i)
-    if (w[i] < w[mi]) mi = i;
-  double n = 0.0;
-  for (int i = 0; i < 9; ++i) n += V[9 * i + mi] * V[9 * i + mi];
-  n = sqrt(n);
-  for (int i = 0; i < 9; ++i) Eout[i] = V[9 * i + mi] / n;
+  const double shift = 1e-14 * tr + 1e-300;
+  for (int i = 0; i < 9; ++i) A[10 * i] += shift;
+  // Cholesky A = L L^T (lower triangle of A overwritten by L)
+  for (int j = 0; j < 9; ++j) {
+    double d = A[10 * j];
+    for (int m = 0; m < j; ++m) d -= A[9 * j + m] * A[9 * j + m];
+    d = sqrt(fmax(d, shift));
+    A[10 * j] = d;
+    for (int i = j + 1; i < 9; ++i) {
+      double s = A[9 * i + j];
+      for (int m = 0; m < j; ++m) s -= A[9 * i + m] * A[9 * j + m];
+      A[9 * i + j] = s / d;
+    }
+  }
+  double x[9];
+  double nx = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    x[i] = warm ? Eio[i] : 1.0 / 3.0;
+    nx += x[i] * x[i];
+  }
+  if (!(nx > 0.0) || !isfinite(nx)) {
+    for (int i = 0; i < 9; ++i) x[i] = 1.0 / 3.0;
+    nx = 1.0;
+  }
+  nx = sqrt(nx);
+  for (int i = 0; i < 9; ++i) x[i] /= nx;
+  for (int it = 0; it < 300; ++it) {
+    double y[9];
+    for (int i = 0; i < 9; ++i) {          // L y = x
+      double s = x[i];
+      for (int m = 0; m < i; ++m) s -= A[9 * i + m] * y[m];
+      y[i] = s / A[10 * i];
+    }
+    for (int i = 8; i >= 0; --i) {         // L^T z = y
+      double s = y[i];
+      for (int m = i + 1; m < 9; ++m) s -= A[9 * m + i] * y[m];
+      y[i] = s / A[10 * i];
+    }
+    double n = 0.0, dot = 0.0;
+    for (int i = 0; i < 9; ++i) n += y[i] * y[i];
+    n = sqrt(n);
+    for (int i = 0; i < 9; ++i) {
+      y[i] /= n;
+      dot += y[i] * x[i];
+    }
+    double diff = 0.0;
+    const double sg = dot < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < 9; ++i) {
+      diff = fmax(diff, fabs(sg * y[i] - x[i]));
+      x[i] = sg * y[i];
+    }
+    if (diff < 1e-15) break;
+  }
+  for (int i = 0; i < 9; ++i) Eio[i] = x[i];
 }
 
 // E = U diag(s) V^T with det U = det V = +1: the two rotations U W V^T and
@@ -265,7 +316,7 @@ cudaError_t launch_eight_point(vd_ctx* c) {
   for (int r = 0; r < VD_IRLS_ITERS; ++r) {
     k_ep_normal<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_E, r > 0 ? 1 : 0,
                                                             c->ep_partial);
-    k_ep_solve<<<1, 64, 0, c->stream>>>(c->ep_partial, c->ep_blocks, c->ep_M, c->ep_E);
+    k_ep_solve<<<1, 64, 0, c->stream>>>(c->ep_partial, c->ep_blocks, c->ep_M, c->ep_E, r > 0);
   }
   k_ep_decompose<<<1, 32, 0, c->stream>>>(c->ep_E, c->ep_cand, c->ep_count);
   k_ep_cheirality<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_cand,

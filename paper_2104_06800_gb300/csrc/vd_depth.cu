@@ -105,42 +105,109 @@ k_depth_sample(DevParams P, const float* __restrict__ posef, const float2* __res
 }
 
 // ---------------------------------------------------------------------------
-// K2: sequential propagation, one thread per chain.  rho_new = rho* unless
-// the predecessor's new value has strictly lower energy.  `restart` > 0 starts
-// afresh every `restart` pixels (local windows of the hierarchical scheme).
+// K2: propagation along the chains.  Walking a chain in its direction,
+// rho_new = rho* unless the predecessor's new value has strictly lower
+// energy; `restart` > 0 starts afresh every `restart` pixels (local windows
+// of the hierarchical scheme).
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// K2, warp version: one warp per chain, lane i owns the contiguous segment
+// [i*seg, (i+1)*seg) of the chain.  Phase A: every lane walks its segment as
+// if its first pixel started the chain.  Correction rounds: a lane whose
+// incoming value (the predecessor lane's end value) changed walks again from
+// its segment start with that value and stops as soon as the carried value
+// equals what it wrote at that pixel before (the rest of the walk depends on
+// the carried value only, so it is unchanged).  The rounds end when no end
+// value changes, so the result is exactly the sequential walk.
 // ---------------------------------------------------------------------------
 template <int NF>
-__global__ void k_propagate(DevParams P, const float* __restrict__ posef,
-                            const float2* __restrict__ flow, const float* __restrict__ q,
-                            const float* __restrict__ prior_val, const float* __restrict__ qhat,
-                            const float* __restrict__ pconf, const float* __restrict__ rho_star,
-                            const float* __restrict__ e_star, float* __restrict__ rho_new,
-                            int direction, int restart) {
+__device__ __forceinline__ float vd_prop_step(const DevParams& P, const float* sPose,
+                                              const float2* __restrict__ flow,
+                                              const float* __restrict__ q,
+                                              const float* __restrict__ prior_val,
+                                              const float* __restrict__ qhat,
+                                              const float* __restrict__ pconf, float cur, float own,
+                                              float e_own, int u, int v, size_t j) {
+  const size_t npix = (size_t)P.W * P.H;
+  VdPixel<NF> px;
+  vd_pixel_setup<NF>(px, P, sPose, u, v, q, npix, j, flow, prior_val, qhat, pconf);
+  const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur);
+  return (Ec < e_own) ? cur : own;
+}
+
+template <int NF>
+__global__ void __launch_bounds__(128)
+k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __restrict__ flow,
+                 const float* __restrict__ q, const float* __restrict__ prior_val,
+                 const float* __restrict__ qhat, const float* __restrict__ pconf,
+                 const float* __restrict__ rho_star, const float* __restrict__ e_star,
+                 float* __restrict__ rho_new, int direction, int restart) {
   __shared__ float sPose[12 * (VD_MAX_FLOWS + 1)];
   vd_load_pose_smem<NF>(sPose, posef);
   const bool rows = (direction & 1) == 0;
   const bool rev = direction >= 2;
   const int nchains = rows ? P.H : P.W;
   const int L = rows ? P.W : P.H;
-  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ch >= nchains) return;
-  const size_t npix = (size_t)P.W * P.H;
-  float cur = 0.0f;
-  for (int m = 0; m < L; ++m) {
+  const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (ch >= nchains) return;          // whole warps leave together
+  const int seg = (L + 31) >> 5;
+  const int m0 = min(L, lane * seg), m1 = min(L, m0 + seg);
+  auto pix = [&](int m, int* u, int* v) -> size_t {
     const int pos = rev ? L - 1 - m : m;
-    const int u = rows ? pos : ch;
-    const int v = rows ? ch : pos;
-    const size_t j = (size_t)v * P.W + u;
+    *u = rows ? pos : ch;
+    *v = rows ? ch : pos;
+    return (size_t)(*v) * P.W + (*u);
+  };
+  // phase A
+  float cur = 0.0f;
+  for (int m = m0; m < m1; ++m) {
+    int u, v;
+    const size_t j = pix(m, &u, &v);
     const float own = rho_star[j];
-    if (m == 0 || (restart > 0 && m % restart == 0)) {
+    if (m == m0 || (restart > 0 && m % restart == 0)) {
       cur = own;
     } else {
-      VdPixel<NF> px;
-      vd_pixel_setup<NF>(px, P, sPose, u, v, q, npix, j, flow, prior_val, qhat, pconf);
-      const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur);
-      if (!(Ec < e_star[j])) cur = own;
+      cur = vd_prop_step<NF>(P, sPose, flow, q, prior_val, qhat, pconf, cur, own, e_star[j], u, v, j);
     }
     rho_new[j] = cur;
+  }
+  float end = cur;                     // value carried out of the segment
+  bool have_in = false;                // phase A assumed no incoming value
+  float last_in = 0.0f;
+  for (int round = 0; round < 32; ++round) {
+    float in = __shfl_up_sync(0xffffffffu, end, 1);
+    const bool has_pred = lane > 0 && m1 > m0 && m0 > 0;
+    bool walk = has_pred && (!have_in || in != last_in);
+    if (walk && restart > 0 && m0 % restart == 0) walk = false;   // forced fresh start
+    bool changed = false;
+    if (walk) {
+      have_in = true;
+      last_in = in;
+      float c = in;
+      bool merged = false;
+      for (int m = m0; m < m1; ++m) {
+        int u, v;
+        const size_t j = pix(m, &u, &v);
+        const float own = rho_star[j];
+        float nc;
+        if (restart > 0 && m % restart == 0)
+          nc = own;
+        else
+          nc = vd_prop_step<NF>(P, sPose, flow, q, prior_val, qhat, pconf, c, own, e_star[j], u, v, j);
+        if (nc == rho_new[j]) {
+          merged = true;
+          break;
+        }
+        rho_new[j] = nc;
+        c = nc;
+      }
+      if (!merged && c != end) {
+        end = c;
+        changed = true;
+      }
+    }
+    if (!__any_sync(0xffffffffu, changed)) break;
   }
 }
 
@@ -249,7 +316,7 @@ cudaError_t launch_depth_propagate(vd_ctx* c, int direction) {
   const bool rows = (direction & 1) == 0;
   if (!c->prm.hierarchical) {
     const int nch = rows ? c->H : c->W;
-    VD_DISPATCH_NF(c->N, (k_propagate<NF><<<(nch + 63) / 64, 64, 0, c->stream>>>(
+    VD_DISPATCH_NF(c->N, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                               c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                               c->rho_star, c->e_star, c->rho, direction, 0)));
     return cudaGetLastError();
@@ -270,7 +337,7 @@ cudaError_t launch_depth_propagate(vd_ctx* c, int direction) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nch = rows ? c->H : c->W;
-  VD_DISPATCH_NF(c->N, (k_propagate<NF><<<(nch + 63) / 64, 64, 0, c->stream>>>(
+  VD_DISPATCH_NF(c->N, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                             c->rho_mid, c->e_mid, c->rho, direction, c->prm.hier_window)));
   return cudaGetLastError();

@@ -77,7 +77,17 @@ __device__ __forceinline__ float vd_ratio_y(const DevParams& P, float r2, float 
   return vd_ratio_general(P, r2, fmaf(P.alpha1, sqrtf(fmag2), P.alpha0));
 }
 
-__device__ __forceinline__ float vd_ell2(float y) { return __log2f(1.0f + y); }
+// log2(1 + y).  Near the optimum y = P0 pi alpha^2 (1 + s^2)^2 is ~1e-3 and
+// the MUFU log2 of 1 + y (absolute error ~2^-22) would lose most digits of
+// the residual-dependent part, so small y uses the series
+// ln(1 + y) = y - y^2/2 + y^3/3 - y^4/4 + y^5/5 (truncation < y^6/6).
+__device__ __forceinline__ float vd_ell2(float y) {
+  const float big = __log2f(1.0f + y);
+  const float ser =
+      y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.2f, -0.25f), 0.33333334f), -0.5f), 1.0f) *
+      1.44269504f;
+  return y < 0.03125f ? ser : big;
+}
 
 // ---------------------------------------------------------------------------
 // Bilinear sample of one flow field at (x, y), which must be inside the image.

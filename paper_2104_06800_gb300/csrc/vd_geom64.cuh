@@ -164,9 +164,17 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
 // Writes at most ncrit + 1 roots.
 VD_HD __forceinline__ int vd_roots_between(const double* c, int deg, const double* crit,
                                                 int ncrit, double* out) {
+  // Fujiwara's bound on the magnitude of every root:
+  // 2 max(|c_{n-1}/c_n|, |c_{n-2}/c_n|^(1/2), ..., |c_0/(2 c_n)|^(1/n))
   double bound = 0.0;
-  for (int i = 0; i < deg; ++i) bound = fmax(bound, fabs(c[i] / c[deg]));
-  bound += 1.0;  // Cauchy bound on the magnitude of every root
+  for (int i = 0; i < deg; ++i) {
+    double r = fabs(c[i] / c[deg]);
+    if (i == 0) r *= 0.5;
+    const int k = deg - i;
+    const double root = k == 1 ? r : (k == 2 ? sqrt(r) : (k == 3 ? cbrt(r) : sqrt(sqrt(r))));
+    bound = fmax(bound, root);
+  }
+  bound = 2.0 * bound * (1.0 + 1e-12) + 1e-300;
   double lo = -bound;
   double flo = vd_poly_eval(c, deg, lo);
   int n = 0;
@@ -261,65 +269,76 @@ VD_HD __forceinline__ void vd_cross3(const double* a, const double* b, double* o
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-template <int NN>
-static VD_HD void vd_jacobi_eig(double* A, double* w, double* V);
-
-// Least-squares rigid motion Q_i ~ R X_i + tau of three point pairs by Horn's
-// closed form with unit quaternions (J. Opt. Soc. Am. A 4, 1987): the rotation
-// is the eigenvector of the largest eigenvalue of the symmetric 4x4 matrix
-// built from the cross-covariance of the centred points.
-static VD_HD void vd_absolute_orientation(const double* X, const double* Q, double* T) {
-  double px[3] = {0, 0, 0}, qx[3] = {0, 0, 0};
-  for (int i = 0; i < 3; ++i)
-    for (int a = 0; a < 3; ++a) {
-      px[a] += X[3 * i + a] / 3.0;
-      qx[a] += Q[3 * i + a] / 3.0;
-    }
-  double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // S_ab = sum (X - mx)_a (Q - mq)_b
-  for (int i = 0; i < 3; ++i)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) S[3 * a + b] += (X[3 * i + a] - px[a]) * (Q[3 * i + b] - qx[b]);
-  const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5];
-  const double Szx = S[6], Szy = S[7], Szz = S[8];
-  double N[16] = {Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx,
-                  Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz,
-                  Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy,
-                  Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz};
-  double w[4], V[16];
-  vd_jacobi_eig<4>(N, w, V);
-  int k = 0;
-  for (int i = 1; i < 4; ++i)
-    if (w[i] > w[k]) k = i;
-  const double q0 = V[k], q1 = V[4 + k], q2 = V[8 + k], q3 = V[12 + k];
-  const double R[9] = {q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3),
-                       2 * (q1 * q3 + q0 * q2),
-                       2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3,
-                       2 * (q2 * q3 - q0 * q1),
-                       2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1),
-                       q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3};
-  const double nq = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
-  for (int i = 0; i < 3; ++i) {
-    for (int a = 0; a < 3; ++a) T[4 * i + a] = R[3 * i + a] / nq;
-    T[4 * i + 3] = qx[i] - (T[4 * i] * px[0] + T[4 * i + 1] * px[1] + T[4 * i + 2] * px[2]);
+// Orthonormal frame of a triangle: e1 along p1->p2, e3 its normal, e2 = e3 x e1.
+VD_HD __forceinline__ void vd_triad(const double* p1, const double* p2, const double* p3,
+                                    double* F) {
+  double e1[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+  double d[3] = {p3[0] - p1[0], p3[1] - p1[1], p3[2] - p1[2]};
+  double e3[3];
+  vd_cross3(e1, d, e3);
+  vd_normalize3(e1);
+  vd_normalize3(e3);
+  double e2[3];
+  vd_cross3(e3, e1, e2);
+  for (int i = 0; i < 3; ++i) {  // columns e1, e2, e3
+    F[3 * i + 0] = e1[i];
+    F[3 * i + 1] = e2[i];
+    F[3 * i + 2] = e3[i];
   }
 }
 
-// bearings f[3][3] (any length), world points X[3][3]; writes up to 4 poses.
-static VD_HD int vd_p3p(const double* fin, const double* X, double* poses) {
+// Rigid motion mapping the triangle X onto the congruent triangle Q
+// (Q_i = R X_i + tau): R = F_Q F_X^T from the two triangles' frames.
+VD_HD __forceinline__ void vd_triangle_motion(const double* X, const double* Q, double* T) {
+  double Fp[9], Fq[9];
+  vd_triad(X, X + 3, X + 6, Fp);
+  vd_triad(Q, Q + 3, Q + 6, Fq);
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k)
+      T[4 * i + k] = Fq[3 * i] * Fp[3 * k] + Fq[3 * i + 1] * Fp[3 * k + 1] + Fq[3 * i + 2] * Fp[3 * k + 2];
+  for (int i = 0; i < 3; ++i)
+    T[4 * i + 3] = Q[i] - (T[4 * i] * X[0] + T[4 * i + 1] * X[1] + T[4 * i + 2] * X[2]);
+}
+
+// One P3P instance: unit bearings, squared side lengths (a: X1X2, b: X0X2,
+// c: X0X1) and the cosines of the angles between the bearings.
+struct VdP3P {
   double f[9];
-  for (int i = 0; i < 9; ++i) f[i] = fin[i];
-  vd_normalize3(f);
-  vd_normalize3(f + 3);
-  vd_normalize3(f + 6);
+  double a2, b2, c2, ca, cb, cg;
+};
+
+// Quartic of the instance (coefficients res[0..4], low order first); -1 for a
+// degenerate triangle, else 0.  bearings f[3][3] (any length), points X[3][3].
+static VD_HD int vd_p3p_quartic(const double* fin, const double* X, VdP3P* g, double* res);
+
+// The quartic's real roots (<= 4, ascending); -1 for a degenerate triangle.
+static VD_HD int vd_p3p_roots(const double* fin, const double* X, VdP3P* g, double* v) {
+  double res[5];
+  if (vd_p3p_quartic(fin, X, g, res) < 0) return -1;
+  return vd_poly_real_roots(res, 4, v);
+}
+
+static VD_HD int vd_p3p_quartic(const double* fin, const double* X, VdP3P* g, double* res) {
+  for (int i = 0; i < 9; ++i) g->f[i] = fin[i];
+  vd_normalize3(g->f);
+  vd_normalize3(g->f + 3);
+  vd_normalize3(g->f + 6);
+  const double* f = g->f;
   auto d2 = [&](int i, int k) {
     const double a = X[3 * i] - X[3 * k], b = X[3 * i + 1] - X[3 * k + 1], c = X[3 * i + 2] - X[3 * k + 2];
     return a * a + b * b + c * c;
   };
   const double a2 = d2(1, 2), b2 = d2(0, 2), c2 = d2(0, 1);
-  if (!(a2 > 0.0 && b2 > 0.0 && c2 > 0.0)) return 0;
+  g->a2 = a2;
+  g->b2 = b2;
+  g->c2 = c2;
+  if (!(a2 > 0.0 && b2 > 0.0 && c2 > 0.0)) return -1;
   const double ca = f[3] * f[6] + f[4] * f[7] + f[5] * f[8];
   const double cb = f[0] * f[6] + f[1] * f[7] + f[2] * f[8];
   const double cg = f[0] * f[3] + f[1] * f[4] + f[2] * f[5];
+  g->ca = ca;
+  g->cb = cb;
+  g->cg = cg;
   // coefficients as polynomials in v (low order first)
   const double p2[1] = {-b2}, p1[1] = {2.0 * b2 * cg};
   const double p0[3] = {c2 - b2, -2.0 * c2 * cb, c2};
@@ -335,32 +354,45 @@ static VD_HD int vd_p3p(const double* fin, const double* X, double* poses) {
   vd_pmul(p1, 0, q0, 2, tmp);
   vd_pmul(p0, 2, q1, 1, tmp2);
   for (int i = 0; i < 4; ++i) C[i] = (i < 3 ? tmp[i] : 0.0) - tmp2[i];
-  double res[5], bc[5];
+  double bc[5];
   vd_pmul(A, 2, A, 2, res);
   vd_pmul(B, 1, C, 3, bc);
   for (int i = 0; i < 5; ++i) res[i] -= bc[i];
-  double roots[4];
-  const int nr = vd_poly_real_roots(res, 4, roots);
+  return 0;
+}
+
+// Camera pose of one root v: u from the common root of the two conics,
+// s1 = b / sqrt(1 + v^2 - 2 v cb), camera points s_i f_i, then the rigid
+// motion of the triangle.  false if the root gives no valid triangle.
+static VD_HD bool vd_p3p_pose(const VdP3P& g, const double* X, double v, double* T) {
+  if (!(v > 0.0)) return false;
+  const double a2 = g.a2, b2 = g.b2, c2 = g.c2, ca = g.ca, cb = g.cb, cg = g.cg;
+  const double pp0 = c2 * (1.0 + v * v - 2.0 * v * cb) - b2;
+  const double qq1 = -2.0 * b2 * ca * v;
+  const double qq0 = b2 * v * v - a2 * (1.0 + v * v - 2.0 * v * cb);
+  const double den = b2 * (2.0 * b2 * cg) + b2 * qq1;
+  if (fabs(den) < 1e-300) return false;
+  const double u = (-b2 * qq0 - b2 * pp0) / den;
+  if (!(u > 0.0)) return false;
+  const double dd = 1.0 + v * v - 2.0 * v * cb;
+  if (!(dd > 0.0)) return false;
+  const double s1 = sqrt(b2 / dd);
+  const double* f = g.f;
+  const double Q[9] = {s1 * f[0], s1 * f[1], s1 * f[2],
+                       u * s1 * f[3], u * s1 * f[4], u * s1 * f[5],
+                       v * s1 * f[6], v * s1 * f[7], v * s1 * f[8]};
+  vd_triangle_motion(X, Q, T);
+  return true;
+}
+
+// All P3P solutions (<= 4 poses, world -> camera) of one instance.
+static VD_HD int vd_p3p(const double* fin, const double* X, double* poses) {
+  VdP3P g;
+  double v[4];
+  const int nr = vd_p3p_roots(fin, X, &g, v);
   int ns = 0;
-  for (int r = 0; r < nr; ++r) {
-    const double v = roots[r];
-    if (!(v > 0.0)) continue;
-    const double pp0 = c2 * (1.0 + v * v - 2.0 * v * cb) - b2;
-    const double qq1 = -2.0 * b2 * ca * v;
-    const double qq0 = b2 * v * v - a2 * (1.0 + v * v - 2.0 * v * cb);
-    const double den = b2 * (2.0 * b2 * cg) + b2 * qq1;
-    if (fabs(den) < 1e-300) continue;
-    const double u = (-b2 * qq0 - b2 * pp0) / den;
-    if (!(u > 0.0)) continue;
-    const double dd = 1.0 + v * v - 2.0 * v * cb;
-    if (!(dd > 0.0)) continue;
-    const double s1 = sqrt(b2 / dd);
-    const double Q[9] = {s1 * f[0], s1 * f[1], s1 * f[2],
-                         u * s1 * f[3], u * s1 * f[4], u * s1 * f[5],
-                         v * s1 * f[6], v * s1 * f[7], v * s1 * f[8]};
-    vd_absolute_orientation(X, Q, poses + 12 * ns);
-    ++ns;
-  }
+  for (int r = 0; r < nr; ++r)
+    if (vd_p3p_pose(g, X, v[r], poses + 12 * ns)) ++ns;
   return ns;
 }
 

@@ -21,6 +21,7 @@
 #define VD_TAG_INIT 2u
 #define VD_MS_MAX_ITERS 100
 #define VD_MS_TOL 1e-12
+#define VD_MS_TOL_F32 1e-6          // float32 mean-shift stop, relative to 1 + |tau|
 #define VD_MAX_ATTEMPTS 8
 #define VD_IRLS_ITERS 8
 

@@ -205,55 +205,141 @@ __device__ void vd_correspondence64(const DevParams& P, const double* __restrict
   bearing[2] = 1.0;
 }
 
-__device__ __forceinline__ bool vd_key_less(const double* a, const double* b) {
-  double ka[6], kb[6];
-  vd_so3_log(a, ka);
-  vd_so3_log(b, kb);
-  ka[3] = a[3]; ka[4] = a[7]; ka[5] = a[11];
-  kb[3] = b[3]; kb[4] = b[7]; kb[5] = b[11];
-  for (int i = 0; i < 6; ++i) {
-    if (ka[i] < kb[i]) return true;
-    if (ka[i] > kb[i]) return false;
+// Real roots of a polynomial of exact degree `deg` split by the sorted points
+// `crit`, with the interval searches spread over the lanes of a warp: the
+// intervals and the bracketed search are those of vd_roots_between, so the
+// roots are bitwise the same; every lane receives all roots.
+__device__ int vd_roots_between_warp(const double* c, int deg, const double* crit, int ncrit,
+                                     double* out, int lane) {
+  double bound = 0.0;
+  for (int i = 0; i < deg; ++i) {
+    double r = fabs(c[i] / c[deg]);
+    if (i == 0) r *= 0.5;
+    const int k = deg - i;
+    const double root = k == 1 ? r : (k == 2 ? sqrt(r) : (k == 3 ? cbrt(r) : sqrt(sqrt(r))));
+    bound = fmax(bound, root);
   }
-  return false;
+  bound = 2.0 * bound * (1.0 + 1e-12) + 1e-300;
+  double lo = -bound;
+  double flo = vd_poly_eval(c, deg, lo);
+  double mlo = 0.0, mhi = 0.0;      // this lane's interval
+  int mkind = 0;                    // 0 none, 1 root at lo, 2 search
+  int kinds = 0;                    // 2 bits per interval
+  int ni = 0;
+  for (int i = 0; i <= ncrit; ++i) {
+    const double hi = i < ncrit ? fmin(fmax(crit[i], -bound), bound) : bound;
+    if (!(hi > lo)) continue;
+    const double fhi = vd_poly_eval(c, deg, hi);
+    const int kind = flo == 0.0 ? 1 : (((flo < 0.0) != (fhi < 0.0) && fhi != 0.0) ? 2 : 0);
+    kinds |= kind << (2 * ni);
+    if (ni == lane) {
+      mlo = lo;
+      mhi = hi;
+      mkind = kind;
+    }
+    ++ni;
+    lo = hi;
+    flo = fhi;
+  }
+  const double mine = mkind == 2 ? vd_poly_bracketed_root(c, deg, mlo, mhi) : mlo;
+  int n = 0;
+  for (int k = 0; k < 5; ++k) {
+    const double r = __shfl_sync(0xffffffffu, mine, k);
+    if (k < ni && ((kinds >> (2 * k)) & 3)) out[n++] = r;
+  }
+  return n;
 }
 
-__global__ void k_p3p_samples(DevParams P, const double* __restrict__ G,
-                              const float2* __restrict__ flow, const float* __restrict__ rho,
-                              const int* __restrict__ idx, const int* __restrict__ n_rigid, int t,
-                              uint32_t itcode, double* __restrict__ roots,
-                              int* __restrict__ root_count) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+// The real roots of the P3P quartic as vd_poly_real_roots finds them
+// (second derivative, first derivative, quartic), each stage's interval
+// searches in parallel lanes.
+__device__ int vd_quartic_roots_warp(const double* cin, double* out, int lane) {
+  double mx = 0.0;
+  for (int i = 0; i <= 4; ++i) mx = fmax(mx, fabs(cin[i]));
+  if (mx == 0.0) return 0;
+  if (fabs(cin[4]) <= 1e-14 * mx) return vd_poly_real_roots(cin, 4, out);   // lower degree
+  const double q[3] = {cin[2] * 2.0, cin[3] * 6.0, cin[4] * 12.0};
+  const double split = -q[1] / (2.0 * q[2]);
+  double r2[2];
+  const int n2 = vd_roots_between_warp(q, 2, &split, 1, r2, lane);
+  const double cc[4] = {cin[1], cin[2] * 2.0, cin[3] * 3.0, cin[4] * 4.0};
+  double r3[3];
+  const int n3 = vd_roots_between_warp(cc, 3, r2, n2, r3, lane);
+  return vd_roots_between_warp(cin, 4, r3, n3, out, lane);
+}
+
+// One warp per sample (samples spread over the SMs: the float64 pipe is
+// narrow, so the solve is latency-bound per warp).  Lanes 0-2 build the three
+// correspondences, every lane forms the quartic, lanes 0-3 turn one root each
+// into a pose and its ordering key; each lane then finds its rank.
+__global__ void __launch_bounds__(32)
+k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restrict__ flow,
+              const float* __restrict__ rho, const int* __restrict__ idx,
+              const int* __restrict__ n_rigid, int t, uint32_t itcode, double* __restrict__ roots,
+              int* __restrict__ root_count) {
+  const int g = blockIdx.x;
+  const int lane = threadIdx.x;
   if (g >= P.S) return;
   const int n = *n_rigid;
-  root_count[g] = 0;
-  if (n < 3) return;
-  int pick[3];
+  int pick[3] = {0, 0, 0};
   bool ok = false;
-  for (uint32_t b = 0; b < VD_MAX_ATTEMPTS && !ok; ++b) {
-    const uint4 w = vd_philox(make_uint4((uint32_t)g + 65536u * (uint32_t)t, itcode, VD_TAG_POSE, b),
-                              P.key0, P.key1);
-    pick[0] = (int)(((unsigned long long)w.x * (unsigned long long)n) >> 32);
-    pick[1] = (int)(((unsigned long long)w.y * (unsigned long long)n) >> 32);
-    pick[2] = (int)(((unsigned long long)w.z * (unsigned long long)n) >> 32);
-    ok = pick[0] != pick[1] && pick[0] != pick[2] && pick[1] != pick[2];
-  }
-  if (!ok) return;
-  double X[9], f[9];
-  for (int k = 0; k < 3; ++k) vd_correspondence64(P, G, flow, rho, t, idx[pick[k]], X + 3 * k, f + 3 * k);
-  double* out = roots + (size_t)g * 48;
-  const int nr = vd_p3p(f, X, out);
-  // insertion sort by (rotation vector, translation)
-  for (int a = 1; a < nr; ++a) {
-    for (int b = a; b > 0 && vd_key_less(out + 12 * b, out + 12 * (b - 1)); --b) {
-      for (int i = 0; i < 12; ++i) {
-        const double tmp = out[12 * b + i];
-        out[12 * b + i] = out[12 * (b - 1) + i];
-        out[12 * (b - 1) + i] = tmp;
-      }
+  if (n >= 3) {
+    for (uint32_t b = 0; b < VD_MAX_ATTEMPTS && !ok; ++b) {
+      const uint4 w = vd_philox(
+          make_uint4((uint32_t)g + 65536u * (uint32_t)t, itcode, VD_TAG_POSE, b), P.key0, P.key1);
+      pick[0] = (int)(((unsigned long long)w.x * (unsigned long long)n) >> 32);
+      pick[1] = (int)(((unsigned long long)w.y * (unsigned long long)n) >> 32);
+      pick[2] = (int)(((unsigned long long)w.z * (unsigned long long)n) >> 32);
+      ok = pick[0] != pick[1] && pick[0] != pick[2] && pick[1] != pick[2];
     }
   }
-  root_count[g] = nr;
+  if (!ok) {
+    if (lane == 0) root_count[g] = 0;
+    return;
+  }
+  double Xl[3] = {0, 0, 0}, fl[3] = {0, 0, 1};
+  if (lane < 3)
+    vd_correspondence64(P, G, flow, rho, t, idx[pick[lane < 3 ? lane : 0]], Xl, fl);
+  double X[9], f[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      X[3 * k + c] = __shfl_sync(0xffffffffu, Xl[c], k);
+      f[3 * k + c] = __shfl_sync(0xffffffffu, fl[c], k);
+    }
+  VdP3P geo;
+  double v[4], res[5];
+  const int nr = vd_p3p_quartic(f, X, &geo, res) < 0 ? 0 : vd_quartic_roots_warp(res, v, lane);
+  double T[12];
+  bool valid = false;
+  if (lane < 4 && lane < nr) valid = vd_p3p_pose(geo, X, v[lane], T);
+  double key[6] = {0, 0, 0, 0, 0, 0};
+  if (valid) {
+    vd_so3_log(T, key);
+    key[3] = T[3];
+    key[4] = T[7];
+    key[5] = T[11];
+  }
+  // rank among the valid roots by (rotation vector, translation), ties by lane
+  int rank = 0, count = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool vk = __shfl_sync(0xffffffffu, valid, k);
+    double kk[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) kk[i] = __shfl_sync(0xffffffffu, key[i], k);
+    if (!vk) continue;
+    ++count;
+    if (!valid || k == lane) continue;
+    int cmp = 0;
+    for (int i = 0; i < 6 && cmp == 0; ++i) cmp = kk[i] < key[i] ? -1 : (kk[i] > key[i] ? 1 : 0);
+    if (cmp < 0 || (cmp == 0 && k < lane)) ++rank;
+  }
+  double* out = roots + (size_t)g * 48;
+  if (valid)
+    for (int i = 0; i < 12; ++i) out[12 * rank + i] = T[i];
+  if (lane == 0) root_count[g] = count;
 }
 
 // float K R | K tau of every root slot (invalid slots: zero).
@@ -361,6 +447,74 @@ __global__ void k_root_energy(const float* __restrict__ partial, int nblk, int M
 }
 
 // ---------------------------------------------------------------------------
+// float32 se(3) maps for the mean-shift iterations, whose arguments are
+// poses relative to the current mode (small unless the sample is far away,
+// in which case its Gaussian weight is zero anyway).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool vd_se3_log_f(const float* T, float* xi) {
+  const float c = 0.5f * (T[0] + T[5] + T[10] - 1.0f);
+  const float vx = 0.5f * (T[9] - T[6]), vy = 0.5f * (T[2] - T[8]), vz = 0.5f * (T[4] - T[1]);
+  const float s = sqrtf(vx * vx + vy * vy + vz * vz);
+  if (c < 0.0f && s < 1e-3f) return false;   // rotation by ~pi: weight 0
+  const float th = atan2f(s, c);
+  const float f = s < 1e-6f ? 1.0f + th * th * (1.0f / 6.0f) : th / s;
+  const float wx = vx * f, wy = vy * f, wz = vz * f;
+  const float th2 = wx * wx + wy * wy + wz * wz;
+  // e = (1 - (th/2) cot(th/2)) / th^2 = 1/12 + th^2/720 + th^4/30240 + ...
+  float e;
+  if (th2 < 1e-2f) {
+    e = (1.0f / 12.0f) + th2 * ((1.0f / 720.0f) + th2 * (1.0f / 30240.0f));
+  } else {
+    const float t = sqrtf(th2);
+    float sn, cs;
+    sincosf(t, &sn, &cs);
+    e = (1.0f - (t * sn) / (2.0f * (1.0f - cs))) / th2;
+  }
+  const float t0 = T[3], t1 = T[7], t2 = T[11];
+  // [w]x t and [w]x^2 t
+  const float k0 = wy * t2 - wz * t1, k1 = wz * t0 - wx * t2, k2 = wx * t1 - wy * t0;
+  const float q0 = wy * k2 - wz * k1, q1 = wz * k0 - wx * k2, q2 = wx * k1 - wy * k0;
+  xi[0] = wx;
+  xi[1] = wy;
+  xi[2] = wz;
+  xi[3] = t0 - 0.5f * k0 + e * q0;
+  xi[4] = t1 - 0.5f * k1 + e * q1;
+  xi[5] = t2 - 0.5f * k2 + e * q2;
+  return true;
+}
+
+__device__ __forceinline__ void vd_se3_exp_f(const float* xi, float* T) {
+  const float wx = xi[0], wy = xi[1], wz = xi[2];
+  const float th2 = wx * wx + wy * wy + wz * wz;
+  float a, b, cc;
+  if (th2 < 1e-2f) {
+    a = 1.0f - th2 * ((1.0f / 6.0f) - th2 * (1.0f / 120.0f));
+    b = 0.5f - th2 * ((1.0f / 24.0f) - th2 * (1.0f / 720.0f));
+    cc = (1.0f / 6.0f) - th2 * ((1.0f / 120.0f) - th2 * (1.0f / 5040.0f));
+  } else {
+    const float th = sqrtf(th2);
+    float s, c;
+    sincosf(th, &s, &c);
+    a = s / th;
+    b = (1.0f - c) / th2;
+    cc = (th - s) / (th2 * th);
+  }
+  const float K[9] = {0, -wz, wy, wz, 0, -wx, -wy, wx, 0};
+  float K2[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+  float V[9];
+  for (int i = 0; i < 9; ++i) {
+    const float I = (i % 4 == 0) ? 1.0f : 0.0f;
+    T[4 * (i / 3) + (i % 3)] = I + a * K[i] + b * K2[i];
+    V[i] = I + b * K[i] + cc * K2[i];
+  }
+  for (int r = 0; r < 3; ++r)
+    T[4 * r + 3] = V[3 * r] * xi[3] + V[3 * r + 1] * xi[4] + V[3 * r + 2] * xi[5];
+}
+
+// ---------------------------------------------------------------------------
 // Per sample: the lowest-energy root; then mean-shift from the best sample:
 // x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
 // w_g = exp(-d^T Sigma^-1 d / 2), until |step| < 1e-12 or 100 steps.
@@ -422,45 +576,60 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   if (g == start)
     for (int i = 0; i < 12; ++i) sX[i] = Tg[i];
   __syncthreads();
-  const double st_ = P.ms_sig_rel * sqrt(sX[3] * sX[3] + sX[7] * sX[7] + sX[11] * sX[11]) + P.ms_sig_abs;
-  const double ivr = 1.0 / (P.ms_sig_rot * P.ms_sig_rot), ivt = 1.0 / (st_ * st_);
+  const double tn = sqrt(sX[3] * sX[3] + sX[7] * sX[7] + sX[11] * sX[11]);
+  const double st_ = P.ms_sig_rel * tn + P.ms_sig_abs;
+  const float ivr = (float)(1.0 / (P.ms_sig_rot * P.ms_sig_rot)), ivt = (float)(1.0 / (st_ * st_));
+  // float32 iterations stop at this step norm (the float32 floor of the
+  // relative poses); the float64 definition stops at 1e-12
+  const float tol = (float)(VD_MS_TOL_F32 * (1.0 + tn));
+  float* sW = (float*)sRed;          // [8 warps][7]
+  const int lane = g & 31, wid = g >> 5;
   if (g == 0) sDone = 0;
   __syncthreads();
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
-    double d[6] = {0, 0, 0, 0, 0, 0};
-    double w = 0.0;
+    float d[6] = {0, 0, 0, 0, 0, 0};
+    float w = 0.0f;
     if (valid) {
-      double xi[12], rel[12];
-      double xl[12];
+      double xi[12], rel[12], xl[12];
       for (int i = 0; i < 12; ++i) xl[i] = sX[i];
       vd_inverse(xl, xi);
       vd_compose(xi, Tg, rel);
-      vd_se3_log(rel, d);
-      const double m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
-                       (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
-      w = exp(-0.5 * m);
+      float relf[12];
+      for (int i = 0; i < 12; ++i) relf[i] = (float)rel[i];
+      if (vd_se3_log_f(relf, d)) {
+        const float m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
+                        (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
+        w = __expf(-0.5f * m);
+      }
     }
-    sRed[g * 7] = w;
-    for (int i = 0; i < 6; ++i) sRed[g * 7 + 1 + i] = w * d[i];
+    float acc[7] = {w, w * d[0], w * d[1], w * d[2], w * d[3], w * d[4], w * d[5]};
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    if (lane == 0)
+      for (int i = 0; i < 7; ++i) sW[wid * 7 + i] = acc[i];
     __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-      if (g < off)
-        for (int i = 0; i < 7; ++i) sRed[g * 7 + i] += sRed[(g + off) * 7 + i];
-      __syncthreads();
-    }
     if (g == 0) {
-      double step[6];
-      double nrm = 0.0;
+      float s[7] = {0, 0, 0, 0, 0, 0, 0};
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+        for (int i = 0; i < 7; ++i) s[i] += sW[k * 7 + i];
+      float step[6];
+      float nrm = 0.0f;
       for (int i = 0; i < 6; ++i) {
-        step[i] = sRed[1 + i] / sRed[0];
+        step[i] = s[1 + i] / s[0];
         nrm += step[i] * step[i];
       }
+      float Ef[12];
+      vd_se3_exp_f(step, Ef);
       double E[12], xn[12], xo[12];
-      for (int i = 0; i < 12; ++i) xo[i] = sX[i];
-      vd_se3_exp(step, E);
+      for (int i = 0; i < 12; ++i) {
+        E[i] = (double)Ef[i];
+        xo[i] = sX[i];
+      }
       vd_compose(xo, E, xn);
       for (int i = 0; i < 12; ++i) sX[i] = xn[i];
-      if (sqrt(nrm) < VD_MS_TOL) sDone = 1;
+      if (sqrtf(nrm) < tol) sDone = 1;
     }
     __syncthreads();
     if (sDone) break;
@@ -488,7 +657,7 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
                                                               c->rigid_idx, c->rpts, c->robs);
   vd_prof_end(c, VD_ST_RIGID, 3);
   vd_prof_begin(c, VD_ST_P3P);
-  k_p3p_samples<<<(P.S + 31) / 32, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
+  k_p3p_samples<<<P.S, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
                                                        c->n_rigid, t, itcode, c->roots,
                                                        c->root_count);
   const int M = 4 * P.S;
