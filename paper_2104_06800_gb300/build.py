@@ -44,8 +44,14 @@ def _digest(extra):
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if sources changed) and return the path of the shared library."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), lib_path: str | None = None,
+          build_dir: str | None = None) -> str:
+    """Compile (if sources changed) and return the path of the shared library.
+
+    extra_flags: additional nvcc flags (for example -D options of the kernels);
+    lib_path / build_dir: where to put the library and the objects."""
+    LIB = lib_path or globals()["LIB"]
+    BUILD = build_dir or globals()["BUILD"]
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
              *ARCH, *extra_flags]
     stamp = os.path.join(BUILD, "stamp")

@@ -54,8 +54,20 @@ __device__ __forceinline__ void vd_load_pose_smem(float* sPose, const float* __r
 // draws Philox word k-1 of counter (j - u mod share, iter, TAG_DEPTH, (k-1)/4):
 // slots 1..(K-1)/2 uniform in [rho_min, rho_max], the rest rho (1 + s (2u-1)).
 // ---------------------------------------------------------------------------
+// Launch shape of the sampling kernel (threads per block and the minimum
+// number of resident blocks requested from the register allocator).
+#ifndef VD_K1_BX
+#define VD_K1_BX 32
+#endif
+#ifndef VD_K1_BY
+#define VD_K1_BY 4
+#endif
+#ifndef VD_K1_MINB
+#define VD_K1_MINB 1
+#endif
+
 template <int NF>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(VD_K1_BX * VD_K1_BY, VD_K1_MINB)
 k_depth_sample(DevParams P, const float* __restrict__ posef, const float2* __restrict__ flow,
                const float* __restrict__ rho, const float* __restrict__ q,
                const float* __restrict__ prior_val, const float* __restrict__ prior_rho,
@@ -94,7 +106,7 @@ k_depth_sample(DevParams P, const float* __restrict__ posef, const float2* __res
     float c = (k <= n_unif) ? vd_cand_uniform(x, rmin, range) : vd_cand_perturb(x, cur, s_pert);
     c = vd_clamp(c, rmin, rmax);
     if (k == 1 && has_prior) c = prior_c;
-    const float E = vd_energy<NF>(px, P, sPose, flow, npix, c);
+    const float E = vd_energy<NF>(px, P, sPose, flow, npix, c, bestE);
     if (E < bestE) {
       bestE = E;
       best = c;
@@ -131,7 +143,7 @@ __device__ __forceinline__ float vd_prop_step(const DevParams& P, const float* s
   const size_t npix = (size_t)P.W * P.H;
   VdPixel<NF> px;
   vd_pixel_setup<NF>(px, P, sPose, u, v, q, npix, j, flow, prior_val, qhat, pconf);
-  const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur);
+  const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur, e_own);
   return (Ec < e_own) ? cur : own;
 }
 
@@ -304,7 +316,7 @@ static inline dim3 pix_grid(const vd_ctx* c, dim3 blk) {
 }
 
 cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, const float*) {
-  const dim3 blk(32, 4);
+  const dim3 blk(VD_K1_BX, VD_K1_BY);
   const dim3 grd = pix_grid(c, blk);
   VD_DISPATCH_NF(c->N, (k_depth_sample<NF><<<grd, blk, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->rho, c->q, c->prior_val, c->prior_rho,

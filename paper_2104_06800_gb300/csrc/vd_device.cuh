@@ -161,16 +161,39 @@ __device__ __forceinline__ void vd_pixel_setup(VdPixel<NF>& px, const DevParams&
 }
 
 // E_j(c): sum_t q_t l_t(c) + w_hat l_hat(c) in natural-log units.
+// Every term is non-negative, so once the partial sum reaches `bound` the
+// candidate cannot beat an energy of `bound`: the sum stops there and the
+// partial value (>= bound) is returned.  The cheap terms come first: the
+// prior, then X_1 (read at the pixel itself), then the gathered flows.
 template <int NF>
 __device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParams& P,
                                            const float* __restrict__ sPose,
                                            const float2* __restrict__ flow, size_t npix,
-                                           float c) {
+                                           float c, float bound = INFINITY) {
   float E = 0.0f;
+  if (px.pw > 0.0f) {
+    if (P.prior_kind == VD_PRIOR_STEREO) {
+      const float d = px.pv - P.fxb * c;
+      float y;
+      if (P.beta == 2.0f) {
+        const float s = fmaf(d * d, P.inv_a2, 1.0f);
+        y = P.c0 * s * s;
+      } else {
+        y = vd_ratio_general(P, d * d, P.alpha0);
+      }
+      E = px.pw * VD_LN2 * vd_ell2(y);
+    } else {
+      const float res = px.pv - c;
+      const float sig = P.c_sigma * px.pv;
+      const float z = fmaf(res * res, 0.5f / (sig * sig), P.logk);
+      E = px.pw * (z > 20.0f ? z : VD_LN2 * vd_ell2(__expf(z)));
+    }
+  }
   float xp = px.u, yp = px.v;
   bool front_prev = true;
 #pragma unroll
   for (int t = 0; t < NF; ++t) {
+    if (E >= bound) return E;
     const float* M = sPose + 12 * (t + 1);
     const float hx = fmaf(c, M[9], px.ax[t]);
     const float hy = fmaf(c, M[10], px.ay[t]);
@@ -204,25 +227,6 @@ __device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParam
     xp = x;
     yp = y;
     front_prev = front;
-  }
-  if (px.pw > 0.0f) {
-    if (P.prior_kind == VD_PRIOR_STEREO) {
-      const float d = px.pv - P.fxb * c;
-      float y;
-      if (P.beta == 2.0f) {
-        const float s = fmaf(d * d, P.inv_a2, 1.0f);
-        y = P.c0 * s * s;
-      } else {
-        y = vd_ratio_general(P, d * d, P.alpha0);
-      }
-      E = fmaf(px.pw * VD_LN2, vd_ell2(y), E);
-    } else {
-      const float res = px.pv - c;
-      const float sig = P.c_sigma * px.pv;
-      const float z = fmaf(res * res, 0.5f / (sig * sig), P.logk);
-      const float l = z > 20.0f ? z : __logf(1.0f + __expf(z));
-      E = fmaf(px.pw, l, E);
-    }
   }
   return E;
 }

@@ -98,55 +98,130 @@ k_emission(DevParams P, const float* __restrict__ posef, const float2* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Forward-backward on one chain per thread (flow t, row or column).  With
-// a = P(rigid | left part), b = P(rigid | right part) normalised:
-//   a_m ~ (a_{m-1} g + (1 - a_{m-1}) h) lam_m  vs  a_{m-1} h + (1 - a_{m-1}) g
-//   b_m ~ g lam_{m+1} b_{m+1} + h (1 - b_{m+1})  vs  h lam_{m+1} b_{m+1} + g (1 - b_{m+1})
-//   q_m = a_m b_m / (a_m b_m + (1 - a_m)(1 - b_m)),  g = gamma, h = 1 - gamma.
-// The forward pass parks a_m in q; the backward pass combines.
+// Forward-backward as an associative scan, one warp per chain.  With
+// M_m = A diag(1, lam_m) (A[s'][s] = gamma if s = s' else 1 - gamma) the
+// forward messages are alpha_m = (1, lam_0) M_1 ... M_m and the backward
+// ones beta_m = M_{m+1} ... M_{L-1} (1, 1)^T.  Lane i owns the contiguous
+// segment [a_i, b_i) of the chain: it forms the product S_i of its segment's
+// matrices, a warp scan of the S_i (normalised 2x2 products) gives the
+// message entering and leaving every segment, and each lane walks its
+// segment forward (parking alpha in q) and backward (combining).
 // ---------------------------------------------------------------------------
-__global__ void k_forward_backward(DevParams P, const float* __restrict__ lam,
-                                   float* __restrict__ q, int direction) {
+struct VdM2 {
+  float a, b, c, d;   // [[a, b], [c, d]]
+};
+
+__device__ __forceinline__ VdM2 vd_m2_mul(const VdM2& x, const VdM2& y) {
+  VdM2 r;
+  r.a = fmaf(x.a, y.a, x.b * y.c);
+  r.b = fmaf(x.a, y.b, x.b * y.d);
+  r.c = fmaf(x.c, y.a, x.d * y.c);
+  r.d = fmaf(x.c, y.b, x.d * y.d);
+  const float s = 1.0f / (r.a + r.b + r.c + r.d);   // first column is positive: s finite
+  r.a *= s;
+  r.b *= s;
+  r.c *= s;
+  r.d *= s;
+  return r;
+}
+
+__device__ __forceinline__ VdM2 vd_m2_shfl_up(const VdM2& x, int off) {
+  VdM2 r;
+  r.a = __shfl_up_sync(0xffffffffu, x.a, off);
+  r.b = __shfl_up_sync(0xffffffffu, x.b, off);
+  r.c = __shfl_up_sync(0xffffffffu, x.c, off);
+  r.d = __shfl_up_sync(0xffffffffu, x.d, off);
+  return r;
+}
+
+__device__ __forceinline__ VdM2 vd_m2_shfl_down(const VdM2& x, int off) {
+  VdM2 r;
+  r.a = __shfl_down_sync(0xffffffffu, x.a, off);
+  r.b = __shfl_down_sync(0xffffffffu, x.b, off);
+  r.c = __shfl_down_sync(0xffffffffu, x.c, off);
+  r.d = __shfl_down_sync(0xffffffffu, x.d, off);
+  return r;
+}
+
+__global__ void __launch_bounds__(128)
+k_forward_backward_warp(DevParams P, const float* __restrict__ lam, float* __restrict__ q,
+                        int direction) {
   const bool rows = (direction & 1) == 0;
   const int nchains = rows ? P.H : P.W;
   const int L = rows ? P.W : P.H;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= nchains * P.N) return;
-  const int t = gid / nchains;
-  const int ch = gid - t * nchains;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (wid >= nchains * P.N) return;               // whole warps leave together
+  const int t = wid / nchains;
+  const int ch = wid - t * nchains;
   const size_t npix = (size_t)P.W * P.H;
   const float* lt = lam + (size_t)t * npix;
   float* qt = q + (size_t)t * npix;
   const size_t base = rows ? (size_t)ch * P.W : (size_t)ch;
   const size_t step = rows ? 1 : (size_t)P.W;
   const float g = P.gamma, h = 1.0f - P.gamma;
-  float a = 0.5f;
-  for (int m = 0; m < L; ++m) {
-    const size_t j = base + step * m;
-    const float l = lt[j];
-    float x1, x0;
-    if (m == 0) {
-      x1 = l;
-      x0 = 1.0f;
-    } else {
-      x1 = fmaf(a, g - h, h) * l;      // (a g + (1 - a) h) lam
-      x0 = fmaf(a, h - g, g);          // a h + (1 - a) g
-    }
-    a = x1 / (x0 + x1);
-    qt[j] = a;
+  const int seg = (L + 31) >> 5;
+  const int a0 = min(L, lane * seg), b0 = min(L, a0 + seg);
+  const int first = max(a0, 1);                   // position 0 carries no matrix
+  // segment product
+  VdM2 S = {1.0f, 0.0f, 0.0f, 1.0f};
+  for (int m = first; m < b0; ++m) {
+    const float l = lt[base + step * m];
+    const VdM2 M = {g, h * l, h, g * l};
+    S = vd_m2_mul(S, M);
   }
-  float b = 0.5f;
-  for (int m = L - 1; m >= 0; --m) {
-    const size_t j = base + step * m;
-    const float am = qt[j];
-    if (m < L - 1) {
-      const float ln = lt[j + step];
-      const float y1 = fmaf(g * ln, b, h * (1.0f - b));
-      const float y0 = fmaf(h * ln, b, g * (1.0f - b));
-      b = y1 / (y0 + y1);
+  // inclusive prefix (left to right) and suffix (right to left) products
+  VdM2 X = S, Z = S;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const VdM2 Y = vd_m2_shfl_up(X, off);
+    if (lane >= off) X = vd_m2_mul(Y, X);
+    const VdM2 Yd = vd_m2_shfl_down(Z, off);
+    if (lane + off < 32) Z = vd_m2_mul(Z, Yd);
+  }
+  VdM2 Pin = vd_m2_shfl_up(X, 1);                 // product of the earlier segments
+  VdM2 Qout = vd_m2_shfl_down(Z, 1);              // product of the later segments
+  if (lane == 0) Pin = {1.0f, 0.0f, 0.0f, 1.0f};
+  if (lane == 31) Qout = {1.0f, 0.0f, 0.0f, 1.0f};
+  if (a0 >= b0) return;
+  // forward walk: alpha entering the segment = (1, lam_0) Pin
+  const float l0 = lt[base];
+  float f0 = fmaf(1.0f, Pin.a, l0 * Pin.c), f1 = fmaf(1.0f, Pin.b, l0 * Pin.d);
+  if (a0 == 0) {
+    const float s = 1.0f / (f0 + f1);
+    f0 *= s;
+    f1 *= s;
+    qt[base] = f1;
+  }
+  for (int m = first; m < b0; ++m) {
+    const float l = lt[base + step * m];
+    const float n0 = fmaf(f0, g, f1 * h);           // (alpha A)_0 * e0
+    const float n1 = fmaf(f0, h, f1 * g) * l;       // (alpha A)_1 * e1
+    const float s = 1.0f / (n0 + n1);
+    f0 = n0 * s;
+    f1 = n1 * s;
+    qt[base + step * m] = f1;
+  }
+  // backward walk: beta leaving the segment = Qout (1, 1)^T
+  float b0v = Qout.a + Qout.b, b1v = Qout.c + Qout.d;
+  {
+    const float s = 1.0f / (b0v + b1v);
+    b0v *= s;
+    b1v *= s;
+  }
+  for (int m = b0 - 1; m >= a0; --m) {
+    if (m < b0 - 1) {
+      const float l = lt[base + step * (m + 1)];
+      const float y1 = b1v * l;
+      const float n0 = fmaf(g, b0v, h * y1);
+      const float n1 = fmaf(h, b0v, g * y1);
+      const float s = 1.0f / (n0 + n1);
+      b0v = n0 * s;
+      b1v = n1 * s;
     }
-    const float num = am * b;
-    qt[j] = num / (num + (1.0f - am) * (1.0f - b));
+    const float am = qt[base + step * m];
+    const float num = am * b1v;
+    qt[base + step * m] = num / (num + (1.0f - am) * b0v);
   }
 }
 
@@ -174,8 +249,8 @@ cudaError_t launch_estep(vd_ctx* c, int direction) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool rows = (direction & 1) == 0;
-  const int nthreads = (rows ? c->H : c->W) * c->N;
-  k_forward_backward<<<(nthreads + 63) / 64, 64, 0, c->stream>>>(c->dp, c->lam, c->q, direction);
+  const int nwarps = (rows ? c->H : c->W) * c->N;
+  k_forward_backward_warp<<<(nwarps + 3) / 4, 128, 0, c->stream>>>(c->dp, c->lam, c->q, direction);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_confidence<<<(unsigned)((c->npix + 255) / 256), 256, 0, c->stream>>>(c->dp, c->q, c->qhat,

@@ -10,6 +10,36 @@
 #define VD_HD __host__ __device__
 #endif
 
+// ---------------------------------------------------------------- fast float64 division
+// On the device a float64 divide or square root is a long instruction
+// sequence on a narrow pipe.  For Newton steps and normalisations a float
+// seed refined by float64 Newton iterations is enough: the relative error
+// squares per step (2^-24 -> ~2^-48 -> below rounding).
+VD_HD __forceinline__ double vd_rcp64(double x) {
+#ifdef __CUDA_ARCH__
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = r * (2.0 - x * r);
+  r = r * (2.0 - x * r);
+  return r;
+#else
+  return 1.0 / x;
+#endif
+}
+
+VD_HD __forceinline__ double vd_rsqrt64(double x) {
+#ifdef __CUDA_ARCH__
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double r = (double)rsqrtf((float)x);
+  r = r * (1.5 - 0.5 * x * r * r);
+  r = r * (1.5 - 0.5 * x * r * r);
+  return r;
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
+
 // ---------------------------------------------------------------- small algebra
 VD_HD __forceinline__ void vd_compose(const double* A, const double* B, double* O) {
   // O = A o B (apply B first)
@@ -133,12 +163,38 @@ VD_HD __forceinline__ double vd_poly_eval(const double* c, int deg, double x) {
   return r;
 }
 
-// Root of a polynomial known to change sign on [lo, hi]: safeguarded Newton.
+// Root of a polynomial known to change sign on [lo, hi]: safeguarded Newton
+// (a Newton step that leaves the bracket becomes a bisection step).  The
+// search first runs in float32 to about 1e-6 and then continues in float64
+// from there inside the float64 bracket, so the float64 phase needs only a
+// few steps; the bracket keeps the result a root of the float64 polynomial.
 static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, double hi) {
   double d[4];
   for (int i = 1; i <= deg; ++i) d[i - 1] = c[i] * i;
   double flo = vd_poly_eval(c, deg, lo);
   double x = 0.5 * (lo + hi);
+  {
+    float cf[5], df[4];
+    for (int i = 0; i <= deg; ++i) cf[i] = (float)c[i];
+    for (int i = 0; i < deg; ++i) df[i] = (float)d[i];
+    float l = (float)lo, h = (float)hi, xf = (float)x;
+    const bool neg_lo = flo < 0.0;
+    for (int it = 0; it < 60; ++it) {
+      float f = cf[deg];
+      for (int i = deg - 1; i >= 0; --i) f = f * xf + cf[i];
+      if (f == 0.0f) break;
+      if ((f < 0.0f) == neg_lo) l = xf;
+      else h = xf;
+      float g = df[deg - 1];
+      for (int i = deg - 2; i >= 0; --i) g = g * xf + df[i];
+      float xn = (g != 0.0f) ? xf - f / g : 0.5f * (l + h);
+      if (!(xn > l && xn < h)) xn = 0.5f * (l + h);
+      const float dx = fabsf(xn - xf);
+      xf = xn;
+      if (dx <= 1e-6f * fmaxf(1.0f, fabsf(xf)) || h - l <= 1e-6f * fmaxf(1.0f, fabsf(l))) break;
+    }
+    if ((double)xf > lo && (double)xf < hi) x = (double)xf;
+  }
   for (int it = 0; it < 100; ++it) {
     const double f = vd_poly_eval(c, deg, x);
     if (f == 0.0) return x;
@@ -149,7 +205,7 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
       hi = x;
     }
     const double df = vd_poly_eval(d, deg - 1, x);
-    double xn = (df != 0.0) ? x - f / df : 0.5 * (lo + hi);
+    double xn = (df != 0.0) ? x - f * vd_rcp64(df) : 0.5 * (lo + hi);
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
     if (fabs(xn - x) <= 1e-16 * fmax(1.0, fabs(xn))) return xn;
     if (hi - lo <= 1e-15 * fmax(1.0, fabs(lo))) return 0.5 * (lo + hi);
@@ -257,10 +313,10 @@ VD_HD __forceinline__ void vd_pmul(const double* a, int da, const double* b, int
 }
 
 VD_HD __forceinline__ void vd_normalize3(double* v) {
-  const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  v[0] /= n;
-  v[1] /= n;
-  v[2] /= n;
+  const double r = vd_rsqrt64(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  v[0] *= r;
+  v[1] *= r;
+  v[2] *= r;
 }
 
 VD_HD __forceinline__ void vd_cross3(const double* a, const double* b, double* o) {

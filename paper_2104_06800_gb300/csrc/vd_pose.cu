@@ -316,7 +316,21 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
   if (lane < 4 && lane < nr) valid = vd_p3p_pose(geo, X, v[lane], T);
   double key[6] = {0, 0, 0, 0, 0, 0};
   if (valid) {
-    vd_so3_log(T, key);
+    // ordering key: rotation vector (float32 is plenty to order distinct
+    // roots; the float64 logarithm near a half turn), then the translation
+    const float cf = 0.5f * ((float)T[0] + (float)T[5] + (float)T[10] - 1.0f);
+    if (cf < -0.9f) {
+      vd_so3_log(T, key);
+    } else {
+      const float vx = 0.5f * (float)(T[9] - T[6]), vy = 0.5f * (float)(T[2] - T[8]);
+      const float vz = 0.5f * (float)(T[4] - T[1]);
+      const float s = sqrtf(vx * vx + vy * vy + vz * vz);
+      const float th = atan2f(s, cf);
+      const float fk = s < 1e-6f ? 1.0f + th * th * (1.0f / 6.0f) : th / s;
+      key[0] = vx * fk;
+      key[1] = vy * fk;
+      key[2] = vz * fk;
+    }
     key[3] = T[3];
     key[4] = T[7];
     key[5] = T[11];
@@ -555,7 +569,7 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   sRed[g] = valid ? Eg : INFINITY;
   sIdx[g] = g;
   __syncthreads();
-  for (int off = 128; off > 0; off >>= 1) {
+  for (int off = (int)blockDim.x / 2; off > 0; off >>= 1) {
     if (g < off) {
       const double a = sRed[g], b = sRed[g + off];
       const int ia = sIdx[g], ib = sIdx[g + off];
@@ -584,18 +598,25 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   const float tol = (float)(VD_MS_TOL_F32 * (1.0 + tn));
   float* sW = (float*)sRed;          // [8 warps][7]
   const int lane = g & 31, wid = g >> 5;
+  float Tgf[12];
+  for (int i = 0; i < 12; ++i) Tgf[i] = valid ? (float)Tg[i] : 0.0f;
   if (g == 0) sDone = 0;
   __syncthreads();
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
     float d[6] = {0, 0, 0, 0, 0, 0};
     float w = 0.0f;
     if (valid) {
-      double xi[12], rel[12], xl[12];
-      for (int i = 0; i < 12; ++i) xl[i] = sX[i];
-      vd_inverse(xl, xi);
-      vd_compose(xi, Tg, rel);
-      float relf[12];
-      for (int i = 0; i < 12; ++i) relf[i] = (float)rel[i];
+      // relative pose x^-1 T_g in float32 (translation error ~|tau| 2^-24,
+      // below the float32 stop tolerance)
+      float xf[12], relf[12];
+      for (int i = 0; i < 12; ++i) xf[i] = (float)sX[i];
+      for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)   // (R_x^T R_g)_{rc}
+          relf[4 * r + c] = xf[r] * Tgf[c] + xf[4 + r] * Tgf[4 + c] + xf[8 + r] * Tgf[8 + c];
+        // R_x^T (tau_g - tau_x)
+        relf[4 * r + 3] = xf[r] * (Tgf[3] - xf[3]) + xf[4 + r] * (Tgf[7] - xf[7]) +
+                          xf[8 + r] * (Tgf[11] - xf[11]);
+      }
       if (vd_se3_log_f(relf, d)) {
         const float m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
                         (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
@@ -673,7 +694,10 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
                                                         c->root_count, c->root_energy);
   vd_prof_end(c, VD_ST_SCORE, 2);
   vd_prof_begin(c, VD_ST_SELECT);
-  k_select_meanshift<<<1, 256, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
+  // one thread per sample, a power of two (>= one warp) for the tree reduction
+  int ms_threads = 32;
+  while (ms_threads < P.S) ms_threads <<= 1;
+  k_select_meanshift<<<1, ms_threads, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
                                                c->posef, c->sample_pose, c->sample_energy,
                                                c->degenerate);
   vd_prof_end(c, VD_ST_SELECT, 1);
