@@ -187,15 +187,22 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
       else h = xf;
       float g = df[deg - 1];
       for (int i = deg - 2; i >= 0; --i) g = g * xf + df[i];
-      float xn = (g != 0.0f) ? xf - f / g : 0.5f * (l + h);
+      const float stp = g != 0.0f ? f / g : 0.0f;
+      if (g != 0.0f && fabsf(stp) <= 1e-6f * fmaxf(1.0f, fabsf(xf))) {   // converged
+        xf -= stp;
+        break;
+      }
+      float xn = (g != 0.0f) ? xf - stp : 0.5f * (l + h);
       if (!(xn > l && xn < h)) xn = 0.5f * (l + h);
-      const float dx = fabsf(xn - xf);
       xf = xn;
-      if (dx <= 1e-6f * fmaxf(1.0f, fabsf(xf)) || h - l <= 1e-6f * fmaxf(1.0f, fabsf(l))) break;
+      if (h - l <= 1e-6f * fmaxf(1.0f, fabsf(l))) break;
     }
     if ((double)xf > lo && (double)xf < hi) x = (double)xf;
   }
-  for (int it = 0; it < 100; ++it) {
+  // float64 phase: Newton converges quadratically from the float32 estimate
+  // for a simple root (two or three steps); clustered roots converge
+  // linearly, hence the cap.  Stops at a 4-ulp step.
+  for (int it = 0; it < 40; ++it) {
     const double f = vd_poly_eval(c, deg, x);
     if (f == 0.0) return x;
     if ((f < 0.0) == (flo < 0.0)) {
@@ -205,13 +212,36 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
       hi = x;
     }
     const double df = vd_poly_eval(d, deg - 1, x);
-    double xn = (df != 0.0) ? x - f * vd_rcp64(df) : 0.5 * (lo + hi);
+    const double stp = df != 0.0 ? f * vd_rcp64(df) : 0.0;
+    // a step below rounding means convergence (testing it after the bracket
+    // safeguard would turn the null step into a bisection jump)
+    if (df != 0.0 && fabs(stp) <= 8.9e-16 * fmax(1.0, fabs(x))) return x - stp;
+    double xn = (df != 0.0) ? x - stp : 0.5 * (lo + hi);
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    if (fabs(xn - x) <= 1e-16 * fmax(1.0, fabs(xn))) return xn;
-    if (hi - lo <= 1e-15 * fmax(1.0, fabs(lo))) return 0.5 * (lo + hi);
+    if (hi - lo <= 8.9e-16 * fmax(1.0, fabs(lo))) return 0.5 * (lo + hi);
     x = xn;
   }
   return x;
+}
+
+// An upper bound on the magnitude of every root (Fujiwara:
+// 2 max(|c_{n-1}/c_n|, |c_{n-2}/c_n|^(1/2), ..., |c_0/(2 c_n)|^(1/n))),
+// evaluated in float32 with a safety margin (a bound needs no precision).
+VD_HD __forceinline__ double vd_root_bound(const double* c, int deg) {
+  float bf = 0.0f;
+  for (int i = 0; i < deg; ++i) {
+    float r = fabsf((float)(c[i] / c[deg]));
+    if (i == 0) r *= 0.5f;
+    const int k = deg - i;
+    const float root = k == 1 ? r : (k == 2 ? sqrtf(r) : (k == 3 ? cbrtf(r) : sqrtf(sqrtf(r))));
+    bf = fmaxf(bf, root);
+  }
+  if (!(bf < 1e30f)) {   // out of float range: the float64 Cauchy bound
+    double b = 0.0;
+    for (int i = 0; i < deg; ++i) b = fmax(b, fabs(c[i] / c[deg]));
+    return b + 1.0;
+  }
+  return 2.0 * (double)bf * 1.001 + 1e-30;
 }
 
 // Real roots of a polynomial of exact degree `deg` (leading coefficient
@@ -220,17 +250,7 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
 // Writes at most ncrit + 1 roots.
 VD_HD __forceinline__ int vd_roots_between(const double* c, int deg, const double* crit,
                                                 int ncrit, double* out) {
-  // Fujiwara's bound on the magnitude of every root:
-  // 2 max(|c_{n-1}/c_n|, |c_{n-2}/c_n|^(1/2), ..., |c_0/(2 c_n)|^(1/n))
-  double bound = 0.0;
-  for (int i = 0; i < deg; ++i) {
-    double r = fabs(c[i] / c[deg]);
-    if (i == 0) r *= 0.5;
-    const int k = deg - i;
-    const double root = k == 1 ? r : (k == 2 ? sqrt(r) : (k == 3 ? cbrt(r) : sqrt(sqrt(r))));
-    bound = fmax(bound, root);
-  }
-  bound = 2.0 * bound * (1.0 + 1e-12) + 1e-300;
+  const double bound = vd_root_bound(c, deg);
   double lo = -bound;
   double flo = vd_poly_eval(c, deg, lo);
   int n = 0;

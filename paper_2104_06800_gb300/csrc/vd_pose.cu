@@ -211,15 +211,7 @@ __device__ void vd_correspondence64(const DevParams& P, const double* __restrict
 // roots are bitwise the same; every lane receives all roots.
 __device__ int vd_roots_between_warp(const double* c, int deg, const double* crit, int ncrit,
                                      double* out, int lane) {
-  double bound = 0.0;
-  for (int i = 0; i < deg; ++i) {
-    double r = fabs(c[i] / c[deg]);
-    if (i == 0) r *= 0.5;
-    const int k = deg - i;
-    const double root = k == 1 ? r : (k == 2 ? sqrt(r) : (k == 3 ? cbrt(r) : sqrt(sqrt(r))));
-    bound = fmax(bound, root);
-  }
-  bound = 2.0 * bound * (1.0 + 1e-12) + 1e-300;
+  const double bound = vd_root_bound(c, deg);
   double lo = -bound;
   double flo = vd_poly_eval(c, deg, lo);
   double mlo = 0.0, mhi = 0.0;      // this lane's interval
