@@ -35,61 +35,91 @@ cudaError_t launch_initial_rho(vd_ctx* c) {
 
 // ---------------------------------------------------------------------------
 // Weighted normal matrix M = sum_j w_j r_j r_j^T, r_j = b (x) a, upper
-// triangle (45 entries), per-block partial sums in float64.
+// triangle (45 entries) accumulated in double-float, per-block partial
+// sums in float64.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double vd_sampson_px(const double* E, const double* a, const double* b,
-                                                double f) {
-  double Ea[3], Etb[3];
-  for (int i = 0; i < 3; ++i) {
-    Ea[i] = E[3 * i] * a[0] + E[3 * i + 1] * a[1] + E[3 * i + 2] * a[2];
-    Etb[i] = E[i] * b[0] + E[3 + i] * b[1] + E[6 + i] * b[2];
-  }
-  const double num = b[0] * Ea[0] + b[1] * Ea[1] + b[2] * Ea[2];
-  const double den = Ea[0] * Ea[0] + Ea[1] * Ea[1] + Etb[0] * Etb[0] + Etb[1] * Etb[1];
-  return f * fabs(num) / sqrt(fmax(den, 1e-300));
+
+// Double-float arithmetic (value = hi + lo, |lo| <= ulp(hi) / 2; Dekker 1971,
+// Knuth's TwoSum): about 2^-44 per operation on the float32 pipes, which
+// are 64 times wider than the float64 pipe of this GPU.
+struct VdDF {
+  float hi, lo;
+};
+__device__ __forceinline__ VdDF vd_df(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ VdDF vd_df_mul(VdDF a, VdDF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);          // exact error of the product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = p + e;
+  return {s, e - (s - p)};
+}
+__device__ __forceinline__ VdDF vd_df_add(VdDF a, VdDF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float err = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum
+  err += a.lo + b.lo;
+  const float t = s + err;
+  return {t, err - (t - s)};
 }
 
 __global__ void __launch_bounds__(EP_THREADS)
 k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restrict__ Eprev,
             int weighted, double* __restrict__ partial) {
   __shared__ double sW[EP_THREADS / 32][45];
-  double acc[45];
+  VdDF acc[45];
 #pragma unroll
-  for (int i = 0; i < 45; ++i) acc[i] = 0.0;
-  double E[9];
-  for (int i = 0; i < 9; ++i) E[i] = weighted ? Eprev[i] : 0.0;
-  const double f = sqrt(P.fx_d * P.fy_d);
-  const double ia = 1.0 / (double)P.alpha0;
+  for (int i = 0; i < 45; ++i) acc[i] = {0.0f, 0.0f};
+  // the IRLS weight needs no extended precision: on noise-free flow every
+  // row is orthogonal to E whatever the weights, on noisy flow a 1e-7
+  // relative weight error moves E far below the pose tolerance
+  float Ef[9];
+  for (int i = 0; i < 9; ++i) Ef[i] = weighted ? (float)Eprev[i] : 0.0f;
+  const float ff = (float)sqrt(P.fx_d * P.fy_d);
+  const float ia = 1.0f / P.alpha0;
+  const double ifx = 1.0 / P.fx_d, ify = 1.0 / P.fy_d;
   const size_t npix = (size_t)P.W * P.H;
   for (size_t j = (size_t)blockIdx.x * EP_THREADS + threadIdx.x; j < npix;
        j += (size_t)gridDim.x * EP_THREADS) {
     const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
     const float2 F = flow[j];
-    const double a[3] = {((double)u - P.cx_d) / P.fx_d, ((double)v - P.cy_d) / P.fy_d, 1.0};
-    const double b[3] = {((double)u + (double)F.x - P.cx_d) / P.fx_d,
-                         ((double)v + (double)F.y - P.cy_d) / P.fy_d, 1.0};
-    double w = 1.0;
+    const double a0 = ((double)u - P.cx_d) * ifx, a1 = ((double)v - P.cy_d) * ify;
+    const double b0 = ((double)u + (double)F.x - P.cx_d) * ifx;
+    const double b1 = ((double)v + (double)F.y - P.cy_d) * ify;
+    float w = 1.0f;
     if (weighted) {
-      const double d = vd_sampson_px(E, a, b, f) * ia;
-      w = 1.0 / (1.0 + d * d);
+      const float af[3] = {(float)a0, (float)a1, 1.0f}, bf[3] = {(float)b0, (float)b1, 1.0f};
+      float Ea[3], Etb[3];
+      for (int i = 0; i < 3; ++i) {
+        Ea[i] = Ef[3 * i] * af[0] + Ef[3 * i + 1] * af[1] + Ef[3 * i + 2] * af[2];
+        Etb[i] = Ef[i] * bf[0] + Ef[3 + i] * bf[1] + Ef[6 + i] * bf[2];
+      }
+      const float num = bf[0] * Ea[0] + bf[1] * Ea[1] + bf[2] * Ea[2];
+      const float den = Ea[0] * Ea[0] + Ea[1] * Ea[1] + Etb[0] * Etb[0] + Etb[1] * Etb[1];
+      const float d = ff * fabsf(num) * rsqrtf(fmaxf(den, 1e-30f)) * ia;
+      w = 1.0f / (1.0f + d * d);
     }
-    double r[9];
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = 0; n < 3; ++n) r[3 * m + n] = b[m] * a[n];
+    // r = b (x) a with a2 = b2 = 1
+    const VdDF A0 = vd_df(a0), A1 = vd_df(a1), B0 = vd_df(b0), B1 = vd_df(b1);
+    const VdDF one = {1.0f, 0.0f};
+    VdDF r[9] = {vd_df_mul(B0, A0), vd_df_mul(B0, A1), B0,
+                 vd_df_mul(B1, A0), vd_df_mul(B1, A1), B1,
+                 A0,                A1,                one};
     int k = 0;
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-      const double wr = w * r[p];
+      const VdDF wr = vd_df_mul(r[p], {w, 0.0f});
 #pragma unroll
-      for (int q = p; q < 9; ++q) acc[k++] += wr * r[q];
+      for (int q = p; q < 9; ++q) acc[k] = vd_df_add(acc[k], vd_df_mul(wr, r[q])), ++k;
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 45; ++i) {
-    double x = acc[i];
+    double x = (double)acc[i].hi + (double)acc[i].lo;
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) sW[wid][i] = x;
   }
@@ -103,84 +133,105 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
 
 // Sum the partials (fixed order) and take the eigenvector of the smallest
 // eigenvalue as E (unit Frobenius norm), by inverse iteration on the
-// symmetric positive semi-definite M shifted by 1e-14 trace(M): Cholesky once,
-// then x <- (M + d I)^-1 x / |.| until the iterate stops moving.  `warm`
-// starts from the previous round's E, else from (1, ..., 1) / 3.
-__global__ void k_ep_solve(const double* __restrict__ partial, int nblk, double* __restrict__ Mout,
-                           double* __restrict__ Eio, int warm) {
+// symmetric positive semi-definite M shifted by 1e-14 trace(M): one warp;
+// lane 0 factors M + d I = L L^T, lanes 0..8 each solve one column of the
+// inverse, then every step x <- (M + d I)^-1 x / |x| is a 9-lane
+// matrix-vector product, until the iterate stops moving.  `warm` starts from
+// the previous round's E, else from (1, ..., 1) / 3.
+__global__ void __launch_bounds__(64)
+k_ep_solve(const double* __restrict__ partial, int nblk, double* __restrict__ Mout,
+           double* __restrict__ Eio, int warm) {
   __shared__ double sM[45];
-  if (threadIdx.x < 45) {
+  __shared__ double sA[81];   // L (lower triangle)
+  __shared__ double sRd[9];   // 1 / L_jj
+  __shared__ double sI[81];   // (M + d I)^-1, column-major by solving lane
+  const int tid = threadIdx.x;
+  if (tid < 45) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * 45 + threadIdx.x];
-    sM[threadIdx.x] = s;
-    Mout[threadIdx.x] = s;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * 45 + tid];
+    sM[tid] = s;
+    Mout[tid] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double A[81];
-  int k = 0;
-  double tr = 0.0;
-  for (int p = 0; p < 9; ++p)
-    for (int q = p; q < 9; ++q) {
-      A[9 * p + q] = sM[k];
-      A[9 * q + p] = sM[k];
-      if (p == q) tr += sM[k];
-      ++k;
+  if (tid >= 32) return;
+  if (tid == 0) {
+    double tr = 0.0;
+    int k = 0;
+    for (int p = 0; p < 9; ++p)
+      for (int q = p; q < 9; ++q) {
+        sA[9 * q + p] = sM[k];   // lower triangle, row q column p
+        if (p == q) tr += sM[k];
+        ++k;
+      }
+    const double shift = 1e-14 * tr + 1e-300;
+    for (int j = 0; j < 9; ++j) {
+      double d = sA[10 * j] + shift;
+      for (int m = 0; m < j; ++m) d -= sA[9 * j + m] * sA[9 * j + m];
+      d = fmax(d, shift);
+      const double r = vd_rsqrt64(d);
+      sRd[j] = r;
+      for (int i = j + 1; i < 9; ++i) {
+        double s = sA[9 * i + j];
+        for (int m = 0; m < j; ++m) s -= sA[9 * i + m] * sA[9 * j + m];
+        sA[9 * i + j] = s * r;
+      }
     }
-  const double shift = 1e-14 * tr + 1e-300;
-  for (int i = 0; i < 9; ++i) A[10 * i] += shift;
-  // Cholesky A = L L^T (lower triangle of A overwritten by L)
-  for (int j = 0; j < 9; ++j) {
-    double d = A[10 * j];
-    for (int m = 0; m < j; ++m) d -= A[9 * j + m] * A[9 * j + m];
-    d = sqrt(fmax(d, shift));
-    A[10 * j] = d;
-    for (int i = j + 1; i < 9; ++i) {
-      double s = A[9 * i + j];
-      for (int m = 0; m < j; ++m) s -= A[9 * i + m] * A[9 * j + m];
-      A[9 * i + j] = s / d;
-    }
   }
-  double x[9];
-  double nx = 0.0;
-  for (int i = 0; i < 9; ++i) {
-    x[i] = warm ? Eio[i] : 1.0 / 3.0;
-    nx += x[i] * x[i];
-  }
-  if (!(nx > 0.0) || !isfinite(nx)) {
-    for (int i = 0; i < 9; ++i) x[i] = 1.0 / 3.0;
-    nx = 1.0;
-  }
-  nx = sqrt(nx);
-  for (int i = 0; i < 9; ++i) x[i] /= nx;
-  for (int it = 0; it < 300; ++it) {
+  __syncwarp();
+  if (tid < 9) {   // column tid of the inverse: L L^T z = e_tid
     double y[9];
-    for (int i = 0; i < 9; ++i) {          // L y = x
-      double s = x[i];
-      for (int m = 0; m < i; ++m) s -= A[9 * i + m] * y[m];
-      y[i] = s / A[10 * i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double s = (i == tid) ? 1.0 : 0.0;
+#pragma unroll
+      for (int m = 0; m < i; ++m) s -= sA[9 * i + m] * y[m];
+      y[i] = s * sRd[i];
     }
-    for (int i = 8; i >= 0; --i) {         // L^T z = y
+#pragma unroll
+    for (int i = 8; i >= 0; --i) {
       double s = y[i];
-      for (int m = i + 1; m < 9; ++m) s -= A[9 * m + i] * y[m];
-      y[i] = s / A[10 * i];
+#pragma unroll
+      for (int m = i + 1; m < 9; ++m) s -= sA[9 * m + i] * y[m];
+      y[i] = s * sRd[i];
     }
-    double n = 0.0, dot = 0.0;
-    for (int i = 0; i < 9; ++i) n += y[i] * y[i];
-    n = sqrt(n);
-    for (int i = 0; i < 9; ++i) {
-      y[i] /= n;
-      dot += y[i] * x[i];
-    }
-    double diff = 0.0;
-    const double sg = dot < 0.0 ? -1.0 : 1.0;
-    for (int i = 0; i < 9; ++i) {
-      diff = fmax(diff, fabs(sg * y[i] - x[i]));
-      x[i] = sg * y[i];
-    }
-    if (diff < 1e-15) break;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sI[9 * tid + i] = y[i];
   }
-  for (int i = 0; i < 9; ++i) Eio[i] = x[i];
+  __syncwarp();
+  // lane i < 9 holds x_i
+  double xi = 0.0;
+  if (tid < 9) xi = warm ? Eio[tid] : 1.0 / 3.0;
+  double n2 = xi * xi;
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  if (!(n2 > 0.0) || !isfinite(n2)) {
+    xi = tid < 9 ? 1.0 / 3.0 : 0.0;
+    n2 = 1.0;
+  }
+  xi *= vd_rsqrt64(n2);
+  double prev_diff = 1e300;
+  for (int it = 0; it < 300; ++it) {
+    double yi = 0.0;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      const double xm = __shfl_sync(0xffffffffu, xi, m);
+      if (tid < 9) yi = fma(sI[9 * m + tid], xm, yi);   // inverse is symmetric
+    }
+    double n = yi * yi, dot = yi * xi;
+    for (int o = 16; o > 0; o >>= 1) {
+      n += __shfl_xor_sync(0xffffffffu, n, o);
+      dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    }
+    yi *= vd_rsqrt64(n);
+    const double sg = dot < 0.0 ? -1.0 : 1.0;
+    double diff = fabs(sg * yi - xi);
+    for (int o = 16; o > 0; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xffffffffu, diff, o));
+    xi = sg * yi;
+    // converged: a change at rounding level, or a change that stopped
+    // shrinking (rounding noise of an already converged iterate)
+    if (diff < 4e-15 || (diff < 1e-12 && diff >= 0.5 * prev_diff)) break;
+    prev_diff = diff;
+  }
+  if (tid < 9) Eio[tid] = xi;
 }
 
 // E = U diag(s) V^T with det U = det V = +1: the two rotations U W V^T and

@@ -63,7 +63,7 @@ __device__ __forceinline__ void vd_load_pose_smem(float* sPose, const float* __r
 #define VD_K1_BY 4
 #endif
 #ifndef VD_K1_MINB
-#define VD_K1_MINB 1
+#define VD_K1_MINB 6
 #endif
 
 template <int NF>
