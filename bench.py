@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Throughput of the dense-indirect EM (VOLDOR+, Sec. III-A) on one GPU per rank.
 
-One step = one whole window of EM on the KITTI-like driving workload
-(1216 x 368, N = 6 flows, K = 128 hypotheses, 8 EM iterations, S = 64 P3P
-samples per frame): the monocular bootstrap plus 8 iterations of depth
-M-step, rigidness E-step and pose M-step.  Inputs are synthetic
-(synth.make_window("driving1216", seed 2000 + rank)) and resident in HBM;
-L2 is flushed before every timed step.
+One step = a batch of --batch (default 8) whole windows of EM on the
+KITTI-like driving workload (1216 x 368, N = 6 flows, K = 128 hypotheses,
+8 EM iterations, S = 64 P3P samples per frame): per window the monocular
+bootstrap plus 8 iterations of depth M-step, rigidness E-step and pose
+M-step, all windows in one CUDA-graph launch (vd_batch_run).  Inputs are
+synthetic (synth.make_window("driving1216", ...)) and resident in HBM; L2 is
+flushed before every timed step.
 
 value  = pixel*frame*iterations per second over all ranks (W*H*N*8 per window)
-e2e    = the same metric through the C ABI with host buffers: flows pushed from
-         pinned host memory, inverse depth and poses read back, every step.
+single_window = the same for one window at a time (vd_bootstrap + vd_run_em),
+         with the per-stage breakdown.
+e2e    = the batched metric through the C ABI with host buffers: flows pushed
+         from pinned host memory, inverse depth and poses read back, every step.
 roofline = the depth-sampling kernel (the dominant kernel), FP32-issue bound:
-         algorithmic FP32 instructions per launch / its CUDA-event time.
+         algorithmic FP32 instructions per launch / its CUDA-event time in the
+         single-window run.
 cpu_baseline = the float64 oracle on a bounded crop of the same window.
 
 --impl reference times the oracle (the CPU definition of the method) instead.
@@ -60,6 +64,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=8, help="windows per step (one graph launch)")
     return ap.parse_args()
 
 
@@ -170,108 +175,151 @@ def cpu_cores_used():
 
 
 # ------------------------------------------------------------------ our arm
+def _timed(stream, flush, fn, steps):
+    """CUDA-event time of `steps` calls of fn on `stream`, L2 flushed before each."""
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
 def run_ours(args, rank, world, local, pg):
     import torch
     from paper_2104_06800_gb300 import build as B
     from paper_2104_06800_gb300 import voldor as V
     import synth
-
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
     V.load()
     stream = torch.cuda.current_stream(dev)
+    sptr = V.C.c_void_p(stream.cuda_stream)
     win = synth.make_window(WORK["name"], WORK["seed"] + rank)
     pr = win.params
     params = V.vd_params_default(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"],
                                  rho_max=pr["rho_max"], n_hyp=WORK["K"],
                                  n_pose_samples=WORK["S"], seed=WORK["seed"] + rank)
     W, H, N, iters = win.W, win.H, win.N, WORK["iters"]
-    ctx = V.vd_create(W, H, N, win.intrinsics, params, V.C.c_void_p(stream.cuda_stream))
+    units_per_window = W * H * N * iters
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # ---- one window at a time (latency, stage breakdown, kernel roofline)
+    ctx = V.vd_create(W, H, N, win.intrinsics, params, sptr)
     flows_dev = torch.from_numpy(win.flow).to(dev)
     for t in range(1, N + 1):
         V.vd_push_flow(ctx, t, flows_dev[t - 1])
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tune = V.vd_autotune(ctx)
 
-    def step():
+    def step1():
         V.vd_bootstrap(ctx)
         V.vd_run_em(ctx, iters, stats=False)
 
     for _ in range(args.warmup):
-        step()
+        step1()
+    torch.cuda.synchronize()
+    V.vd_profile_enable(ctx, True)
+    t1 = _timed(stream, flush, step1, args.steps)
+    torch.cuda.synchronize()
+    prof = V.vd_get_profile(ctx)
+    V.vd_profile_enable(ctx, False)
+    single_ms = statistics.median(t1)
+    smp = prof["depth_sample"]
+    launch_ms = smp["ms"] / max(smp["calls"], 1)
+    fp32 = W * H * WORK["K"] * fp32_per_pixel_hyp(N)
+    achieved = fp32 / (launch_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_depth_sample_q", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "launch_ms": round(launch_ms, 4),
+                "evals_per_s": round(W * H * N * WORK["K"] / (launch_ms / 1e3), 1),
+                "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)",
+                "measured_in": "single-window run, kernel timed alone (CUDA events)"}
+    stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
+    single = {"windows_per_s": round(1e3 / single_ms, 3), "ms_per_window": round(single_ms, 3),
+              "value": round(units_per_window / (single_ms / 1e3), 1),
+              "gpu_launches_per_window": int(prof["total_launches"] / args.steps),
+              "stage_ms_per_window": stages, "tune": tune}
+
+    # ---- a batch of windows in one graph launch (the headline throughput)
+    nb = max(1, args.batch)
+    bw = [win] + [synth.make_window(WORK["name"], WORK["seed"] + 100 * (rank + 1) + i)
+                  for i in range(1, nb)]
+    b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in bw], params, sptr)
+    for i, w in enumerate(bw):
+        fl = torch.from_numpy(w.flow).to(dev)
+        for t in range(1, N + 1):
+            V.vd_push_flow(V.vd_batch_window(b, i), t, fl[t - 1])
+    V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP | V.VD_BATCH_AUTOTUNE)
+
+    def stepb():
+        V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
+
+    for _ in range(args.warmup):
+        stepb()
     torch.cuda.synchronize()
     barrier(pg)
     clocks = Clocks(local)
     clocks.start()
-    V.vd_profile_enable(ctx, True)
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+    tb = _timed(stream, flush, stepb, args.steps)
     torch.cuda.synchronize()
-    prof = V.vd_get_profile(ctx)
-    V.vd_profile_enable(ctx, False)
     clk = clocks.stop()
     barrier(pg)
-    total_ms = sum(times)
-    total_ms = max_over_ranks(pg, total_ms, dev)
-    units_per_window = W * H * N * iters
-    value = units_per_window * args.steps * world / (total_ms / 1e3)
-    ms_per_step = total_ms / args.steps
-
-    # roofline of the depth-sampling kernel
-    smp = prof["depth_sample"]
-    launch_ms = smp["ms"] / max(smp["calls"], 1)
-    evals = W * H * N * WORK["K"]
-    fp32 = W * H * WORK["K"] * fp32_per_pixel_hyp(N)
-    achieved = fp32 / (launch_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_depth_sample", "achieved": round(achieved, 3),
-                "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "launch_ms": round(launch_ms, 4),
-                "evals_per_s": round(evals / (launch_ms / 1e3), 1),
-                "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)"}
-    stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
+    bstats = V.vd_batch_get_stats(b)
+    total_ms = max_over_ranks(pg, sum(tb), dev)
+    value = units_per_window * nb * args.steps * world / (total_ms / 1e3)
 
     e2e = None
     if not args.no_e2e:
-        host_flows = [torch.from_numpy(win.flow[t]).pin_memory() for t in range(N)]
+        host = [torch.from_numpy(w.flow).pin_memory() for w in bw]
         host_rho = torch.empty((H, W), dtype=torch.float32).pin_memory()
         n_e2e = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
         barrier(pg)
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            for t in range(N):
-                V.vd_push_flow(ctx, t + 1, host_flows[t].numpy())
-            V.vd_run_em(ctx, iters, stats=False)
-            V.vd_get_inv_depth(ctx, host_rho.numpy())
-            V.vd_get_poses(ctx, N)
+            for i in range(nb):
+                c = V.vd_batch_window(b, i)
+                for t in range(N):
+                    V.vd_push_flow(c, t + 1, host[i][t].numpy())
+            V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
+            for i in range(nb):
+                c = V.vd_batch_window(b, i)
+                V.vd_get_inv_depth(c, host_rho.numpy())
+                V.vd_get_poses(c, N)
         torch.cuda.synchronize()
         dt = max_over_ranks(pg, time.perf_counter() - t0, dev)
-        e2e = {"value": round(units_per_window * n_e2e * world / dt, 1), "unit": UNIT,
-               "h2d_bytes_per_step": int(win.flow.nbytes),
-               "d2h_bytes_per_step": int(W * H * 4 + (N + 1) * 12 * 8), "steps": n_e2e}
+        e2e = {"value": round(units_per_window * nb * n_e2e * world / dt, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(w.flow.nbytes for w in bw)),
+               "d2h_bytes_per_step": int(nb * (W * H * 4 + (N + 1) * 12 * 8)), "steps": n_e2e,
+               "path": "vd_push_flow from pinned host memory, vd_batch_run, vd_get_inv_depth + "
+                       "vd_get_poses per window"}
 
+    V.vd_batch_destroy(b)
     V.vd_destroy(ctx)
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "driving1216: 1216x368, N=6 flows, K=128 hypotheses, 8 EM "
-                                   "iterations, S=64 P3P samples, monocular bootstrap",
-                       "windows_per_step_per_gpu": 1, "l2": "flushed (256 MB write) before "
-                                                            "every timed step",
+            "config": {"workload": f"driving1216 x {nb} windows per step: 1216x368, N=6 flows, "
+                                   "K=128 hypotheses, 8 EM iterations, S=64 P3P samples, "
+                                   "monocular bootstrap; all windows in one CUDA-graph launch",
+                       "windows_per_step_per_gpu": nb,
+                       "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
-            "windows_per_s": round(args.steps * world / (total_ms / 1e3), 3),
+            "windows_per_s": round(nb * args.steps * world / (total_ms / 1e3), 3),
+            "single_window": single, "batch": bstats,
             "roofline": roofline, "stage_ms_per_window": stages,
-            "gpu_launches": int(prof["total_launches"]), "clocks": clk, "e2e": e2e}
+            "gpu_launches": int(bstats["kernels_per_run"] * args.steps), "clocks": clk,
+            "e2e": e2e}
     return line
 
 

@@ -223,6 +223,69 @@ vd_status vd_score_poses_noalloc(const float* points, const float* obs, int n,
                                  const double* poses, int m, const double* intrinsics,
                                  float beta, float p0, double* energies, void* cuda_stream);
 
+/* ---- Launch tuning (the paper has none: GPU launch shapes) ---------------
+ * Two launch shapes are tunable per context: the warps per block of the
+ * depth-sampling kernel (1, 2 or 4; default 4) and the blocks per SM of the
+ * dense pose scoring (1..4; default 2).  Neither changes any result bit
+ * except the float32 summation grouping of the pose scores (a rounding-level
+ * change).  vd_autotune times every variant on this window and keeps the
+ * fastest: it needs all flows pushed, and it OVERWRITES the EM state (it runs
+ * the bootstrap and one iteration to reach a representative state), so call
+ * it before vd_bootstrap.  Synchronises the stream. */
+typedef struct {
+  int k1_warps;                 /* 1, 2 or 4                                  */
+  int score_blocks_per_sm;      /* 1..4                                       */
+  float k1_ms[3];               /* measured, for 1, 2, 4 warps (0 if unset)   */
+  float score_ms[4];            /* measured, for 1..4 blocks per SM           */
+} vd_tune;
+vd_status vd_autotune(vd_ctx* ctx, vd_tune* out /* nullable */);
+vd_status vd_set_tune(vd_ctx* ctx, const vd_tune* tune);
+vd_status vd_get_tune(vd_ctx* ctx, vd_tune* out);
+
+/* ---- Batched EM over many windows (the paper has no counterpart: it runs
+ * one window at a time; a server or an offline job runs many) ------------
+ * A batch owns n independent windows (each its own vd_ctx, of its own size,
+ * N and parameters).  vd_batch_run runs the bootstrap (if asked) and
+ * n_iters EM iterations of every window as ONE CUDA graph: each window's
+ * kernel sequence is one branch, forked from and joined to the batch stream,
+ * so the latency-bound pose kernels of one window overlap the others' work.
+ * Each window's results are bit-identical to vd_bootstrap + vd_run_em on
+ * that window alone (same kernels, same order, same inputs).
+ *   - descs/params: n entries each; params may be NULL (defaults) or point
+ *     at one vd_params shared by all windows (params_stride = 0) or at n of
+ *     them (params_stride = 1).
+ *   - vd_batch_window gives window i's context for the per-window calls
+ *     (push flows and priors, set poses, read results).  Those calls run on
+ *     the batch stream; vd_set_stream on a window context is refused.
+ *   - The graph is captured on the first run and replayed while every
+ *     window starts from the same state as at capture (iteration counter,
+ *     bootstrap flag, prior kind, poses set, parameters, tuning); otherwise it
+ *     is captured again (vd_batch_stats counts captures).
+ *   - flags: VD_BATCH_BOOTSTRAP re-bootstraps every window first (a new
+ *     batch of flows); VD_BATCH_AUTOTUNE (with BOOTSTRAP) first tunes one
+ *     window of every distinct (size, N, K, S, prior) and gives its choice to
+ *     the others.
+ *   - degenerate: optional int[n] receiving each window's count of frames
+ *     whose pose step kept the previous pose; the status is
+ *     VD_WARN_DEGENERATE if any is non-zero.
+ *   - Synchronises the batch stream. */
+typedef struct vd_batch vd_batch;
+#define VD_BATCH_BOOTSTRAP 1
+#define VD_BATCH_AUTOTUNE 2
+typedef struct {
+  int windows;
+  long long captures;           /* graph captures so far                     */
+  long long replays;            /* runs that reused the captured graph       */
+  long long graph_nodes;        /* nodes of the current graph                */
+  long long kernels_per_run;    /* kernel launches one run performs          */
+} vd_batch_stats;
+vd_status vd_batch_create(int n, const vd_window_desc* descs, const vd_params* params,
+                          int params_stride, void* cuda_stream, vd_batch** out);
+vd_status vd_batch_destroy(vd_batch* b);
+vd_status vd_batch_window(vd_batch* b, int i, vd_ctx** out);
+vd_status vd_batch_run(vd_batch* b, int n_iters, int flags, int* degenerate);
+vd_status vd_batch_get_stats(vd_batch* b, vd_batch_stats* out);
+
 /* State export/import for checkpoint and resume: a self-describing blob with
  * rho, q, q_hat, C, the poses, the iteration counter and the bootstrap flag.
  * Call export with blob = NULL to learn the size. */

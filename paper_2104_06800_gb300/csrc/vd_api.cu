@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "vd_internal.h"
@@ -173,6 +174,7 @@ static bool params_ok(const vd_params* p) {
 }
 
 static void fill_devparams(vd_ctx* c) {
+  ++c->cfg_version;
   DevParams& d = c->dp;
   const vd_params& p = c->prm;
   d.W = c->W;
@@ -219,8 +221,12 @@ static cudaError_t dalloc(T** p, size_t n) {
 
 extern "C" vd_status vd_destroy(vd_ctx* c) {
   if (!c) return VD_ERR_ARG;
+  if (c->batch_owned) {
+    vd_set_error("a batch window is destroyed with its batch");
+    return VD_ERR_STATE;
+  }
   void* ptrs[] = {c->flow, c->prior_val, c->prior_rho, c->prior_conf, c->rho, c->q, c->qhat,
-                  c->conf, c->G, c->posef, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
+                  c->conf, c->G, c->G_init, c->posef, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
                   c->coarse, c->lam, c->flags, c->blk_counts, c->blk_offsets, c->n_rigid,
                   c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->partial,
                   c->root_energy, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
@@ -257,7 +263,20 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   const size_t np = c->npix, N = c->N;
   const int S = VD_MAX_SAMPLES;
   c->nblk_scan = (int)((np + 255) / 256);
-  c->nblk_score = 2 * 152;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0 || vd_pose_prepare() != cudaSuccess) {
+      vd_set_error("cannot query the device");
+      delete c;
+      return VD_ERR_CUDA;
+    }
+    c->num_sms = sms;
+  }
+  c->k1_warps = 4;
+  c->score_bps = 2;
+  c->nblk_score = VD_SCORE_BPS_MAX * c->num_sms;   // capacity of the partial sums
   c->ep_blocks = 2 * 152;
   c->stat_blocks = 152;
   const int s = p.hier_scale;
@@ -272,6 +291,7 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(qhat, np);
   A(conf, np);
   A(G, 12 * (N + 1));
+  A(G_init, 12 * (N + 1));
   A(posef, 12 * (N + 1));
   A(rho_star, np);
   A(e_star, np);
@@ -312,6 +332,9 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   std::vector<double> G(12 * (N + 1), 0.0);
   for (size_t t = 0; t <= N; ++t) G[12 * t] = G[12 * t + 5] = G[12 * t + 10] = 1.0;
   e = cudaMemcpyAsync(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->G_init, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
+                        c->stream);
   if (e == cudaSuccess) e = launch_fill(c->q, 1.0f, N * np, c->stream);
   if (e == cudaSuccess) e = launch_fill(c->qhat, 1.0f, np, c->stream);
   if (e == cudaSuccess) e = launch_fill(c->prior_conf, 1.0f, np, c->stream);
@@ -332,6 +355,10 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
 
 extern "C" vd_status vd_set_stream(vd_ctx* c, void* stream) {
   if (!c) return VD_ERR_ARG;
+  if (c->batch_owned) {
+    vd_set_error("the stream of a batch window belongs to the batch");
+    return VD_ERR_STATE;
+  }
   c->stream = (cudaStream_t)stream;
   return VD_OK;
 }
@@ -467,9 +494,12 @@ extern "C" vd_status vd_set_poses(vd_ctx* c, const double* poses, vd_pose_kind k
   }
   VD_CU(cudaMemcpyAsync(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
                         c->stream));
+  VD_CU(cudaMemcpyAsync(c->G_init, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
+                        c->stream));
   VD_CU(launch_posef(c));
   VD_CU(cudaStreamSynchronize(c->stream));
   c->poses_set = 1;
+  ++c->cfg_version;
   return VD_OK;
 }
 
@@ -524,16 +554,21 @@ static cudaError_t posef_step(vd_ctx* c) {
   return e;
 }
 
-static cudaError_t depth_step(vd_ctx* c, int iter, int direction) {
+// One depth M-step.  boot: the monocular bootstrap's depth from X_1 alone
+// (one flow; timed with the rest of the bootstrap).
+static cudaError_t depth_step(vd_ctx* c, int iter, int direction, bool boot = false) {
   cudaError_t e = posef_step(c);
   if (e != cudaSuccess) return e;
-  vd_prof_begin(c, VD_ST_SAMPLE);
-  e = launch_depth_sample(c, itcode_of(iter), perturb_scale(iter), nullptr);
-  vd_prof_end(c, VD_ST_SAMPLE, 1);
+  const int nf = boot ? 1 : c->N;
+  const int st_sample = boot ? VD_ST_OTHER : VD_ST_SAMPLE;
+  const int st_prop = boot ? VD_ST_OTHER : VD_ST_PROPAGATE;
+  vd_prof_begin(c, st_sample);
+  e = launch_depth_sample(c, itcode_of(iter), perturb_scale(iter), nf);
+  vd_prof_end(c, st_sample, 1);
   if (e != cudaSuccess) return e;
-  vd_prof_begin(c, VD_ST_PROPAGATE);
-  e = launch_depth_propagate(c, direction);
-  vd_prof_end(c, VD_ST_PROPAGATE, c->prm.hierarchical ? 3 : 1);
+  vd_prof_begin(c, st_prop);
+  e = launch_depth_propagate(c, direction, nf);
+  vd_prof_end(c, st_prop, c->prm.hierarchical ? 3 : 1);
   return e;
 }
 
@@ -551,12 +586,17 @@ static cudaError_t pose_step(vd_ctx* c, int iter, int t) {
   return e;
 }
 
+// The bootstrap is a function of the inputs alone: it starts from the initial
+// poses (identity, or those of vd_set_poses), not from a previous run's.
 static cudaError_t bootstrap(vd_ctx* c) {
   vd_prof_begin(c, VD_ST_OTHER);
-  cudaError_t e = launch_initial_rho(c);
+  cudaError_t e = cudaMemcpyAsync(c->G, c->G_init, sizeof(double) * 12 * (c->N + 1),
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_posef(c);
+  if (e == cudaSuccess) e = launch_initial_rho(c);
   if (e == cudaSuccess) e = launch_fill(c->q, 1.0f, c->npix * c->N, c->stream);
   if (e == cudaSuccess) e = launch_fill(c->qhat, 1.0f, c->npix, c->stream);
-  int n = 3;
+  int n = 4;
   if (e == cudaSuccess && c->prior_kind == VD_PRIOR_NONE) {
     if (!c->poses_set) {
       e = launch_eight_point(c);
@@ -571,7 +611,7 @@ static cudaError_t bootstrap(vd_ctx* c) {
   if (e != cudaSuccess) return e;
   if (c->prior_kind == VD_PRIOR_NONE) {
     // depth from X_1 alone, then every flow rigid again
-    e = depth_step(c, -1, 0);
+    e = depth_step(c, -1, 0, true);
     if (e == cudaSuccess) e = launch_fill(c->q, 1.0f, c->npix * c->N, c->stream);
     vd_prof_end(c, VD_ST_OTHER, 1);
     if (e == cudaSuccess && !c->poses_set) e = pose_step(c, -1, 0);
@@ -599,25 +639,36 @@ extern "C" vd_status vd_bootstrap(vd_ctx* c) {
   return finish_sync(c, nullptr);
 }
 
-extern "C" vd_status vd_run_em(vd_ctx* c, int n_iters, vd_stats* stats) {
-  if (!c || n_iters < 0) return VD_ERR_ARG;
-  if (!flows_ready(c)) return VD_ERR_STATE;
-  VD_CU(cudaMemsetAsync(c->degenerate, 0, sizeof(int), c->stream));
-  int booted = 0;
-  if (!c->bootstrapped) {
-    VD_CU(bootstrap(c));
+// Bootstrap (when asked, or when the state is not bootstrapped) and n_iters
+// EM iterations of one window, issued on its stream without any host
+// synchronisation (so that the sequence can be captured into a graph).
+static cudaError_t enqueue_em(vd_ctx* c, int n_iters, bool boot, int* booted) {
+  cudaError_t e = cudaMemsetAsync(c->degenerate, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return e;
+  if (booted) *booted = 0;
+  if (boot || !c->bootstrapped) {
+    e = bootstrap(c);
+    if (e != cudaSuccess) return e;
     c->bootstrapped = 1;
     c->iter = 0;
-    booted = 1;
+    if (booted) *booted = 1;
   }
   for (int k = 0; k < n_iters; ++k) {
     const int i = c->iter;
     const int d = i & 3;
-    VD_CU(depth_step(c, i, d));
-    VD_CU(estep(c, d));
-    VD_CU(pose_step(c, i, 0));
+    if ((e = depth_step(c, i, d)) != cudaSuccess) return e;
+    if ((e = estep(c, d)) != cudaSuccess) return e;
+    if ((e = pose_step(c, i, 0)) != cudaSuccess) return e;
     c->iter = i + 1;
   }
+  return cudaSuccess;
+}
+
+extern "C" vd_status vd_run_em(vd_ctx* c, int n_iters, vd_stats* stats) {
+  if (!c || n_iters < 0) return VD_ERR_ARG;
+  if (!flows_ready(c)) return VD_ERR_STATE;
+  int booted = 0;
+  VD_CU(enqueue_em(c, n_iters, false, &booted));
   int deg = 0;
   vd_status st = finish_sync(c, &deg);
   if (st < 0) return st;
@@ -633,6 +684,325 @@ extern "C" vd_status vd_run_em(vd_ctx* c, int n_iters, vd_stats* stats) {
     stats->rigid_fraction = h[1] / (double)(c->npix * c->N);
   }
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// Launch tuning: time every launch shape of the two tunable kernels on this
+// window and keep the fastest (median of a few launches each).
+// ---------------------------------------------------------------------------
+static const int kK1Warps[3] = {1, 2, 4};
+
+static bool tune_ok(const vd_tune* t) {
+  return t && (t->k1_warps == 1 || t->k1_warps == 2 || t->k1_warps == 4) &&
+         t->score_blocks_per_sm >= 1 && t->score_blocks_per_sm <= VD_SCORE_BPS_MAX;
+}
+
+template <class F>
+static cudaError_t time_median(vd_ctx* c, int reps, F launch, float* ms_out) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  std::vector<float> t;
+  if (e == cudaSuccess) e = launch();   // warm-up
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(a, c->stream);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    t.push_back(ms);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return e;
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  return cudaSuccess;
+}
+
+extern "C" vd_status vd_autotune(vd_ctx* c, vd_tune* out) {
+  if (!c) return VD_ERR_ARG;
+  if (!flows_ready(c)) return VD_ERR_STATE;
+  const int prof = c->prof_on;
+  c->prof_on = 0;
+  vd_tune t;
+  memset(&t, 0, sizeof t);
+  // a representative state: the bootstrap and one EM iteration
+  cudaError_t e = enqueue_em(c, 1, true, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  const int it = c->iter;
+  float best = INFINITY;
+  t.k1_warps = c->k1_warps;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    c->k1_warps = kK1Warps[i];
+    e = time_median(c, 5, [&] { return launch_depth_sample(c, itcode_of(it), perturb_scale(it), c->N); },
+                    &t.k1_ms[i]);
+    if (e == cudaSuccess && t.k1_ms[i] < best) {
+      best = t.k1_ms[i];
+      t.k1_warps = kK1Warps[i];
+    }
+  }
+  best = INFINITY;
+  t.score_blocks_per_sm = c->score_bps;
+  for (int b = 1; b <= VD_SCORE_BPS_MAX && e == cudaSuccess; ++b) {
+    c->score_bps = b;
+    e = time_median(c, 5, [&] { return launch_pose_score_only(c); }, &t.score_ms[b - 1]);
+    if (e == cudaSuccess && t.score_ms[b - 1] < best) {
+      best = t.score_ms[b - 1];
+      t.score_blocks_per_sm = b;
+    }
+  }
+  c->prof_on = prof;
+  c->k1_warps = t.k1_warps;
+  c->score_bps = t.score_blocks_per_sm;
+  c->tune_meas = t;
+  ++c->cfg_version;
+  VD_CU(e);
+  if (out) *out = t;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_set_tune(vd_ctx* c, const vd_tune* t) {
+  if (!c || !tune_ok(t)) return VD_ERR_ARG;
+  c->k1_warps = t->k1_warps;
+  c->score_bps = t->score_blocks_per_sm;
+  ++c->cfg_version;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_get_tune(vd_ctx* c, vd_tune* out) {
+  if (!c || !out) return VD_ERR_ARG;
+  *out = c->tune_meas;
+  out->k1_warps = c->k1_warps;
+  out->score_blocks_per_sm = c->score_bps;
+  return VD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched EM: one CUDA graph runs the bootstrap and the iterations of every
+// window, one graph branch per window.
+// ---------------------------------------------------------------------------
+struct vd_batch {
+  std::vector<vd_ctx*> win;
+  std::vector<cudaStream_t> branch;    // capture streams, one per window
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t stream = nullptr;       // the batch stream (the caller's; may be the legacy stream)
+  cudaStream_t origin = nullptr;       // capture origin (a capture cannot start on the legacy stream)
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> key;          // launch signature of the captured graph
+  int* d_deg = nullptr;                // [n] degenerate counters, gathered by the graph
+  int* h_deg = nullptr;                // pinned host copy
+  vd_batch_stats st;
+};
+
+static void batch_free(vd_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (vd_ctx* c : b->win) {
+    c->batch_owned = 0;
+    vd_destroy(c);
+  }
+  for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->d_deg) cudaFree(b->d_deg);
+  if (b->h_deg) cudaFreeHost(b->h_deg);
+  delete b;
+}
+
+extern "C" vd_status vd_batch_create(int n, const vd_window_desc* descs, const vd_params* params,
+                                     int params_stride, void* stream, vd_batch** out) {
+  if (!out) return VD_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !descs || (params_stride != 0 && params_stride != 1)) return VD_ERR_ARG;
+  vd_batch* b = new vd_batch();
+  memset(&b->st, 0, sizeof b->st);
+  b->stream = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    vd_ctx* c = nullptr;
+    const vd_status s = vd_create(&descs[i], params ? params + (params_stride ? i : 0) : nullptr,
+                                  stream, &c);
+    if (s != VD_OK) {
+      batch_free(b);
+      return s;
+    }
+    c->batch_owned = 1;
+    b->win.push_back(c);
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branch.push_back(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->join.push_back(ev);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_deg, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_deg, sizeof(int) * n);
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    batch_free(b);
+    return e == cudaErrorMemoryAllocation ? VD_ERR_OOM : VD_ERR_CUDA;
+  }
+  b->st.windows = n;
+  *out = b;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_batch_destroy(vd_batch* b) {
+  if (!b) return VD_ERR_ARG;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return VD_OK;
+}
+
+extern "C" vd_status vd_batch_window(vd_batch* b, int i, vd_ctx** out) {
+  if (!b || !out || i < 0 || i >= (int)b->win.size()) return VD_ERR_ARG;
+  *out = b->win[i];
+  return VD_OK;
+}
+
+extern "C" vd_status vd_batch_get_stats(vd_batch* b, vd_batch_stats* out) {
+  if (!b || !out) return VD_ERR_ARG;
+  *out = b->st;
+  return VD_OK;
+}
+
+// Tune one window of every distinct launch configuration and hand its
+// choice to the windows that share it.
+static vd_status batch_autotune(vd_batch* b) {
+  const int n = (int)b->win.size();
+  std::vector<int> done(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (done[i]) continue;
+    vd_ctx* c = b->win[i];
+    const vd_status s = vd_autotune(c, nullptr);
+    if (s < 0) return s;
+    for (int k = i; k < n; ++k) {
+      vd_ctx* o = b->win[k];
+      if (o->W == c->W && o->H == c->H && o->N == c->N && o->dp.K == c->dp.K &&
+          o->dp.S == c->dp.S && o->prior_kind == c->prior_kind) {
+        done[k] = 1;
+        if (o != c && (o->k1_warps != c->k1_warps || o->score_bps != c->score_bps)) {
+          o->k1_warps = c->k1_warps;
+          o->score_bps = c->score_bps;
+          ++o->cfg_version;
+        }
+      }
+    }
+  }
+  return VD_OK;
+}
+
+static vd_status batch_capture(vd_batch* b, int n_iters, bool boot) {
+  const int n = (int)b->win.size();
+  std::vector<int> boot0(n), iter0(n);
+  long long launches0 = 0, launches1 = 0;
+  for (int i = 0; i < n; ++i) {
+    boot0[i] = b->win[i]->bootstrapped;
+    iter0[i] = b->win[i]->iter;
+    for (int k = 0; k < VD_N_STAGES; ++k) launches0 += b->win[i]->launches[k];
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  e = cudaEventRecord(b->fork, b->origin);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    vd_ctx* c = b->win[i];
+    const int prof = c->prof_on;
+    c->prof_on = 0;
+    c->stream = b->branch[i];
+    e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    if (e == cudaSuccess) e = enqueue_em(c, n_iters, boot, nullptr);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_deg + i, c->degenerate, sizeof(int), cudaMemcpyDeviceToDevice,
+                          c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[i], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    c->stream = b->stream;
+    c->prof_on = prof;
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+  }
+  size_t nodes = 0;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nodes);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < n; ++i) {   // nothing of the capture ran
+      b->win[i]->bootstrapped = boot0[i];
+      b->win[i]->iter = iter0[i];
+    }
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    b->key.clear();
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < VD_N_STAGES; ++k) launches1 += b->win[i]->launches[k];
+  b->st.captures += 1;
+  b->st.graph_nodes = (long long)nodes;
+  b->st.kernels_per_run = launches1 - launches0;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_batch_run(vd_batch* b, int n_iters, int flags, int* degenerate) {
+  if (!b || n_iters < 0 || (flags & ~(VD_BATCH_BOOTSTRAP | VD_BATCH_AUTOTUNE)) ||
+      ((flags & VD_BATCH_AUTOTUNE) && !(flags & VD_BATCH_BOOTSTRAP)))
+    return VD_ERR_ARG;
+  const int n = (int)b->win.size();
+  for (vd_ctx* c : b->win)
+    if (!flows_ready(c)) return VD_ERR_STATE;
+  const bool boot = (flags & VD_BATCH_BOOTSTRAP) != 0;
+  if (flags & VD_BATCH_AUTOTUNE) {
+    const vd_status s = batch_autotune(b);
+    if (s < 0) return s;
+  }
+  // signature of the launches this run issues
+  std::vector<long long> key = {n_iters, boot ? 1 : 0};
+  for (vd_ctx* c : b->win) {
+    key.push_back(c->cfg_version);
+    key.push_back(boot ? -1 : ((long long)c->bootstrapped << 32) + c->iter);
+  }
+  if (!b->exec || key != b->key) {
+    const vd_status s = batch_capture(b, n_iters, boot);
+    if (s < 0) return s;
+    b->key = key;
+  } else {
+    for (vd_ctx* c : b->win) {   // the host state the captured sequence leaves
+      if (boot || !c->bootstrapped) {
+        c->bootstrapped = 1;
+        c->iter = 0;
+      }
+      c->iter += n_iters;
+    }
+    b->st.replays += 1;
+  }
+  VD_CU(cudaGraphLaunch(b->exec, b->stream));
+  VD_CU(cudaMemcpyAsync(b->h_deg, b->d_deg, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream));
+  VD_CU(cudaStreamSynchronize(b->stream));
+  int any = 0;
+  for (int i = 0; i < n; ++i) {
+    if (degenerate) degenerate[i] = b->h_deg[i];
+    any |= b->h_deg[i] != 0;
+  }
+  return any ? VD_WARN_DEGENERATE : VD_OK;
 }
 
 extern "C" vd_status vd_depth_mstep(vd_ctx* c, int iter, int direction) {
@@ -781,10 +1151,17 @@ extern "C" vd_status vd_import_state(vd_ctx* c, const void* blob, size_t bytes) 
                         c->stream));
   VD_CU(cudaMemcpyAsync(c->G, (const double*)(f + nf), sizeof(double) * 12 * (c->N + 1),
                         cudaMemcpyHostToDevice, c->stream));
+  // a later bootstrap starts from the imported poses if they were set by the
+  // caller (the blob keeps no other copy of them), else from the identity
+  std::vector<double> I(12 * (c->N + 1), 0.0);
+  for (int t = 0; t <= c->N; ++t) I[12 * t] = I[12 * t + 5] = I[12 * t + 10] = 1.0;
+  VD_CU(cudaMemcpyAsync(c->G_init, h.poses_set ? (const void*)(f + nf) : (const void*)I.data(),
+                        sizeof(double) * 12 * (c->N + 1), cudaMemcpyHostToDevice, c->stream));
   VD_CU(launch_posef(c));
   VD_CU(cudaStreamSynchronize(c->stream));
   c->iter = h.iter;
   c->bootstrapped = h.bootstrapped;
   c->poses_set = h.poses_set;
+  ++c->cfg_version;
   return VD_OK;
 }

@@ -17,6 +17,19 @@
     default: return cudaErrorInvalidValue;  \
   }
 
+// The same for kernels that need at least two flows.
+#define VD_DISPATCH_NF2(N, KERNEL_CALL)     \
+  switch (N) {                              \
+    case 2: { constexpr int NF = 2; KERNEL_CALL; } break; \
+    case 3: { constexpr int NF = 3; KERNEL_CALL; } break; \
+    case 4: { constexpr int NF = 4; KERNEL_CALL; } break; \
+    case 5: { constexpr int NF = 5; KERNEL_CALL; } break; \
+    case 6: { constexpr int NF = 6; KERNEL_CALL; } break; \
+    case 7: { constexpr int NF = 7; KERNEL_CALL; } break; \
+    case 8: { constexpr int NF = 8; KERNEL_CALL; } break; \
+    default: return cudaErrorInvalidValue;  \
+  }
+
 // ---------------------------------------------------------------------------
 // float K R | K tau of every frame from the float64 absolute poses.
 // ---------------------------------------------------------------------------
@@ -114,6 +127,245 @@ k_depth_sample(DevParams P, const float* __restrict__ posef, const float2* __res
   }
   rho_star[j] = best;
   e_star[j] = bestE;
+}
+
+// Candidate of slot k >= 1 (the value k_depth_sample draws for that slot).
+__device__ __forceinline__ float vd_slot_candidate(const DevParams& P, uint32_t ctr0,
+                                                   uint32_t itcode, int k, float cur, float s_pert,
+                                                   bool has_prior, float prior_c) {
+  if (k == 1 && has_prior) return prior_c;
+  const int wi = k - 1;
+  const uint4 w =
+      vd_philox(make_uint4(ctr0, itcode, VD_TAG_DEPTH, (uint32_t)(wi >> 2)), P.key0, P.key1);
+  const uint32_t x = vd_word(w, wi & 3);
+  const float range = __fsub_rn(P.rho_max, P.rho_min);
+  const float c = (k <= (P.K - 1) / 2) ? vd_cand_uniform(x, P.rho_min, range)
+                                       : vd_cand_perturb(x, cur, s_pert);
+  return vd_clamp(c, P.rho_min, P.rho_max);
+}
+
+// ---------------------------------------------------------------------------
+// K1, staged schedule (N >= 2): the same candidates, energies and argmin as
+// k_depth_sample, scheduled so that pruning frees lanes instead of leaving
+// them idle.  A warp owns a row segment of 32 pixels.
+//  * Pre-pass (lane = pixel): draw four slots per pixel, add the prior and
+//    the X_1 term (neither needs a gather) and drop every candidate whose
+//    partial key already exceeds the pixel's best key; the survivors go to
+//    ring 1 in shared memory (most candidates end here).
+//  * Stage 1: while ring 1 holds a full chunk, lane i takes its i-th entry,
+//    of whichever pixel, adds flows 1..T1-1 and passes survivors to ring 2.
+//  * Stage 2: full chunks of ring 2 add flows T1..N-1; a finished candidate
+//    folds its key into the pixel's best key with atomicMin.
+// Partial chunks wait for more entries until the last pre-pass.
+// Key = energy bits << 32 | slot.  Energies are >= 0, so key order is
+// (energy, slot) order and the minimum key is the argmin with ties to the
+// lowest slot.  Dropping a candidate whose partial key exceeds a pixel's best
+// key is exact: terms are non-negative, so its full key is at least the
+// partial key, and the best key is that of a finished candidate.
+// Ring bounds: the pre-pass runs only with fewer than 32 entries in ring 1
+// and adds at most 128; a stage-1 chunk runs only with fewer than 32 entries
+// in ring 2 and adds at most 32.
+// ---------------------------------------------------------------------------
+#define VD_KQ_R1 160
+#define VD_KQ_R2 64
+// resident blocks requested from the register allocator for 4 warps per
+// block (scaled for other block sizes)
+#ifndef VD_KQ_MINB
+#define VD_KQ_MINB 5
+#endif
+#ifndef VD_KQ_T1
+#define VD_KQ_T1 3
+#endif
+
+// Flows [TA, TB) of one entry; false as soon as its key exceeds `bound`.
+template <int TA, int TB>
+__device__ __forceinline__ bool vd_stage_terms(const DevParams& P, const float4 (*sTw)[32],
+                                               const float4* sTail,
+                                               const float2* __restrict__ flow, size_t npix,
+                                               int p, unsigned slot, unsigned long long bound,
+                                               float c, float& E, float& xp, float& yp) {
+  const float NaN = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int t = TA; t < TB; ++t) {
+    const float4 A = sTw[t - 1][p];
+    const float4 M = sTail[t];
+    const float hx = fmaf(c, M.x, A.x);
+    const float hy = fmaf(c, M.y, A.y);
+    const float hz = fmaf(c, M.z, A.z);
+    const bool obs = vd_inside(xp, yp, P.W, P.H);   // false for NaN: behind camera t-1
+    float2 F = make_float2(0.0f, 0.0f);
+    if (obs) F = vd_bilinear(flow + (size_t)t * npix, P.W, P.H, xp, yp);
+    float x, y;
+    bool front;
+    const float l2 = vd_flow_term(P, hx, hy, hz, obs, F.x, F.y, xp, yp, &x, &y, &front);
+    E = fmaf(A.w, l2, E);
+    xp = front ? x : NaN;
+    yp = y;
+    if ((((unsigned long long)__float_as_uint(E) << 32) | slot) > bound) return false;
+  }
+  return true;
+}
+
+template <int NF, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS, (4 * VD_KQ_MINB) / WARPS)
+k_depth_sample_q(DevParams P, const float* __restrict__ posef, const float2* __restrict__ flow,
+                 const float* __restrict__ rho, const float* __restrict__ q,
+                 const float* __restrict__ prior_val, const float* __restrict__ prior_rho,
+                 const float* __restrict__ qhat, const float* __restrict__ pconf,
+                 uint32_t itcode, float s_pert, float* __restrict__ rho_star,
+                 float* __restrict__ e_star) {
+  static_assert(NF >= 2, "the staged schedule needs a gathered flow term");
+  constexpr int T1 = NF < VD_KQ_T1 ? NF : VD_KQ_T1;  // stage 1: flows [1, T1), stage 2: [T1, NF)
+  __shared__ float sPose[12 * (VD_MAX_FLOWS + 1)];
+  __shared__ float4 sTail[NF];                     // K tau of frame t+1 for flow t
+  __shared__ float4 sT[WARPS][NF - 1][32];   // (a_x, a_y, a_z, q ln2) of flows 1..NF-1
+  __shared__ float4 sR1[WARPS][VD_KQ_R1];    // (c, E, x, y) after flow T-1
+  __shared__ float4 sR2[WARPS][VD_KQ_R2];
+  __shared__ unsigned short sI1[WARPS][VD_KQ_R1];  // lane | slot << 5
+  __shared__ unsigned short sI2[WARPS][VD_KQ_R2];
+  __shared__ unsigned long long sBest[WARPS][32];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 12 * (NF + 1); i += blockDim.x) sPose[i] = posef[i];
+  if (tid < NF)
+    sTail[tid] = make_float4(posef[12 * (tid + 1) + 9], posef[12 * (tid + 1) + 10],
+                             posef[12 * (tid + 1) + 11], 0.0f);
+  __syncthreads();
+  const int lane = tid & 31, wq = tid >> 5;
+  const int u = blockIdx.x * 32 + lane;
+  const int v = blockIdx.y * WARPS + wq;
+  if (v >= P.H) return;                          // whole warps leave together
+  const bool valid = u < P.W;
+  const int uc = min(u, P.W - 1);
+  const size_t npix = (size_t)P.W * P.H;
+  const size_t j = (size_t)v * P.W + uc;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned lt = (1u << lane) - 1u;
+  const float NaN = __int_as_float(0x7fc00000);
+
+  VdPixel<NF> px;
+  vd_pixel_setup<NF>(px, P, sPose, uc, v, q, npix, j, flow, prior_val, qhat, pconf);
+#pragma unroll
+  for (int t = 1; t < NF; ++t)
+    sT[wq][t - 1][lane] = make_float4(px.ax[t], px.ay[t], px.az[t], px.wl[t]);
+  const float rmin = P.rho_min, rmax = P.rho_max;
+  const float range = __fsub_rn(rmax, rmin);
+  const float cur = rho[j];
+  const float cur_c = vd_clamp(cur, rmin, rmax);
+  {
+    const float E0 = vd_energy<NF>(px, P, sPose, flow, npix, cur_c);
+    sBest[wq][lane] = valid ? ((unsigned long long)__float_as_uint(E0) << 32) : 0ull;
+  }
+  const uint32_t ctr0 = (uint32_t)(j - (size_t)(uc % P.share));
+  const int n_unif = (P.K - 1) / 2;
+  bool has_prior = false;
+  float prior_c = 0.0f;
+  if (P.prior_kind != VD_PRIOR_NONE) {
+    const float pr = prior_rho[j];
+    has_prior = isfinite(pr);
+    prior_c = vd_clamp(pr, rmin, rmax);
+  }
+  const float4 tail0 = sTail[0];
+  const float4 (*sTw)[32] = sT[wq];
+  unsigned long long* sBw = sBest[wq];
+  __syncwarp();
+
+  int h1 = 0, e1 = 0, h2 = 0, e2 = 0, k0 = 1;
+  // one chunk of ring 2: flows T1..NF-1, then fold finished keys
+  auto stage2 = [&]() {
+    const int idx = h2 + lane;
+    if (idx < e2) {
+      const float4 e = sR2[wq][idx % VD_KQ_R2];
+      const unsigned id = sI2[wq][idx % VD_KQ_R2];
+      const int p = id & 31u;
+      const unsigned slot = id >> 5;
+      const unsigned long long bound = *(volatile unsigned long long*)&sBw[p];
+      float E = e.y, xp = e.z, yp = e.w;
+      if (vd_stage_terms<T1, NF>(P, sTw, sTail, flow, npix, p, slot, bound, e.x, E, xp, yp))
+        atomicMin(&sBw[p], ((unsigned long long)__float_as_uint(E) << 32) | slot);
+    }
+    h2 = min(h2 + 32, e2);
+    __syncwarp();
+  };
+  while (true) {
+    if (k0 < P.K) {
+      // pre-pass over slots k0 .. k0+3 of every pixel of the warp
+      const uint4 w = vd_philox(make_uint4(ctr0, itcode, VD_TAG_DEPTH, (uint32_t)((k0 - 1) >> 2)),
+                                P.key0, P.key1);
+      const unsigned long long bnd = *(volatile unsigned long long*)&sBw[lane];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        if (k >= P.K) break;
+        const uint32_t x = vd_word(w, i);
+        float cc = (k <= n_unif) ? vd_cand_uniform(x, rmin, range) : vd_cand_perturb(x, cur, s_pert);
+        cc = vd_clamp(cc, rmin, rmax);
+        if (k == 1 && has_prior) cc = prior_c;
+        float Ek = vd_prior_energy<NF>(px, P, cc);
+        const float hx = fmaf(cc, tail0.x, px.ax[0]);
+        const float hy = fmaf(cc, tail0.y, px.ay[0]);
+        const float hz = fmaf(cc, tail0.z, px.az[0]);
+        float x1, y1;
+        bool f1;
+        const float l2 = vd_flow_term(P, hx, hy, hz, true, px.f1x, px.f1y, px.u, px.v, &x1, &y1, &f1);
+        Ek = fmaf(px.wl[0], l2, Ek);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(Ek) << 32) | (unsigned)k;
+        const bool keep = valid && key < bnd;
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+          const int pos = (e1 + __popc(m & lt)) % VD_KQ_R1;
+          sR1[wq][pos] = make_float4(cc, Ek, f1 ? x1 : NaN, y1);
+          sI1[wq][pos] = (unsigned short)(lane | (k << 5));
+        }
+        e1 += __popc(m);
+      }
+      k0 += 4;
+      __syncwarp();
+    }
+    const bool last = k0 >= P.K;
+    while (e1 - h1 >= 32 || (last && e1 > h1)) {
+      // one chunk of ring 1: flows 1..T1-1
+      const int idx = h1 + lane;
+      bool keep = false;
+      float4 st = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      unsigned id = 0;
+      if (idx < e1) {
+        st = sR1[wq][idx % VD_KQ_R1];
+        id = sI1[wq][idx % VD_KQ_R1];
+        const int p = id & 31u;
+        const unsigned slot = id >> 5;
+        const unsigned long long bound = *(volatile unsigned long long*)&sBw[p];
+        keep = vd_stage_terms<1, T1>(P, sTw, sTail, flow, npix, p, slot, bound, st.x, st.y, st.z,
+                                     st.w);
+        if (T1 == NF && keep)
+          atomicMin(&sBw[p], ((unsigned long long)__float_as_uint(st.y) << 32) | slot);
+      }
+      h1 = min(h1 + 32, e1);
+      if (T1 < NF) {
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (keep) {
+          const int pos = (e2 + __popc(m & lt)) % VD_KQ_R2;
+          sR2[wq][pos] = st;
+          sI2[wq][pos] = (unsigned short)id;
+        }
+        e2 += __popc(m);
+        __syncwarp();
+        while (e2 - h2 >= 32) stage2();
+      } else {
+        __syncwarp();
+      }
+    }
+    if (last) {
+      while (e2 > h2) stage2();
+      break;
+    }
+  }
+  __syncwarp();
+  if (!valid) return;
+  const unsigned long long kb = *(volatile unsigned long long*)&sBw[lane];
+  const int kslot = (int)(kb & 0xffffffffull);
+  rho_star[j] = kslot == 0 ? cur_c
+                           : vd_slot_candidate(P, ctr0, itcode, kslot, cur, s_pert, has_prior, prior_c);
+  e_star[j] = __uint_as_float((unsigned)(kb >> 32));
 }
 
 // ---------------------------------------------------------------------------
@@ -315,20 +567,40 @@ static inline dim3 pix_grid(const vd_ctx* c, dim3 blk) {
   return dim3((c->W + blk.x - 1) / blk.x, (c->H + blk.y - 1) / blk.y);
 }
 
-cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, const float*) {
+template <int WARPS>
+static cudaError_t launch_depth_sample_q(vd_ctx* c, uint32_t itcode, float s_pert, int nf) {
+  const dim3 blk(32 * WARPS);
+  const dim3 grd((c->W + 31) / 32, (c->H + WARPS - 1) / WARPS);
+  VD_DISPATCH_NF2(nf, (k_depth_sample_q<NF, WARPS><<<grd, blk, 0, c->stream>>>(
+                          c->dp, c->posef, c->flow, c->rho, c->q, c->prior_val, c->prior_rho,
+                          c->qhat, c->prior_conf, itcode, s_pert, c->rho_star, c->e_star)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, int nf) {
+#ifndef VD_K1_DIRECT
+  if (nf >= 2) {
+    switch (c->k1_warps) {
+      case 1: return launch_depth_sample_q<1>(c, itcode, s_pert, nf);
+      case 2: return launch_depth_sample_q<2>(c, itcode, s_pert, nf);
+      case 4: return launch_depth_sample_q<4>(c, itcode, s_pert, nf);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+#endif
   const dim3 blk(VD_K1_BX, VD_K1_BY);
   const dim3 grd = pix_grid(c, blk);
-  VD_DISPATCH_NF(c->N, (k_depth_sample<NF><<<grd, blk, 0, c->stream>>>(
+  VD_DISPATCH_NF(nf, (k_depth_sample<NF><<<grd, blk, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->rho, c->q, c->prior_val, c->prior_rho,
                             c->qhat, c->prior_conf, itcode, s_pert, c->rho_star, c->e_star)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_depth_propagate(vd_ctx* c, int direction) {
+cudaError_t launch_depth_propagate(vd_ctx* c, int direction, int nf) {
   const bool rows = (direction & 1) == 0;
   if (!c->prm.hierarchical) {
     const int nch = rows ? c->H : c->W;
-    VD_DISPATCH_NF(c->N, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
+    VD_DISPATCH_NF(nf, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                               c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                               c->rho_star, c->e_star, c->rho, direction, 0)));
     return cudaGetLastError();
@@ -336,20 +608,20 @@ cudaError_t launch_depth_propagate(vd_ctx* c, int direction) {
   const int s = c->prm.hier_scale;
   const int Wc = (c->W + s - 1) / s, Hc = (c->H + s - 1) / s;
   const int nchc = rows ? Hc : Wc;
-  VD_DISPATCH_NF(c->N, (k_hier_coarse<NF><<<(nchc + 63) / 64, 64, 0, c->stream>>>(
+  VD_DISPATCH_NF(nf, (k_hier_coarse<NF><<<(nchc + 63) / 64, 64, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                             c->rho_star, c->e_star, c->coarse, direction, s)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 blk(32, 4);
   const dim3 grd = pix_grid(c, blk);
-  VD_DISPATCH_NF(c->N, (k_hier_mix<NF><<<grd, blk, 0, c->stream>>>(
+  VD_DISPATCH_NF(nf, (k_hier_mix<NF><<<grd, blk, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                             c->rho_star, c->e_star, c->coarse, s, c->rho_mid, c->e_mid)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nch = rows ? c->H : c->W;
-  VD_DISPATCH_NF(c->N, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
+  VD_DISPATCH_NF(nf, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
                             c->rho_mid, c->e_mid, c->rho, direction, c->prm.hier_window)));
   return cudaGetLastError();

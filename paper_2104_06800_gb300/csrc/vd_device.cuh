@@ -18,10 +18,10 @@
 __device__ __forceinline__ uint4 vd_philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;   // one wide multiply per product
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
@@ -160,6 +160,54 @@ __device__ __forceinline__ void vd_pixel_setup(VdPixel<NF>& px, const DevParams&
   }
 }
 
+// Prior term w_hat l_hat(c) of E_j (0 where the pixel has no prior).
+template <int NF>
+__device__ __forceinline__ float vd_prior_energy(const VdPixel<NF>& px, const DevParams& P,
+                                                 float c) {
+  if (!(px.pw > 0.0f)) return 0.0f;
+  if (P.prior_kind == VD_PRIOR_STEREO) {
+    const float d = px.pv - P.fxb * c;
+    float y;
+    if (P.beta == 2.0f) {
+      const float s = fmaf(d * d, P.inv_a2, 1.0f);
+      y = P.c0 * s * s;
+    } else {
+      y = vd_ratio_general(P, d * d, P.alpha0);
+    }
+    return px.pw * VD_LN2 * vd_ell2(y);
+  }
+  const float res = px.pv - c;
+  const float sig = P.c_sigma * px.pv;
+  const float z = fmaf(res * res, 0.5f / (sig * sig), P.logk);
+  return px.pw * (z > 20.0f ? z : VD_LN2 * vd_ell2(__expf(z)));
+}
+
+// One flow term in log2 units.  (hx, hy, hz): homogeneous image point of the
+// candidate in frame t; (xp, yp): its image point in frame t-1, where the
+// flow (Fx, Fy) was read; obs: the point is in front of camera t-1 and
+// inside image t-1.  Writes the image point in frame t and whether it is in
+// front of camera t.
+__device__ __forceinline__ float vd_flow_term(const DevParams& P, float hx, float hy, float hz,
+                                              bool obs, float Fx, float Fy, float xp, float yp,
+                                              float* x_out, float* y_out, bool* front_out) {
+  const bool front = hz > VD_Z_EPS;
+  const float iz = __fdividef(1.0f, hz);
+  const float x = hx * iz, y = hy * iz;
+  float l2;
+  if (obs && front) {
+    const float dx = Fx - (x - xp);
+    const float dy = Fy - (y - yp);
+    const float r2 = fmaf(dx, dx, dy * dy);
+    l2 = vd_ell2(vd_ratio_y(P, r2, fmaf(Fx, Fx, Fy * Fy)));
+  } else {
+    l2 = obs ? (VD_L_BEHIND / VD_LN2) : 0.0f;
+  }
+  *x_out = x;
+  *y_out = y;
+  *front_out = front;
+  return l2;
+}
+
 // E_j(c): sum_t q_t l_t(c) + w_hat l_hat(c) in natural-log units.
 // Every term is non-negative, so once the partial sum reaches `bound` the
 // candidate cannot beat an energy of `bound`: the sum stops there and the
@@ -170,25 +218,7 @@ __device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParam
                                            const float* __restrict__ sPose,
                                            const float2* __restrict__ flow, size_t npix,
                                            float c, float bound = INFINITY) {
-  float E = 0.0f;
-  if (px.pw > 0.0f) {
-    if (P.prior_kind == VD_PRIOR_STEREO) {
-      const float d = px.pv - P.fxb * c;
-      float y;
-      if (P.beta == 2.0f) {
-        const float s = fmaf(d * d, P.inv_a2, 1.0f);
-        y = P.c0 * s * s;
-      } else {
-        y = vd_ratio_general(P, d * d, P.alpha0);
-      }
-      E = px.pw * VD_LN2 * vd_ell2(y);
-    } else {
-      const float res = px.pv - c;
-      const float sig = P.c_sigma * px.pv;
-      const float z = fmaf(res * res, 0.5f / (sig * sig), P.logk);
-      E = px.pw * (z > 20.0f ? z : VD_LN2 * vd_ell2(__expf(z)));
-    }
-  }
+  float E = vd_prior_energy<NF>(px, P, c);
   float xp = px.u, yp = px.v;
   bool front_prev = true;
 #pragma unroll
@@ -198,9 +228,6 @@ __device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParam
     const float hx = fmaf(c, M[9], px.ax[t]);
     const float hy = fmaf(c, M[10], px.ay[t]);
     const float hz = fmaf(c, M[11], px.az[t]);
-    const bool front = hz > VD_Z_EPS;
-    const float iz = __fdividef(1.0f, hz);
-    const float x = hx * iz, y = hy * iz;
     bool obs;
     float Fx, Fy;
     if (t == 0) {
@@ -214,15 +241,9 @@ __device__ __forceinline__ float vd_energy(const VdPixel<NF>& px, const DevParam
       Fx = F.x;
       Fy = F.y;
     }
-    float l2;
-    if (obs && front) {
-      const float dx = Fx - (x - xp);
-      const float dy = Fy - (y - yp);
-      const float r2 = fmaf(dx, dx, dy * dy);
-      l2 = vd_ell2(vd_ratio_y(P, r2, fmaf(Fx, Fx, Fy * Fy)));
-    } else {
-      l2 = obs ? (VD_L_BEHIND / VD_LN2) : 0.0f;
-    }
+    float x, y;
+    bool front;
+    const float l2 = vd_flow_term(P, hx, hy, hz, obs, Fx, Fy, xp, yp, &x, &y, &front);
     E = fmaf(px.wl[t], l2, E);
     xp = x;
     yp = y;

@@ -9,6 +9,7 @@
 
 #define VD_MAX_FLOWS 8
 #define VD_MAX_SAMPLES 256
+#define VD_SCORE_BPS_MAX 4          // pose-scoring blocks per SM, upper bound of vd_tune
 #define VD_MAX_ROOTS (4 * VD_MAX_SAMPLES)
 
 // Constants of the model that both hosts and kernels use.
@@ -71,6 +72,7 @@ struct vd_ctx {
   float* qhat;             // [H][W]
   float* conf;             // [H][W] Eq. 6
   double* G;               // [N+1][12] absolute poses
+  double* G_init;          // [N+1][12] poses every bootstrap starts from (identity or vd_set_poses)
   float* posef;            // [N+1][12] float K R | K tau
   int bootstrapped;
   int poses_set;
@@ -111,6 +113,14 @@ struct vd_ctx {
   int* ep_count;           // [4]
   int ep_blocks;
 
+  // launch shapes (vd_tune) and the device they were sized for
+  int num_sms;
+  int k1_warps;            // warps per block of the depth-sampling kernel
+  int score_bps;           // pose-scoring blocks per SM
+  int batch_owned;         // window of a vd_batch (stream owned by the batch)
+  vd_tune tune_meas;       // last vd_autotune measurement
+  long long cfg_version;   // bumped by every change that alters a captured launch
+
   // profiling: event pairs per recorded stage execution, launch counters
   int prof_on;
   void* prof;              // ProfState (vd_api.cu)
@@ -124,11 +134,17 @@ struct vd_ctx {
 
 // ---- launchers (one per translation unit family) --------------------------
 cudaError_t launch_posef(vd_ctx* c);
-cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, const float* q_override);
-cudaError_t launch_depth_propagate(vd_ctx* c, int direction);
+// nf: flows that enter the energy (c->N, or 1 for the depth-from-X_1 step of
+// the monocular bootstrap, where q_t = 0 for t > 1 makes the other terms 0).
+cudaError_t launch_depth_sample(vd_ctx* c, uint32_t itcode, float s_pert, int nf);
+cudaError_t launch_depth_propagate(vd_ctx* c, int direction, int nf);
 cudaError_t launch_eval_energy(vd_ctx* c, const float* rho_in, float* e_out);
 cudaError_t launch_estep(vd_ctx* c, int direction);
 cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t);
+// one dense scoring pass of the current roots (frame t's rigid set), for tuning
+cudaError_t launch_pose_score_only(vd_ctx* c);
+// function attributes set once per device before any launch or capture
+cudaError_t vd_pose_prepare(void);
 cudaError_t launch_initial_rho(vd_ctx* c);
 cudaError_t launch_eight_point(vd_ctx* c);
 cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t s);

@@ -9,7 +9,7 @@
 
 #define SCAN_BLOCK 256
 #define SCORE_THREADS 256
-#define SCORE_PPT 4
+#define SCORE_PPT 8
 
 // ---------------------------------------------------------------------------
 // Float64 track position x_{t-1} of pixel j at inverse depth rho (t >= 2).
@@ -403,11 +403,14 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
   for (int i = threadIdx.x; i < nwarp * M; i += SCORE_THREADS) sAcc[i] = 0.0f;
   __syncthreads();
   const int n = n_ptr ? *n_ptr : n_host;
-  const int per = (n + gridDim.x - 1) / gridDim.x;
-  const int beg = blockIdx.x * per;
+  // contiguous ranges of whole warps, so that only the last warp is ragged
+  const int per = (((n + gridDim.x - 1) / gridDim.x) + 31) & ~31;
+  const int beg = min(n, blockIdx.x * per);
   const int end = min(n, beg + per);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int base = beg; base < end; base += SCORE_THREADS * SCORE_PPT) {
+    // passes of this tile that hold at least one pixel (block-uniform)
+    const int kact = min(SCORE_PPT, (end - base + SCORE_THREADS - 1) / SCORE_THREADS);
     float4 pt[SCORE_PPT], ob[SCORE_PPT];
 #pragma unroll
     for (int k = 0; k < SCORE_PPT; ++k) {
@@ -416,7 +419,7 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
         pt[k] = rpts[i];
         ob[k] = robs[i];
       } else {
-        pt[k] = make_float4(0.f, 0.f, 1.f, 0.f);
+        pt[k] = make_float4(0.f, 0.f, 1.f, 0.f);   // weight 0
         ob[k] = make_float4(0.f, 0.f, 1.f, 0.f);
       }
     }
@@ -425,7 +428,8 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
       const float* Mr = sRoot + 12 * r;
       float acc = 0.0f;
 #pragma unroll
-      for (int k = 0; k < SCORE_PPT; ++k) acc += vd_score_term(P, Mr, pt[k], ob[k]);
+      for (int k = 0; k < SCORE_PPT; ++k)
+        if (k < kact) acc += vd_score_term(P, Mr, pt[k], ob[k]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) sAcc[wid * M + r] += acc;
@@ -659,6 +663,29 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   }
 }
 
+// Largest dynamic shared memory of the scoring kernel (VD_MAX_SAMPLES
+// samples of 4 roots), granted once per device so that no launch, and no
+// stream capture, has to change a function attribute.
+cudaError_t vd_pose_prepare(void) {
+  const size_t smem = sizeof(float) * (size_t)(4 * VD_MAX_SAMPLES) * (12 + SCORE_THREADS / 32);
+  return cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+// Dense scoring of the current roots against the current rigid set, then the
+// float64 sum of the block partials: score_bps blocks per SM.
+cudaError_t launch_pose_score_only(vd_ctx* c) {
+  const DevParams& P = c->dp;
+  const int M = 4 * P.S;
+  const size_t smem = sizeof(float) * (size_t)M * (12 + SCORE_THREADS / 32);
+  const int nblk = c->score_bps * c->num_sms;
+  k_pose_score<<<nblk, SCORE_THREADS, smem, c->stream>>>(
+      P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
+  k_root_energy<<<(M + 127) / 128, 128, 0, c->stream>>>(c->partial, nblk, M, c->root_count,
+                                                        c->root_energy);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   const DevParams& P = c->dp;
   vd_prof_begin(c, VD_ST_RIGID);
@@ -677,13 +704,7 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   k_roots_float<<<(M + 127) / 128, 128, 0, c->stream>>>(P, c->roots, c->root_count, c->rootsf);
   vd_prof_end(c, VD_ST_P3P, 2);
   vd_prof_begin(c, VD_ST_SCORE);
-  const size_t smem = sizeof(float) * (size_t)M * (12 + SCORE_THREADS / 32);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_pose_score<<<c->nblk_score, SCORE_THREADS, smem, c->stream>>>(
-      P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
-  k_root_energy<<<(M + 127) / 128, 128, 0, c->stream>>>(c->partial, c->nblk_score, M,
-                                                        c->root_count, c->root_energy);
+  launch_pose_score_only(c);
   vd_prof_end(c, VD_ST_SCORE, 2);
   vd_prof_begin(c, VD_ST_SELECT);
   // one thread per sample, a power of two (>= one warp) for the tree reduction

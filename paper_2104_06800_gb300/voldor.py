@@ -56,6 +56,20 @@ class vd_profile(C.Structure):
                 ("launches", C.c_longlong * VD_N_STAGES), ("total_launches", C.c_longlong)]
 
 
+class vd_tune(C.Structure):
+    _fields_ = [("k1_warps", C.c_int), ("score_blocks_per_sm", C.c_int),
+                ("k1_ms", C.c_float * 3), ("score_ms", C.c_float * 4)]
+
+
+class vd_batch_stats(C.Structure):
+    _fields_ = [("windows", C.c_int), ("captures", C.c_longlong), ("replays", C.c_longlong),
+                ("graph_nodes", C.c_longlong), ("kernels_per_run", C.c_longlong)]
+
+
+VD_BATCH_BOOTSTRAP = 1
+VD_BATCH_AUTOTUNE = 2
+
+
 class VoldorError(RuntimeError):
     def __init__(self, fn, status, lib):
         msg = lib.vd_status_str(status).decode()
@@ -94,6 +108,15 @@ _SIGS = {
     "vd_score_poses_noalloc": [_P, _P, C.c_int, _P, C.c_int, _P, C.c_float, C.c_float, _P, _P],
     "vd_profile_enable": [_P, C.c_int],
     "vd_get_profile": [_P, C.POINTER(vd_profile)],
+    "vd_autotune": [_P, C.POINTER(vd_tune)],
+    "vd_set_tune": [_P, C.POINTER(vd_tune)],
+    "vd_get_tune": [_P, C.POINTER(vd_tune)],
+    "vd_batch_create": [C.c_int, C.POINTER(vd_window_desc), C.POINTER(vd_params), C.c_int, _P,
+                        C.POINTER(_P)],
+    "vd_batch_destroy": [_P],
+    "vd_batch_window": [_P, C.c_int, C.POINTER(_P)],
+    "vd_batch_run": [_P, C.c_int, C.c_int, _P],
+    "vd_batch_get_stats": [_P, C.POINTER(vd_batch_stats)],
     "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
     "vd_import_state": [_P, _P, C.c_size_t],
 }
@@ -350,6 +373,72 @@ def vd_score_poses_noalloc(points, obs, poses, intrinsics, beta, p0, energies, s
           float(beta), float(p0), C.c_void_p(energies.data_ptr()),
           stream if stream is not None else current_stream())
     return energies
+
+
+def _tune_dict(t):
+    return dict(k1_warps=t.k1_warps, score_blocks_per_sm=t.score_blocks_per_sm,
+                k1_ms=list(t.k1_ms), score_ms=list(t.score_ms))
+
+
+def vd_autotune(ctx):
+    t = vd_tune()
+    _call("vd_autotune", ctx, C.byref(t))
+    return _tune_dict(t)
+
+
+def vd_set_tune(ctx, k1_warps, score_blocks_per_sm):
+    t = vd_tune()
+    t.k1_warps, t.score_blocks_per_sm = int(k1_warps), int(score_blocks_per_sm)
+    _call("vd_set_tune", ctx, C.byref(t))
+
+
+def vd_get_tune(ctx):
+    t = vd_tune()
+    _call("vd_get_tune", ctx, C.byref(t))
+    return _tune_dict(t)
+
+
+def vd_batch_create(windows, params=None, stream=None):
+    """windows: list of (W, H, N, (fx, fy, cx, cy)); params: None, one
+    vd_params for all, or a list with one per window."""
+    n = len(windows)
+    descs = (vd_window_desc * n)(*[vd_window_desc(int(W), int(H), int(N), *[float(v) for v in K])
+                                   for (W, H, N, K) in windows])
+    if params is None:
+        pp, stride = None, 0
+    elif isinstance(params, vd_params):
+        pp, stride = C.byref(params), 0
+    else:
+        arr = (vd_params * n)(*params)
+        pp, stride = arr, 1
+    h = C.c_void_p()
+    _call("vd_batch_create", n, descs, pp, stride,
+          stream if stream is not None else current_stream(), C.byref(h))
+    return h
+
+
+def vd_batch_destroy(batch):
+    _call("vd_batch_destroy", batch)
+
+
+def vd_batch_window(batch, i):
+    h = C.c_void_p()
+    _call("vd_batch_window", batch, int(i), C.byref(h))
+    return h
+
+
+def vd_batch_run(batch, n_iters, flags=VD_BATCH_BOOTSTRAP, n_windows=None):
+    """Returns the per-window degenerate-frame counts when n_windows is given."""
+    deg = (C.c_int * n_windows)() if n_windows else None
+    _call("vd_batch_run", batch, int(n_iters), int(flags), deg)
+    return list(deg) if deg is not None else None
+
+
+def vd_batch_get_stats(batch):
+    st = vd_batch_stats()
+    _call("vd_batch_get_stats", batch, C.byref(st))
+    return dict(windows=st.windows, captures=st.captures, replays=st.replays,
+                graph_nodes=st.graph_nodes, kernels_per_run=st.kernels_per_run)
 
 
 def vd_export_state(ctx):

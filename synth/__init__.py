@@ -106,15 +106,21 @@ class _Scene:
                 l = (d - n @ C) / den
             l = np.where((l > 1e-6) & np.isfinite(l), l, np.inf)
             lam = np.minimum(lam, l)
+        with np.errstate(divide="ignore"):
+            inv = [1.0 / D[..., k] for k in range(3)]
         for lo, hi in self.boxes:
             lo = np.asarray(lo, np.float64)
             hi = np.asarray(hi, np.float64)
-            with np.errstate(divide="ignore", invalid="ignore"):
-                inv = 1.0 / D
-                t1 = (lo - C) * inv
-                t2 = (hi - C) * inv
-            tmin = np.nanmax(np.minimum(t1, t2), axis=-1)
-            tmax = np.nanmin(np.maximum(t1, t2), axis=-1)
+            # slab test; fmax / fmin skip the NaN of a ray parallel to a slab
+            # face (0 * inf), as a NaN-ignoring max / min over the axes would
+            tmin = tmax = None
+            with np.errstate(invalid="ignore"):
+                for k in range(3):
+                    t1 = (lo[k] - C[k]) * inv[k]
+                    t2 = (hi[k] - C[k]) * inv[k]
+                    a, b = np.minimum(t1, t2), np.maximum(t1, t2)
+                    tmin = a if tmin is None else np.fmax(tmin, a)
+                    tmax = b if tmax is None else np.fmin(tmax, b)
             hit = (tmax >= tmin) & (tmin > 1e-6)
             lam = np.minimum(lam, np.where(hit, tmin, np.inf))
         lam = np.where(np.isfinite(lam), lam, 1e3)

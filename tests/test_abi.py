@@ -67,3 +67,34 @@ def test_struct_layouts_match_the_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b([a-z_0-9]+)\s*[,;]", body.replace("typedef struct {", ""))
     assert [f for f, _ in V.vd_params._fields_] == fields
+
+
+def _struct_fields(src, closing):
+    body = src[:src.index(closing)]
+    body = body[body.rindex("typedef struct {"):]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S).replace("typedef struct {", "")
+    return re.findall(r"\b([a-z_0-9]+)\s*(?:\[[A-Z0-9_]+\])?\s*[,;]", body)
+
+
+def test_tune_and_batch_structs_match_the_header():
+    from paper_2104_06800_gb300 import voldor as V
+    src = open(os.path.join(ROOT, "include", "voldor_em.h")).read()
+    assert [f for f, _ in V.vd_tune._fields_] == _struct_fields(src, "} vd_tune;")
+    assert [f for f, _ in V.vd_batch_stats._fields_] == _struct_fields(src, "} vd_batch_stats;")
+    assert V.VD_BATCH_BOOTSTRAP == 1 and V.VD_BATCH_AUTOTUNE == 2
+
+
+def test_batch_and_tune_argument_checks(lib):
+    """Argument validation of the batch and tuning calls needs no GPU."""
+    from paper_2104_06800_gb300 import voldor as V
+    h = V.C.c_void_p()
+    d = (V.vd_window_desc * 1)(V.vd_window_desc(10, 10, 3, 100.0, 100.0, 5.0, 5.0))
+    assert lib.vd_batch_create(0, d, None, 0, None, V.C.byref(h)) == V.VD_ERR_ARG
+    assert lib.vd_batch_create(1, None, None, 0, None, V.C.byref(h)) == V.VD_ERR_ARG
+    assert lib.vd_batch_create(1, d, None, 2, None, V.C.byref(h)) == V.VD_ERR_ARG
+    assert lib.vd_batch_run(None, 1, V.VD_BATCH_BOOTSTRAP, None) == V.VD_ERR_ARG
+    assert lib.vd_batch_window(None, 0, V.C.byref(h)) == V.VD_ERR_ARG
+    assert lib.vd_batch_destroy(None) == V.VD_ERR_ARG
+    t = V.vd_tune()
+    assert lib.vd_set_tune(None, V.C.byref(t)) == V.VD_ERR_ARG
+    assert lib.vd_autotune(None, None) == V.VD_ERR_ARG
