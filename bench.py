@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="windows per step (one graph launch)")
+    ap.add_argument("--phase", default="both", choices=["both", "single", "batch"],
+                    help="single: only the one-window run (for profiling); batch: skip it")
     return ap.parse_args()
 
 
@@ -212,6 +214,9 @@ def run_ours(args, rank, world, local, pg):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # ---- one window at a time (latency, stage breakdown, kernel roofline)
+    if args.phase == "batch":
+        return run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream, flush,
+                         dev, None, None, None)
     ctx = V.vd_create(W, H, N, win.intrinsics, params, sptr)
     flows_dev = torch.from_numpy(win.flow).to(dev)
     for t in range(1, N + 1):
@@ -247,7 +252,24 @@ def run_ours(args, rank, world, local, pg):
               "value": round(units_per_window / (single_ms / 1e3), 1),
               "gpu_launches_per_window": int(prof["total_launches"] / args.steps),
               "stage_ms_per_window": stages, "tune": tune}
+    V.vd_destroy(ctx)
+    if args.phase == "single":
+        return {"metric": METRIC, "value": single["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(single_ms, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "phase": "single",
+                "config": {"workload": "driving1216: one window per step"},
+                "single_window": single, "roofline": roofline,
+                "gpu_launches": int(prof["total_launches"])}
+    return run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream, flush, dev,
+                     single, roofline, stages)
 
+
+def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream, flush, dev,
+              single, roofline, stages):
+    import torch
+    W, H, N, iters = win.W, win.H, win.N, WORK["iters"]
+    units_per_window = W * H * N * iters
     # ---- a batch of windows in one graph launch (the headline throughput)
     nb = max(1, args.batch)
     bw = [win] + [synth.make_window(WORK["name"], WORK["seed"] + 100 * (rank + 1) + i)
@@ -303,7 +325,6 @@ def run_ours(args, rank, world, local, pg):
                        "vd_get_poses per window"}
 
     V.vd_batch_destroy(b)
-    V.vd_destroy(ctx)
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3),

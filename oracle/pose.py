@@ -117,7 +117,8 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
     it_code = philox.ITER_BOOT if it < 0 else int(it)
     rs = rigid_set(P, S, t, p)
     n = len(rs["j"])
-    out = dict(n_rigid=n, degenerate=False, samples=[], scores=[], roots=[], root_scores=[])
+    out = dict(n_rigid=n, degenerate=False, samples=[], scores=[], roots=[], root_scores=[],
+               tri_X=[], tri_bear=[])
     if n < 3:
         out["degenerate"] = True
         return out
@@ -128,6 +129,8 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
         if tri is None:
             out["roots"].append([])
             out["root_scores"].append([])
+            out["tri_X"].append(None)
+            out["tri_bear"].append(None)
             continue
         X3 = rs["X"][tri]
         xo = rs["xobs"][tri]
@@ -135,6 +138,8 @@ def pose_mstep_frame(P, S: model.State, t, it, p, detail=False):
         roots = sorted(p3p.solve(bear, X3), key=root_key)
         if detail:
             out["roots"].append(roots)
+            out["tri_X"].append(X3)
+            out["tri_bear"].append(bear)
         Es = [score(P, G, rs, p) for G in roots]
         if detail:
             out["root_scores"].append(Es)

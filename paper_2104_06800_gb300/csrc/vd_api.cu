@@ -196,6 +196,7 @@ static void fill_devparams(vd_ctx* c) {
   d.p0 = p.outlier_density;
   d.fast_beta2 = (p.fisk_beta == 2.0f && p.fisk_alpha1 == 0.0f) ? 1 : 0;
   d.c0 = (float)((double)p.outlier_density * M_PI * (double)p.fisk_alpha0 * p.fisk_alpha0);
+  d.log2c0 = (float)log2((double)p.outlier_density * M_PI * (double)p.fisk_alpha0 * p.fisk_alpha0);
   d.inv_a2 = (float)(1.0 / ((double)p.fisk_alpha0 * p.fisk_alpha0));
   d.cgen = (float)((double)p.outlier_density * 2.0 * M_PI / p.fisk_beta);
   d.gamma = p.gamma_stay;
@@ -276,6 +277,7 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   }
   c->k1_warps = 4;
   c->score_bps = 2;
+  c->score_threads = 256;
   c->nblk_score = VD_SCORE_BPS_MAX * c->num_sms;   // capacity of the partial sums
   c->ep_blocks = 2 * 152;
   c->stat_blocks = 152;
@@ -694,6 +696,7 @@ static const int kK1Warps[3] = {1, 2, 4};
 
 static bool tune_ok(const vd_tune* t) {
   return t && (t->k1_warps == 1 || t->k1_warps == 2 || t->k1_warps == 4) &&
+         (t->score_threads == 256 || t->score_threads == 512) &&
          t->score_blocks_per_sm >= 1 && t->score_blocks_per_sm <= VD_SCORE_BPS_MAX;
 }
 
@@ -745,17 +748,24 @@ extern "C" vd_status vd_autotune(vd_ctx* c, vd_tune* out) {
   }
   best = INFINITY;
   t.score_blocks_per_sm = c->score_bps;
-  for (int b = 1; b <= VD_SCORE_BPS_MAX && e == cudaSuccess; ++b) {
-    c->score_bps = b;
-    e = time_median(c, 5, [&] { return launch_pose_score_only(c); }, &t.score_ms[b - 1]);
-    if (e == cudaSuccess && t.score_ms[b - 1] < best) {
-      best = t.score_ms[b - 1];
-      t.score_blocks_per_sm = b;
+  t.score_threads = c->score_threads;
+  for (int ti = 0; ti < 2 && e == cudaSuccess; ++ti) {
+    c->score_threads = ti ? 512 : 256;
+    for (int b = 1; b <= VD_SCORE_BPS_MAX && e == cudaSuccess; ++b) {
+      c->score_bps = b;
+      float* ms = &t.score_ms[ti][b - 1];
+      e = time_median(c, 5, [&] { return launch_pose_score_only(c); }, ms);
+      if (e == cudaSuccess && *ms < best) {
+        best = *ms;
+        t.score_blocks_per_sm = b;
+        t.score_threads = c->score_threads;
+      }
     }
   }
   c->prof_on = prof;
   c->k1_warps = t.k1_warps;
   c->score_bps = t.score_blocks_per_sm;
+  c->score_threads = t.score_threads;
   c->tune_meas = t;
   ++c->cfg_version;
   VD_CU(e);
@@ -767,6 +777,7 @@ extern "C" vd_status vd_set_tune(vd_ctx* c, const vd_tune* t) {
   if (!c || !tune_ok(t)) return VD_ERR_ARG;
   c->k1_warps = t->k1_warps;
   c->score_bps = t->score_blocks_per_sm;
+  c->score_threads = t->score_threads;
   ++c->cfg_version;
   return VD_OK;
 }
@@ -776,6 +787,7 @@ extern "C" vd_status vd_get_tune(vd_ctx* c, vd_tune* out) {
   *out = c->tune_meas;
   out->k1_warps = c->k1_warps;
   out->score_blocks_per_sm = c->score_bps;
+  out->score_threads = c->score_threads;
   return VD_OK;
 }
 
@@ -887,9 +899,11 @@ static vd_status batch_autotune(vd_batch* b) {
       if (o->W == c->W && o->H == c->H && o->N == c->N && o->dp.K == c->dp.K &&
           o->dp.S == c->dp.S && o->prior_kind == c->prior_kind) {
         done[k] = 1;
-        if (o != c && (o->k1_warps != c->k1_warps || o->score_bps != c->score_bps)) {
+        if (o != c && (o->k1_warps != c->k1_warps || o->score_bps != c->score_bps ||
+                       o->score_threads != c->score_threads)) {
           o->k1_warps = c->k1_warps;
           o->score_bps = c->score_bps;
+          o->score_threads = c->score_threads;
           ++o->cfg_version;
         }
       }

@@ -176,16 +176,25 @@ __device__ __forceinline__ float vd_slot_candidate(const DevParams& P, uint32_t 
 #ifndef VD_KQ_T1
 #define VD_KQ_T1 3
 #endif
+#ifndef VD_KQ_PRE_UNROLL
+#define VD_KQ_PRE_UNROLL 1
+#endif
+#ifndef VD_KQ_STAGE_UNROLL
+#define VD_KQ_STAGE_UNROLL 8
+#endif
+#define VD_STR(x) #x
+#define VD_UNROLL(n) _Pragma(VD_STR(unroll n))
 
-// Flows [TA, TB) of one entry; false as soon as its key exceeds `bound`.
+// Flows [TA, TB) of one entry; false as soon as its partial energy exceeds
+// `thr`, the entry's drop threshold (see vd_drop_threshold).
 template <int TA, int TB>
 __device__ __forceinline__ bool vd_stage_terms(const DevParams& P, const float4 (*sTw)[32],
                                                const float4* sTail,
                                                const float2* __restrict__ flow, size_t npix,
-                                               int p, unsigned slot, unsigned long long bound,
-                                               float c, float& E, float& xp, float& yp) {
+                                               int p, float thr, float c, float& E, float& xp,
+                                               float& yp) {
   const float NaN = __int_as_float(0x7fc00000);
-#pragma unroll
+  VD_UNROLL(VD_KQ_STAGE_UNROLL)
   for (int t = TA; t < TB; ++t) {
     const float4 A = sTw[t - 1][p];
     const float4 M = sTail[t];
@@ -201,9 +210,20 @@ __device__ __forceinline__ bool vd_stage_terms(const DevParams& P, const float4 
     E = fmaf(A.w, l2, E);
     xp = front ? x : NaN;
     yp = y;
-    if ((((unsigned long long)__float_as_uint(E) << 32) | slot) > bound) return false;
+    if (E > thr) return false;
   }
   return true;
+}
+
+// The key test "partial key > best key" as one float compare: for energies
+// >= 0 the key order is the (energy, slot) order, so a candidate of a lower
+// slot than the best is dropped when its energy exceeds the best energy, and
+// one of a higher slot already when it equals it.
+__device__ __forceinline__ float vd_drop_threshold(unsigned long long best, unsigned slot) {
+  const float bE = __uint_as_float((unsigned)(best >> 32));
+  if (slot < (unsigned)best) return bE;
+  // the next float below bE (NaN stays NaN: a NaN best is beaten by any key)
+  return bE <= 0.0f ? -1.0f : __int_as_float(__float_as_int(bE) - 1);
 }
 
 template <int NF, int WARPS>
@@ -278,9 +298,9 @@ k_depth_sample_q(DevParams P, const float* __restrict__ posef, const float2* __r
       const unsigned id = sI2[wq][idx % VD_KQ_R2];
       const int p = id & 31u;
       const unsigned slot = id >> 5;
-      const unsigned long long bound = *(volatile unsigned long long*)&sBw[p];
+      const float thr = vd_drop_threshold(*(volatile unsigned long long*)&sBw[p], slot);
       float E = e.y, xp = e.z, yp = e.w;
-      if (vd_stage_terms<T1, NF>(P, sTw, sTail, flow, npix, p, slot, bound, e.x, E, xp, yp))
+      if (vd_stage_terms<T1, NF>(P, sTw, sTail, flow, npix, p, thr, e.x, E, xp, yp))
         atomicMin(&sBw[p], ((unsigned long long)__float_as_uint(E) << 32) | slot);
     }
     h2 = min(h2 + 32, e2);
@@ -292,7 +312,7 @@ k_depth_sample_q(DevParams P, const float* __restrict__ posef, const float2* __r
       const uint4 w = vd_philox(make_uint4(ctr0, itcode, VD_TAG_DEPTH, (uint32_t)((k0 - 1) >> 2)),
                                 P.key0, P.key1);
       const unsigned long long bnd = *(volatile unsigned long long*)&sBw[lane];
-#pragma unroll
+VD_UNROLL(VD_KQ_PRE_UNROLL)
       for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
         if (k >= P.K) break;
@@ -333,9 +353,8 @@ k_depth_sample_q(DevParams P, const float* __restrict__ posef, const float2* __r
         id = sI1[wq][idx % VD_KQ_R1];
         const int p = id & 31u;
         const unsigned slot = id >> 5;
-        const unsigned long long bound = *(volatile unsigned long long*)&sBw[p];
-        keep = vd_stage_terms<1, T1>(P, sTw, sTail, flow, npix, p, slot, bound, st.x, st.y, st.z,
-                                     st.w);
+        const float thr = vd_drop_threshold(*(volatile unsigned long long*)&sBw[p], slot);
+        keep = vd_stage_terms<1, T1>(P, sTw, sTail, flow, npix, p, thr, st.x, st.y, st.z, st.w);
         if (T1 == NF && keep)
           atomicMin(&sBw[p], ((unsigned long long)__float_as_uint(st.y) << 32) | slot);
       }

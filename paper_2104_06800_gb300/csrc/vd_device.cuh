@@ -89,6 +89,38 @@ __device__ __forceinline__ float vd_ell2(float y) {
   return y < 0.03125f ? ser : big;
 }
 
+// log2(1 + P0 / p1) of a residual with r2 = r^2 and Fisk scale alpha.  Where
+// the ratio y = P0 / p1 would overflow float32 (a residual of ~1e10 px and
+// beyond), log2(1 + y) equals log2 y to float32 precision and is taken in the
+// log domain; below that the value is vd_ell2(y).
+__device__ __forceinline__ float vd_l2_general(const DevParams& P, float r2, float alpha) {
+  float r = sqrtf(r2);
+  if (P.beta != 2.0f) r = fmaxf(r, VD_R_FLOOR);
+  const float s = r / alpha;
+  const float ls = __log2f(s);
+  const float sb = exp2f(P.beta * ls);
+  const float s2b = exp2f((2.0f - P.beta) * ls);
+  const float one = 1.0f + sb;
+  const float y = P.cgen * alpha * alpha * s2b * one * one;
+  if (y < 1e30f) return vd_ell2(y);
+  const float l1 = sb < 1e30f ? __log2f(one) : P.beta * ls;   // log2(1 + s^beta)
+  return __log2f(P.cgen * alpha * alpha) + (2.0f - P.beta) * ls + 2.0f * l1;
+}
+
+__device__ __forceinline__ float vd_l2_beta2(const DevParams& P, float r2) {
+  // beta = 2: P0 / p1 = P0 pi alpha^2 (1 + r^2 / alpha^2)^2
+  const float s = fmaf(r2, P.inv_a2, 1.0f);
+  const float y = P.c0 * s * s;
+  if (y < 1e30f) return vd_ell2(y);
+  return fmaf(2.0f, __log2f(s), P.log2c0);
+}
+
+// The flow term's log2(1 + P0 / p1): alpha = alpha0 + alpha1 |X_t(x)|.
+__device__ __forceinline__ float vd_l2_flow(const DevParams& P, float r2, float fmag2) {
+  if (P.fast_beta2) return vd_l2_beta2(P, r2);
+  return vd_l2_general(P, r2, fmaf(P.alpha1, sqrtf(fmag2), P.alpha0));
+}
+
 // ---------------------------------------------------------------------------
 // Bilinear sample of one flow field at (x, y), which must be inside the image.
 // Taps (x0, y0)..(x0+1, y0+1) with x0 = min(floor(x), W-2).
@@ -167,14 +199,8 @@ __device__ __forceinline__ float vd_prior_energy(const VdPixel<NF>& px, const De
   if (!(px.pw > 0.0f)) return 0.0f;
   if (P.prior_kind == VD_PRIOR_STEREO) {
     const float d = px.pv - P.fxb * c;
-    float y;
-    if (P.beta == 2.0f) {
-      const float s = fmaf(d * d, P.inv_a2, 1.0f);
-      y = P.c0 * s * s;
-    } else {
-      y = vd_ratio_general(P, d * d, P.alpha0);
-    }
-    return px.pw * VD_LN2 * vd_ell2(y);
+    const float l2 = P.beta == 2.0f ? vd_l2_beta2(P, d * d) : vd_l2_general(P, d * d, P.alpha0);
+    return px.pw * VD_LN2 * l2;
   }
   const float res = px.pv - c;
   const float sig = P.c_sigma * px.pv;
@@ -198,7 +224,7 @@ __device__ __forceinline__ float vd_flow_term(const DevParams& P, float hx, floa
     const float dx = Fx - (x - xp);
     const float dy = Fy - (y - yp);
     const float r2 = fmaf(dx, dx, dy * dy);
-    l2 = vd_ell2(vd_ratio_y(P, r2, fmaf(Fx, Fx, Fy * Fy)));
+    l2 = vd_l2_flow(P, r2, fmaf(Fx, Fx, Fy * Fy));
   } else {
     l2 = obs ? (VD_L_BEHIND / VD_LN2) : 0.0f;
   }

@@ -63,7 +63,8 @@ k_emission(DevParams P, const float* __restrict__ posef, const float2* __restric
     if (obs && front) {
       const float dx = F.x - (x - xp);
       const float dy = F.y - (y - yp);
-      l = __frcp_rn(vd_ratio_y(P, fmaf(dx, dx, dy * dy), fmaf(F.x, F.x, F.y * F.y)));
+      const float y = vd_ratio_y(P, fmaf(dx, dx, dy * dy), fmaf(F.x, F.x, F.y * F.y));
+      l = y < 1e30f ? __frcp_rn(y) : 0.0f;   // an overflowing (or 0 * inf) ratio: p1 / P0 = 0
     } else {
       l = obs ? 0.0f : 1.0f;
     }
@@ -85,7 +86,7 @@ k_emission(DevParams P, const float* __restrict__ posef, const float2* __restric
         } else {
           yv = vd_ratio_general(P, d * d, P.alpha0);
         }
-        qh = 1.0f / (1.0f + yv);
+        qh = yv < 1e30f ? 1.0f / (1.0f + yv) : 0.0f;
       } else {
         const float res = pv - c;
         const float sig = P.c_sigma * pv;

@@ -36,6 +36,7 @@ struct DevParams {
   float alpha0, alpha1, beta, p0;
   int fast_beta2;          // beta == 2 and alpha1 == 0: closed-form energy
   float c0;                // P0 * pi * alpha0^2
+  float log2c0;            // log2 c0
   float inv_a2;            // 1 / alpha0^2
   float cgen;              // P0 * 2 pi / beta (general path factor, times alpha^2)
   float gamma;
@@ -117,6 +118,7 @@ struct vd_ctx {
   int num_sms;
   int k1_warps;            // warps per block of the depth-sampling kernel
   int score_bps;           // pose-scoring blocks per SM
+  int score_threads;       // pose-scoring threads per block (256 or 512)
   int batch_owned;         // window of a vd_batch (stream owned by the batch)
   vd_tune tune_meas;       // last vd_autotune measurement
   long long cfg_version;   // bumped by every change that alters a captured launch

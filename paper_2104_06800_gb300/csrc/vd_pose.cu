@@ -381,40 +381,55 @@ __device__ __forceinline__ float vd_score_term(const DevParams& P, const float* 
   const float iz = __fdividef(1.0f, hz);
   const float dx = ob.x - hx * iz, dy = ob.y - hy * iz;
   const float r2 = fmaf(dx, dx, dy * dy);
-  float y;
-  if (P.fast_beta2) {
-    const float s = fmaf(r2, P.inv_a2, 1.0f);
-    y = P.c0 * s * s;
-  } else {
-    y = vd_ratio_general(P, r2, ob.z);
-  }
-  return pt.w * VD_LN2 * vd_ell2(y);
+  const float l2 = P.fast_beta2 ? vd_l2_beta2(P, r2) : vd_l2_general(P, r2, ob.z);
+  return pt.w * VD_LN2 * l2;
 }
 
-__global__ void __launch_bounds__(SCORE_THREADS)
+// Dynamic shared memory of k_pose_score<THREADS> for M roots.
+static inline size_t vd_score_smem(int M, int threads) {
+  return sizeof(float) * (size_t)M * (12 + threads / 32) + sizeof(int) * (size_t)(M + 1);
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
 k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restrict__ robs,
              const int* __restrict__ n_ptr, int n_host, const float* __restrict__ rootsf,
              const int* __restrict__ root_count, int M, float* __restrict__ partial) {
   extern __shared__ float smem[];
+  constexpr int nwarp = THREADS / 32;
   float* sRoot = smem;                       // M * 12
-  float* sAcc = smem + 12 * M;               // (SCORE_THREADS / 32) * M
-  const int nwarp = SCORE_THREADS / 32;
-  for (int i = threadIdx.x; i < 12 * M; i += SCORE_THREADS) sRoot[i] = rootsf[i];
-  for (int i = threadIdx.x; i < nwarp * M; i += SCORE_THREADS) sAcc[i] = 0.0f;
+  float* sAcc = smem + 12 * M;               // nwarp * M
+  int* sList = (int*)(sAcc + nwarp * M);     // the real roots, in index order
+  int* sNum = sList + M;
+  for (int i = threadIdx.x; i < 12 * M; i += THREADS) sRoot[i] = rootsf[i];
+  for (int i = threadIdx.x; i < nwarp * M; i += THREADS) sAcc[i] = 0.0f;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+    // compact the roots that exist (slot r & 3 below its sample's root count)
+    int cnt = 0;
+    for (int base = 0; base < M; base += 32) {
+      const int r = base + lane;
+      const bool ok = r < M && (!root_count || (r & 3) < root_count[r >> 2]);
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) sList[cnt + __popc(m & ((1u << lane) - 1u))] = r;
+      cnt += __popc(m);
+    }
+    if (lane == 0) *sNum = cnt;
+  }
   __syncthreads();
+  const int nroot = *sNum;
   const int n = n_ptr ? *n_ptr : n_host;
   // contiguous ranges of whole warps, so that only the last warp is ragged
   const int per = (((n + gridDim.x - 1) / gridDim.x) + 31) & ~31;
   const int beg = min(n, blockIdx.x * per);
   const int end = min(n, beg + per);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = beg; base < end; base += SCORE_THREADS * SCORE_PPT) {
+  for (int base = beg; base < end; base += THREADS * SCORE_PPT) {
     // passes of this tile that hold at least one pixel (block-uniform)
-    const int kact = min(SCORE_PPT, (end - base + SCORE_THREADS - 1) / SCORE_THREADS);
+    const int kact = min(SCORE_PPT, (end - base + THREADS - 1) / THREADS);
     float4 pt[SCORE_PPT], ob[SCORE_PPT];
 #pragma unroll
     for (int k = 0; k < SCORE_PPT; ++k) {
-      const int i = base + k * SCORE_THREADS + threadIdx.x;
+      const int i = base + k * THREADS + threadIdx.x;
       if (i < end) {
         pt[k] = rpts[i];
         ob[k] = robs[i];
@@ -423,8 +438,8 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
         ob[k] = make_float4(0.f, 0.f, 1.f, 0.f);
       }
     }
-    for (int r = 0; r < M; ++r) {
-      if (root_count && (r & 3) >= root_count[r >> 2]) continue;
+    for (int m = 0; m < nroot; ++m) {
+      const int r = sList[m];
       const float* Mr = sRoot + 12 * r;
       float acc = 0.0f;
 #pragma unroll
@@ -436,24 +451,38 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < M; r += SCORE_THREADS) {
+  for (int m = threadIdx.x; m < nroot; m += THREADS) {
+    const int r = sList[m];
     float s = 0.0f;
     for (int w = 0; w < nwarp; ++w) s += sAcc[w * M + r];
     partial[(size_t)r * gridDim.x + blockIdx.x] = s;
   }
 }
 
+// float64 sum of the block partials of every root that exists (infinity for
+// the others): one warp per root, each lane sums a strided subset, then a
+// fixed-order butterfly over the lanes.
 __global__ void k_root_energy(const float* __restrict__ partial, int nblk, int M,
                               const int* __restrict__ root_count, double* __restrict__ energy) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= M) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= M) return;                 // whole warps leave together
   if (root_count && (r & 3) >= root_count[r >> 2]) {
-    energy[r] = INFINITY;
+    if (lane == 0) energy[r] = INFINITY;
     return;
   }
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += (double)partial[(size_t)r * nblk + b];
-  energy[r] = s;
+  for (int b = lane; b < nblk; b += 32) s += (double)partial[(size_t)r * nblk + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) energy[r] = s;
+}
+
+static inline cudaError_t launch_root_energy(const float* partial, int nblk, int M,
+                                             const int* root_count, double* energy,
+                                             cudaStream_t s) {
+  k_root_energy<<<(M + 3) / 4, 128, 0, s>>>(partial, nblk, M, root_count, energy);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -525,26 +554,30 @@ __device__ __forceinline__ void vd_se3_exp_f(const float* xi, float* T) {
 }
 
 // ---------------------------------------------------------------------------
-// Per sample: the lowest-energy root; then mean-shift from the best sample:
-// x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
-// w_g = exp(-d^T Sigma^-1 d / 2), until |step| < 1e-12 or 100 steps.
-// One block of 256 threads, one sample per thread.
+// Per sample: the lowest-energy root; then mean-shift (Eq. 7) from the best
+// sample: x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
+// w_g = exp(-d^T Sigma^-1 d / 2), at most 100 steps.  The float64 definition
+// stops at |step| < 1e-12; these float32 iterations stop at the float32
+// floor of the relative poses, 1e-6 (1 + |tau|).  One warp: the sums are
+// warp butterflies, every lane updates the same mode, no block barrier.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32)
 k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __restrict__ root_count,
                    const double* __restrict__ root_energy, int t, double* __restrict__ G,
                    float* __restrict__ posef, double* __restrict__ sample_pose,
                    double* __restrict__ sample_energy, int* __restrict__ degenerate) {
-  __shared__ double sRed[256 * 7];
-  __shared__ int sIdx[256];
-  __shared__ double sX[12];
-  __shared__ int sDone;
-  const int g = threadIdx.x;
-  double Tg[12];
-  double Eg = INFINITY;
-  if (g < P.S) {
+  // one warp; lane l owns samples l, l + 32, ...
+  __shared__ float sT[VD_MAX_SAMPLES][12];
+  __shared__ unsigned char sValid[VD_MAX_SAMPLES];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  double bestE = INFINITY;
+  int bestS = 0x7fffffff;
+  for (int g = lane; g < P.S; g += 32) {
+    // the sample's lowest-energy root (ties: lower index in the sorted order)
     const int nr = root_count[g];
     int best = -1;
+    double Eg = INFINITY;
     for (int r = 0; r < nr; ++r) {
       const double e = root_energy[4 * g + r];
       if (best < 0 || e < Eg) {
@@ -552,114 +585,122 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
         best = r;
       }
     }
-    if (best >= 0) {
-      for (int i = 0; i < 12; ++i) Tg[i] = roots[(size_t)48 * g + 12 * best + i];
-    } else {
-      Eg = INFINITY;
+    const double* src = roots + (size_t)48 * g + 12 * (best < 0 ? 0 : best);
+    for (int i = 0; i < 12; ++i) {
+      const double v = best >= 0 ? src[i] : 0.0;
+      sample_pose[12 * g + i] = v;
+      sT[g][i] = (float)v;
     }
-    for (int i = 0; i < 12; ++i) sample_pose[12 * g + i] = best >= 0 ? Tg[i] : 0.0;
+    if (best < 0) Eg = INFINITY;
     sample_energy[g] = Eg;
-  }
-  const bool valid = g < P.S && Eg < INFINITY;
-  // argmin over samples (lowest energy, then lowest index)
-  sRed[g] = valid ? Eg : INFINITY;
-  sIdx[g] = g;
-  __syncthreads();
-  for (int off = (int)blockDim.x / 2; off > 0; off >>= 1) {
-    if (g < off) {
-      const double a = sRed[g], b = sRed[g + off];
-      const int ia = sIdx[g], ib = sIdx[g + off];
-      if (b < a || (b == a && ib < ia)) {
-        sRed[g] = b;
-        sIdx[g] = ib;
-      }
+    sValid[g] = Eg < INFINITY;
+    if (Eg < bestE) {           // g ascends per lane: ties keep the lower index
+      bestE = Eg;
+      bestS = g;
     }
-    __syncthreads();
   }
-  const int start = sIdx[0];
-  const bool any = sRed[0] < INFINITY;
-  __syncthreads();
-  if (!any) {
-    if (g == 0) atomicAdd(degenerate, 1);
+  // argmin over samples (lowest energy, then lowest index): a total order, so
+  // every lane ends with the same pair
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double oE = __shfl_xor_sync(FULL, bestE, o);
+    const int oS = __shfl_xor_sync(FULL, bestS, o);
+    if (oE < bestE || (oE == bestE && oS < bestS)) {
+      bestE = oE;
+      bestS = oS;
+    }
+  }
+  __syncwarp();
+  if (!(bestE < INFINITY)) {
+    if (lane == 0) atomicAdd(degenerate, 1);
     return;
   }
-  if (g == start)
-    for (int i = 0; i < 12; ++i) sX[i] = Tg[i];
-  __syncthreads();
-  const double tn = sqrt(sX[3] * sX[3] + sX[7] * sX[7] + sX[11] * sX[11]);
-  const double st_ = P.ms_sig_rel * tn + P.ms_sig_abs;
+  float x[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) x[i] = sT[bestS][i];
+  const float tn = sqrtf(x[3] * x[3] + x[7] * x[7] + x[11] * x[11]);
+  const double st_ = P.ms_sig_rel * (double)tn + P.ms_sig_abs;
   const float ivr = (float)(1.0 / (P.ms_sig_rot * P.ms_sig_rot)), ivt = (float)(1.0 / (st_ * st_));
-  // float32 iterations stop at this step norm (the float32 floor of the
+  // the float32 iterations stop at this step norm (the float32 floor of the
   // relative poses); the float64 definition stops at 1e-12
-  const float tol = (float)(VD_MS_TOL_F32 * (1.0 + tn));
-  float* sW = (float*)sRed;          // [8 warps][7]
-  const int lane = g & 31, wid = g >> 5;
-  float Tgf[12];
-  for (int i = 0; i < 12; ++i) Tgf[i] = valid ? (float)Tg[i] : 0.0f;
-  if (g == 0) sDone = 0;
-  __syncthreads();
+  const float tol = (float)(VD_MS_TOL_F32 * (1.0 + (double)tn));
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
-    float d[6] = {0, 0, 0, 0, 0, 0};
-    float w = 0.0f;
-    if (valid) {
-      // relative pose x^-1 T_g in float32 (translation error ~|tau| 2^-24,
-      // below the float32 stop tolerance)
-      float xf[12], relf[12];
-      for (int i = 0; i < 12; ++i) xf[i] = (float)sX[i];
+    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int g = lane; g < P.S; g += 32) {
+      if (!sValid[g]) continue;
+      const float* Tg = sT[g];
+      // relative pose x^-1 T_g (translation error ~|tau| 2^-24, below the stop tolerance)
+      float rel[12], d[6];
+#pragma unroll
       for (int r = 0; r < 3; ++r) {
+#pragma unroll
         for (int c = 0; c < 3; ++c)   // (R_x^T R_g)_{rc}
-          relf[4 * r + c] = xf[r] * Tgf[c] + xf[4 + r] * Tgf[4 + c] + xf[8 + r] * Tgf[8 + c];
+          rel[4 * r + c] = x[r] * Tg[c] + x[4 + r] * Tg[4 + c] + x[8 + r] * Tg[8 + c];
         // R_x^T (tau_g - tau_x)
-        relf[4 * r + 3] = xf[r] * (Tgf[3] - xf[3]) + xf[4 + r] * (Tgf[7] - xf[7]) +
-                          xf[8 + r] * (Tgf[11] - xf[11]);
+        rel[4 * r + 3] = x[r] * (Tg[3] - x[3]) + x[4 + r] * (Tg[7] - x[7]) +
+                         x[8 + r] * (Tg[11] - x[11]);
       }
-      if (vd_se3_log_f(relf, d)) {
+      if (vd_se3_log_f(rel, d)) {
         const float m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
                         (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
-        w = __expf(-0.5f * m);
+        const float w = __expf(-0.5f * m);
+        acc[0] += w;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[1 + i] += w * d[i];
       }
     }
-    float acc[7] = {w, w * d[0], w * d[1], w * d[2], w * d[3], w * d[4], w * d[5]};
+    // xor butterflies: float addition commutes, so partners hold equal sums
+    // after every level and all lanes end with the same totals
 #pragma unroll
     for (int i = 0; i < 7; ++i)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-    if (lane == 0)
-      for (int i = 0; i < 7; ++i) sW[wid * 7 + i] = acc[i];
-    __syncthreads();
-    if (g == 0) {
-      float s[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
-        for (int i = 0; i < 7; ++i) s[i] += sW[k * 7 + i];
-      float step[6];
-      float nrm = 0.0f;
-      for (int i = 0; i < 6; ++i) {
-        step[i] = s[1 + i] / s[0];
-        nrm += step[i] * step[i];
-      }
-      float Ef[12];
-      vd_se3_exp_f(step, Ef);
-      double E[12], xn[12], xo[12];
-      for (int i = 0; i < 12; ++i) {
-        E[i] = (double)Ef[i];
-        xo[i] = sX[i];
-      }
-      vd_compose(xo, E, xn);
-      for (int i = 0; i < 12; ++i) sX[i] = xn[i];
-      if (sqrtf(nrm) < tol) sDone = 1;
+      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(FULL, acc[i], o);
+    if (!(acc[0] > 0.0f)) break;
+    float step[6], nrm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      step[i] = acc[1 + i] / acc[0];
+      nrm += step[i] * step[i];
     }
-    __syncthreads();
-    if (sDone) break;
+    float E[12], xn[12];
+    vd_se3_exp_f(step, E);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {   // x <- x o exp(step)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        xn[4 * r + c] = x[4 * r] * E[c] + x[4 * r + 1] * E[4 + c] + x[4 * r + 2] * E[8 + c];
+      xn[4 * r + 3] = x[4 * r] * E[3] + x[4 * r + 1] * E[7] + x[4 * r + 2] * E[11] + x[4 * r + 3];
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) x[i] = xn[i];
+    if (sqrtf(nrm) < tol) break;
   }
-  if (g < 12) G[12 * t + g] = sX[g];
-  if (g == 0) {
-    // float K R | K tau of the updated pose
-    float* o = posef + 12 * t;
-    for (int i = 0; i < 4; ++i) {
-      o[i < 3 ? i : 9] = (float)(P.fx_d * sX[i] + P.cx_d * sX[8 + i]);
-      o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * sX[4 + i] + P.cy_d * sX[8 + i]);
-      o[i < 3 ? 6 + i : 11] = (float)sX[8 + i];
-    }
+  if (lane != 0) return;
+  // re-orthonormalise the rotation in float64 (Gram-Schmidt on the rows,
+  // third row as the cross product) and store the pose
+  double R[9], o[12];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) R[3 * r + c] = (double)x[4 * r + c];
+  double n0 = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+  for (int c = 0; c < 3; ++c) R[c] /= n0;
+  const double d01 = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
+  for (int c = 0; c < 3; ++c) R[3 + c] -= d01 * R[c];
+  const double n1 = sqrt(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
+  for (int c = 0; c < 3; ++c) R[3 + c] /= n1;
+  R[6] = R[1] * R[5] - R[2] * R[4];
+  R[7] = R[2] * R[3] - R[0] * R[5];
+  R[8] = R[0] * R[4] - R[1] * R[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) o[4 * r + c] = R[3 * r + c];
+    o[4 * r + 3] = (double)x[4 * r + 3];
+  }
+  for (int i = 0; i < 12; ++i) G[12 * t + i] = o[i];
+  // float K R | K tau of the updated pose
+  float* pf = posef + 12 * t;
+  for (int i = 0; i < 4; ++i) {
+    pf[i < 3 ? i : 9] = (float)(P.fx_d * o[i] + P.cx_d * o[8 + i]);
+    pf[i < 3 ? 3 + i : 10] = (float)(P.fy_d * o[4 + i] + P.cy_d * o[8 + i]);
+    pf[i < 3 ? 6 + i : 11] = (float)o[8 + i];
   }
 }
 
@@ -667,9 +708,13 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
 // samples of 4 roots), granted once per device so that no launch, and no
 // stream capture, has to change a function attribute.
 cudaError_t vd_pose_prepare(void) {
-  const size_t smem = sizeof(float) * (size_t)(4 * VD_MAX_SAMPLES) * (12 + SCORE_THREADS / 32);
-  return cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  const int M = 4 * VD_MAX_SAMPLES;
+  cudaError_t e = cudaFuncSetAttribute(k_pose_score<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)vd_score_smem(M, 256));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pose_score<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)vd_score_smem(M, 512));
+  return e;
 }
 
 // Dense scoring of the current roots against the current rigid set, then the
@@ -677,13 +722,16 @@ cudaError_t vd_pose_prepare(void) {
 cudaError_t launch_pose_score_only(vd_ctx* c) {
   const DevParams& P = c->dp;
   const int M = 4 * P.S;
-  const size_t smem = sizeof(float) * (size_t)M * (12 + SCORE_THREADS / 32);
   const int nblk = c->score_bps * c->num_sms;
-  k_pose_score<<<nblk, SCORE_THREADS, smem, c->stream>>>(
-      P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
-  k_root_energy<<<(M + 127) / 128, 128, 0, c->stream>>>(c->partial, nblk, M, c->root_count,
-                                                        c->root_energy);
-  return cudaGetLastError();
+  if (c->score_threads == 512)
+    k_pose_score<512><<<nblk, 512, vd_score_smem(M, 512), c->stream>>>(
+        P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
+  else
+    k_pose_score<256><<<nblk, 256, vd_score_smem(M, 256), c->stream>>>(
+        P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_root_energy(c->partial, nblk, M, c->root_count, c->root_energy, c->stream);
 }
 
 cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
@@ -707,10 +755,7 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   launch_pose_score_only(c);
   vd_prof_end(c, VD_ST_SCORE, 2);
   vd_prof_begin(c, VD_ST_SELECT);
-  // one thread per sample, a power of two (>= one warp) for the tree reduction
-  int ms_threads = 32;
-  while (ms_threads < P.S) ms_threads <<= 1;
-  k_select_meanshift<<<1, ms_threads, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
+  k_select_meanshift<<<1, 32, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
                                                c->posef, c->sample_pose, c->sample_energy,
                                                c->degenerate);
   vd_prof_end(c, VD_ST_SELECT, 1);
@@ -794,10 +839,10 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
   float* rootsf = scratch;                          // m x 12
   float* partial = scratch + 12 * VD_NOALLOC_MAX_POSES;   // m x VD_NOALLOC_BLOCKS
   k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
-  const size_t smem = sizeof(float) * (size_t)m * (12 + SCORE_THREADS / 32);
-  k_pose_score<<<VD_NOALLOC_BLOCKS, SCORE_THREADS, smem, s>>>(
+  const size_t smem = vd_score_smem(m, SCORE_THREADS);
+  k_pose_score<SCORE_THREADS><<<VD_NOALLOC_BLOCKS, SCORE_THREADS, smem, s>>>(
       P, (const float4*)points, (const float4*)obs, nullptr, n, rootsf, nullptr, m, partial);
-  k_root_energy<<<(m + 127) / 128, 128, 0, s>>>(partial, VD_NOALLOC_BLOCKS, m, nullptr, energies);
+  launch_root_energy(partial, VD_NOALLOC_BLOCKS, m, nullptr, energies, s);
   e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -837,12 +882,13 @@ extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n
     return VD_ERR_OOM;
   }
   k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
-  const size_t smem = sizeof(float) * (size_t)m * (12 + SCORE_THREADS / 32);
+  const size_t smem = vd_score_smem(m, SCORE_THREADS);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_pose_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_pose_score<<<nblk, SCORE_THREADS, smem, s>>>(P, (const float4*)points, (const float4*)obs,
+    cudaFuncSetAttribute(k_pose_score<SCORE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  k_pose_score<SCORE_THREADS><<<nblk, SCORE_THREADS, smem, s>>>(P, (const float4*)points, (const float4*)obs,
                                                  nullptr, n, rootsf, nullptr, m, partial);
-  k_root_energy<<<(m + 127) / 128, 128, 0, s>>>(partial, nblk, m, nullptr, energies);
+  launch_root_energy(partial, nblk, m, nullptr, energies, s);
   e = cudaGetLastError();
   cudaFreeAsync(rootsf, s);
   cudaFreeAsync(partial, s);

@@ -57,8 +57,9 @@ class vd_profile(C.Structure):
 
 
 class vd_tune(C.Structure):
-    _fields_ = [("k1_warps", C.c_int), ("score_blocks_per_sm", C.c_int),
-                ("k1_ms", C.c_float * 3), ("score_ms", C.c_float * 4)]
+    _fields_ = [("k1_warps", C.c_int), ("score_threads", C.c_int),
+                ("score_blocks_per_sm", C.c_int), ("k1_ms", C.c_float * 3),
+                ("score_ms", (C.c_float * 4) * 2)]
 
 
 class vd_batch_stats(C.Structure):
@@ -376,8 +377,9 @@ def vd_score_poses_noalloc(points, obs, poses, intrinsics, beta, p0, energies, s
 
 
 def _tune_dict(t):
-    return dict(k1_warps=t.k1_warps, score_blocks_per_sm=t.score_blocks_per_sm,
-                k1_ms=list(t.k1_ms), score_ms=list(t.score_ms))
+    return dict(k1_warps=t.k1_warps, score_threads=t.score_threads,
+                score_blocks_per_sm=t.score_blocks_per_sm, k1_ms=list(t.k1_ms),
+                score_ms=[list(r) for r in t.score_ms])
 
 
 def vd_autotune(ctx):
@@ -386,9 +388,10 @@ def vd_autotune(ctx):
     return _tune_dict(t)
 
 
-def vd_set_tune(ctx, k1_warps, score_blocks_per_sm):
+def vd_set_tune(ctx, k1_warps, score_blocks_per_sm, score_threads=256):
     t = vd_tune()
     t.k1_warps, t.score_blocks_per_sm = int(k1_warps), int(score_blocks_per_sm)
+    t.score_threads = int(score_threads)
     _call("vd_set_tune", ctx, C.byref(t))
 
 

@@ -154,6 +154,9 @@ def _blob_mask(rng, H, W, frac, rmin, rmax):
     return m
 
 
+Z_NEAR = 0.5   # m
+
+
 def _flows(rng, scene, G, W, H, N, K, noise_alpha, noise_beta, moving_frac, noisy, blob_r):
     fx, fy, cx, cy = K
     u, v = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
@@ -161,8 +164,12 @@ def _flows(rng, scene, G, W, H, N, K, noise_alpha, noise_beta, moving_frac, nois
     moving = np.zeros((N, H, W), bool)
     for t in range(1, N + 1):
         P, _ = scene.cast(G[t - 1], W, H, fx, fy, cx, cy)
-        x, _ = _project(G[t], P, fx, fy, cx, cy)
+        x, zt = _project(G[t], P, fx, fy, cx, cy)
         f = np.stack([x[..., 0] - u, x[..., 1] - v], axis=-1)
+        # a scene point less than Z_NEAR in front of camera t (the camera has
+        # passed it) has no flow: an estimator returns a bounded guess there,
+        # which the model must treat as an outlier; take zero motion
+        f[zt < Z_NEAR] = 0.0
         m = _blob_mask(rng, H, W, moving_frac, *blob_r)
         if m.any():
             # independently moving blobs: one constant random flow per blob image

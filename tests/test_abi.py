@@ -73,7 +73,7 @@ def _struct_fields(src, closing):
     body = src[:src.index(closing)]
     body = body[body.rindex("typedef struct {"):]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S).replace("typedef struct {", "")
-    return re.findall(r"\b([a-z_0-9]+)\s*(?:\[[A-Z0-9_]+\])?\s*[,;]", body)
+    return re.findall(r"\b([a-z_0-9]+)\s*(?:\[[A-Z0-9_]+\])*\s*[,;]", body)
 
 
 def test_tune_and_batch_structs_match_the_header():

@@ -57,7 +57,7 @@ def _same(a, b):
 def _alone(V, w, tune=None):
     ctx = V.vd_create(w.W, w.H, w.N, w.intrinsics, V.vd_params_default(**params_for(w)))
     if tune is not None:
-        V.vd_set_tune(ctx, tune["k1_warps"], tune["score_blocks_per_sm"])
+        V.vd_set_tune(ctx, tune["k1_warps"], tune["score_blocks_per_sm"], tune["score_threads"])
     _push(V, ctx, w)
     return ctx
 
@@ -114,9 +114,10 @@ def test_batch_autotune_shares_choices_and_matches_alone(V):
         tunes = [V.vd_get_tune(V.vd_batch_window(b, i)) for i in range(len(wins))]
         for t in tunes:
             assert t["k1_warps"] in (1, 2, 4) and 1 <= t["score_blocks_per_sm"] <= 4
-        same = ("k1_warps", "score_blocks_per_sm")
+            assert t["score_threads"] in (256, 512)
+        same = ("k1_warps", "score_blocks_per_sm", "score_threads")
         assert all(tunes[0][k] == tunes[1][k] for k in same)   # same launch configuration
-        assert all(v > 0 for v in tunes[0]["k1_ms"] + tunes[0]["score_ms"])
+        assert all(v > 0 for v in tunes[0]["k1_ms"] + tunes[0]["score_ms"][0] + tunes[0]["score_ms"][1])
         for i, w in enumerate(wins):
             ctx = _alone(V, w, tunes[i])
             V.vd_bootstrap(ctx)
@@ -156,8 +157,8 @@ def test_depth_sampling_launch_shapes_are_bit_identical(V):
 
 
 def test_score_launch_shapes_agree_to_rounding(V):
-    """Blocks per SM of the dense pose scoring only regroup float32 partial
-    sums: the per-sample energies agree to rounding."""
+    """Threads per block and blocks per SM of the dense pose scoring only
+    regroup float32 partial sums: the per-sample energies agree to rounding."""
     w = window("planes160", 0)
     rng = np.random.default_rng(4)
     ctx = _alone(V, w)
@@ -166,8 +167,8 @@ def test_score_launch_shapes_agree_to_rounding(V):
         P = omodel.problem_from_window(w)
         S = noisy_state(w, P, rng, rel=0.02, qmode="ones")
         energies = []
-        for bps in (1, 2, 3, 4):
-            V.vd_set_tune(ctx, 4, bps)
+        for threads, bps in ((256, 1), (256, 2), (256, 4), (512, 1), (512, 3)):
+            V.vd_set_tune(ctx, 4, bps, threads)
             push_state(V, ctx, S)
             V.vd_pose_mstep(ctx, 1, 1)
             _, e, _ = V.vd_get_pose_samples(ctx, 64)

@@ -190,7 +190,15 @@ def test_estep_parity(V, name, kw, direction):
 
 
 # ------------------------------------------------------------------ pose step
-@pytest.mark.parametrize("name,kw", [("planes160", {}), ("boxes640_stereo", dict(size=(160, 120), N=3))])
+def _p3p_reproj(G, X3, bear):
+    """Largest bearing error of pose G over the three correspondences."""
+    Y = X3 @ G[:, :3].T + G[:, 3]
+    f = bear / np.linalg.norm(bear, axis=1, keepdims=True)
+    return float(np.abs(Y / np.linalg.norm(Y, axis=1, keepdims=True) - f).max())
+
+
+@pytest.mark.parametrize("name,kw", [("planes160", {}), ("boxes640_stereo", dict(size=(160, 120), N=3)),
+                                     ("driving1216", dict(size=(304, 92), N=4))])
 def test_pose_step_parity(V, name, kw):
     win = window(name, 8, **kw)
     ctx, P, p = make_ctx(V, win, prior="none")
@@ -206,8 +214,12 @@ def test_pose_step_parity(V, name, kw):
             assert st == V.VD_OK
             poses, en, n = V.vd_get_pose_samples(ctx, p.n_pose_samples)
             assert n == out["n_rigid"]
-            # every GPU sample is the oracle's lowest-energy root of the same draw
-            # (an ill-conditioned P3P instance may round differently: at most 2)
+            # every GPU sample is the oracle's lowest-energy root of the same draw;
+            # an ill-conditioned P3P instance (far points, long baselines) may
+            # come out differently from the two float64 solvers: then both must
+            # still solve the sample's minimal problem (reproject its three
+            # bearings to 1e-6), on at most 1/8 of the samples; the bound that
+            # matters, on the mean-shift pose, is checked below
             mism = 0
             for g in range(p.n_pose_samples):
                 roots, Es = out["roots"][g], out["root_scores"][g]
@@ -221,10 +233,12 @@ def test_pose_step_parity(V, name, kw):
                 d = np.abs(poses[g] - roots[k]).max()
                 if d >= 1e-7:
                     mism += 1
-                    assert d < 1e-4
+                    X3, bear = out["tri_X"][g], out["tri_bear"][g]
+                    assert _p3p_reproj(poses[g], X3, bear) < 1e-6, (g, d)
+                    assert _p3p_reproj(roots[k], X3, bear) < 1e-6, (g, d)
                     continue
                 assert abs(en[g] - Es[k]) <= 2e-5 * abs(Es[k])
-            assert mism <= 2
+            assert mism <= max(2, p.n_pose_samples // 8), mism
             assert np.allclose(np.sort(en[np.isfinite(en)]), np.sort(out["scores"]), rtol=2e-5)
             Gg = V.vd_get_poses(ctx, P.N)
             rot, trans = _pose_err(So.G[t], Gg[t])
