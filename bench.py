@@ -49,6 +49,10 @@ WORK = dict(name="driving1216", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2
 # MUFU operations (one reciprocal, one log2).
 FP32_T1, FP32_TN, MUFU_PER_EVAL = 17, 33, 2
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+# DRAM bytes (read + write) per launch of k_depth_sample_q on this workload,
+# from one ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of three launches); re-measure when it changes.
+K1_TRAFFIC_BYTES = 32.4e6
 SM_MAX_MHZ = 2070.0
 
 
@@ -65,6 +69,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="windows per step (one graph launch)")
+    ap.add_argument("--workload", default="driving1216", choices=["driving1216", "rgbd_batch64"],
+                    help="rgbd_batch64: 64 RGB-D windows of uneven size and N, plain vs batched")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes (no vd_autotune; for profiling)")
     ap.add_argument("--phase", default="both", choices=["both", "single", "batch"],
                     help="single: only the one-window run (for profiling); batch: skip it")
     return ap.parse_args()
@@ -144,13 +152,13 @@ def max_over_ranks(pg, x, device):
 
 # ------------------------------------------------------------------ oracle timing
 def oracle_sample(seconds_hint=20.0):
-    """Time the float64 oracle on a centred 304 x 92 crop of the same window
-    (1/16 of the pixels, same N, K, S): one EM iteration from a mid-EM state."""
+    """Time the float64 oracle on a centred 608 x 184 crop of the same window
+    (1/4 of the pixels, same N, K, S): one EM iteration from a mid-EM state."""
     import synth
     from oracle import em as oem
     from oracle import model as omodel
     win = synth.make_window(WORK["name"], WORK["seed"])
-    cw, ch = WORK["W"] // 4, WORK["H"] // 4
+    cw, ch = WORK["W"] // 2, WORK["H"] // 2
     u0, v0 = (WORK["W"] - cw) // 2, (WORK["H"] - ch) // 2
     fx, fy, cx, cy = win.intrinsics
     P = omodel.Problem(cw, ch, WORK["N"], (fx, fy, cx - u0, cy - v0),
@@ -221,7 +229,7 @@ def run_ours(args, rank, world, local, pg):
     flows_dev = torch.from_numpy(win.flow).to(dev)
     for t in range(1, N + 1):
         V.vd_push_flow(ctx, t, flows_dev[t - 1])
-    tune = V.vd_autotune(ctx)
+    tune = V.vd_get_tune(ctx) if args.no_tune else V.vd_autotune(ctx)
 
     def step1():
         V.vd_bootstrap(ctx)
@@ -243,7 +251,8 @@ def run_ours(args, rank, world, local, pg):
     peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_depth_sample_q", "achieved": round(achieved, 3),
                 "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "launch_ms": round(launch_ms, 4),
+                "traffic": K1_TRAFFIC_BYTES, "traffic_unit": "B per launch",
+                "launch_ms": round(launch_ms, 4),
                 "evals_per_s": round(W * H * N * WORK["K"] / (launch_ms / 1e3), 1),
                 "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)",
                 "measured_in": "single-window run, kernel timed alone (CUDA events)"}
@@ -279,7 +288,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
         fl = torch.from_numpy(w.flow).to(dev)
         for t in range(1, N + 1):
             V.vd_push_flow(V.vd_batch_window(b, i), t, fl[t - 1])
-    V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP | V.VD_BATCH_AUTOTUNE)
+    V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP | (0 if args.no_tune else V.VD_BATCH_AUTOTUNE))
 
     def stepb():
         V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
@@ -344,6 +353,102 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
     return line
 
 
+def run_rgbd64(args, rank, world, local, pg):
+    """64 windows with an RGB-D prior, sizes drawn from 320x240 / 640x480 /
+    1216x368 and N from 3..8 (seeds 5000..5063), 5 EM iterations each: one
+    window at a time (vd_bootstrap + vd_run_em per window) versus all of them
+    in one graph launch (vd_batch_run).  Both give bit-identical results."""
+    import torch
+    from paper_2104_06800_gb300 import build as B
+    from paper_2104_06800_gb300 import voldor as V
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    V.load()
+    stream = torch.cuda.current_stream(dev)
+    sptr = V.C.c_void_p(stream.cuda_stream)
+    nw, iters = 64, 5
+    wins = [synth.make_window("rgbd_batch", 5000 + 64 * rank + i) for i in range(nw)]
+    prms = [V.vd_params_default(fisk_alpha0=w.params["fisk_alpha0"], rho_min=w.params["rho_min"],
+                                rho_max=w.params["rho_max"], n_hyp=w.params["n_hyp"],
+                                n_pose_samples=64) for w in wins]
+    units = sum(w.W * w.H * w.N * iters for w in wins)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def push(ctx, w):
+        for t in range(1, w.N + 1):
+            V.vd_push_flow(ctx, t, w.flow[t - 1])
+        V.vd_push_depth_prior(ctx, w.depth_prior)
+
+    # one window at a time, each on its own context
+    ctxs = []
+    for w, p in zip(wins, prms):
+        c = V.vd_create(w.W, w.H, w.N, w.intrinsics, p, sptr)
+        push(c, w)
+        ctxs.append(c)
+
+    def plain():
+        for c in ctxs:
+            V.vd_bootstrap(c)
+            V.vd_run_em(c, iters, stats=False)
+
+    for _ in range(max(1, args.warmup)):
+        plain()
+    torch.cuda.synchronize()
+    tp = _timed(stream, flush, plain, args.steps)
+    # the same windows as one batch
+    b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in wins], prms, sptr)
+    for i, w in enumerate(wins):
+        push(V.vd_batch_window(b, i), w)
+    V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP | V.VD_BATCH_AUTOTUNE)
+    for _ in range(args.warmup):
+        V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    tb = _timed(stream, flush, lambda: V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP), args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    # accuracy against the scenes' true depth (metric: the prior fixes the scale)
+    errs, same = [], True
+    for i, w in enumerate(wins):
+        rb = np.empty((w.H, w.W), np.float32)
+        rp = np.empty((w.H, w.W), np.float32)
+        V.vd_get_inv_depth(V.vd_batch_window(b, i), rb)
+        V.vd_get_inv_depth(ctxs[i], rp)
+        same &= bool(np.array_equal(rb, rp))
+        d = 1.0 / np.maximum(rb, 1e-9)
+        errs.append(float(np.median(np.abs(d - w.depth0) / w.depth0)))
+    bstats = V.vd_batch_get_stats(b)
+    V.vd_batch_destroy(b)
+    for c in ctxs:
+        V.vd_destroy(c)
+    tot_b = max_over_ranks(pg, sum(tb), dev)
+    tot_p = max_over_ranks(pg, sum(tp), dev)
+    sizes = {}
+    for w in wins:
+        sizes[f"{w.W}x{w.H}"] = sizes.get(f"{w.W}x{w.H}", 0) + 1
+    return {"metric": METRIC, "value": round(units * args.steps * world / (tot_b / 1e3), 1),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_b / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rgbd_batch64: {nw} windows, RGB-D prior (1% noise, 10% holes), "
+                                   f"{iters} EM iterations, K=64, S=64; sizes {sizes}, "
+                                   f"N {min(w.N for w in wins)}..{max(w.N for w in wins)}",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "windows_per_s": round(nw * args.steps * world / (tot_b / 1e3), 3),
+            "plain": {"windows_per_s": round(nw * args.steps * world / (tot_p / 1e3), 3),
+                      "value": round(units * args.steps * world / (tot_p / 1e3), 1),
+                      "ms_per_step": round(tot_p / args.steps, 3)},
+            "batched_equals_plain": same,
+            "median_depth_rel_err": {"median_over_windows": round(float(np.median(errs)), 5),
+                                     "max_over_windows": round(float(np.max(errs)), 5)},
+            "batch": bstats, "gpu_launches": int(bstats["kernels_per_run"] * args.steps),
+            "clocks": clk, "e2e": None}
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup(args.gpus)
@@ -369,6 +474,13 @@ def main():
                 "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return 0
+    if args.workload == "rgbd_batch64":
+        line = run_rgbd64(args, rank, world, local, pg)
+        if rank == 0:
+            print(json.dumps(line))
+        if pg is not None:
+            pg.destroy_process_group()
         return 0
     line = run_ours(args, rank, world, local, pg)
     if rank == 0:
