@@ -26,4 +26,7 @@ Modules and the passage each follows (Min & Dunn, "VOLDOR+SLAM", 2021):
               in se(3) (Eq. 7).
   eightpoint -- monocular bootstrap (8-point essential matrix on X_1).
   em       -- the iteration schedule tying the steps together.
+  cnn      -- the learned initialiser (no counterpart in the paper): a small
+              3x3 convolutional network from the flows to an initial inverse
+              depth and rigidness, its backward pass, loss and Adam step.
 """

@@ -1,0 +1,140 @@
+"""Learned initialiser of the EM state (test infrastructure; no counterpart in
+the paper, which starts every window from its bootstrap): a small
+convolutional network mapping the N flow fields of a window to an initial
+inverse depth and rigidness.  Plain float64 definition of its forward pass,
+backward pass, loss and Adam step, for the GPU kernels to be checked against.
+
+Storage precision follows the GPU: weights and the activations between
+layers are bfloat16 (round to nearest, ties to even); products and sums are
+float64 here (float32 accumulation of exact bf16 x bf16 products on the GPU).
+Pass ``bf16=False`` for the unrounded function (the finite-difference pins).
+
+Architecture (all convolutions 3x3, stride 1, zero padding 1):
+  input   a0[c][y][x]: c < 2N is component c % 2 of flow c // 2 divided by
+          FLOW_SCALE; channels 2N .. C0-1 are zero (C0 = 2N rounded up to 8)
+  layer l z_l = conv(a_l, W_l) + b_l, W_l[co][ky][kx][ci];
+          a_{l+1} = relu(z_l) for every layer but the last
+  output  rho = rho_min + (rho_max - rho_min) sigmoid(z[0]),  q = sigmoid(z[1])
+Loss over pixels with mask m:
+  L = sum m (rho / rho* - 1)^2 / sum m  +  w_q sum m BCE(q, q*) / sum m
+Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+      theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+"""
+import numpy as np
+
+FLOW_SCALE = 32.0
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def in_channels(n_flows):
+    return (2 * n_flows + 7) // 8 * 8
+
+
+def layer_shapes(n_flows, width=32, layers=6):
+    """[(C_in, C_out)] of every layer."""
+    c = [in_channels(n_flows)] + [width] * (layers - 1) + [2]
+    return [(c[i], c[i + 1]) for i in range(layers)]
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest, ties to even) and widen to float64."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def input_planes(flow, n_pad=None):
+    """flow [N][H][W][2] -> a0 [C0][H][W] (float64, bf16-rounded)."""
+    flow = np.asarray(flow, np.float64)
+    N, H, W, _ = flow.shape
+    C0 = n_pad or in_channels(N)
+    a = np.zeros((C0, H, W))
+    for t in range(N):
+        a[2 * t] = flow[t, :, :, 0] / FLOW_SCALE
+        a[2 * t + 1] = flow[t, :, :, 1] / FLOW_SCALE
+    return bf16(a)
+
+
+def conv(a, W, b):
+    """z[co][y][x] = b[co] + sum_{ky,kx,ci} W[co][ky][kx][ci] a[ci][y+ky-1][x+kx-1]."""
+    C, H, Wd = a.shape
+    ap = np.pad(a, ((0, 0), (1, 1), (1, 1)))
+    z = np.broadcast_to(np.asarray(b, np.float64)[:, None, None], (W.shape[0], H, Wd)).copy()
+    for ky in range(3):
+        for kx in range(3):
+            z += np.einsum("oc,chw->ohw", W[:, ky, kx, :], ap[:, ky:ky + H, kx:kx + Wd])
+    return z
+
+
+def conv_backward(a, W, dz):
+    """Gradients of conv(a, W, b) given dL/dz: (da, dW, db)."""
+    C, H, Wd = a.shape
+    ap = np.pad(a, ((0, 0), (1, 1), (1, 1)))
+    dzp = np.pad(dz, ((0, 0), (1, 1), (1, 1)))
+    dW = np.zeros_like(W, dtype=np.float64)
+    da = np.zeros_like(a, dtype=np.float64)
+    for ky in range(3):
+        for kx in range(3):
+            dW[:, ky, kx, :] = np.einsum("ohw,chw->oc", dz, ap[:, ky:ky + H, kx:kx + Wd])
+            # z[y][x] uses a[y+ky-1][x+kx-1], so a[y][x] feeds z[y-ky+1][x-kx+1]
+            da += np.einsum("oc,ohw->chw", W[:, ky, kx, :],
+                            dzp[:, 2 - ky:2 - ky + H, 2 - kx:2 - kx + Wd])
+    return da, dW, dz.sum(axis=(1, 2))
+
+
+def forward(params, a0, bf16_storage=True):
+    """params: [(W_l, b_l)].  Returns (z of the last layer, [a_l], [z_l])."""
+    rnd = bf16 if bf16_storage else (lambda v: np.asarray(v, np.float64))
+    acts, zs = [rnd(a0)], []
+    for l, (W, b) in enumerate(params):
+        z = conv(acts[-1], rnd(W), b)
+        zs.append(z)
+        if l + 1 < len(params):
+            acts.append(rnd(np.maximum(z, 0.0)))
+    return zs[-1], acts, zs
+
+
+def heads(z, rho_min, rho_max):
+    s0 = 1.0 / (1.0 + np.exp(-z[0]))
+    s1 = 1.0 / (1.0 + np.exp(-z[1]))
+    return rho_min + (rho_max - rho_min) * s0, s1
+
+
+def loss_and_grad(z, rho_t, q_t, mask, rho_min, rho_max, w_q):
+    """Loss L and dL/dz for the two output channels."""
+    rho, q = heads(z, rho_min, rho_max)
+    m = np.asarray(mask, np.float64)
+    nm = max(m.sum(), 1.0)
+    r = rho / rho_t - 1.0
+    eps = 1e-12
+    bce = -(q_t * np.log(np.maximum(q, eps)) + (1 - q_t) * np.log(np.maximum(1 - q, eps)))
+    L = float((m * r * r).sum() / nm + w_q * (m * bce).sum() / nm)
+    s0 = (rho - rho_min) / (rho_max - rho_min)
+    dz = np.zeros_like(z)
+    dz[0] = m * 2.0 * r / rho_t * (rho_max - rho_min) * s0 * (1.0 - s0) / nm
+    dz[1] = w_q * m * (q - q_t) / nm
+    return L, dz
+
+
+def backward(params, acts, zs, dz_last, bf16_storage=True):
+    """[(dW_l, db_l)] given dL/dz of the last layer (weights as used: bf16)."""
+    rnd = bf16 if bf16_storage else (lambda v: np.asarray(v, np.float64))
+    grads = [None] * len(params)
+    dz = dz_last
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = params[l]
+        da, dW, db = conv_backward(acts[l], rnd(W), dz)
+        grads[l] = (dW, db)
+        if l > 0:
+            dz = da * (zs[l - 1] > 0.0)
+    return grads
+
+
+def adam_step(theta, m, v, g, t, lr):
+    """One Adam step (t = 1 for the first); returns new (theta, m, v)."""
+    m = ADAM_B1 * m + (1 - ADAM_B1) * g
+    v = ADAM_B2 * v + (1 - ADAM_B2) * g * g
+    mh = m / (1 - ADAM_B1 ** t)
+    vh = v / (1 - ADAM_B2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + ADAM_EPS), m, v

@@ -1,0 +1,107 @@
+"""Pins of the learned initialiser's float64 oracle (oracle/cnn.py) against
+facts that do not come from it: a library correlation, finite differences,
+the Adam closed form of a first step, and torch's bfloat16 rounding."""
+import numpy as np
+import pytest
+from scipy.signal import correlate2d
+
+from oracle import cnn
+
+
+def test_bf16_rounding_matches_torch_and_known_values():
+    torch = pytest.importorskip("torch")
+    x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, -2.5, 3.14159, 1e-3, 65504.0])
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.bf16(x), ref)
+    # ties to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert cnn.bf16(1 + 2 ** -8) == 1.0 and cnn.bf16(1 + 3 * 2 ** -8) == 1 + 2 ** -6
+    r = np.random.default_rng(0).normal(size=1000) * 10
+    ref = torch.tensor(r, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(cnn.bf16(r), ref)
+
+
+def test_conv_equals_channel_sum_of_library_correlation():
+    rng = np.random.default_rng(1)
+    a = rng.normal(size=(3, 7, 9))
+    W = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    z = cnn.conv(a, W, b)
+    for co in range(4):
+        ref = b[co] + sum(correlate2d(a[ci], W[co, :, :, ci], mode="same") for ci in range(3))
+        assert np.allclose(z[co], ref, atol=1e-12)
+
+
+def _tiny(rng, layers=3):
+    shapes = [(4, 5), (5, 5), (5, 2)][:layers]
+    return [(rng.normal(size=(co, 3, 3, ci)) * 0.5, rng.normal(size=co) * 0.1) for ci, co in shapes]
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    params = _tiny(rng)
+    a0 = rng.normal(size=(4, 6, 5))
+    rho_t = rng.uniform(0.1, 1.0, size=(6, 5))
+    q_t = rng.uniform(0, 1, size=(6, 5))
+    mask = rng.uniform(size=(6, 5)) > 0.2
+    args = (rho_t, q_t, mask, 0.05, 2.0, 0.3)
+
+    def L_of(ps):
+        z, _, _ = cnn.forward(ps, a0, bf16_storage=False)
+        return cnn.loss_and_grad(z, *args)[0]
+
+    z, acts, zs = cnn.forward(params, a0, bf16_storage=False)
+    _, dz = cnn.loss_and_grad(z, *args)
+    grads = cnn.backward(params, acts, zs, dz, bf16_storage=False)
+    h = 1e-6
+    for l, (W, b) in enumerate(params):
+        for idx in [(0, 0, 0, 0), (1, 2, 1, 3), (-1, 1, 2, -1)]:
+            Wp = [(w.copy(), bb.copy()) for w, bb in params]
+            Wm = [(w.copy(), bb.copy()) for w, bb in params]
+            Wp[l][0][idx] += h
+            Wm[l][0][idx] -= h
+            fd = (L_of(Wp) - L_of(Wm)) / (2 * h)
+            assert abs(fd - grads[l][0][idx]) <= 1e-6 * max(1.0, abs(fd)), (l, idx)
+        for i in range(len(b)):
+            Wp = [(w.copy(), bb.copy()) for w, bb in params]
+            Wm = [(w.copy(), bb.copy()) for w, bb in params]
+            Wp[l][1][i] += h
+            Wm[l][1][i] -= h
+            fd = (L_of(Wp) - L_of(Wm)) / (2 * h)
+            assert abs(fd - grads[l][1][i]) <= 1e-6 * max(1.0, abs(fd)), (l, i)
+
+
+def test_input_gradient_of_conv_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(3, 5, 4))
+    W = rng.normal(size=(2, 3, 3, 3))
+    dz = rng.normal(size=(2, 5, 4))
+    da, _, _ = cnn.conv_backward(a, W, dz)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 4, 1)]:
+        ap, am = a.copy(), a.copy()
+        ap[idx] += h
+        am[idx] -= h
+        fd = ((cnn.conv(ap, W, np.zeros(2)) - cnn.conv(am, W, np.zeros(2))) * dz).sum() / (2 * h)
+        assert abs(fd - da[idx]) < 1e-6
+
+
+def test_adam_first_step_closed_form():
+    # from zero moments, m_hat = g and v_hat = g^2: the step is lr g / (|g| + eps)
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    th, m, v = cnn.adam_step(np.ones(4), np.zeros(4), np.zeros(4), g, 1, 0.01)
+    assert np.allclose(th, 1 - 0.01 * g / (np.abs(g) + cnn.ADAM_EPS), atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+    # a constant gradient keeps m_hat = g, v_hat = g^2 at every step
+    th, m, v = np.ones(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 6):
+        th, m, v = cnn.adam_step(th, m, v, g, t, 0.01)
+    assert np.allclose(th, 1 - 5 * 0.01 * g / (np.abs(g) + cnn.ADAM_EPS), atol=1e-12)
+
+
+def test_shapes_and_input_planes():
+    assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 8
+    assert cnn.layer_shapes(6) == [(16, 32)] + [(32, 32)] * 4 + [(32, 2)]
+    flow = np.zeros((2, 3, 4, 2), np.float32)
+    flow[1, 2, 3] = (32.0, -64.0)
+    a = cnn.input_planes(flow)
+    assert a.shape == (8, 3, 4) and a[2, 2, 3] == 1.0 and a[3, 2, 3] == -2.0 and a[4:].sum() == 0
