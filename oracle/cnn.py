@@ -4,14 +4,16 @@ convolutional network mapping the N flow fields of a window to an initial
 inverse depth and rigidness.  Plain float64 definition of its forward pass,
 backward pass, loss and Adam step, for the GPU kernels to be checked against.
 
-Storage precision follows the GPU: weights and the activations between
-layers are bfloat16 (round to nearest, ties to even); products and sums are
-float64 here (float32 accumulation of exact bf16 x bf16 products on the GPU).
+Storage precision follows the GPU: weights, the activations between layers
+and the gradients dL/dz_l are bfloat16 (round to nearest, ties to even);
+products and sums are float64 here (float32 accumulation of exact
+bf16 x bf16 products on the GPU).
 Pass ``bf16=False`` for the unrounded function (the finite-difference pins).
 
 Architecture (all convolutions 3x3, stride 1, zero padding 1):
   input   a0[c][y][x]: c < 2N is component c % 2 of flow c // 2 divided by
-          FLOW_SCALE; channels 2N .. C0-1 are zero (C0 = 2N rounded up to 8)
+          FLOW_SCALE; channels 2N .. C0-1 are zero (C0 = 2N rounded up to a
+          multiple of 8, at least 16)
   layer l z_l = conv(a_l, W_l) + b_l, W_l[co][ky][kx][ci];
           a_{l+1} = relu(z_l) for every layer but the last
   output  rho = rho_min + (rho_max - rho_min) sigmoid(z[0]),  q = sigmoid(z[1])
@@ -27,7 +29,8 @@ ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
 
 
 def in_channels(n_flows):
-    return (2 * n_flows + 7) // 8 * 8
+    """Input planes: 2N rounded up to a multiple of 8, at least 16."""
+    return max(16, (2 * n_flows + 7) // 8 * 8)
 
 
 def layer_shapes(n_flows, width=32, layers=6):
@@ -118,16 +121,18 @@ def loss_and_grad(z, rho_t, q_t, mask, rho_min, rho_max, w_q):
 
 
 def backward(params, acts, zs, dz_last, bf16_storage=True):
-    """[(dW_l, db_l)] given dL/dz of the last layer (weights as used: bf16)."""
+    """[(dW_l, db_l)] given dL/dz of the last layer.  With bf16 storage the
+    weights are used as rounded and every dL/dz_l is stored as bf16 (as the
+    activations are), before it enters the weight and input gradients."""
     rnd = bf16 if bf16_storage else (lambda v: np.asarray(v, np.float64))
     grads = [None] * len(params)
-    dz = dz_last
+    dz = rnd(dz_last)
     for l in range(len(params) - 1, -1, -1):
         W, _ = params[l]
         da, dW, db = conv_backward(acts[l], rnd(W), dz)
         grads[l] = (dW, db)
         if l > 0:
-            dz = da * (zs[l - 1] > 0.0)
+            dz = rnd(da * (zs[l - 1] > 0.0))
     return grads
 
 

@@ -128,15 +128,6 @@ extern "C" const char* vd_status_str(vd_status s) {
   return "unknown status";
 }
 
-#define VD_CU(call)                                   \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) {                          \
-      vd_set_error(cudaGetErrorString(e_));           \
-      return e_ == cudaErrorMemoryAllocation ? VD_ERR_OOM : VD_ERR_CUDA; \
-    }                                                 \
-  } while (0)
-
 extern "C" vd_status vd_params_default(vd_params* p) {
   if (!p) return VD_ERR_ARG;
   memset(p, 0, sizeof *p);
@@ -623,6 +614,27 @@ static cudaError_t bootstrap(vd_ctx* c) {
   return e;
 }
 
+// Bootstrap from the learned initialiser: the network's rho and q replace
+// the random depth, the depth step on X_1 and q = 1 of the monocular
+// bootstrap (R11); the poses come from the 8-point bootstrap (monocular, no
+// poses set) or the initial poses, then one pose M-step as in bootstrap().
+static cudaError_t bootstrap_learned(vd_ctx* c, vd_cnn* net) {
+  vd_prof_begin(c, VD_ST_OTHER);
+  cudaError_t e = cudaMemcpyAsync(c->G, c->G_init, sizeof(double) * 12 * (c->N + 1),
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_posef(c);
+  if (e == cudaSuccess) e = launch_fill(c->qhat, 1.0f, c->npix, c->stream);
+  int n = 2;
+  if (e == cudaSuccess && c->prior_kind == VD_PRIOR_NONE && !c->poses_set) {
+    e = launch_eight_point(c);
+    n += 2 * VD_IRLS_ITERS + 3;
+  }
+  if (e == cudaSuccess) e = launch_cnn_init(net, c);
+  vd_prof_end(c, VD_ST_OTHER, n + 2 + 2 * VD_CNN_LAYERS);
+  if (e == cudaSuccess && !c->poses_set) e = pose_step(c, -1, 0);
+  return e;
+}
+
 static vd_status finish_sync(vd_ctx* c, int* degenerate_out) {
   int h = 0;
   VD_CU(cudaMemcpyAsync(&h, c->degenerate, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -664,6 +676,28 @@ static cudaError_t enqueue_em(vd_ctx* c, int n_iters, bool boot, int* booted) {
     c->iter = i + 1;
   }
   return cudaSuccess;
+}
+
+extern "C" vd_status vd_bootstrap_learned(vd_ctx* c, vd_cnn* net) {
+  if (!c || !net) return VD_ERR_ARG;
+  if (vd_cnn_flows(net) != c->N) {
+    vd_set_error("the network was built for another number of flows");
+    return VD_ERR_ARG;
+  }
+  if (!flows_ready(c)) return VD_ERR_STATE;
+  VD_CU(cudaMemsetAsync(c->degenerate, 0, sizeof(int), c->stream));
+  VD_CU(bootstrap_learned(c, net));
+  c->bootstrapped = 1;
+  c->iter = 0;
+  int tc = 0;
+  VD_CU(cudaMemcpyAsync(&tc, vd_cnn_err_flag(net), sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream));
+  const vd_status st = finish_sync(c, nullptr);
+  if (tc) {
+    vd_set_error("a tensor-core wait gave up");
+    return VD_ERR_TIMEOUT;
+  }
+  return st;
 }
 
 extern "C" vd_status vd_run_em(vd_ctx* c, int n_iters, vd_stats* stats) {

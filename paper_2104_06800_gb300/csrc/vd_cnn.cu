@@ -1,0 +1,835 @@
+// Learned initialiser of the EM state (no counterpart in the paper): six 3x3
+// convolutions, 32 channels, bfloat16 weights and activations, float32
+// accumulation, from the N flow fields to an initial inverse depth and
+// rigidness.
+//
+// Convolutions are implicit GEMMs on the 5th-generation tensor cores:
+// D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = (ky * 3 + kx) * C_in + c_in,
+// with one CTA per 128 consecutive pixels.  The whole im2col tile A (128 x K)
+// and the weights B (N x K) are staged in shared memory in the canonical
+// K-major layout without swizzle (core matrices of 8 rows x 16 bytes, LBO =
+// 128 B between core matrices along K, SBO = 16 K bytes between 8-row
+// groups); one thread issues K/16 tcgen05.mma (kind::f16, bf16 x bf16 ->
+// f32) into a tensor-memory accumulator of N columns and commits them to an
+// mbarrier; each warp reads its 32 accumulator lanes with tcgen05.ld.  The
+// backward data gradient is the same GEMM on dL/dz with the weights flipped
+// by 180 degrees and transposed; the weight gradient is a float32 reduction
+// over pixels on the CUDA cores, in a fixed order.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "vd_device.cuh"
+
+#define CNN_L 6
+#define CNN_WIDTH 32
+#define CNN_TILE 128
+#define CNN_WAIT_LIMIT (1 << 22)   // mbarrier polls before a wait gives up
+
+// ---------------------------------------------------------------------------
+// tcgen05 / mbarrier primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t vd_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t vd_umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t vd_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void vd_tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(vd_smem_u32(dst)), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void vd_tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void vd_umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                             uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void vd_umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   vd_smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void vd_mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(vd_smem_u32(m)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool vd_mbar_try_wait(uint64_t* m, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(vd_smem_u32(m)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within the poll limit.
+__device__ __forceinline__ bool vd_mbar_wait_bounded(uint64_t* m, uint32_t phase) {
+  for (int i = 0; i < CNN_WAIT_LIMIT; ++i)
+    if (vd_mbar_try_wait(m, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void vd_fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void vd_tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void vd_tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive f32 columns of this warp's 32 accumulator lanes.
+__device__ __forceinline__ void vd_tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void vd_tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// The convolution GEMM.  X: NHWC bf16 with C_in = K / 9 channels (a multiple
+// of 8).  Wt: [N][K] bf16.  Epilogues:
+//   EPI_RELU  out = bf16 NHWC [HW][N]: relu(D + bias)
+//   EPI_LAST  out = f32 [HW][2]: D[0..1] + bias[0..1]
+//   EPI_DGRAD out = bf16 NHWC [HW][N]: D where mask[p][c] > 0, else 0
+// ---------------------------------------------------------------------------
+enum { EPI_RELU = 0, EPI_LAST = 1, EPI_DGRAD = 2 };
+
+template <int K, int N>
+constexpr size_t vd_conv_smem() {
+  return (size_t)CNN_TILE * K * 2 + (size_t)N * K * 2;
+}
+
+template <int K, int N, int EPI>
+__global__ void __launch_bounds__(CNN_TILE)
+k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
+          const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
+          void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int* __restrict__ err) {
+  static_assert(K % 144 == 0 && (N == 16 || N == 32), "shapes of this network");
+  constexpr int CIN = K / 9, CPT = CIN / 8, KG = K / 8;
+  constexpr uint32_t NCOLS = 32;   // smallest tensor-memory allocation
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + (size_t)CNN_TILE * K * 2;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int HW = Wimg * Himg;
+  const int p0 = blockIdx.x * CNN_TILE;
+  if (warp == 0) vd_tmem_alloc(&tmem_base, NCOLS);
+  if (tid == 0) vd_mbar_init(&mbar, 1);
+  // A: im2col rows of the tile's pixels (zeros outside the image)
+  for (int idx = tid; idx < CNN_TILE * 9 * CPT; idx += CNN_TILE) {
+    const int m = idx / (9 * CPT);
+    const int rem = idx - m * (9 * CPT);
+    const int tap = rem / CPT, ch = rem - tap * CPT;
+    const int p = p0 + m;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (p < HW) {
+      const int y = p / Wimg, x = p - y * Wimg;
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * Wimg + xx) * CIN + ch * 8);
+    }
+    const int kg = tap * CPT + ch;
+    *reinterpret_cast<uint4*>(sA + (size_t)(m >> 3) * (K * 16) + kg * 128 + (m & 7) * 16) = v;
+  }
+  // B: the weights
+  for (int idx = tid; idx < N * KG; idx += CNN_TILE) {
+    const int n = idx / KG, kg = idx - n * KG;
+    const uint4 v = *reinterpret_cast<const uint4*>(Wt + (size_t)n * K + kg * 8);
+    *reinterpret_cast<uint4*>(sB + (size_t)(n >> 3) * (K * 16) + kg * 128 + (n & 7) * 16) = v;
+  }
+  vd_fence_async_smem();   // the generic-proxy stores above feed the tensor core
+  vd_tc_fence_before();
+  __syncthreads();
+  vd_tc_fence_after();
+  const uint32_t dt = tmem_base;
+  if (tid == 0) {
+    const uint32_t a0 = vd_smem_u32(sA), b0 = vd_smem_u32(sB);
+    constexpr uint32_t idesc = vd_idesc_bf16(CNN_TILE, N);
+#pragma unroll 1
+    for (int s = 0; s < K / 16; ++s)   // two core matrices (16 k) per instruction
+      vd_umma_bf16(dt, vd_umma_desc(a0 + s * 256, 128, K * 16),
+                   vd_umma_desc(b0 + s * 256, 128, K * 16), idesc, s > 0 ? 1u : 0u);
+    vd_umma_commit(&mbar);
+  }
+  bool ok = vd_mbar_wait_bounded(&mbar, 0);
+  if (!ok) {
+    atomicExch(err, 1);
+    ok = vd_mbar_wait_bounded(&mbar, 0);   // give the tensor core a second bound before freeing
+  }
+  vd_tc_fence_after();
+  const int p = p0 + warp * 32 + lane;     // accumulator lane = pixel of the tile
+  const uint32_t taddr = dt + ((uint32_t)(warp * 32) << 16);
+  if (ok) {
+    float v[32];
+    if (N == 32)
+      vd_tmem_ld32(taddr, v);
+    else
+      vd_tmem_ld16(taddr, v);
+    if (p < HW) {
+      if (EPI == EPI_LAST) {
+        reinterpret_cast<float2*>(out)[p] = make_float2(v[0] + bias[0], v[1] + bias[1]);
+      } else {
+        __align__(16) __nv_bfloat16 o[N];
+        if (EPI == EPI_RELU) {
+#pragma unroll
+          for (int c = 0; c < N; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.0f));
+        } else {
+          __align__(16) __nv_bfloat16 mk[N];
+#pragma unroll
+          for (int c = 0; c < N; c += 8)
+            *reinterpret_cast<uint4*>(mk + c) =
+                *reinterpret_cast<const uint4*>(mask + (size_t)p * N + c);
+#pragma unroll
+          for (int c = 0; c < N; ++c)
+            o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
+        }
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)p * N;
+#pragma unroll
+        for (int c = 0; c < N; c += 8)
+          *reinterpret_cast<uint4*>(dst + c) = *reinterpret_cast<const uint4*>(o + c);
+      }
+    }
+  }
+  vd_tc_fence_before();
+  __syncthreads();
+  if (warp == 0) vd_tmem_dealloc(dt, NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Input planes: flow [N][H][W][2] -> bf16 NHWC with C0 channels.
+// ---------------------------------------------------------------------------
+__global__ void k_cnn_input(const float2* __restrict__ flow, int N, int HW, int C0,
+                            __nv_bfloat16* __restrict__ a0) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= HW) return;
+  for (int c = 0; c < C0; ++c) {
+    float v = 0.0f;
+    if (c < 2 * N) {
+      const float2 f = flow[(size_t)(c >> 1) * HW + p];
+      v = ((c & 1) ? f.y : f.x) * (1.0f / 32.0f);
+    }
+    a0[(size_t)p * C0 + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Heads, loss and dL/dz of the last layer (bf16, 16 channels, 2 used).
+// Per-block partial sums of the loss terms and the mask count.
+// ---------------------------------------------------------------------------
+__global__ void k_cnn_heads(const float2* __restrict__ z, int HW, float rho_min, float rho_max,
+                            float* __restrict__ rho, float* __restrict__ q) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= HW) return;
+  const float2 v = z[p];
+  const float s0 = 1.0f / (1.0f + __expf(-v.x));
+  const float s1 = 1.0f / (1.0f + __expf(-v.y));
+  if (rho) rho[p] = rho_min + (rho_max - rho_min) * s0;
+  if (q) q[p] = s1;
+}
+
+__global__ void k_cnn_loss(const float2* __restrict__ z, int HW, const float* __restrict__ rho_t,
+                           const float* __restrict__ q_t, const unsigned char* __restrict__ mask,
+                           float rho_min, float rho_max, float w_q, const float* __restrict__ nmask,
+                           __nv_bfloat16* __restrict__ dz, double* __restrict__ partial) {
+  __shared__ double s_l[256];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (p < HW) {
+    const float2 v = z[p];
+    const float s0 = 1.0f / (1.0f + __expf(-v.x));
+    const float s1 = 1.0f / (1.0f + __expf(-v.y));
+    const float rho = rho_min + (rho_max - rho_min) * s0;
+    const float m = mask[p] ? 1.0f : 0.0f;
+    const float inv_n = 1.0f / *nmask;
+    const float rt = rho_t[p];
+    const float r = rho / rt - 1.0f;
+    const float qt = q_t[p];
+    const float bce = -(qt * __logf(fmaxf(s1, 1e-12f)) + (1.0f - qt) * __logf(fmaxf(1.0f - s1, 1e-12f)));
+    l = (double)(m * (r * r + w_q * bce));
+    const float d0 = m * 2.0f * r / rt * (rho_max - rho_min) * s0 * (1.0f - s0) * inv_n;
+    const float d1 = w_q * m * (s1 - qt) * inv_n;
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+    o[0] = __float2bfloat16_rn(d0);
+    o[1] = __float2bfloat16_rn(d1);
+    *reinterpret_cast<uint4*>(dz + (size_t)p * 16) = *reinterpret_cast<uint4*>(o);
+    *reinterpret_cast<uint4*>(dz + (size_t)p * 16 + 8) = *reinterpret_cast<uint4*>(o + 8);
+  }
+  s_l[threadIdx.x] = l;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_l[threadIdx.x] += s_l[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = s_l[0];
+}
+
+__global__ void k_cnn_count(const unsigned char* __restrict__ mask, int HW, float* __restrict__ n) {
+  __shared__ int s[256];
+  int c = 0;
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) c += mask[p] ? 1 : 0;
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n = (float)(s[0] > 0 ? s[0] : 1);
+}
+
+__global__ void k_cnn_sum(const double* __restrict__ partial, int n, float* __restrict__ nmask,
+                          double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += partial[i];
+  *out = s / (double)*nmask;
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on the CUDA cores: dW[co][k] = sum_p dz[p][co] A[p][k],
+// db[co] = sum_p dz[p][co].  Block b sums a contiguous pixel range in fixed
+// order into partial[b][co][k] (and partial_b[b][co]); k_cnn_wgrad_reduce
+// adds the blocks in index order.  dz: bf16 [HW][DZC], COUT of its channels
+// used; X: bf16 NHWC with CIN channels.
+// ---------------------------------------------------------------------------
+#define WG_BLOCKS 152
+#define WG_CHUNK 32
+
+template <int CIN, int COUT, int DZC>
+__global__ void __launch_bounds__(256)
+k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dz, int Wimg,
+            int Himg, float* __restrict__ partial, float* __restrict__ partial_b) {
+  constexpr int K = 9 * CIN, NOUT = COUT * K;
+  constexpr int PER = (NOUT + 255) / 256;
+  __shared__ float sA[WG_CHUNK][K];
+  __shared__ float sD[WG_CHUNK][COUT];
+  const int HW = Wimg * Himg;
+  const int per = (HW + gridDim.x - 1) / gridDim.x;
+  const int beg = min(HW, (int)blockIdx.x * per), end = min(HW, beg + per);
+  float acc[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc[i] = 0.0f;
+  float accb = 0.0f;
+  for (int base = beg; base < end; base += WG_CHUNK) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < WG_CHUNK * K; idx += 256) {
+      const int j = idx / K, k = idx - j * K;
+      const int p = base + j;
+      float v = 0.0f;
+      if (p < end) {
+        const int tap = k / CIN, ci = k - tap * CIN;
+        const int y = p / Wimg, x = p - y * Wimg;
+        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+        if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
+          v = __bfloat162float(X[((size_t)yy * Wimg + xx) * CIN + ci]);
+      }
+      sA[j][k] = v;
+    }
+    for (int idx = threadIdx.x; idx < WG_CHUNK * COUT; idx += 256) {
+      const int j = idx / COUT, c = idx - j * COUT;
+      const int p = base + j;
+      sD[j][c] = p < end ? __bfloat162float(dz[(size_t)p * DZC + c]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < WG_CHUNK; ++j) {
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int o = threadIdx.x + 256 * i;
+        if (o < NOUT) acc[i] = fmaf(sD[j][o / K], sA[j][o - (o / K) * K], acc[i]);
+      }
+      if ((int)threadIdx.x < COUT) accb += sD[j][threadIdx.x];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int o = threadIdx.x + 256 * i;
+    if (o < NOUT) partial[(size_t)blockIdx.x * NOUT + o] = acc[i];
+  }
+  if ((int)threadIdx.x < COUT) partial_b[blockIdx.x * COUT + threadIdx.x] = accb;
+}
+
+__global__ void k_cnn_wgrad_reduce(const float* __restrict__ partial,
+                                   const float* __restrict__ partial_b, int nblk, int nout,
+                                   int cout, float* __restrict__ gW, float* __restrict__ gb) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < nout) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * nout + o];
+    gW[o] = s;
+  }
+  if (o < cout) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += partial_b[b * cout + o];
+    gb[o] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adam on the float32 master parameters, then the bf16 copies the GEMMs
+// read: forward Wt[co][k] (rows padded to NPAD) and data-gradient
+// Wd[ci][tap' * COUT_P + co] = W[co][8 - tap'][ci] (COUT padded to COUT_P).
+// ---------------------------------------------------------------------------
+__global__ void k_cnn_adam(float* __restrict__ theta, float* __restrict__ m,
+                           float* __restrict__ v, const float* __restrict__ g, int n, float lr,
+                           float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+__global__ void k_cnn_pack(const float* __restrict__ W, int cout, int cin, int npad, int coutp,
+                           __nv_bfloat16* __restrict__ Wt, __nv_bfloat16* __restrict__ Wd) {
+  const int K = 9 * cin;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // forward copy: [npad][K]
+  if (i < npad * K) {
+    const int co = i / K, k = i - co * K;
+    Wt[i] = __float2bfloat16_rn(co < cout ? W[(size_t)co * K + k] : 0.0f);
+  }
+  // data-gradient copy: [cin][9 * coutp]
+  if (Wd && i < cin * 9 * coutp) {
+    const int ci = i / (9 * coutp), r = i - ci * (9 * coutp);
+    const int tp = r / coutp, co = r - tp * coutp;
+    const int tap = 8 - tp;
+    Wd[i] = __float2bfloat16_rn(co < cout ? W[(size_t)co * K + tap * cin + ci] : 0.0f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct vd_cnn {
+  int N;               // flows
+  int cin[CNN_L], cout[CNN_L];
+  size_t woff[CNN_L], boff[CNN_L];   // offsets of W_l, b_l in the parameter vector
+  size_t nparam;
+  float* theta;        // master parameters (f32)
+  float* mom1;
+  float* mom2;
+  float* grad;
+  __nv_bfloat16* wt[CNN_L];   // forward weights [npad][K]
+  __nv_bfloat16* wd[CNN_L];   // data-gradient weights [cin][9 coutp]
+  int step;
+  // per-image buffers (grown on demand)
+  int cap_hw;
+  __nv_bfloat16* act[CNN_L];  // a_0 .. a_5 (NHWC bf16)
+  __nv_bfloat16* g0;          // dL/dz ping-pong (bf16, 32 channels)
+  __nv_bfloat16* g1;
+  float2* zlast;
+  float* wg_partial;
+  float* wg_partial_b;
+  double* loss_partial;
+  double* loss;
+  float* nmask;
+  int* err;
+};
+
+static void cnn_free_images(vd_cnn* n) {
+  for (int l = 0; l < CNN_L; ++l)
+    if (n->act[l]) cudaFree(n->act[l]), n->act[l] = nullptr;
+  void* p[] = {n->g0, n->g1, n->zlast, n->loss_partial};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  n->g0 = n->g1 = nullptr;
+  n->zlast = nullptr;
+  n->loss_partial = nullptr;
+  n->cap_hw = 0;
+}
+
+static cudaError_t cnn_reserve(vd_cnn* n, int HW) {
+  if (HW <= n->cap_hw) return cudaSuccess;
+  cnn_free_images(n);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < CNN_L && e == cudaSuccess; ++l)
+    e = cudaMalloc(&n->act[l], sizeof(__nv_bfloat16) * (size_t)HW * n->cin[l]);
+  if (e == cudaSuccess) e = cudaMalloc(&n->g0, sizeof(__nv_bfloat16) * (size_t)HW * CNN_WIDTH);
+  if (e == cudaSuccess) e = cudaMalloc(&n->g1, sizeof(__nv_bfloat16) * (size_t)HW * CNN_WIDTH);
+  if (e == cudaSuccess) e = cudaMalloc(&n->zlast, sizeof(float2) * (size_t)HW);
+  if (e == cudaSuccess) e = cudaMalloc(&n->loss_partial, sizeof(double) * ((HW + 255) / 256));
+  if (e == cudaSuccess) n->cap_hw = HW;
+  return e;
+}
+
+template <int K, int N, int EPI>
+static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_bfloat16* Wt,
+                               const float* b, void* out, const __nv_bfloat16* mask, int* err,
+                               cudaStream_t s) {
+  const size_t smem = vd_conv_smem<K, N>();
+  cudaError_t e = cudaFuncSetAttribute(k_conv_tc<K, N, EPI>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int HW = W * H;
+  k_conv_tc<K, N, EPI><<<(HW + CNN_TILE - 1) / CNN_TILE, CNN_TILE, smem, s>>>(X, W, H, Wt, b,
+                                                                             out, mask, err);
+  return cudaGetLastError();
+}
+
+// Forward pass of the whole network on flow [N][H][W][2] (device); keeps the
+// activations for a backward pass.
+static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaStream_t s) {
+  const int HW = W * H;
+  cudaError_t e = cnn_reserve(n, HW);
+  if (e != cudaSuccess) return e;
+  k_cnn_input<<<(HW + 255) / 256, 256, 0, s>>>((const float2*)flow, n->N, HW, n->cin[0],
+                                               n->act[0]);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int l = 0; l < CNN_L; ++l) {
+    const float* b = n->theta + n->boff[l];
+    const int K = 9 * n->cin[l];
+    if (l == CNN_L - 1) {
+      e = launch_conv<288, 16, EPI_LAST>(n->act[l], W, H, n->wt[l], b, n->zlast, nullptr, n->err, s);
+    } else if (K == 144) {
+      e = launch_conv<144, 32, EPI_RELU>(n->act[l], W, H, n->wt[l], b, n->act[l + 1], nullptr,
+                                         n->err, s);
+    } else {
+      e = launch_conv<288, 32, EPI_RELU>(n->act[l], W, H, n->wt[l], b, n->act[l + 1], nullptr,
+                                         n->err, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Gradients of the loss with respect to every parameter, after cnn_forward
+// on the same image; dz of the last layer comes from k_cnn_loss (in g0 with
+// 16 channels).
+template <int CIN, int COUT, int DZC>
+static cudaError_t launch_wgrad(vd_cnn* n, int l, const __nv_bfloat16* dz, int W, int H,
+                                cudaStream_t s) {
+  k_cnn_wgrad<CIN, COUT, DZC><<<WG_BLOCKS, 256, 0, s>>>(n->act[l], dz, W, H, n->wg_partial,
+                                                       n->wg_partial_b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nout = COUT * 9 * CIN;
+  k_cnn_wgrad_reduce<<<(nout + 255) / 256, 256, 0, s>>>(n->wg_partial, n->wg_partial_b,
+                                                        WG_BLOCKS, nout, COUT,
+                                                        n->grad + n->woff[l], n->grad + n->boff[l]);
+  return cudaGetLastError();
+}
+
+static cudaError_t cnn_backward(vd_cnn* n, int W, int H, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  __nv_bfloat16* dz = n->g0;    // dL/dz of layer l
+  __nv_bfloat16* nxt = n->g1;
+  for (int l = CNN_L - 1; l >= 0 && e == cudaSuccess; --l) {
+    if (l == CNN_L - 1)
+      e = launch_wgrad<32, 2, 16>(n, l, dz, W, H, s);
+    else if (l == 0)
+      e = launch_wgrad<16, 32, 32>(n, l, dz, W, H, s);
+    else
+      e = launch_wgrad<32, 32, 32>(n, l, dz, W, H, s);
+    if (e != cudaSuccess || l == 0) break;
+    // dL/dz_{l-1} = (W_l^T * dL/dz_l) where a_l > 0
+    if (l == CNN_L - 1)
+      e = launch_conv<144, 32, EPI_DGRAD>(dz, W, H, n->wd[l], nullptr, nxt, n->act[l], n->err, s);
+    else
+      e = launch_conv<288, 32, EPI_DGRAD>(dz, W, H, n->wd[l], nullptr, nxt, n->act[l], n->err, s);
+    __nv_bfloat16* t = dz;
+    dz = nxt;
+    nxt = t;
+  }
+  return e;
+}
+
+static cudaError_t cnn_pack_all(vd_cnn* n, cudaStream_t s) {
+  for (int l = 0; l < CNN_L; ++l) {
+    const int cin = n->cin[l], cout = n->cout[l];
+    const int npad = cout < 16 ? 16 : cout;
+    const int coutp = cout < 16 ? 16 : cout;
+    const int cnt = max(npad * 9 * cin, cin * 9 * coutp);
+    k_cnn_pack<<<(cnt + 255) / 256, 256, 0, s>>>(n->theta + n->woff[l], cout, cin, npad, coutp,
+                                                 n->wt[l], l > 0 ? n->wd[l] : nullptr);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static vd_status cnn_check_err(vd_cnn* n, cudaStream_t s) {
+  int h = 0;
+  VD_CU(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VD_CU(cudaStreamSynchronize(s));
+  if (h) {
+    vd_set_error("a tensor-core wait gave up");
+    return VD_ERR_TIMEOUT;
+  }
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn** out) {
+  if (!out || n_flows < 1 || n_flows > 8) return VD_ERR_ARG;
+  *out = nullptr;
+  vd_cnn* n = new vd_cnn();
+  memset((void*)n, 0, sizeof *n);
+  n->N = n_flows;
+  // input planes: 2N rounded up to 8, at least 16 (the GEMM tiles take 16 or
+  // 32 input channels)
+  const int c0 = (2 * n_flows + 7) / 8 * 8;
+  const int c0p = c0 <= 16 ? 16 : c0;
+  size_t off = 0;
+  for (int l = 0; l < CNN_L; ++l) {
+    n->cin[l] = l == 0 ? c0p : CNN_WIDTH;
+    n->cout[l] = l == CNN_L - 1 ? 2 : CNN_WIDTH;
+    n->woff[l] = off;
+    off += (size_t)n->cout[l] * 9 * n->cin[l];
+    n->boff[l] = off;
+    off += n->cout[l];
+  }
+  n->nparam = off;
+  // He-normal weights (std sqrt(2 / fan_in)) from a host generator seeded by
+  // `seed` (Box-Muller on a 64-bit LCG); zero biases.  Padding channels of
+  // the input layer get zero weights.
+  std::vector<float> h(off, 0.0f);
+  unsigned long long st = seed * 6364136223846793005ull + 1442695040888963407ull;
+  auto u01 = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (int l = 0; l < CNN_L; ++l) {
+    const int cin_real = l == 0 ? 2 * n_flows : n->cin[l];
+    const double sd = sqrt(2.0 / (9.0 * cin_real));
+    for (int co = 0; co < n->cout[l]; ++co)
+      for (int t = 0; t < 9; ++t)
+        for (int ci = 0; ci < n->cin[l]; ++ci) {
+          const double g = sqrt(-2.0 * log(u01())) * cos(6.283185307179586 * u01());
+          h[n->woff[l] + ((size_t)co * 9 + t) * n->cin[l] + ci] =
+              ci < cin_real ? (float)(g * sd) : 0.0f;
+        }
+  }
+  cudaError_t e = cudaMalloc(&n->theta, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMalloc(&n->mom1, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMalloc(&n->mom2, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMalloc(&n->grad, sizeof(float) * off);
+  for (int l = 0; l < CNN_L && e == cudaSuccess; ++l) {
+    const int npad = n->cout[l] < 16 ? 16 : n->cout[l];
+    e = cudaMalloc(&n->wt[l], sizeof(__nv_bfloat16) * npad * 9 * n->cin[l]);
+    if (e == cudaSuccess && l > 0)
+      e = cudaMalloc(&n->wd[l], sizeof(__nv_bfloat16) * n->cin[l] * 9 * npad);
+  }
+  if (e == cudaSuccess)
+    e = cudaMalloc(&n->wg_partial, sizeof(float) * WG_BLOCKS * CNN_WIDTH * 9 * CNN_WIDTH);
+  if (e == cudaSuccess) e = cudaMalloc(&n->wg_partial_b, sizeof(float) * WG_BLOCKS * CNN_WIDTH);
+  if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&n->nmask, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(n->theta, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->mom1, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(n->mom2, 0, sizeof(float) * off);
+  if (e == cudaSuccess) e = cudaMemset(n->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cnn_pack_all(n, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    vd_cnn_destroy(n);
+    return e == cudaErrorMemoryAllocation ? VD_ERR_OOM : VD_ERR_CUDA;
+  }
+  *out = n;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_destroy(vd_cnn* n) {
+  if (!n) return VD_ERR_ARG;
+  cudaDeviceSynchronize();
+  cnn_free_images(n);
+  void* p[] = {n->theta, n->mom1, n->mom2, n->grad, n->wg_partial, n->wg_partial_b,
+               n->loss, n->nmask, n->err};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  for (int l = 0; l < CNN_L; ++l) {
+    if (n->wt[l]) cudaFree(n->wt[l]);
+    if (n->wd[l]) cudaFree(n->wd[l]);
+  }
+  delete n;
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_layout(vd_cnn* n, int* n_params, int* cin, int* cout, long* woff,
+                                   long* boff) {
+  if (!n || !n_params) return VD_ERR_ARG;
+  *n_params = (int)n->nparam;
+  for (int l = 0; l < CNN_L; ++l) {
+    if (cin) cin[l] = n->cin[l];
+    if (cout) cout[l] = n->cout[l];
+    if (woff) woff[l] = (long)n->woff[l];
+    if (boff) boff[l] = (long)n->boff[l];
+  }
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_get_params(vd_cnn* n, float* out) {
+  if (!n || !out) return VD_ERR_ARG;
+  VD_CU(cudaMemcpy(out, n->theta, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost));
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_set_params(vd_cnn* n, const float* in) {
+  if (!n || !in) return VD_ERR_ARG;
+  for (size_t i = 0; i < n->nparam; ++i)
+    if (!isfinite(in[i])) return VD_ERR_ARG;
+  VD_CU(cudaMemcpy(n->theta, in, sizeof(float) * n->nparam, cudaMemcpyHostToDevice));
+  VD_CU(cudaMemset(n->mom1, 0, sizeof(float) * n->nparam));
+  VD_CU(cudaMemset(n->mom2, 0, sizeof(float) * n->nparam));
+  n->step = 0;
+  VD_CU(cnn_pack_all(n, 0));
+  VD_CU(cudaDeviceSynchronize());
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_get_grads(vd_cnn* n, float* out) {
+  if (!n || !out) return VD_ERR_ARG;
+  VD_CU(cudaMemcpy(out, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost));
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_get_activation(vd_cnn* n, int layer, float* out, int width,
+                                           int height) {
+  if (!n || !out || layer < 0 || layer > CNN_L || width * height > n->cap_hw) return VD_ERR_ARG;
+  const size_t HW = (size_t)width * height;
+  if (layer == CNN_L) {   // z of the last layer, [HW][2]
+    VD_CU(cudaMemcpy(out, n->zlast, sizeof(float2) * HW, cudaMemcpyDeviceToHost));
+    return VD_OK;
+  }
+  const int C = n->cin[layer];
+  std::vector<__nv_bfloat16> h(HW * C);
+  VD_CU(cudaMemcpy(h.data(), n->act[layer], sizeof(__nv_bfloat16) * h.size(),
+                   cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < h.size(); ++i) out[i] = __bfloat162float(h[i]);
+  return VD_OK;
+}
+
+extern "C" vd_status vd_cnn_forward(vd_cnn* n, const float* flow, int width, int height,
+                                    float rho_min, float rho_max, float* rho_out, float* q_out,
+                                    void* stream) {
+  if (!n || !flow || width < 1 || height < 1 || !(rho_max > rho_min)) return VD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  VD_CU(cudaMemsetAsync(n->err, 0, sizeof(int), s));
+  VD_CU(cnn_forward(n, flow, width, height, s));
+  const int HW = width * height;
+  if (rho_out || q_out) {
+    k_cnn_heads<<<(HW + 255) / 256, 256, 0, s>>>(n->zlast, HW, rho_min, rho_max, rho_out, q_out);
+    VD_CU(cudaGetLastError());
+  }
+  return cnn_check_err(n, s);
+}
+
+extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, const float* rho_t,
+                                       const float* q_t, const unsigned char* mask, int width,
+                                       int height, float rho_min, float rho_max, float w_q,
+                                       float lr, int update, double* loss_out, void* stream) {
+  if (!n || !flow || !rho_t || !q_t || !mask || width < 1 || height < 1 ||
+      !(rho_max > rho_min) || !(lr >= 0.0f))
+    return VD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int HW = width * height;
+  VD_CU(cudaMemsetAsync(n->err, 0, sizeof(int), s));
+  VD_CU(cnn_forward(n, flow, width, height, s));
+  k_cnn_count<<<1, 256, 0, s>>>(mask, HW, n->nmask);
+  const int nb = (HW + 255) / 256;
+  k_cnn_loss<<<nb, 256, 0, s>>>(n->zlast, HW, rho_t, q_t, mask, rho_min, rho_max, w_q, n->nmask,
+                                n->g0, n->loss_partial);
+  k_cnn_sum<<<1, 32, 0, s>>>(n->loss_partial, nb, n->nmask, n->loss);
+  VD_CU(cudaGetLastError());
+  VD_CU(cnn_backward(n, width, height, s));
+  if (update) {
+    n->step += 1;
+    const float bc1 = (float)(1.0 - pow(0.9, n->step)), bc2 = (float)(1.0 - pow(0.999, n->step));
+    k_cnn_adam<<<(int)((n->nparam + 255) / 256), 256, 0, s>>>(n->theta, n->mom1, n->mom2, n->grad,
+                                                              (int)n->nparam, lr, bc1, bc2);
+    VD_CU(cudaGetLastError());
+    VD_CU(cnn_pack_all(n, s));
+  }
+  if (loss_out) VD_CU(cudaMemcpyAsync(loss_out, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return cnn_check_err(n, s);
+}
+
+// ---------------------------------------------------------------------------
+// Initial EM state of a context from the network: rho (in the context's
+// range) and q for every flow (plane 0 copied to the others).
+// ---------------------------------------------------------------------------
+int vd_cnn_flows(const vd_cnn* n) { return n->N; }
+
+cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(n->err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cnn_forward(n, (const float*)c->flow, c->W, c->H, c->stream);
+  if (e != cudaSuccess) return e;
+  const int HW = c->W * c->H;
+  k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, c->prm.rho_min,
+                                                       c->prm.rho_max, c->rho, c->q);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int t = 1; t < c->N && e == cudaSuccess; ++t)
+    e = cudaMemcpyAsync(c->q + (size_t)t * HW, c->q, sizeof(float) * HW,
+                        cudaMemcpyDeviceToDevice, c->stream);
+  return e;
+}
+
+int* vd_cnn_err_flag(vd_cnn* n) { return n->err; }

@@ -154,8 +154,22 @@ cudaError_t launch_stats(vd_ctx* c, double* out2);
 cudaError_t launch_prior_prepare(vd_ctx* c, const float* raw, const float* conf);
 cudaError_t launch_check_finite(const float* p, size_t n, int* flag, cudaStream_t s);
 cudaError_t launch_copy_flow(vd_ctx* c, int t, const float* src, long pitch);
+// learned initialiser (vd_cnn.cu): rho and q of the context from the network
+int vd_cnn_flows(const vd_cnn* n);
+cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c);
+int* vd_cnn_err_flag(vd_cnn* n);
 
 void vd_set_error(const char* msg);
+
+// Return from a vd_status function on a CUDA error (recording its message).
+#define VD_CU(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) {                          \
+      vd_set_error(cudaGetErrorString(e_));           \
+      return e_ == cudaErrorMemoryAllocation ? VD_ERR_OOM : VD_ERR_CUDA; \
+    }                                                 \
+  } while (0)
 // stage profiling hooks (no-ops unless enabled); `n_launch` kernels are counted
 void vd_prof_begin(vd_ctx* c, int stage);
 void vd_prof_end(vd_ctx* c, int stage, int n_launch);

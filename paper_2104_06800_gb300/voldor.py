@@ -118,6 +118,17 @@ _SIGS = {
     "vd_batch_window": [_P, C.c_int, C.POINTER(_P)],
     "vd_batch_run": [_P, C.c_int, C.c_int, _P],
     "vd_batch_get_stats": [_P, C.POINTER(vd_batch_stats)],
+    "vd_cnn_create": [C.c_int, C.c_ulonglong, C.POINTER(_P)],
+    "vd_cnn_destroy": [_P],
+    "vd_cnn_layout": [_P, C.POINTER(C.c_int), _P, _P, _P, _P],
+    "vd_cnn_get_params": [_P, _P],
+    "vd_cnn_set_params": [_P, _P],
+    "vd_cnn_get_grads": [_P, _P],
+    "vd_cnn_forward": [_P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P, _P, _P],
+    "vd_cnn_get_activation": [_P, C.c_int, _P, C.c_int, C.c_int],
+    "vd_cnn_train_step": [_P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+                          C.c_float, C.c_int, C.POINTER(C.c_double), _P],
+    "vd_bootstrap_learned": [_P, _P],
     "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
     "vd_import_state": [_P, _P, C.c_size_t],
 }
@@ -442,6 +453,86 @@ def vd_batch_get_stats(batch):
     _call("vd_batch_get_stats", batch, C.byref(st))
     return dict(windows=st.windows, captures=st.captures, replays=st.replays,
                 graph_nodes=st.graph_nodes, kernels_per_run=st.kernels_per_run)
+
+
+# ------------------------------------------------------------------ learned initialiser
+VD_CNN_LAYERS = 6
+
+
+def _dev(x):
+    """Pointer of a CUDA tensor (the learned-initialiser calls take device memory)."""
+    if not (_is_tensor(x) and x.is_cuda and x.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    return C.c_void_p(x.data_ptr())
+
+
+def vd_cnn_create(n_flows, seed=0):
+    h = C.c_void_p()
+    _call("vd_cnn_create", int(n_flows), int(seed), C.byref(h))
+    return h
+
+
+def vd_cnn_destroy(net):
+    _call("vd_cnn_destroy", net)
+
+
+def vd_cnn_layout(net):
+    n = C.c_int(0)
+    cin = (C.c_int * VD_CNN_LAYERS)()
+    cout = (C.c_int * VD_CNN_LAYERS)()
+    wo = (C.c_long * VD_CNN_LAYERS)()
+    bo = (C.c_long * VD_CNN_LAYERS)()
+    _call("vd_cnn_layout", net, C.byref(n), cin, cout, wo, bo)
+    return dict(n_params=n.value, c_in=list(cin), c_out=list(cout), w_offset=list(wo),
+                b_offset=list(bo))
+
+
+def vd_cnn_get_params(net):
+    out = np.zeros(vd_cnn_layout(net)["n_params"], np.float32)
+    _call("vd_cnn_get_params", net, out.ctypes.data_as(C.c_void_p))
+    return out
+
+
+def vd_cnn_set_params(net, params):
+    p = np.ascontiguousarray(params, np.float32)
+    _call("vd_cnn_set_params", net, p.ctypes.data_as(C.c_void_p))
+
+
+def vd_cnn_get_grads(net):
+    out = np.zeros(vd_cnn_layout(net)["n_params"], np.float32)
+    _call("vd_cnn_get_grads", net, out.ctypes.data_as(C.c_void_p))
+    return out
+
+
+def vd_cnn_forward(net, flow, rho_min, rho_max, rho_out=None, q_out=None, stream=None):
+    """flow: CUDA float32 tensor [N][H][W][2]; outputs CUDA float32 [H][W]."""
+    H, W = flow.shape[1], flow.shape[2]
+    _call("vd_cnn_forward", net, _dev(flow), int(W), int(H), float(rho_min), float(rho_max),
+          _dev(rho_out) if rho_out is not None else None,
+          _dev(q_out) if q_out is not None else None,
+          stream if stream is not None else current_stream())
+
+
+def vd_cnn_get_activation(net, layer, W, H, channels):
+    out = np.zeros((H, W, channels), np.float32)
+    _call("vd_cnn_get_activation", net, int(layer), out.ctypes.data_as(C.c_void_p), int(W), int(H))
+    return out
+
+
+def vd_cnn_train_step(net, flow, rho_t, q_t, mask, rho_min, rho_max, w_q, lr, update=True,
+                      stream=None):
+    """All arrays CUDA tensors ([N][H][W][2] flow; [H][W] targets, uint8 mask).
+    Returns the loss of the forward pass before the update."""
+    H, W = flow.shape[1], flow.shape[2]
+    loss = C.c_double(0.0)
+    _call("vd_cnn_train_step", net, _dev(flow), _dev(rho_t), _dev(q_t), _dev(mask), int(W), int(H),
+          float(rho_min), float(rho_max), float(w_q), float(lr), 1 if update else 0,
+          C.byref(loss), stream if stream is not None else current_stream())
+    return loss.value
+
+
+def vd_bootstrap_learned(ctx, net):
+    _call("vd_bootstrap_learned", ctx, net)
 
 
 def vd_export_state(ctx):

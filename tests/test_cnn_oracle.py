@@ -99,9 +99,9 @@ def test_adam_first_step_closed_form():
 
 
 def test_shapes_and_input_planes():
-    assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 8
+    assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 16 and cnn.in_channels(8) == 16
     assert cnn.layer_shapes(6) == [(16, 32)] + [(32, 32)] * 4 + [(32, 2)]
     flow = np.zeros((2, 3, 4, 2), np.float32)
     flow[1, 2, 3] = (32.0, -64.0)
     a = cnn.input_planes(flow)
-    assert a.shape == (8, 3, 4) and a[2, 2, 3] == 1.0 and a[3, 2, 3] == -2.0 and a[4:].sum() == 0
+    assert a.shape == (16, 3, 4) and a[2, 2, 3] == 1.0 and a[3, 2, 3] == -2.0 and a[4:].sum() == 0
