@@ -16,9 +16,10 @@ Architecture (all convolutions 3x3, stride 1, zero padding 1):
           multiple of 8, at least 16)
   layer l z_l = conv(a_l, W_l) + b_l, W_l[co][ky][kx][ci];
           a_{l+1} = relu(z_l) for every layer but the last
-  output  rho = rho_min + (rho_max - rho_min) sigmoid(z[0]),  q = sigmoid(z[1])
+  output  rho = rho_min + (rho_max - rho_min) sigmoid(z[0]),
+          q_t = sigmoid(z[t]) for flows t = 1..N (one rigidness map per flow)
 Loss over pixels with mask m:
-  L = sum m (rho / rho* - 1)^2 / sum m  +  w_q sum m BCE(q, q*) / sum m
+  L = sum m (rho / rho* - 1)^2 / sum m  +  w_q sum_t sum m BCE(q_t, q*_t) / (N sum m)
 Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
       theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 """
@@ -34,8 +35,8 @@ def in_channels(n_flows):
 
 
 def layer_shapes(n_flows, width=32, layers=6):
-    """[(C_in, C_out)] of every layer."""
-    c = [in_channels(n_flows)] + [width] * (layers - 1) + [2]
+    """[(C_in, C_out)] of every layer (the last has 1 + N outputs)."""
+    c = [in_channels(n_flows)] + [width] * (layers - 1) + [1 + n_flows]
     return [(c[i], c[i + 1]) for i in range(layers)]
 
 
@@ -99,24 +100,26 @@ def forward(params, a0, bf16_storage=True):
 
 
 def heads(z, rho_min, rho_max):
-    s0 = 1.0 / (1.0 + np.exp(-z[0]))
-    s1 = 1.0 / (1.0 + np.exp(-z[1]))
-    return rho_min + (rho_max - rho_min) * s0, s1
+    """(rho [H][W], q [N][H][W]) from the last layer's z [1 + N][H][W]."""
+    s = 1.0 / (1.0 + np.exp(-z))
+    return rho_min + (rho_max - rho_min) * s[0], s[1:]
 
 
 def loss_and_grad(z, rho_t, q_t, mask, rho_min, rho_max, w_q):
-    """Loss L and dL/dz for the two output channels."""
+    """Loss L and dL/dz of the last layer; q_t: [N][H][W] targets."""
     rho, q = heads(z, rho_min, rho_max)
+    q_t = np.asarray(q_t, np.float64).reshape(q.shape)
     m = np.asarray(mask, np.float64)
     nm = max(m.sum(), 1.0)
+    nq = q.shape[0]
     r = rho / rho_t - 1.0
     eps = 1e-12
     bce = -(q_t * np.log(np.maximum(q, eps)) + (1 - q_t) * np.log(np.maximum(1 - q, eps)))
-    L = float((m * r * r).sum() / nm + w_q * (m * bce).sum() / nm)
+    L = float((m * r * r).sum() / nm + w_q * (m * bce).sum() / (nq * nm))
     s0 = (rho - rho_min) / (rho_max - rho_min)
     dz = np.zeros_like(z)
     dz[0] = m * 2.0 * r / rho_t * (rho_max - rho_min) * s0 * (1.0 - s0) / nm
-    dz[1] = w_q * m * (q - q_t) / nm
+    dz[1:] = w_q * m * (q - q_t) / (nq * nm)
     return L, dz
 
 

@@ -614,10 +614,11 @@ static cudaError_t bootstrap(vd_ctx* c) {
   return e;
 }
 
-// Bootstrap from the learned initialiser: the network's rho and q replace
-// the random depth, the depth step on X_1 and q = 1 of the monocular
-// bootstrap (R11); the poses come from the 8-point bootstrap (monocular, no
-// poses set) or the initial poses, then one pose M-step as in bootstrap().
+// Bootstrap with the learned initialiser: the monocular bootstrap of R11
+// with the network's inverse depth as the initial value of its depth step
+// (slot 0 of every pixel's candidates, in place of the random draw) and the
+// network's per-flow rigidness in place of q = 1 afterwards.  With a prior,
+// the prior's inverse depth stays the initial value and only q changes.
 static cudaError_t bootstrap_learned(vd_ctx* c, vd_cnn* net) {
   vd_prof_begin(c, VD_ST_OTHER);
   cudaError_t e = cudaMemcpyAsync(c->G, c->G_init, sizeof(double) * 12 * (c->N + 1),
@@ -625,12 +626,27 @@ static cudaError_t bootstrap_learned(vd_ctx* c, vd_cnn* net) {
   if (e == cudaSuccess) e = launch_posef(c);
   if (e == cudaSuccess) e = launch_fill(c->qhat, 1.0f, c->npix, c->stream);
   int n = 2;
+  if (e == cudaSuccess && c->prior_kind != VD_PRIOR_NONE) {
+    e = launch_initial_rho(c);
+    ++n;
+  }
   if (e == cudaSuccess && c->prior_kind == VD_PRIOR_NONE && !c->poses_set) {
     e = launch_eight_point(c);
     n += 2 * VD_IRLS_ITERS + 3;
   }
-  if (e == cudaSuccess) e = launch_cnn_init(net, c);
+  // the network's rho (into the state when there is no prior, else into
+  // scratch) and its rigidness of every flow
+  if (e == cudaSuccess)
+    e = launch_cnn_init(net, c, c->prior_kind == VD_PRIOR_NONE ? c->rho : c->rho_mid);
   vd_prof_end(c, VD_ST_OTHER, n + 2 + 2 * VD_CNN_LAYERS);
+  if (e != cudaSuccess) return e;
+  if (c->prior_kind == VD_PRIOR_NONE) {
+    // depth from X_1 alone (the argmin does not depend on q_1 > 0), then the
+    // network's q again for every flow
+    e = depth_step(c, -1, 0, true);
+    if (e == cudaSuccess) e = launch_cnn_rigidness(net, c);
+    vd_prof_end(c, VD_ST_OTHER, 1);
+  }
   if (e == cudaSuccess && !c->poses_set) e = pose_step(c, -1, 0);
   return e;
 }

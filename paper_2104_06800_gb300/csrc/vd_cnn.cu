@@ -150,7 +150,7 @@ __device__ __forceinline__ void vd_tmem_ld16(uint32_t taddr, float* v) {
 // The convolution GEMM.  X: NHWC bf16 with C_in = K / 9 channels (a multiple
 // of 8).  Wt: [N][K] bf16.  Epilogues:
 //   EPI_RELU  out = bf16 NHWC [HW][N]: relu(D + bias)
-//   EPI_LAST  out = f32 [HW][2]: D[0..1] + bias[0..1]
+//   EPI_LAST  out = f32 [HW][16]: D + bias for the nout real channels, 0 after
 //   EPI_DGRAD out = bf16 NHWC [HW][N]: D where mask[p][c] > 0, else 0
 // ---------------------------------------------------------------------------
 enum { EPI_RELU = 0, EPI_LAST = 1, EPI_DGRAD = 2 };
@@ -164,7 +164,8 @@ template <int K, int N, int EPI>
 __global__ void __launch_bounds__(CNN_TILE)
 k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
           const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
-          void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int* __restrict__ err) {
+          void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int nout,
+          int* __restrict__ err) {
   static_assert(K % 144 == 0 && (N == 16 || N == 32), "shapes of this network");
   constexpr int CIN = K / 9, CPT = CIN / 8, KG = K / 8;
   constexpr uint32_t NCOLS = 32;   // smallest tensor-memory allocation
@@ -230,7 +231,14 @@ k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
       vd_tmem_ld16(taddr, v);
     if (p < HW) {
       if (EPI == EPI_LAST) {
-        reinterpret_cast<float2*>(out)[p] = make_float2(v[0] + bias[0], v[1] + bias[1]);
+        float* dst = reinterpret_cast<float*>(out) + (size_t)p * 16;
+#pragma unroll
+        for (int c = 0; c < 16; c += 4)
+          *reinterpret_cast<float4*>(dst + c) =
+              make_float4(c + 0 < nout ? v[c + 0] + bias[c + 0] : 0.0f,
+                          c + 1 < nout ? v[c + 1] + bias[c + 1] : 0.0f,
+                          c + 2 < nout ? v[c + 2] + bias[c + 2] : 0.0f,
+                          c + 3 < nout ? v[c + 3] + bias[c + 3] : 0.0f);
       } else {
         __align__(16) __nv_bfloat16 o[N];
         if (EPI == EPI_RELU) {
@@ -276,46 +284,49 @@ __global__ void k_cnn_input(const float2* __restrict__ flow, int N, int HW, int 
 }
 
 // ---------------------------------------------------------------------------
-// Heads, loss and dL/dz of the last layer (bf16, 16 channels, 2 used).
-// Per-block partial sums of the loss terms and the mask count.
+// Heads, loss and dL/dz of the last layer (z: f32 [HW][16], channel 0 the
+// inverse depth, 1..N the rigidness of each flow; dz: bf16 [HW][16]).
+// Per-block partial sums of the loss.
 // ---------------------------------------------------------------------------
-__global__ void k_cnn_heads(const float2* __restrict__ z, int HW, float rho_min, float rho_max,
-                            float* __restrict__ rho, float* __restrict__ q) {
+__global__ void k_cnn_heads(const float* __restrict__ z, int HW, int N, float rho_min,
+                            float rho_max, float* __restrict__ rho, float* __restrict__ q) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
-  const float2 v = z[p];
-  const float s0 = 1.0f / (1.0f + __expf(-v.x));
-  const float s1 = 1.0f / (1.0f + __expf(-v.y));
-  if (rho) rho[p] = rho_min + (rho_max - rho_min) * s0;
-  if (q) q[p] = s1;
+  const float* v = z + (size_t)p * 16;
+  if (rho) rho[p] = rho_min + (rho_max - rho_min) / (1.0f + __expf(-v[0]));
+  if (q)
+    for (int t = 0; t < N; ++t) q[(size_t)t * HW + p] = 1.0f / (1.0f + __expf(-v[1 + t]));
 }
 
-__global__ void k_cnn_loss(const float2* __restrict__ z, int HW, const float* __restrict__ rho_t,
-                           const float* __restrict__ q_t, const unsigned char* __restrict__ mask,
-                           float rho_min, float rho_max, float w_q, const float* __restrict__ nmask,
+__global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
+                           const float* __restrict__ rho_t, const float* __restrict__ q_t,
+                           const unsigned char* __restrict__ mask, float rho_min, float rho_max,
+                           float w_q, const float* __restrict__ nmask,
                            __nv_bfloat16* __restrict__ dz, double* __restrict__ partial) {
   __shared__ double s_l[256];
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   double l = 0.0;
   if (p < HW) {
-    const float2 v = z[p];
-    const float s0 = 1.0f / (1.0f + __expf(-v.x));
-    const float s1 = 1.0f / (1.0f + __expf(-v.y));
+    const float* v = z + (size_t)p * 16;
+    const float s0 = 1.0f / (1.0f + __expf(-v[0]));
     const float rho = rho_min + (rho_max - rho_min) * s0;
     const float m = mask[p] ? 1.0f : 0.0f;
     const float inv_n = 1.0f / *nmask;
+    const float wq_n = w_q / (float)N;
     const float rt = rho_t[p];
     const float r = rho / rt - 1.0f;
-    const float qt = q_t[p];
-    const float bce = -(qt * __logf(fmaxf(s1, 1e-12f)) + (1.0f - qt) * __logf(fmaxf(1.0f - s1, 1e-12f)));
-    l = (double)(m * (r * r + w_q * bce));
-    const float d0 = m * 2.0f * r / rt * (rho_max - rho_min) * s0 * (1.0f - s0) * inv_n;
-    const float d1 = w_q * m * (s1 - qt) * inv_n;
     __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
-    o[0] = __float2bfloat16_rn(d0);
-    o[1] = __float2bfloat16_rn(d1);
+    o[0] = __float2bfloat16_rn(m * 2.0f * r / rt * (rho_max - rho_min) * s0 * (1.0f - s0) * inv_n);
+    float bce = 0.0f;
+    for (int t = 0; t < N; ++t) {
+      const float s = 1.0f / (1.0f + __expf(-v[1 + t]));
+      const float qt = q_t[(size_t)t * HW + p];
+      bce += -(qt * __logf(fmaxf(s, 1e-12f)) + (1.0f - qt) * __logf(fmaxf(1.0f - s, 1e-12f)));
+      o[1 + t] = __float2bfloat16_rn(wq_n * m * (s - qt) * inv_n);
+    }
+    l = (double)(m * (r * r + wq_n * bce));
     *reinterpret_cast<uint4*>(dz + (size_t)p * 16) = *reinterpret_cast<uint4*>(o);
     *reinterpret_cast<uint4*>(dz + (size_t)p * 16 + 8) = *reinterpret_cast<uint4*>(o + 8);
   }
@@ -413,18 +424,21 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   if ((int)threadIdx.x < COUT) partial_b[blockIdx.x * COUT + threadIdx.x] = accb;
 }
 
+// The partials hold COUT_P (padded) rows per block; the first cout rows are
+// the real ones.
 __global__ void k_cnn_wgrad_reduce(const float* __restrict__ partial,
-                                   const float* __restrict__ partial_b, int nblk, int nout,
-                                   int cout, float* __restrict__ gW, float* __restrict__ gb) {
+                                   const float* __restrict__ partial_b, int nblk, int stride,
+                                   int nout, int stride_b, int cout, float* __restrict__ gW,
+                                   float* __restrict__ gb) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o < nout) {
     float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * nout + o];
+    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * stride + o];
     gW[o] = s;
   }
   if (o < cout) {
     float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += partial_b[b * cout + o];
+    for (int b = 0; b < nblk; ++b) s += partial_b[b * stride_b + o];
     gb[o] = s;
   }
 }
@@ -485,7 +499,7 @@ struct vd_cnn {
   __nv_bfloat16* act[CNN_L];  // a_0 .. a_5 (NHWC bf16)
   __nv_bfloat16* g0;          // dL/dz ping-pong (bf16, 32 channels)
   __nv_bfloat16* g1;
-  float2* zlast;
+  float* zlast;        // [HW][16] f32
   float* wg_partial;
   float* wg_partial_b;
   double* loss_partial;
@@ -514,7 +528,7 @@ static cudaError_t cnn_reserve(vd_cnn* n, int HW) {
     e = cudaMalloc(&n->act[l], sizeof(__nv_bfloat16) * (size_t)HW * n->cin[l]);
   if (e == cudaSuccess) e = cudaMalloc(&n->g0, sizeof(__nv_bfloat16) * (size_t)HW * CNN_WIDTH);
   if (e == cudaSuccess) e = cudaMalloc(&n->g1, sizeof(__nv_bfloat16) * (size_t)HW * CNN_WIDTH);
-  if (e == cudaSuccess) e = cudaMalloc(&n->zlast, sizeof(float2) * (size_t)HW);
+  if (e == cudaSuccess) e = cudaMalloc(&n->zlast, sizeof(float) * 16 * (size_t)HW);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss_partial, sizeof(double) * ((HW + 255) / 256));
   if (e == cudaSuccess) n->cap_hw = HW;
   return e;
@@ -523,14 +537,14 @@ static cudaError_t cnn_reserve(vd_cnn* n, int HW) {
 template <int K, int N, int EPI>
 static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_bfloat16* Wt,
                                const float* b, void* out, const __nv_bfloat16* mask, int* err,
-                               cudaStream_t s) {
+                               cudaStream_t s, int nout = N) {
   const size_t smem = vd_conv_smem<K, N>();
   cudaError_t e = cudaFuncSetAttribute(k_conv_tc<K, N, EPI>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int HW = W * H;
   k_conv_tc<K, N, EPI><<<(HW + CNN_TILE - 1) / CNN_TILE, CNN_TILE, smem, s>>>(X, W, H, Wt, b,
-                                                                             out, mask, err);
+                                                                             out, mask, nout, err);
   return cudaGetLastError();
 }
 
@@ -547,7 +561,8 @@ static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaS
     const float* b = n->theta + n->boff[l];
     const int K = 9 * n->cin[l];
     if (l == CNN_L - 1) {
-      e = launch_conv<288, 16, EPI_LAST>(n->act[l], W, H, n->wt[l], b, n->zlast, nullptr, n->err, s);
+      e = launch_conv<288, 16, EPI_LAST>(n->act[l], W, H, n->wt[l], b, n->zlast, nullptr, n->err,
+                                         s, n->cout[l]);
     } else if (K == 144) {
       e = launch_conv<144, 32, EPI_RELU>(n->act[l], W, H, n->wt[l], b, n->act[l + 1], nullptr,
                                          n->err, s);
@@ -570,10 +585,10 @@ static cudaError_t launch_wgrad(vd_cnn* n, int l, const __nv_bfloat16* dz, int W
                                                        n->wg_partial_b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nout = COUT * 9 * CIN;
-  k_cnn_wgrad_reduce<<<(nout + 255) / 256, 256, 0, s>>>(n->wg_partial, n->wg_partial_b,
-                                                        WG_BLOCKS, nout, COUT,
-                                                        n->grad + n->woff[l], n->grad + n->boff[l]);
+  const int stride = COUT * 9 * CIN, nout = n->cout[l] * 9 * CIN;
+  k_cnn_wgrad_reduce<<<(stride + 255) / 256, 256, 0, s>>>(
+      n->wg_partial, n->wg_partial_b, WG_BLOCKS, stride, nout, COUT, n->cout[l],
+      n->grad + n->woff[l], n->grad + n->boff[l]);
   return cudaGetLastError();
 }
 
@@ -583,7 +598,7 @@ static cudaError_t cnn_backward(vd_cnn* n, int W, int H, cudaStream_t s) {
   __nv_bfloat16* nxt = n->g1;
   for (int l = CNN_L - 1; l >= 0 && e == cudaSuccess; --l) {
     if (l == CNN_L - 1)
-      e = launch_wgrad<32, 2, 16>(n, l, dz, W, H, s);
+      e = launch_wgrad<32, 16, 16>(n, l, dz, W, H, s);   // 1 + N of 16 rows used
     else if (l == 0)
       e = launch_wgrad<16, 32, 32>(n, l, dz, W, H, s);
     else
@@ -639,7 +654,7 @@ extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn*
   size_t off = 0;
   for (int l = 0; l < CNN_L; ++l) {
     n->cin[l] = l == 0 ? c0p : CNN_WIDTH;
-    n->cout[l] = l == CNN_L - 1 ? 2 : CNN_WIDTH;
+    n->cout[l] = l == CNN_L - 1 ? 1 + n_flows : CNN_WIDTH;
     n->woff[l] = off;
     off += (size_t)n->cout[l] * 9 * n->cin[l];
     n->boff[l] = off;
@@ -755,8 +770,8 @@ extern "C" vd_status vd_cnn_get_activation(vd_cnn* n, int layer, float* out, int
                                            int height) {
   if (!n || !out || layer < 0 || layer > CNN_L || width * height > n->cap_hw) return VD_ERR_ARG;
   const size_t HW = (size_t)width * height;
-  if (layer == CNN_L) {   // z of the last layer, [HW][2]
-    VD_CU(cudaMemcpy(out, n->zlast, sizeof(float2) * HW, cudaMemcpyDeviceToHost));
+  if (layer == CNN_L) {   // z of the last layer, [HW][16]
+    VD_CU(cudaMemcpy(out, n->zlast, sizeof(float) * 16 * HW, cudaMemcpyDeviceToHost));
     return VD_OK;
   }
   const int C = n->cin[layer];
@@ -776,7 +791,8 @@ extern "C" vd_status vd_cnn_forward(vd_cnn* n, const float* flow, int width, int
   VD_CU(cnn_forward(n, flow, width, height, s));
   const int HW = width * height;
   if (rho_out || q_out) {
-    k_cnn_heads<<<(HW + 255) / 256, 256, 0, s>>>(n->zlast, HW, rho_min, rho_max, rho_out, q_out);
+    k_cnn_heads<<<(HW + 255) / 256, 256, 0, s>>>(n->zlast, HW, n->N, rho_min, rho_max, rho_out,
+                                                 q_out);
     VD_CU(cudaGetLastError());
   }
   return cnn_check_err(n, s);
@@ -795,8 +811,8 @@ extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, const float
   VD_CU(cnn_forward(n, flow, width, height, s));
   k_cnn_count<<<1, 256, 0, s>>>(mask, HW, n->nmask);
   const int nb = (HW + 255) / 256;
-  k_cnn_loss<<<nb, 256, 0, s>>>(n->zlast, HW, rho_t, q_t, mask, rho_min, rho_max, w_q, n->nmask,
-                                n->g0, n->loss_partial);
+  k_cnn_loss<<<nb, 256, 0, s>>>(n->zlast, HW, n->N, rho_t, q_t, mask, rho_min, rho_max, w_q,
+                                n->nmask, n->g0, n->loss_partial);
   k_cnn_sum<<<1, 32, 0, s>>>(n->loss_partial, nb, n->nmask, n->loss);
   VD_CU(cudaGetLastError());
   VD_CU(cnn_backward(n, width, height, s));
@@ -814,22 +830,24 @@ extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, const float
 
 // ---------------------------------------------------------------------------
 // Initial EM state of a context from the network: rho (in the context's
-// range) and q for every flow (plane 0 copied to the others).
-// ---------------------------------------------------------------------------
+// range) into rho_dst and the rigidness of every flow into c->q.
 int vd_cnn_flows(const vd_cnn* n) { return n->N; }
 
-cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c) {
+cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst) {
   cudaError_t e = cudaMemsetAsync(n->err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cnn_forward(n, (const float*)c->flow, c->W, c->H, c->stream);
   if (e != cudaSuccess) return e;
   const int HW = c->W * c->H;
-  k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, c->prm.rho_min,
-                                                       c->prm.rho_max, c->rho, c->q);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int t = 1; t < c->N && e == cudaSuccess; ++t)
-    e = cudaMemcpyAsync(c->q + (size_t)t * HW, c->q, sizeof(float) * HW,
-                        cudaMemcpyDeviceToDevice, c->stream);
-  return e;
+  k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, n->N, c->prm.rho_min,
+                                                       c->prm.rho_max, rho_dst, c->q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cnn_rigidness(vd_cnn* n, vd_ctx* c) {
+  const int HW = c->W * c->H;
+  k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, n->N, 0.0f, 1.0f, nullptr,
+                                                       c->q);
+  return cudaGetLastError();
 }
 
 int* vd_cnn_err_flag(vd_cnn* n) { return n->err; }

@@ -505,7 +505,8 @@ def vd_cnn_get_grads(net):
 
 
 def vd_cnn_forward(net, flow, rho_min, rho_max, rho_out=None, q_out=None, stream=None):
-    """flow: CUDA float32 tensor [N][H][W][2]; outputs CUDA float32 [H][W]."""
+    """flow: CUDA float32 tensor [N][H][W][2]; outputs CUDA float32, rho
+    [H][W] and q [N][H][W]."""
     H, W = flow.shape[1], flow.shape[2]
     _call("vd_cnn_forward", net, _dev(flow), int(W), int(H), float(rho_min), float(rho_max),
           _dev(rho_out) if rho_out is not None else None,
@@ -521,8 +522,9 @@ def vd_cnn_get_activation(net, layer, W, H, channels):
 
 def vd_cnn_train_step(net, flow, rho_t, q_t, mask, rho_min, rho_max, w_q, lr, update=True,
                       stream=None):
-    """All arrays CUDA tensors ([N][H][W][2] flow; [H][W] targets, uint8 mask).
-    Returns the loss of the forward pass before the update."""
+    """All arrays CUDA tensors ([N][H][W][2] flow, [H][W] rho target, [N][H][W]
+    rigidness targets, [H][W] uint8 mask).  Returns the loss of the forward
+    pass before the update."""
     H, W = flow.shape[1], flow.shape[2]
     loss = C.c_double(0.0)
     _call("vd_cnn_train_step", net, _dev(flow), _dev(rho_t), _dev(q_t), _dev(mask), int(W), int(H),
