@@ -293,24 +293,33 @@ vd_status vd_batch_get_stats(vd_batch* b, vd_batch_stats* out);
  * A convolutional network maps a window's flows to an initial inverse depth
  * and rigidness, to start the EM closer to its fixed point.  Six 3x3
  * convolutions, zero padding 1: C0 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 + N,
- * ReLU between layers; C0 = 2N rounded up to a multiple of 8, at least 16;
- * input plane 2t + c is component c of flow t+1 divided by 32 px (the rest
- * zero).  Heads: rho = rho_min + (rho_max - rho_min) sigmoid(z_0) and the
- * rigidness of flow t, q_t = sigmoid(z_t), t = 1..N.
+ * ReLU between layers; C0 = 16 if 2N + 4 <= 16, else 32.  Input planes, all
+ * divided by 32 px: 2t + c is component c of flow t+1; then four geometry
+ * planes from the pose T_1 of flow 1 (unit translation, the monocular
+ * gauge): the flow the rotation of T_1 alone gives the pixel (2 planes), and
+ * the extra flow of a point at inverse depth 0.1 under the whole T_1 (2
+ * planes); the rest zero (the geometry planes too when no pose is given).
+ * Heads: rho = clip(rho_c exp(z_0), rho_min, rho_max) with rho_c =
+ * sqrt(rho_min rho_max), and the rigidness of flow t, q_t = sigmoid(z_t).
  * Weights and activations are bfloat16 with float32 accumulation on the
  * tensor cores; the master parameters are float32.
  * Parameter vector (vd_cnn_layout gives the offsets): for each layer l the
  * weights W_l[c_out][ky][kx][c_in] then the biases b_l[c_out].
  * Training (vd_cnn_train_step): loss over pixels with mask m,
- *   L = sum m (rho / rho* - 1)^2 / sum m
+ *   L = sum m (z_0 + log rho_c - log rho*)^2 / sum m
  *     + w_q sum_t sum m BCE(q_t, q*_t) / (N sum m),
  * gradients with dL/dz of every layer stored in bfloat16, then one Adam
  * step (b1 0.9, b2 0.999, eps 1e-8) when `update` is set.
  * All image buffers are device memory: flow [N][H][W][2] float32 (the layout
- * of vd_push_flow), inverse depth and mask [H][W], rigidness [N][H][W].  Calls run on `stream` and synchronise it;
+ * of vd_push_flow), inverse depth and mask [H][W], rigidness [N][H][W].
+ * Calls run on `stream` and synchronise it;
  * a tensor-core wait that gives up returns VD_ERR_TIMEOUT. */
 typedef struct vd_cnn vd_cnn;
 #define VD_CNN_LAYERS 6
+typedef struct {
+  double fx, fy, cx, cy;    /* intrinsics of the window                     */
+  double T1[12];            /* pose of flow 1, [R | tau] row-major           */
+} vd_cnn_geometry;
 vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn** out);
 vd_status vd_cnn_destroy(vd_cnn* net);
 vd_status vd_cnn_layout(vd_cnn* net, int* n_params, int* c_in /*[6]*/, int* c_out /*[6]*/,
@@ -318,22 +327,29 @@ vd_status vd_cnn_layout(vd_cnn* net, int* n_params, int* c_in /*[6]*/, int* c_ou
 vd_status vd_cnn_get_params(vd_cnn* net, float* params /*host [n_params]*/);
 vd_status vd_cnn_set_params(vd_cnn* net, const float* params /*host*/);   /* resets Adam */
 vd_status vd_cnn_get_grads(vd_cnn* net, float* grads /*host [n_params]*/);
-vd_status vd_cnn_forward(vd_cnn* net, const float* flow, int width, int height, float rho_min,
-                         float rho_max, float* rho_out /*nullable*/, float* q_out /*nullable*/,
+vd_status vd_cnn_forward(vd_cnn* net, const float* flow, int width, int height,
+                         const vd_cnn_geometry* geom /*nullable*/, float rho_min, float rho_max,
+                         float* rho_out /*nullable*/, float* q_out /*nullable*/,
                          void* cuda_stream);
 /* Activations of the last forward pass, as float32 on the host: layer l in
  * 0..5 is the input a_l of layer l, [H][W][C_in(l)]; layer 6 is z of the
  * last layer, [H][W][16] (the first 1 + N channels used). */
 vd_status vd_cnn_get_activation(vd_cnn* net, int layer, float* out, int width, int height);
-vd_status vd_cnn_train_step(vd_cnn* net, const float* flow, const float* rho_target,
-                            const float* q_target, const unsigned char* mask, int width,
-                            int height, float rho_min, float rho_max, float w_q, float lr,
-                            int update, double* loss_out /*host, nullable*/, void* cuda_stream);
-/* Bootstrap a context with the network: the bootstrap of vd_bootstrap with
- * the network's inverse depth (within the context's [rho_min, rho_max]) as
- * the initial value of the monocular depth step (in place of the random
- * draw; with a prior the prior's value stays) and the network's rigidness of
- * every flow in place of q = 1, then the same pose M-step.  The network must
+vd_status vd_cnn_train_step(vd_cnn* net, const float* flow, int width, int height,
+                            const vd_cnn_geometry* geom /*nullable*/, const float* rho_target,
+                            const float* q_target, const unsigned char* mask, float rho_min,
+                            float rho_max, float w_q, float lr, int update,
+                            double* loss_out /*host, nullable*/, void* cuda_stream);
+/* The monocular bootstrap's pose of flow 1 (IRLS 8-point on X_1, unit
+ * translation), computed without changing the context's state: the geometry
+ * a network is trained with.  Needs X_1 pushed.  Synchronises the stream. */
+vd_status vd_eight_point(vd_ctx* ctx, double* T1_out /*host, 12*/);
+/* Bootstrap a context with the network: vd_bootstrap with the network's
+ * inverse depth (geometry planes from the 8-point pose, or from the poses
+ * set on the context; within [rho_min, rho_max]) as the initial value of the
+ * monocular depth step, in place of the random draw; the rest as in
+ * vd_bootstrap (q = 1; with a prior, exactly vd_bootstrap).  The network's
+ * rigidness is not used here (vd_cnn_forward gives it).  The network must
  * have the context's N. */
 vd_status vd_bootstrap_learned(vd_ctx* ctx, vd_cnn* net);
 

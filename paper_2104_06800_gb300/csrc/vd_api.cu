@@ -614,39 +614,32 @@ static cudaError_t bootstrap(vd_ctx* c) {
   return e;
 }
 
-// Bootstrap with the learned initialiser: the monocular bootstrap of R11
-// with the network's inverse depth as the initial value of its depth step
-// (slot 0 of every pixel's candidates, in place of the random draw) and the
-// network's per-flow rigidness in place of q = 1 afterwards.  With a prior,
-// the prior's inverse depth stays the initial value and only q changes.
+// Bootstrap with the learned initialiser: the bootstrap of R11 with the
+// network's inverse depth as the initial value of its monocular depth step
+// (slot 0 of every pixel's candidates, in place of the random draw).  The
+// rest is the plain bootstrap (q = 1; with a prior, the prior's inverse
+// depth and no depth step).  The network's rigidness is not used here: its
+// geometry input comes from the 8-point pose, and where that pose is poor a
+// rigidness that excludes pixels from the first pose step keeps the EM from
+// recovering, while q = 1 lets it.
 static cudaError_t bootstrap_learned(vd_ctx* c, vd_cnn* net) {
+  if (c->prior_kind != VD_PRIOR_NONE) return bootstrap(c);
   vd_prof_begin(c, VD_ST_OTHER);
   cudaError_t e = cudaMemcpyAsync(c->G, c->G_init, sizeof(double) * 12 * (c->N + 1),
                                   cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = launch_posef(c);
   if (e == cudaSuccess) e = launch_fill(c->qhat, 1.0f, c->npix, c->stream);
   int n = 2;
-  if (e == cudaSuccess && c->prior_kind != VD_PRIOR_NONE) {
-    e = launch_initial_rho(c);
-    ++n;
-  }
-  if (e == cudaSuccess && c->prior_kind == VD_PRIOR_NONE && !c->poses_set) {
+  if (e == cudaSuccess && !c->poses_set) {
     e = launch_eight_point(c);
     n += 2 * VD_IRLS_ITERS + 3;
   }
-  // the network's rho (into the state when there is no prior, else into
-  // scratch) and its rigidness of every flow
-  if (e == cudaSuccess)
-    e = launch_cnn_init(net, c, c->prior_kind == VD_PRIOR_NONE ? c->rho : c->rho_mid);
-  vd_prof_end(c, VD_ST_OTHER, n + 2 + 2 * VD_CNN_LAYERS);
+  if (e == cudaSuccess) e = launch_cnn_init(net, c, c->rho, nullptr);
+  if (e == cudaSuccess) e = launch_fill(c->q, 1.0f, c->npix * c->N, c->stream);
+  vd_prof_end(c, VD_ST_OTHER, n + 3 + 2 * VD_CNN_LAYERS);
   if (e != cudaSuccess) return e;
-  if (c->prior_kind == VD_PRIOR_NONE) {
-    // depth from X_1 alone (the argmin does not depend on q_1 > 0), then the
-    // network's q again for every flow
-    e = depth_step(c, -1, 0, true);
-    if (e == cudaSuccess) e = launch_cnn_rigidness(net, c);
-    vd_prof_end(c, VD_ST_OTHER, 1);
-  }
+  // depth from X_1 alone, starting from the network's value
+  e = depth_step(c, -1, 0, true);
   if (e == cudaSuccess && !c->poses_set) e = pose_step(c, -1, 0);
   return e;
 }
@@ -692,6 +685,21 @@ static cudaError_t enqueue_em(vd_ctx* c, int n_iters, bool boot, int* booted) {
     c->iter = i + 1;
   }
   return cudaSuccess;
+}
+
+extern "C" vd_status vd_eight_point(vd_ctx* c, double* T1) {
+  if (!c || !T1) return VD_ERR_ARG;
+  if (!(c->flow_pushed & 1u)) return VD_ERR_STATE;
+  std::vector<double> G(12 * (c->N + 1));
+  VD_CU(cudaMemcpyAsync(G.data(), c->G, sizeof(double) * G.size(), cudaMemcpyDeviceToHost,
+                        c->stream));
+  VD_CU(launch_eight_point(c));
+  VD_CU(cudaMemcpyAsync(T1, c->G + 12, sizeof(double) * 12, cudaMemcpyDeviceToHost, c->stream));
+  VD_CU(cudaMemcpyAsync(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
+                        c->stream));
+  VD_CU(launch_posef(c));
+  VD_CU(cudaStreamSynchronize(c->stream));
+  return VD_OK;
 }
 
 extern "C" vd_status vd_bootstrap_learned(vd_ctx* c, vd_cnn* net) {

@@ -269,15 +269,41 @@ k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
 // ---------------------------------------------------------------------------
 // Input planes: flow [N][H][W][2] -> bf16 NHWC with C0 channels.
 // ---------------------------------------------------------------------------
-__global__ void k_cnn_input(const float2* __restrict__ flow, int N, int HW, int C0,
-                            __nv_bfloat16* __restrict__ a0) {
+// Geometry planes 2N .. 2N+3 (zero without a pose): the flow that the
+// rotation of T_1 alone gives pixel (u, v), and the extra flow of a point at
+// inverse depth GEO_RHO (units of |tau_1|) under the whole T_1, both / 32 px.
+#define GEO_RHO 0.1f
+
+__global__ void k_cnn_input(const float2* __restrict__ flow, int N, int Wimg, int HW, int C0,
+                            const double* __restrict__ G1, float fx, float fy, float cx,
+                            float cy, __nv_bfloat16* __restrict__ a0) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
+  float geo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (G1) {
+    const float u = (float)(p % Wimg), v = (float)(p / Wimg);
+    const float rx = (u - cx) / fx, ry = (v - cy) / fy;
+    float h[3], d[3];
+    for (int r = 0; r < 3; ++r) {
+      h[r] = (float)G1[4 * r] * rx + (float)G1[4 * r + 1] * ry + (float)G1[4 * r + 2];
+      d[r] = h[r] + GEO_RHO * (float)G1[4 * r + 3];
+    }
+    if (h[2] > 1e-6f && d[2] > 1e-6f) {
+      const float x0 = fx * h[0] / h[2] + cx, y0 = fy * h[1] / h[2] + cy;
+      const float x1 = fx * d[0] / d[2] + cx, y1 = fy * d[1] / d[2] + cy;
+      geo[0] = (x0 - u) * (1.0f / 32.0f);
+      geo[1] = (y0 - v) * (1.0f / 32.0f);
+      geo[2] = (x1 - x0) * (1.0f / 32.0f);
+      geo[3] = (y1 - y0) * (1.0f / 32.0f);
+    }
+  }
   for (int c = 0; c < C0; ++c) {
     float v = 0.0f;
     if (c < 2 * N) {
       const float2 f = flow[(size_t)(c >> 1) * HW + p];
       v = ((c & 1) ? f.y : f.x) * (1.0f / 32.0f);
+    } else if (c < 2 * N + 4) {
+      v = geo[c - 2 * N];
     }
     a0[(size_t)p * C0 + c] = __float2bfloat16_rn(v);
   }
@@ -293,7 +319,7 @@ __global__ void k_cnn_heads(const float* __restrict__ z, int HW, int N, float rh
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
   const float* v = z + (size_t)p * 16;
-  if (rho) rho[p] = rho_min + (rho_max - rho_min) / (1.0f + __expf(-v[0]));
+  if (rho) rho[p] = fminf(fmaxf(sqrtf(rho_min * rho_max) * __expf(v[0]), rho_min), rho_max);
   if (q)
     for (int t = 0; t < N; ++t) q[(size_t)t * HW + p] = 1.0f / (1.0f + __expf(-v[1 + t]));
 }
@@ -308,17 +334,15 @@ __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
   double l = 0.0;
   if (p < HW) {
     const float* v = z + (size_t)p * 16;
-    const float s0 = 1.0f / (1.0f + __expf(-v[0]));
-    const float rho = rho_min + (rho_max - rho_min) * s0;
     const float m = mask[p] ? 1.0f : 0.0f;
     const float inv_n = 1.0f / *nmask;
     const float wq_n = w_q / (float)N;
-    const float rt = rho_t[p];
-    const float r = rho / rt - 1.0f;
+    // log error of the inverse-depth head
+    const float r = v[0] + 0.5f * logf(rho_min * rho_max) - logf(rho_t[p]);
     __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
-    o[0] = __float2bfloat16_rn(m * 2.0f * r / rt * (rho_max - rho_min) * s0 * (1.0f - s0) * inv_n);
+    o[0] = __float2bfloat16_rn(m * 2.0f * r * inv_n);
     float bce = 0.0f;
     for (int t = 0; t < N; ++t) {
       const float s = 1.0f / (1.0f + __expf(-v[1 + t]));
@@ -505,6 +529,7 @@ struct vd_cnn {
   double* loss_partial;
   double* loss;
   float* nmask;
+  double* geo;         // [12] T_1 given to the host-API calls
   int* err;
 };
 
@@ -550,12 +575,20 @@ static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_
 
 // Forward pass of the whole network on flow [N][H][W][2] (device); keeps the
 // activations for a backward pass.
-static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaStream_t s) {
+// Geometry of the input planes: intrinsics and T_1 (device, 12 doubles) or
+// none (zero planes).
+struct VdCnnGeo {
+  const double* G1;
+  float fx, fy, cx, cy;
+};
+
+static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaStream_t s,
+                               VdCnnGeo g) {
   const int HW = W * H;
   cudaError_t e = cnn_reserve(n, HW);
   if (e != cudaSuccess) return e;
-  k_cnn_input<<<(HW + 255) / 256, 256, 0, s>>>((const float2*)flow, n->N, HW, n->cin[0],
-                                               n->act[0]);
+  k_cnn_input<<<(HW + 255) / 256, 256, 0, s>>>((const float2*)flow, n->N, W, HW, n->cin[0],
+                                               g.G1, g.fx, g.fy, g.cx, g.cy, n->act[0]);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = 0; l < CNN_L; ++l) {
     const float* b = n->theta + n->boff[l];
@@ -647,10 +680,9 @@ extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn*
   vd_cnn* n = new vd_cnn();
   memset((void*)n, 0, sizeof *n);
   n->N = n_flows;
-  // input planes: 2N rounded up to 8, at least 16 (the GEMM tiles take 16 or
-  // 32 input channels)
-  const int c0 = (2 * n_flows + 7) / 8 * 8;
-  const int c0p = c0 <= 16 ? 16 : c0;
+  // input planes: 2N flow planes and 4 geometry planes, padded to 16 or 32
+  // (the GEMM tiles take 16 or 32 input channels)
+  const int c0p = 2 * n_flows + 4 <= 16 ? 16 : 32;
   size_t off = 0;
   for (int l = 0; l < CNN_L; ++l) {
     n->cin[l] = l == 0 ? c0p : CNN_WIDTH;
@@ -671,7 +703,7 @@ extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn*
     return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
   };
   for (int l = 0; l < CNN_L; ++l) {
-    const int cin_real = l == 0 ? 2 * n_flows : n->cin[l];
+    const int cin_real = l == 0 ? 2 * n_flows + 4 : n->cin[l];
     const double sd = sqrt(2.0 / (9.0 * cin_real));
     for (int co = 0; co < n->cout[l]; ++co)
       for (int t = 0; t < 9; ++t)
@@ -697,6 +729,7 @@ extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn*
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&n->nmask, sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&n->geo, sizeof(double) * 12);
   if (e == cudaSuccess) e = cudaMemcpy(n->theta, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->mom1, 0, sizeof(float) * off);
   if (e == cudaSuccess) e = cudaMemset(n->mom2, 0, sizeof(float) * off);
@@ -717,7 +750,7 @@ extern "C" vd_status vd_cnn_destroy(vd_cnn* n) {
   cudaDeviceSynchronize();
   cnn_free_images(n);
   void* p[] = {n->theta, n->mom1, n->mom2, n->grad, n->wg_partial, n->wg_partial_b,
-               n->loss, n->nmask, n->err};
+               n->loss, n->nmask, n->err, n->geo};
   for (void* q : p)
     if (q) cudaFree(q);
   for (int l = 0; l < CNN_L; ++l) {
@@ -782,13 +815,37 @@ extern "C" vd_status vd_cnn_get_activation(vd_cnn* n, int layer, float* out, int
   return VD_OK;
 }
 
+// Host-given geometry: T_1 copied to the network's device slot.
+static cudaError_t cnn_host_geo(vd_cnn* n, const vd_cnn_geometry* g, cudaStream_t s,
+                                VdCnnGeo* out) {
+  *out = VdCnnGeo{nullptr, 1.0f, 1.0f, 0.0f, 0.0f};
+  if (!g) return cudaSuccess;
+  out->G1 = n->geo;
+  out->fx = (float)g->fx;
+  out->fy = (float)g->fy;
+  out->cx = (float)g->cx;
+  out->cy = (float)g->cy;
+  return cudaMemcpyAsync(n->geo, g->T1, sizeof(double) * 12, cudaMemcpyHostToDevice, s);
+}
+
+static bool geo_ok(const vd_cnn_geometry* g) {
+  if (!g) return true;
+  if (!(g->fx > 0) || !(g->fy > 0) || !isfinite(g->cx) || !isfinite(g->cy)) return false;
+  for (int i = 0; i < 12; ++i)
+    if (!isfinite(g->T1[i])) return false;
+  return true;
+}
+
 extern "C" vd_status vd_cnn_forward(vd_cnn* n, const float* flow, int width, int height,
-                                    float rho_min, float rho_max, float* rho_out, float* q_out,
-                                    void* stream) {
-  if (!n || !flow || width < 1 || height < 1 || !(rho_max > rho_min)) return VD_ERR_ARG;
+                                    const vd_cnn_geometry* geom, float rho_min, float rho_max,
+                                    float* rho_out, float* q_out, void* stream) {
+  if (!n || !flow || width < 1 || height < 1 || !(rho_max > rho_min) || !geo_ok(geom))
+    return VD_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   VD_CU(cudaMemsetAsync(n->err, 0, sizeof(int), s));
-  VD_CU(cnn_forward(n, flow, width, height, s));
+  VdCnnGeo g;
+  VD_CU(cnn_host_geo(n, geom, s, &g));
+  VD_CU(cnn_forward(n, flow, width, height, s, g));
   const int HW = width * height;
   if (rho_out || q_out) {
     k_cnn_heads<<<(HW + 255) / 256, 256, 0, s>>>(n->zlast, HW, n->N, rho_min, rho_max, rho_out,
@@ -798,17 +855,20 @@ extern "C" vd_status vd_cnn_forward(vd_cnn* n, const float* flow, int width, int
   return cnn_check_err(n, s);
 }
 
-extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, const float* rho_t,
-                                       const float* q_t, const unsigned char* mask, int width,
-                                       int height, float rho_min, float rho_max, float w_q,
-                                       float lr, int update, double* loss_out, void* stream) {
+extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, int width, int height,
+                                       const vd_cnn_geometry* geom, const float* rho_t,
+                                       const float* q_t, const unsigned char* mask,
+                                       float rho_min, float rho_max, float w_q, float lr,
+                                       int update, double* loss_out, void* stream) {
   if (!n || !flow || !rho_t || !q_t || !mask || width < 1 || height < 1 ||
-      !(rho_max > rho_min) || !(lr >= 0.0f))
+      !(rho_max > rho_min) || !(lr >= 0.0f) || !geo_ok(geom))
     return VD_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int HW = width * height;
   VD_CU(cudaMemsetAsync(n->err, 0, sizeof(int), s));
-  VD_CU(cnn_forward(n, flow, width, height, s));
+  VdCnnGeo g;
+  VD_CU(cnn_host_geo(n, geom, s, &g));
+  VD_CU(cnn_forward(n, flow, width, height, s, g));
   k_cnn_count<<<1, 256, 0, s>>>(mask, HW, n->nmask);
   const int nb = (HW + 255) / 256;
   k_cnn_loss<<<nb, 256, 0, s>>>(n->zlast, HW, n->N, rho_t, q_t, mask, rho_min, rho_max, w_q,
@@ -830,23 +890,20 @@ extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, const float
 
 // ---------------------------------------------------------------------------
 // Initial EM state of a context from the network: rho (in the context's
-// range) into rho_dst and the rigidness of every flow into c->q.
+// range) into rho_dst and the rigidness of every flow into q_dst.
 int vd_cnn_flows(const vd_cnn* n) { return n->N; }
 
-cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst) {
+cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst, float* q_dst) {
   cudaError_t e = cudaMemsetAsync(n->err, 0, sizeof(int), c->stream);
-  if (e == cudaSuccess) e = cnn_forward(n, (const float*)c->flow, c->W, c->H, c->stream);
+  // geometry from the context's current T_1 (the 8-point bootstrap's, or
+  // the poses it was given)
+  const VdCnnGeo g{c->G + 12, (float)c->desc.fx, (float)c->desc.fy, (float)c->desc.cx,
+                   (float)c->desc.cy};
+  if (e == cudaSuccess) e = cnn_forward(n, (const float*)c->flow, c->W, c->H, c->stream, g);
   if (e != cudaSuccess) return e;
   const int HW = c->W * c->H;
   k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, n->N, c->prm.rho_min,
-                                                       c->prm.rho_max, rho_dst, c->q);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cnn_rigidness(vd_cnn* n, vd_ctx* c) {
-  const int HW = c->W * c->H;
-  k_cnn_heads<<<(HW + 255) / 256, 256, 0, c->stream>>>(n->zlast, HW, n->N, 0.0f, 1.0f, nullptr,
-                                                       c->q);
+                                                       c->prm.rho_max, rho_dst, q_dst);
   return cudaGetLastError();
 }
 

@@ -156,11 +156,9 @@ cudaError_t launch_check_finite(const float* p, size_t n, int* flag, cudaStream_
 cudaError_t launch_copy_flow(vd_ctx* c, int t, const float* src, long pitch);
 // learned initialiser (vd_cnn.cu): rho and q of the context from the network
 int vd_cnn_flows(const vd_cnn* n);
-// forward pass on the context's flows; rho (context range) into rho_dst and
-// the rigidness of every flow into c->q
-cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst);
-// the rigidness heads of the last forward pass into c->q again
-cudaError_t launch_cnn_rigidness(vd_cnn* n, vd_ctx* c);
+// forward pass on the context's flows (geometry from its T_1); rho (context
+// range) into rho_dst and the rigidness of every flow into q_dst (nullable)
+cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst, float* q_dst);
 int* vd_cnn_err_flag(vd_cnn* n);
 
 void vd_set_error(const char* msg);

@@ -80,22 +80,25 @@ def depth_error(rho, ref, rigid):
 
 
 def label(V, win):
-    """(rho [H][W], q [N][H][W]) of the plain EM after LABEL_ITERS iterations."""
+    """(rho [H][W], q [N][H][W]) of the plain EM after LABEL_ITERS iterations,
+    and the bootstrap's pose of flow 1 (the network's geometry input)."""
     ctx = context(V, win)
     try:
+        T1 = V.vd_eight_point(ctx)
         V.vd_bootstrap(ctx)
         V.vd_run_em(ctx, LABEL_ITERS)
         rho = np.empty((win.H, win.W), np.float32)
         q = np.empty((win.N, win.H, win.W), np.float32)
         V.vd_get_inv_depth(ctx, rho)
         V.vd_get_rigidness(ctx, q)
-        return rho, q
+        return rho, q, T1
     finally:
         V.vd_destroy(ctx)
 
 
 def train(V, net, data, epochs, lr0, seed=0, log=print):
-    """data: list of (flow, rho, q, rho_min, rho_max) with CUDA tensors."""
+    """data: list of (flow, rho, q, rho_min, rho_max, geometry) with CUDA
+    tensors; geometry = (K, T1)."""
     import torch
     rng = np.random.default_rng(seed)
     H, W = data[0][0].shape[1], data[0][0].shape[2]
@@ -106,9 +109,10 @@ def train(V, net, data, epochs, lr0, seed=0, log=print):
     for ep in range(epochs):
         losses = []
         for i in rng.permutation(len(data)):
-            flow, rho, q, rmin, rmax = data[i]
+            flow, rho, q, rmin, rmax, geom = data[i]
             lr = lr0 * (0.1 + 0.9 * 0.5 * (1 + np.cos(np.pi * step / total)))   # cosine to lr0/10
-            losses.append(V.vd_cnn_train_step(net, flow, rho, q, mask, rmin, rmax, W_Q, lr))
+            losses.append(V.vd_cnn_train_step(net, flow, rho, q, mask, rmin, rmax, W_Q, lr,
+                                              geom=geom))
             step += 1
         history.append(float(np.mean(losses)))
         log(f"epoch {ep}: mean loss {history[-1]:.5f}", flush=True)
@@ -219,10 +223,10 @@ def main(argv=None):
             chunk = gen(seeds[c:c + 128])
             t1 = time.time()
             for w in chunk:
-                rho, q = label(V, w)
+                rho, q, T1 = label(V, w)
                 rmin, rmax = mono_range(w)
                 data.append((torch.from_numpy(w.flow).to(dev), torch.from_numpy(rho).to(dev),
-                             torch.from_numpy(q).to(dev), rmin, rmax))
+                             torch.from_numpy(q).to(dev), rmin, rmax, (w.intrinsics, T1)))
             t_lab += time.time() - t1
             del chunk
             print(f"training windows: {len(data)}", flush=True)

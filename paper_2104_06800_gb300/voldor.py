@@ -62,6 +62,11 @@ class vd_tune(C.Structure):
                 ("score_ms", (C.c_float * 4) * 2)]
 
 
+class vd_cnn_geometry(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("T1", C.c_double * 12)]
+
+
 class vd_batch_stats(C.Structure):
     _fields_ = [("windows", C.c_int), ("captures", C.c_longlong), ("replays", C.c_longlong),
                 ("graph_nodes", C.c_longlong), ("kernels_per_run", C.c_longlong)]
@@ -124,10 +129,13 @@ _SIGS = {
     "vd_cnn_get_params": [_P, _P],
     "vd_cnn_set_params": [_P, _P],
     "vd_cnn_get_grads": [_P, _P],
-    "vd_cnn_forward": [_P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P, _P, _P],
+    "vd_cnn_forward": [_P, _P, C.c_int, C.c_int, C.POINTER(vd_cnn_geometry), C.c_float,
+                       C.c_float, _P, _P, _P],
     "vd_cnn_get_activation": [_P, C.c_int, _P, C.c_int, C.c_int],
-    "vd_cnn_train_step": [_P, _P, _P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
-                          C.c_float, C.c_int, C.POINTER(C.c_double), _P],
+    "vd_cnn_train_step": [_P, _P, C.c_int, C.c_int, C.POINTER(vd_cnn_geometry), _P, _P, _P,
+                          C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                          C.POINTER(C.c_double), _P],
+    "vd_eight_point": [_P, _P],
     "vd_bootstrap_learned": [_P, _P],
     "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
     "vd_import_state": [_P, _P, C.c_size_t],
@@ -504,11 +512,24 @@ def vd_cnn_get_grads(net):
     return out
 
 
-def vd_cnn_forward(net, flow, rho_min, rho_max, rho_out=None, q_out=None, stream=None):
-    """flow: CUDA float32 tensor [N][H][W][2]; outputs CUDA float32, rho
-    [H][W] and q [N][H][W]."""
+def _geom(geom):
+    """(K, T1) -> vd_cnn_geometry pointer (None: no geometry planes)."""
+    if geom is None:
+        return None
+    K, T1 = geom
+    g = vd_cnn_geometry(*[float(v) for v in K])
+    for i, v in enumerate(np.asarray(T1, np.float64).reshape(12)):
+        g.T1[i] = float(v)
+    return C.byref(g)
+
+
+def vd_cnn_forward(net, flow, rho_min, rho_max, rho_out=None, q_out=None, geom=None,
+                   stream=None):
+    """flow: CUDA float32 tensor [N][H][W][2]; geom: (K, T1) or None; outputs
+    CUDA float32, rho [H][W] and q [N][H][W]."""
     H, W = flow.shape[1], flow.shape[2]
-    _call("vd_cnn_forward", net, _dev(flow), int(W), int(H), float(rho_min), float(rho_max),
+    _call("vd_cnn_forward", net, _dev(flow), int(W), int(H), _geom(geom), float(rho_min),
+          float(rho_max),
           _dev(rho_out) if rho_out is not None else None,
           _dev(q_out) if q_out is not None else None,
           stream if stream is not None else current_stream())
@@ -521,16 +542,24 @@ def vd_cnn_get_activation(net, layer, W, H, channels):
 
 
 def vd_cnn_train_step(net, flow, rho_t, q_t, mask, rho_min, rho_max, w_q, lr, update=True,
-                      stream=None):
+                      geom=None, stream=None):
     """All arrays CUDA tensors ([N][H][W][2] flow, [H][W] rho target, [N][H][W]
     rigidness targets, [H][W] uint8 mask).  Returns the loss of the forward
     pass before the update."""
     H, W = flow.shape[1], flow.shape[2]
     loss = C.c_double(0.0)
-    _call("vd_cnn_train_step", net, _dev(flow), _dev(rho_t), _dev(q_t), _dev(mask), int(W), int(H),
-          float(rho_min), float(rho_max), float(w_q), float(lr), 1 if update else 0,
+    _call("vd_cnn_train_step", net, _dev(flow), int(W), int(H), _geom(geom), _dev(rho_t),
+          _dev(q_t), _dev(mask), float(rho_min), float(rho_max), float(w_q), float(lr),
+          1 if update else 0,
           C.byref(loss), stream if stream is not None else current_stream())
     return loss.value
+
+
+def vd_eight_point(ctx):
+    """The monocular bootstrap's pose of flow 1 (3x4), state unchanged."""
+    T = np.zeros(12, np.float64)
+    _call("vd_eight_point", ctx, T.ctypes.data_as(C.c_void_p))
+    return T.reshape(3, 4)
 
 
 def vd_bootstrap_learned(ctx, net):

@@ -102,9 +102,31 @@ def test_adam_first_step_closed_form():
 
 
 def test_shapes_and_input_planes():
-    assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 16 and cnn.in_channels(8) == 16
+    assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 16 and cnn.in_channels(8) == 32
     assert cnn.layer_shapes(6) == [(16, 32)] + [(32, 32)] * 4 + [(32, 7)]
     flow = np.zeros((2, 3, 4, 2), np.float32)
     flow[1, 2, 3] = (32.0, -64.0)
     a = cnn.input_planes(flow)
     assert a.shape == (16, 3, 4) and a[2, 2, 3] == 1.0 and a[3, 2, 3] == -2.0 and a[4:].sum() == 0
+
+
+def test_geometry_planes_closed_forms():
+    """Identity rotation: no rotational flow; a pure translation along the
+    optical axis moves a pixel radially (away from the principal point for a
+    camera moving forward, tau_z < 0 in frame-1 coordinates) by the classic
+    x (rho tau_z) / (1 + rho tau_z) law; a pure rotation about the optical
+    axis gives the rotated pixel."""
+    K = (100.0, 100.0, 20.0, 10.0)
+    H, W = 21, 41
+    T = np.concatenate([np.eye(3), [[0.0], [0.0], [-1.0]]], axis=1)
+    g = cnn.geometry_planes(K, T, H, W)
+    v, u = np.mgrid[0:H, 0:W].astype(float)
+    assert np.allclose(g[:2], 0.0)
+    k = -cnn.GEO_RHO / (1 - cnn.GEO_RHO)      # point moved from z=1/rho to z=1/rho - 1
+    assert np.allclose(g[2], -(u - 20) * k) and np.allclose(g[3], -(v - 10) * k)
+    th = 0.1
+    Rz = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    g = cnn.geometry_planes(K, np.concatenate([Rz, np.zeros((3, 1))], 1), H, W)
+    xr = np.cos(th) * (u - 20) - np.sin(th) * (v - 10) + 20
+    yr = np.sin(th) * (u - 20) + np.cos(th) * (v - 10) + 10
+    assert np.allclose(g[0], xr - u) and np.allclose(g[1], yr - v) and np.allclose(g[2:], 0.0)

@@ -55,6 +55,16 @@ def _setup(V, N=6, H=61, W=100, seed=1):
     return net, lay, theta, flow, rho_t, q_t, mask, T
 
 
+def _geom(seed=0):
+    """Intrinsics and a pose of flow 1 (small rotation, unit translation)."""
+    from oracle import geometry as ogeo
+    rng = np.random.default_rng(100 + seed)
+    tau = rng.normal(size=3)
+    T1 = ogeo.se3_exp(np.concatenate([rng.normal(size=3) * 0.02, tau / np.linalg.norm(tau)]))
+    T1[:, 3] /= np.linalg.norm(T1[:, 3])
+    return (80.0, 82.0, 50.0, 30.0), T1
+
+
 def _acts(V, net, lay, W, H):
     a = [_chw(V.vd_cnn_get_activation(net, l, W, H, lay["c_in"][l])) for l in range(6)]
     z = _chw(V.vd_cnn_get_activation(net, 6, W, H, 16))
@@ -69,10 +79,17 @@ def test_forward_layers_match_oracle(V):
     try:
         rho = torch.zeros((H, W), device="cuda")
         q = torch.zeros((N, H, W), device="cuda")
-        V.vd_cnn_forward(net, T(flow), RHO_MIN, RHO_MAX, rho, q)
+        geom = _geom()
+        V.vd_cnn_forward(net, T(flow), RHO_MIN, RHO_MAX, rho, q, geom=geom)
         params = _unpack(theta, lay)
         a, z = _acts(V, net, lay, W, H)
-        assert np.array_equal(a[0], cnn.input_planes(flow))
+        # input planes: the flows exactly; the geometry planes (float32 here,
+        # float64 in the oracle) to one bf16 step next to a rounding boundary
+        ref0 = cnn.input_planes(flow, *geom)
+        assert np.array_equal(a[0][:2 * N], ref0[:2 * N])
+        d0 = np.abs(a[0] - ref0)
+        assert np.mean(d0 == 0) > 0.99 and np.all(d0 <= 2.0 ** -7 * np.abs(ref0) + 1e-6)
+        assert np.abs(ref0[2 * N:2 * N + 4]).max() > 0.1     # the geometry is there
         for l in range(6):
             Wl, bl = params[l]
             zl = cnn.conv(a[l], cnn.bf16(Wl), bl)
@@ -101,7 +118,7 @@ def test_loss_and_gradients_match_oracle(V):
     net, lay, theta, flow, rho_t, q_t, mask, T = _setup(V, N, H, W, seed=2)
     try:
         loss = V.vd_cnn_train_step(net, T(flow), T(rho_t), T(q_t), T(mask), RHO_MIN, RHO_MAX,
-                                   W_Q, 0.0, update=False)
+                                   W_Q, 0.0, update=False, geom=_geom(2))
         g = V.vd_cnn_get_grads(net)
         params = _unpack(theta, lay)
         a, z = _acts(V, net, lay, W, H)
@@ -157,6 +174,11 @@ def test_learned_bootstrap_runs_the_em(V):
     try:
         for t in range(1, w.N + 1):
             V.vd_push_flow(ctx, t, w.flow[t - 1])
+        G0 = V.vd_get_poses(ctx, w.N)
+        T1 = V.vd_eight_point(ctx)
+        assert np.array_equal(V.vd_get_poses(ctx, w.N), G0)      # state unchanged
+        assert abs(np.linalg.norm(T1[:, 3]) - 1.0) < 1e-9
+        assert np.allclose(T1[:, :3] @ T1[:, :3].T, np.eye(3), atol=1e-9)
         V.vd_bootstrap_learned(ctx, net)
         rho = np.empty((w.H, w.W), np.float32)
         q = np.empty((w.N, w.H, w.W), np.float32)
