@@ -20,7 +20,10 @@ error against the reference, over the reference's rigid pixels and after
 the monocular scale alignment, is recorded.  For a tolerance (1 %, 2 %, 5 %)
 the iterations a window needs are the first at or below it (MAX_ITERS if
 none), and windows/s at that accuracy is the number of windows over the
-summed GPU time of the bootstrap and those iterations.
+summed GPU time of the bootstrap and those iterations.  The same error
+against the scene's true inverse depth is recorded too: the reference is
+the plain EM's own future (same random draws), which favours the plain
+start; the true depth favours neither.
 
     python -m paper_2104_06800_gb300.learned_init --train 2000 --epochs 8 \\
         --eval 100 --out weights.npy --report report.json
@@ -137,12 +140,13 @@ def evaluate(V, net, wins, log=print):
             V.vd_get_inv_depth(ctx, ref)
             V.vd_get_rigidness(ctx, qr)
             rigid = qr.mean(axis=0) > 0.5
+            truth = (np.linalg.norm(win.G[1][:, 3]) / win.depth0).astype(np.float32)
             row = {}
             for kind in ("plain", "learned"):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 rho = np.empty((win.H, win.W), np.float32)
-                errs, ms = [], []
+                errs, ms, terrs = [], [], []
                 for k in range(MAX_ITERS + 1):
                     e0.record(stream)
                     if k > 0:
@@ -156,7 +160,8 @@ def evaluate(V, net, wins, log=print):
                     ms.append(e0.elapsed_time(e1))
                     V.vd_get_inv_depth(ctx, rho)
                     errs.append(depth_error(rho, ref, rigid))
-                row[kind] = {"err": errs, "ms": ms}
+                    terrs.append(depth_error(rho, truth, rigid))
+                row[kind] = {"err": errs, "ms": ms, "truth_err": terrs}
             rows.append(row)
             log("window: error after bootstrap plain %.3f learned %.3f; after %d iterations "
                 "plain %.3f learned %.3f" % (row["plain"]["err"][0], row["learned"]["err"][0],
@@ -168,6 +173,9 @@ def evaluate(V, net, wins, log=print):
     for kind in ("plain", "learned"):
         d = {"mean_error_by_iteration": [float(np.mean([r[kind]["err"][k] for r in rows]))
                                          for k in range(MAX_ITERS + 1)],
+             "median_truth_error_by_iteration": [
+                 float(np.median([r[kind]["truth_err"][k] for r in rows]))
+                 for k in range(MAX_ITERS + 1)],
              "ms_bootstrap": float(np.mean([r[kind]["ms"][0] for r in rows])),
              "ms_iteration": float(np.mean([np.mean(r[kind]["ms"][1:]) for r in rows]))}
         for tol in TOLS:
@@ -183,6 +191,7 @@ def evaluate(V, net, wins, log=print):
                                  "windows_per_s": len(rows) / (total / 1e3)}
         out[kind] = d
     out["per_window"] = [{k: {"err": [round(e, 5) for e in r[k]["err"]],
+                              "truth_err": [round(e, 5) for e in r[k]["truth_err"]],
                               "ms": [round(m, 3) for m in r[k]["ms"]]} for k in r} for r in rows]
     return out
 
