@@ -4,17 +4,24 @@
 // rigidness.
 //
 // Convolutions are implicit GEMMs on the 5th-generation tensor cores:
-// D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = (ky * 3 + kx) * C_in + c_in,
-// with one CTA per 128 consecutive pixels.  The whole im2col tile A (128 x K)
-// and the weights B (N x K) are staged in shared memory in the canonical
-// K-major layout without swizzle (core matrices of 8 rows x 16 bytes, LBO =
-// 128 B between core matrices along K, SBO = 16 K bytes between 8-row
-// groups); one thread issues K/16 tcgen05.mma (kind::f16, bf16 x bf16 ->
-// f32) into a tensor-memory accumulator of N columns and commits them to an
-// mbarrier; each warp reads its 32 accumulator lanes with tcgen05.ld.  The
-// backward data gradient is the same GEMM on dL/dz with the weights flipped
-// by 180 degrees and transposed; the weight gradient is a float32 reduction
-// over pixels on the CUDA cores, in a fixed order.
+// D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = (ky * 3 + kx) * C_in + c_in.
+// A CTA computes R image rows of 128 consecutive pixels.  It never builds
+// the im2col matrix: TMA loads the halo tile (R + 2 rows of 130 pixels,
+// zero outside the image) once, one box per group of 8 input channels,
+// into [group][row][x][8 channels]; with 16 bytes per pixel and a stride of
+// 128 B between 8-pixel core matrices this is the canonical K-major layout
+// without swizzle, so tap (ky, kx) of output row r is the same tile with
+// its start address moved by ((r + ky) * 130 + kx) * 16 bytes (LBO = the
+// group stride).  The weights, stored pre-tiled in that layout (LBO = 128 B,
+// SBO = 16 K bytes), arrive by one bulk copy.  One thread issues
+// R * 9 * C_in / 16 tcgen05.mma (kind::f16, bf16 x bf16 -> f32) into R
+// tensor-memory accumulators of N columns and commits them to an mbarrier;
+// each warp reads its 32 accumulator lanes with tcgen05.ld.  The backward
+// data gradient is the same GEMM on dL/dz with the weights flipped by 180
+// degrees and transposed; the weight gradient is a float32 reduction over
+// pixels on the CUDA cores, in a fixed order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -24,7 +31,11 @@
 
 #define CNN_L 6
 #define CNN_WIDTH 32
-#define CNN_TILE 128
+#define CNN_TILE 128               // output pixels of a row per tile (the MMA's M)
+#define CNN_HALO_X (CNN_TILE + 2)
+#ifndef CNN_ROWS
+#define CNN_ROWS 4                 // output rows per CTA
+#endif
 #define CNN_WAIT_LIMIT (1 << 22)   // mbarrier polls before a wait gives up
 
 // ---------------------------------------------------------------------------
@@ -104,6 +115,39 @@ __device__ __forceinline__ bool vd_mbar_wait_bounded(uint64_t* m, uint32_t phase
 __device__ __forceinline__ void vd_fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+__device__ __forceinline__ void vd_mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vd_smem_u32(m)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void vd_mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(vd_smem_u32(m)) : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// into shared memory, completing on the mbarrier's transaction count.
+__device__ __forceinline__ void vd_bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                             uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(vd_smem_u32(m))
+      : "memory");
+}
+
+// Tiled TMA load of one box of a rank-3 tensor map at (c0, c1, c2); c0 (the
+// innermost coordinate) must be a multiple of 16 bytes' worth of elements.
+__device__ __forceinline__ void vd_tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0,
+                                               int c1, int c2, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(vd_smem_u32(m))
+      : "memory");
+}
+
 __device__ __forceinline__ void vd_tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -147,91 +191,121 @@ __device__ __forceinline__ void vd_tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ---------------------------------------------------------------------------
-// The convolution GEMM.  X: NHWC bf16 with C_in = K / 9 channels (a multiple
-// of 8).  Wt: [N][K] bf16.  Epilogues:
+// The convolution GEMM.  X (through the tensor map `xmap`): NHWC bf16 with
+// C_in = K / 9 channels (a multiple of 16), dims {C_in, W, H}, box
+// {8, 130, R + 2}.  Wt: the N x K weights pre-tiled (vd_tile_index).
+// Epilogues:
 //   EPI_RELU  out = bf16 NHWC [HW][N]: relu(D + bias)
 //   EPI_LAST  out = f32 [HW][16]: D + bias for the nout real channels, 0 after
 //   EPI_DGRAD out = bf16 NHWC [HW][N]: D where mask[p][c] > 0, else 0
 // ---------------------------------------------------------------------------
 enum { EPI_RELU = 0, EPI_LAST = 1, EPI_DGRAD = 2 };
 
-template <int K, int N>
-constexpr size_t vd_conv_smem() {
-  return (size_t)CNN_TILE * K * 2 + (size_t)N * K * 2;
+// Element (n, k) of an N x K operand in the K-major no-swizzle layout with
+// LBO = 128 B and SBO = 16 K bytes.
+__host__ __device__ constexpr size_t vd_tile_index(int n, int k, int K) {
+  return (size_t)(n >> 3) * (K * 8) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
 }
 
-template <int K, int N, int EPI>
+__host__ __device__ constexpr uint32_t vd_round128(uint32_t b) { return (b + 127u) & ~127u; }
+
+template <int K, int N, int R>
+struct VdConvShape {
+  static constexpr int CIN = K / 9, G = CIN / 8;
+  static constexpr uint32_t B_BYTES = (uint32_t)N * K * 2;
+  static constexpr uint32_t BOX_BYTES = (uint32_t)(R + 2) * CNN_HALO_X * 16;
+  static constexpr uint32_t GS = vd_round128(BOX_BYTES);   // stride between channel groups
+  static constexpr uint32_t A_OFF = vd_round128(B_BYTES);
+  static constexpr uint32_t TX_BYTES = B_BYTES + G * BOX_BYTES;
+  // tensor-memory columns: R accumulators of N, as a power of two >= 32
+  static constexpr uint32_t NCOLS = R * N <= 32 ? 32 : R * N <= 64 ? 64 : R * N <= 128 ? 128
+                                  : R * N <= 256 ? 256 : 512;
+  // shared memory: the tiles, 128 B of alignment slack, and at least enough
+  // that no more CTAs share an SM than its 512 tensor-memory columns hold
+  // (228 KB per SM, 1 KB reserved per CTA)
+  static constexpr uint32_t NEED = A_OFF + G * GS + 128;
+  static constexpr uint32_t FLOOR = 233472u / (512u / NCOLS + 1u) - 1024u + 16u;
+  static constexpr uint32_t SMEM = NEED > FLOOR ? NEED : FLOOR;
+};
+
+template <int K, int N, int EPI, int R>
 __global__ void __launch_bounds__(CNN_TILE)
-k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
+k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg,
           const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
           void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int nout,
           int* __restrict__ err) {
+  using S = VdConvShape<K, N, R>;
   static_assert(K % 144 == 0 && (N == 16 || N == 32), "shapes of this network");
-  constexpr int CIN = K / 9, CPT = CIN / 8, KG = K / 8;
-  constexpr uint32_t NCOLS = 32;   // smallest tensor-memory allocation
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + (size_t)CNN_TILE * K * 2;
-  __shared__ uint64_t mbar;
+  static_assert(S::NCOLS <= 512 && R + 2 <= 256, "tile");
+  constexpr int CIN = S::CIN;
+  extern __shared__ uint8_t smem[];
+  __shared__ uint64_t bar_load, bar_mma;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int HW = Wimg * Himg;
-  const int p0 = blockIdx.x * CNN_TILE;
-  if (warp == 0) vd_tmem_alloc(&tmem_base, NCOLS);
-  if (tid == 0) vd_mbar_init(&mbar, 1);
-  // A: im2col rows of the tile's pixels (zeros outside the image)
-  for (int idx = tid; idx < CNN_TILE * 9 * CPT; idx += CNN_TILE) {
-    const int m = idx / (9 * CPT);
-    const int rem = idx - m * (9 * CPT);
-    const int tap = rem / CPT, ch = rem - tap * CPT;
-    const int p = p0 + m;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (p < HW) {
-      const int y = p / Wimg, x = p - y * Wimg;
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * Wimg + xx) * CIN + ch * 8);
-    }
-    const int kg = tap * CPT + ch;
-    *reinterpret_cast<uint4*>(sA + (size_t)(m >> 3) * (K * 16) + kg * 128 + (m & 7) * 16) = v;
+  const int x0 = blockIdx.x * CNN_TILE, y0 = blockIdx.y * R;
+  if (warp == 0) vd_tmem_alloc(&tmem_base, S::NCOLS);
+  if (tid == 0) {
+    vd_mbar_init(&bar_load, 1);
+    vd_mbar_init(&bar_mma, 1);
+    s_fail = 0;
   }
-  // B: the weights
-  for (int idx = tid; idx < N * KG; idx += CNN_TILE) {
-    const int n = idx / KG, kg = idx - n * KG;
-    const uint4 v = *reinterpret_cast<const uint4*>(Wt + (size_t)n * K + kg * 8);
-    *reinterpret_cast<uint4*>(sB + (size_t)(n >> 3) * (K * 16) + kg * 128 + (n & 7) * 16) = v;
-  }
-  vd_fence_async_smem();   // the generic-proxy stores above feed the tensor core
   vd_tc_fence_before();
   __syncthreads();
   vd_tc_fence_after();
   const uint32_t dt = tmem_base;
   if (tid == 0) {
-    const uint32_t a0 = vd_smem_u32(sA), b0 = vd_smem_u32(sB);
-    constexpr uint32_t idesc = vd_idesc_bf16(CNN_TILE, N);
+    const uint32_t sB = (vd_smem_u32(smem) + 127u) & ~127u, sA = sB + S::A_OFF;
+    vd_mbar_expect_tx(&bar_load, S::TX_BYTES);
+    vd_bulk_load(sB, Wt, S::B_BYTES, &bar_load);
+#pragma unroll
+    for (int g = 0; g < S::G; ++g)   // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128
+      vd_tma_load_3d(sA + g * S::GS, &xmap, 8 * g, x0 - 1, y0 - 1, &bar_load);
+    if (vd_mbar_wait_bounded(&bar_load, 0)) {
+      vd_tc_fence_after();
+      constexpr uint32_t idesc = vd_idesc_bf16(CNN_TILE, N);
 #pragma unroll 1
-    for (int s = 0; s < K / 16; ++s)   // two core matrices (16 k) per instruction
-      vd_umma_bf16(dt, vd_umma_desc(a0 + s * 256, 128, K * 16),
-                   vd_umma_desc(b0 + s * 256, 128, K * 16), idesc, s > 0 ? 1u : 0u);
-    vd_umma_commit(&mbar);
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+          for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (two groups) per MMA
+            const uint32_t a = sA + 2 * j * S::GS + ((r + t / 3) * CNN_HALO_X + t % 3) * 16;
+            const uint32_t b = sB + ((t * CIN + 16 * j) >> 3) * 128;
+            vd_umma_bf16(dt + r * N, vd_umma_desc(a, S::GS, 128), vd_umma_desc(b, 128, K * 16),
+                         idesc, (t | j) ? 1u : 0u);
+          }
+      vd_umma_commit(&bar_mma);
+    } else {
+      atomicExch(err, 1);
+      s_fail = 1;
+      vd_mbar_wait_bounded(&bar_load, 0);   // let copies in flight land before the CTA ends
+      vd_mbar_arrive(&bar_mma);
+    }
   }
-  bool ok = vd_mbar_wait_bounded(&mbar, 0);
+  bool ok = vd_mbar_wait_bounded(&bar_mma, 0);
   if (!ok) {
     atomicExch(err, 1);
-    ok = vd_mbar_wait_bounded(&mbar, 0);   // give the tensor core a second bound before freeing
+    ok = vd_mbar_wait_bounded(&bar_mma, 0);   // a second bound before the memory is freed
   }
   vd_tc_fence_after();
-  const int p = p0 + warp * 32 + lane;     // accumulator lane = pixel of the tile
-  const uint32_t taddr = dt + ((uint32_t)(warp * 32) << 16);
+  ok = ok && !*(volatile int*)&s_fail;
+  const int x = x0 + warp * 32 + lane;       // accumulator lane = pixel of the row
+  const uint32_t tl = dt + ((uint32_t)(warp * 32) << 16);
   if (ok) {
-    float v[32];
-    if (N == 32)
-      vd_tmem_ld32(taddr, v);
-    else
-      vd_tmem_ld16(taddr, v);
-    if (p < HW) {
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      const int y = y0 + r;
+      if (y >= Himg) break;
+      float v[N];
+      if (N == 32)
+        vd_tmem_ld32(tl + r * N, v);
+      else
+        vd_tmem_ld16(tl + r * N, v);
+      if (x >= Wimg) continue;
+      const size_t p = (size_t)y * Wimg + x;
       if (EPI == EPI_LAST) {
-        float* dst = reinterpret_cast<float*>(out) + (size_t)p * 16;
+        float* dst = reinterpret_cast<float*>(out) + p * 16;
 #pragma unroll
         for (int c = 0; c < 16; c += 4)
           *reinterpret_cast<float4*>(dst + c) =
@@ -248,13 +322,12 @@ k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
           __align__(16) __nv_bfloat16 mk[N];
 #pragma unroll
           for (int c = 0; c < N; c += 8)
-            *reinterpret_cast<uint4*>(mk + c) =
-                *reinterpret_cast<const uint4*>(mask + (size_t)p * N + c);
+            *reinterpret_cast<uint4*>(mk + c) = *reinterpret_cast<const uint4*>(mask + p * N + c);
 #pragma unroll
           for (int c = 0; c < N; ++c)
             o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
         }
-        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)p * N;
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + p * N;
 #pragma unroll
         for (int c = 0; c < N; c += 8)
           *reinterpret_cast<uint4*>(dst + c) = *reinterpret_cast<const uint4*>(o + c);
@@ -263,7 +336,7 @@ k_conv_tc(const __nv_bfloat16* __restrict__ X, int Wimg, int Himg,
   }
   vd_tc_fence_before();
   __syncthreads();
-  if (warp == 0) vd_tmem_dealloc(dt, NCOLS);
+  if (warp == 0) vd_tmem_dealloc(dt, S::NCOLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,8 +542,9 @@ __global__ void k_cnn_wgrad_reduce(const float* __restrict__ partial,
 
 // ---------------------------------------------------------------------------
 // Adam on the float32 master parameters, then the bf16 copies the GEMMs
-// read: forward Wt[co][k] (rows padded to NPAD) and data-gradient
-// Wd[ci][tap' * COUT_P + co] = W[co][8 - tap'][ci] (COUT padded to COUT_P).
+// read, both pre-tiled (vd_tile_index): forward Wt[co][k] (rows padded to
+// NPAD) and data-gradient Wd[ci][tap' * COUT_P + co] = W[co][8 - tap'][ci]
+// (COUT padded to COUT_P).
 // ---------------------------------------------------------------------------
 __global__ void k_cnn_adam(float* __restrict__ theta, float* __restrict__ m,
                            float* __restrict__ v, const float* __restrict__ g, int n, float lr,
@@ -489,17 +563,18 @@ __global__ void k_cnn_pack(const float* __restrict__ W, int cout, int cin, int n
                            __nv_bfloat16* __restrict__ Wt, __nv_bfloat16* __restrict__ Wd) {
   const int K = 9 * cin;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // forward copy: [npad][K]
+  // forward copy: npad x K
   if (i < npad * K) {
     const int co = i / K, k = i - co * K;
-    Wt[i] = __float2bfloat16_rn(co < cout ? W[(size_t)co * K + k] : 0.0f);
+    Wt[vd_tile_index(co, k, K)] = __float2bfloat16_rn(co < cout ? W[(size_t)co * K + k] : 0.0f);
   }
-  // data-gradient copy: [cin][9 * coutp]
+  // data-gradient copy: cin x 9 coutp
   if (Wd && i < cin * 9 * coutp) {
     const int ci = i / (9 * coutp), r = i - ci * (9 * coutp);
     const int tp = r / coutp, co = r - tp * coutp;
     const int tap = 8 - tp;
-    Wd[i] = __float2bfloat16_rn(co < cout ? W[(size_t)co * K + tap * cin + ci] : 0.0f);
+    Wd[vd_tile_index(ci, r, 9 * coutp)] =
+        __float2bfloat16_rn(co < cout ? W[(size_t)co * K + tap * cin + ci] : 0.0f);
   }
 }
 
@@ -515,8 +590,8 @@ struct vd_cnn {
   float* mom1;
   float* mom2;
   float* grad;
-  __nv_bfloat16* wt[CNN_L];   // forward weights [npad][K]
-  __nv_bfloat16* wd[CNN_L];   // data-gradient weights [cin][9 coutp]
+  __nv_bfloat16* wt[CNN_L];   // forward weights npad x K, pre-tiled
+  __nv_bfloat16* wd[CNN_L];   // data-gradient weights cin x 9 coutp, pre-tiled
   int step;
   // per-image buffers (grown on demand)
   int cap_hw;
@@ -559,17 +634,52 @@ static cudaError_t cnn_reserve(vd_cnn* n, int HW) {
   return e;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 vd_encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// Tensor map of an NHWC bf16 image with cin channels: dims {cin, W, H},
+// box {8, 130, rows + 2}, zero fill outside the image.
+static cudaError_t vd_halo_map(CUtensorMap* m, const void* X, int cin, int W, int H, int rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = vd_encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) || cin % 16) return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[2] = {(cuuint64_t)cin * 2, (cuuint64_t)W * cin * 2};
+  const cuuint32_t box[3] = {8, CNN_HALO_X, (cuuint32_t)rows + 2};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int K, int N, int EPI>
 static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_bfloat16* Wt,
                                const float* b, void* out, const __nv_bfloat16* mask, int* err,
                                cudaStream_t s, int nout = N) {
-  const size_t smem = vd_conv_smem<K, N>();
-  cudaError_t e = cudaFuncSetAttribute(k_conv_tc<K, N, EPI>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int R = CNN_ROWS;
+  using S = VdConvShape<K, N, R>;
+  CUtensorMap map;
+  cudaError_t e = vd_halo_map(&map, X, K / 9, W, H, R);
   if (e != cudaSuccess) return e;
-  const int HW = W * H;
-  k_conv_tc<K, N, EPI><<<(HW + CNN_TILE - 1) / CNN_TILE, CNN_TILE, smem, s>>>(X, W, H, Wt, b,
-                                                                             out, mask, nout, err);
+  if (reinterpret_cast<uintptr_t>(Wt) & 15u) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(k_conv_tc<K, N, EPI, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((W + CNN_TILE - 1) / CNN_TILE, (H + R - 1) / R);
+  k_conv_tc<K, N, EPI, R><<<grid, CNN_TILE, S::SMEM, s>>>(map, W, H, Wt, b, out, mask, nout, err);
   return cudaGetLastError();
 }
 
