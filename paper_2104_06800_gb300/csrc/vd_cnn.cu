@@ -400,7 +400,7 @@ __global__ void k_cnn_heads(const float* __restrict__ z, int HW, int N, float rh
 __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
                            const float* __restrict__ rho_t, const float* __restrict__ q_t,
                            const unsigned char* __restrict__ mask, float rho_min, float rho_max,
-                           float w_q, const float* __restrict__ nmask,
+                           float w_q, const int* __restrict__ nmask,
                            __nv_bfloat16* __restrict__ dz, double* __restrict__ partial) {
   __shared__ double s_l[256];
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,7 +408,7 @@ __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
   if (p < HW) {
     const float* v = z + (size_t)p * 16;
     const float m = mask[p] ? 1.0f : 0.0f;
-    const float inv_n = 1.0f / *nmask;
+    const float inv_n = 1.0f / (float)max(*nmask, 1);
     const float wq_n = w_q / (float)N;
     // log error of the inverse-depth head
     const float r = v[0] + 0.5f * logf(rho_min * rho_max) - logf(rho_t[p]);
@@ -436,107 +436,174 @@ __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
   if (threadIdx.x == 0) partial[blockIdx.x] = s_l[0];
 }
 
-__global__ void k_cnn_count(const unsigned char* __restrict__ mask, int HW, float* __restrict__ n) {
+// Pixels inside the mask (integer atomics: the count does not depend on the
+// order of the blocks); *n is zero on entry.
+__global__ void k_cnn_count(const unsigned char* __restrict__ mask, int HW, int* __restrict__ n) {
   __shared__ int s[256];
-  int c = 0;
-  for (int p = threadIdx.x; p < HW; p += blockDim.x) c += mask[p] ? 1 : 0;
-  s[threadIdx.x] = c;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  s[threadIdx.x] = p < HW && mask[p] ? 1 : 0;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *n = (float)(s[0] > 0 ? s[0] : 1);
+  if (threadIdx.x == 0 && s[0]) atomicAdd(n, s[0]);
 }
 
-__global__ void k_cnn_sum(const double* __restrict__ partial, int n, float* __restrict__ nmask,
+// Mean loss: the per-block partials summed by one block of 1024 threads in
+// a fixed order (strided per thread, then a tree), divided by the count.
+__global__ void k_cnn_sum(const double* __restrict__ partial, int n, const int* __restrict__ nmask,
                           double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += partial[i];
-  *out = s / (double)*nmask;
+  __shared__ double s[1024];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0] / (double)max(*nmask, 1);
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient on the CUDA cores: dW[co][k] = sum_p dz[p][co] A[p][k],
-// db[co] = sum_p dz[p][co].  Block b sums a contiguous pixel range in fixed
-// order into partial[b][co][k] (and partial_b[b][co]); k_cnn_wgrad_reduce
-// adds the blocks in index order.  dz: bf16 [HW][DZC], COUT of its channels
-// used; X: bf16 NHWC with CIN channels.
+// Weight gradient on the CUDA cores: dW[co][tap * CIN + ci] =
+// sum_p dz[p][co] X[p + offset(tap)][ci], db[co] = sum_p dz[p][co].  dz: bf16
+// [HW][DZC], COUT of its channels used; X: bf16 NHWC with CIN channels.
+// The image is cut into tiles of WG_ROWS rows x WG_COLS pixels; block b
+// takes tiles b, b + gridDim.x, ... in order.  A block stages a tile's
+// input halo and dz in shared memory; thread (co8, ci) holds dW for 8
+// output channels x 9 taps of input channel ci in registers and walks the
+// tile's pixels row by row, sliding its 3 x 3 window of X along the row (3
+// new values, one 16-byte dz load and 72 FMAs per pixel).  The block's sums
+// go to partial[b][co][k] (and partial_b[b][co]); k_cnn_wgrad_reduce adds
+// the blocks in index order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-#define WG_BLOCKS 152
-#define WG_CHUNK 32
+#ifndef WG_BLOCKS
+#define WG_BLOCKS 608
+#endif
+#define WG_ROWS 4
+#define WG_COLS 64
 
 template <int CIN, int COUT, int DZC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(COUT / 8 * CIN)
 k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dz, int Wimg,
             int Himg, float* __restrict__ partial, float* __restrict__ partial_b) {
-  constexpr int K = 9 * CIN, NOUT = COUT * K;
-  constexpr int PER = (NOUT + 255) / 256;
-  __shared__ float sA[WG_CHUNK][K];
-  __shared__ float sD[WG_CHUNK][COUT];
-  const int HW = Wimg * Himg;
-  const int per = (HW + gridDim.x - 1) / gridDim.x;
-  const int beg = min(HW, (int)blockIdx.x * per), end = min(HW, beg + per);
-  float acc[PER];
+  constexpr int K = 9 * CIN, NT = COUT / 8 * CIN;
+  constexpr int HR = WG_ROWS + 2, HC = WG_COLS + 2;
+  __shared__ __align__(16) __nv_bfloat16 sX[HR * HC * CIN];
+  __shared__ __align__(16) __nv_bfloat16 sD[WG_ROWS * WG_COLS * COUT];
+  const int tid = threadIdx.x, ci = tid % CIN, co8 = tid / CIN;
+  const int tiles_x = (Wimg + WG_COLS - 1) / WG_COLS;
+  const int n_tiles = tiles_x * ((Himg + WG_ROWS - 1) / WG_ROWS);
+  float acc[8][9];
 #pragma unroll
-  for (int i = 0; i < PER; ++i) acc[i] = 0.0f;
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[c][t] = 0.0f;
   float accb = 0.0f;
-  for (int base = beg; base < end; base += WG_CHUNK) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < WG_CHUNK * K; idx += 256) {
-      const int j = idx / K, k = idx - j * K;
-      const int p = base + j;
-      float v = 0.0f;
-      if (p < end) {
-        const int tap = k / CIN, ci = k - tap * CIN;
-        const int y = p / Wimg, x = p - y * Wimg;
-        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-        if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
-          v = __bfloat162float(X[((size_t)yy * Wimg + xx) * CIN + ci]);
-      }
-      sA[j][k] = v;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int y0 = tile / tiles_x * WG_ROWS, x0 = tile % tiles_x * WG_COLS;
+    __syncthreads();   // the previous tile's values are no longer read
+    for (int i = tid; i < HR * HC * (CIN / 8); i += NT) {
+      const int g = i % (CIN / 8), px = i / (CIN / 8);
+      const int yy = y0 - 1 + px / HC, xx = x0 - 1 + px % HC;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * Wimg + xx) * CIN + 8 * g);
+      *reinterpret_cast<uint4*>(sX + (size_t)px * CIN + 8 * g) = v;
     }
-    for (int idx = threadIdx.x; idx < WG_CHUNK * COUT; idx += 256) {
-      const int j = idx / COUT, c = idx - j * COUT;
-      const int p = base + j;
-      sD[j][c] = p < end ? __bfloat162float(dz[(size_t)p * DZC + c]) : 0.0f;
+    for (int i = tid; i < WG_ROWS * WG_COLS * (COUT / 8); i += NT) {
+      const int g = i % (COUT / 8), px = i / (COUT / 8);
+      const int yy = y0 + px / WG_COLS, xx = x0 + px % WG_COLS;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (yy < Himg && xx < Wimg)
+        v = *reinterpret_cast<const uint4*>(dz + ((size_t)yy * Wimg + xx) * DZC + 8 * g);
+      *reinterpret_cast<uint4*>(sD + (size_t)px * COUT + 8 * g) = v;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int j = 0; j < WG_CHUNK; ++j) {
+#pragma unroll 1
+    for (int r = 0; r < WG_ROWS; ++r) {
+      float w[3][3];   // X at rows r .. r + 2, columns x .. x + 2 of the halo
 #pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int o = threadIdx.x + 256 * i;
-        if (o < NOUT) acc[i] = fmaf(sD[j][o / K], sA[j][o - (o / K) * K], acc[i]);
+      for (int dy = 0; dy < 3; ++dy) {
+        w[dy][0] = __bfloat162float(sX[((r + dy) * HC + 0) * CIN + ci]);
+        w[dy][1] = __bfloat162float(sX[((r + dy) * HC + 1) * CIN + ci]);
       }
-      if ((int)threadIdx.x < COUT) accb += sD[j][threadIdx.x];
+#pragma unroll 2
+      for (int x = 0; x < WG_COLS; ++x) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+          w[dy][2] = __bfloat162float(sX[((r + dy) * HC + x + 2) * CIN + ci]);
+        const __nv_bfloat16* d = sD + (size_t)(r * WG_COLS + x) * COUT + co8 * 8;
+        const uint4 dv = *reinterpret_cast<const uint4*>(d);
+        const __nv_bfloat162* d2 = reinterpret_cast<const __nv_bfloat162*>(&dv);
+        float dzv[8];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float2 f = __bfloat1622float2(d2[c]);
+          dzv[2 * c] = f.x;
+          dzv[2 * c + 1] = f.y;
+        }
+        accb += __bfloat162float(d[ci & 7]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+              acc[c][dy * 3 + dx] = fmaf(dzv[c], w[dy][dx], acc[c][dy * 3 + dx]);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          w[dy][0] = w[dy][1];
+          w[dy][1] = w[dy][2];
+        }
+      }
     }
   }
+  float* out = partial + (size_t)blockIdx.x * COUT * K;
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int o = threadIdx.x + 256 * i;
-    if (o < NOUT) partial[(size_t)blockIdx.x * NOUT + o] = acc[i];
-  }
-  if ((int)threadIdx.x < COUT) partial_b[blockIdx.x * COUT + threadIdx.x] = accb;
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) out[(size_t)(co8 * 8 + c) * K + t * CIN + ci] = acc[c][t];
+  if (ci < 8) partial_b[blockIdx.x * COUT + co8 * 8 + ci] = accb;
 }
 
-// The partials hold COUT_P (padded) rows per block; the first cout rows are
-// the real ones.
-__global__ void k_cnn_wgrad_reduce(const float* __restrict__ partial,
-                                   const float* __restrict__ partial_b, int nblk, int stride,
-                                   int nout, int stride_b, int cout, float* __restrict__ gW,
-                                   float* __restrict__ gb) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o < nout) {
-    float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * stride + o];
-    gW[o] = s;
+// Sum of the blocks' partials.  The partials hold `stride` values per block
+// (COUT_P padded rows); the first nout are the real ones.  A CTA of 8 warps
+// takes 32 outputs: warp w adds blocks w, w + 8, ... in order, then warp 0
+// adds the 8 warps' sums in order.  CTA 0 also sums the bias partials.
+__global__ void __launch_bounds__(256)
+k_cnn_wgrad_reduce(const float* __restrict__ partial, const float* __restrict__ partial_b,
+                   int nblk, int stride, int nout, int stride_b, int cout,
+                   float* __restrict__ gW, float* __restrict__ gb) {
+  __shared__ float s[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  float v = 0.0f;
+  if (o < nout)
+#pragma unroll 4
+    for (int b = w; b < nblk; b += 8) v += partial[(size_t)b * stride + o];
+  s[w][lane] = v;
+  __syncthreads();
+  if (w == 0 && o < nout) {
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += s[i][lane];
+    gW[o] = t;
   }
-  if (o < cout) {
-    float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += partial_b[b * stride_b + o];
-    gb[o] = s;
+  if (blockIdx.x != 0) return;
+  __syncthreads();
+  v = 0.0f;
+  if (lane < cout)
+    for (int b = w; b < nblk; b += 8) v += partial_b[b * stride_b + lane];
+  s[w][lane] = v;
+  __syncthreads();
+  if (w == 0 && lane < cout) {
+    float t = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += s[i][lane];
+    gb[lane] = t;
   }
 }
 
@@ -603,7 +670,7 @@ struct vd_cnn {
   float* wg_partial_b;
   double* loss_partial;
   double* loss;
-  float* nmask;
+  int* nmask;          // pixels inside the training mask
   double* geo;         // [12] T_1 given to the host-API calls
   int* err;
 };
@@ -724,12 +791,13 @@ static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaS
 template <int CIN, int COUT, int DZC>
 static cudaError_t launch_wgrad(vd_cnn* n, int l, const __nv_bfloat16* dz, int W, int H,
                                 cudaStream_t s) {
-  k_cnn_wgrad<CIN, COUT, DZC><<<WG_BLOCKS, 256, 0, s>>>(n->act[l], dz, W, H, n->wg_partial,
-                                                       n->wg_partial_b);
+  k_cnn_wgrad<CIN, COUT, DZC><<<WG_BLOCKS, COUT / 8 * CIN, 0, s>>>(n->act[l], dz, W, H,
+                                                                   n->wg_partial,
+                                                                   n->wg_partial_b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int stride = COUT * 9 * CIN, nout = n->cout[l] * 9 * CIN;
-  k_cnn_wgrad_reduce<<<(stride + 255) / 256, 256, 0, s>>>(
+  k_cnn_wgrad_reduce<<<(nout + 31) / 32, 256, 0, s>>>(
       n->wg_partial, n->wg_partial_b, WG_BLOCKS, stride, nout, COUT, n->cout[l],
       n->grad + n->woff[l], n->grad + n->boff[l]);
   return cudaGetLastError();
@@ -837,7 +905,7 @@ extern "C" vd_status vd_cnn_create(int n_flows, unsigned long long seed, vd_cnn*
     e = cudaMalloc(&n->wg_partial, sizeof(float) * WG_BLOCKS * CNN_WIDTH * 9 * CNN_WIDTH);
   if (e == cudaSuccess) e = cudaMalloc(&n->wg_partial_b, sizeof(float) * WG_BLOCKS * CNN_WIDTH);
   if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&n->nmask, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->nmask, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&n->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&n->geo, sizeof(double) * 12);
   if (e == cudaSuccess) e = cudaMemcpy(n->theta, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
@@ -979,11 +1047,12 @@ extern "C" vd_status vd_cnn_train_step(vd_cnn* n, const float* flow, int width, 
   VdCnnGeo g;
   VD_CU(cnn_host_geo(n, geom, s, &g));
   VD_CU(cnn_forward(n, flow, width, height, s, g));
-  k_cnn_count<<<1, 256, 0, s>>>(mask, HW, n->nmask);
   const int nb = (HW + 255) / 256;
+  VD_CU(cudaMemsetAsync(n->nmask, 0, sizeof(int), s));
+  k_cnn_count<<<nb, 256, 0, s>>>(mask, HW, n->nmask);
   k_cnn_loss<<<nb, 256, 0, s>>>(n->zlast, HW, n->N, rho_t, q_t, mask, rho_min, rho_max, w_q,
                                 n->nmask, n->g0, n->loss_partial);
-  k_cnn_sum<<<1, 32, 0, s>>>(n->loss_partial, nb, n->nmask, n->loss);
+  k_cnn_sum<<<1, 1024, 0, s>>>(n->loss_partial, nb, n->nmask, n->loss);
   VD_CU(cudaGetLastError());
   VD_CU(cnn_backward(n, width, height, s));
   if (update) {

@@ -27,6 +27,11 @@ start; the true depth favours neither.
 
     python -m paper_2104_06800_gb300.learned_init --train 2000 --epochs 8 \\
         --eval 100 --out weights.npy --report report.json
+
+`--timing` instead times the network's kernels alone on one window of the
+workload's size (random flow, pose and targets): the forward pass and a
+training step (forward, loss, backward, no update), as the median of CUDA
+event timings on the launching stream.
 """
 from __future__ import annotations
 
@@ -196,6 +201,45 @@ def evaluate(V, net, wins, log=print):
     return out
 
 
+def timing(V, reps=20, H=480, W=640, seed=0):
+    """Median GPU time (ms) of the forward pass and of a training step of the
+    network at H x W with N_FLOWS flows, after three untimed calls."""
+    import torch
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(seed)
+    T = lambda a: torch.from_numpy(a).to(dev)
+    flow = T((rng.normal(size=(N_FLOWS, H, W, 2)) * 20).astype(np.float32))
+    rho_t = T(rng.uniform(0.1, 1.5, size=(H, W)).astype(np.float32))
+    q_t = T((rng.uniform(size=(N_FLOWS, H, W)) > 0.3).astype(np.float32))
+    mask = torch.ones((H, W), dtype=torch.uint8, device=dev)
+    rho = torch.zeros((H, W), device=dev)
+    geom = ((0.8 * W, 0.8 * W, W / 2, H / 2), np.hstack([np.eye(3), [[0.0], [0.0], [1.0]]]))
+    net = V.vd_cnn_create(N_FLOWS, seed=1)
+    stream = torch.cuda.current_stream()
+
+    def med(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    try:
+        fwd = med(lambda: V.vd_cnn_forward(net, flow, 0.05, 2.0, rho_out=rho, geom=geom))
+        step = med(lambda: V.vd_cnn_train_step(net, flow, rho_t, q_t, mask, 0.05, 2.0, W_Q, 0.0,
+                                               update=False, geom=geom))
+    finally:
+        V.vd_cnn_destroy(net)
+    return {"size": [W, H], "flows": N_FLOWS, "forward_ms": round(fwd, 4),
+            "train_step_ms": round(step, 4), "reps": reps}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--train", type=int, default=2000, help="training windows")
@@ -206,7 +250,15 @@ def main(argv=None):
     ap.add_argument("--weights", default=None, help="evaluate these weights (skip training)")
     ap.add_argument("--out", default=None, help="write the trained parameters (.npy)")
     ap.add_argument("--report", default=None, help="write the evaluation report (.json)")
+    ap.add_argument("--timing", action="store_true",
+                    help="only time the forward pass and a training step (640 x 480)")
     args = ap.parse_args(argv)
+    if args.timing:
+        from . import build, voldor as V
+        build.build()
+        V.load()
+        print(json.dumps(timing(V)))
+        return 0
     # the host pool (spawned processes, no CUDA) makes the scenes; the labels
     # and the training data live on the GPU, a chunk of windows at a time
     pool = mp.get_context("spawn").Pool(args.workers) if args.workers > 1 else None
