@@ -614,8 +614,9 @@ static cudaError_t bootstrap(vd_ctx* c) {
   return e;
 }
 
-// Bootstrap with the learned initialiser: the bootstrap of R11 with the
-// network's inverse depth as the initial value of its monocular depth step
+// Bootstrap with the learned initialiser: the monocular bootstrap above
+// (8-point pose, depth from X_1 alone, pose step) with the network's
+// inverse depth as the initial value of its depth step
 // (slot 0 of every pixel's candidates, in place of the random draw).  The
 // rest is the plain bootstrap (q = 1; with a prior, the prior's inverse
 // depth and no depth step).  The network's rigidness is not used here: its

@@ -810,8 +810,8 @@ static cudaError_t cnn_backward(vd_cnn* n, int W, int H, cudaStream_t s) {
   for (int l = CNN_L - 1; l >= 0 && e == cudaSuccess; --l) {
     if (l == CNN_L - 1)
       e = launch_wgrad<32, 16, 16>(n, l, dz, W, H, s);   // 1 + N of 16 rows used
-    else if (l == 0)
-      e = launch_wgrad<16, 32, 32>(n, l, dz, W, H, s);
+    else if (l == 0 && n->cin[0] == 16)
+      e = launch_wgrad<16, 32, 32>(n, l, dz, W, H, s);   // 16 input planes (2N + 4 <= 16)
     else
       e = launch_wgrad<32, 32, 32>(n, l, dz, W, H, s);
     if (e != cudaSuccess || l == 0) break;

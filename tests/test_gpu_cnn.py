@@ -72,9 +72,15 @@ def _acts(V, net, lay, W, H):
     return a, z[:lay["c_out"][5]]
 
 
-def test_forward_layers_match_oracle(V):
+# (N, H, W): one 128-pixel tile, ragged in x and in the 4-row blocks, with
+# 16 input planes; three tiles (the halo columns of each tile come from its
+# neighbours), ragged rows, and 32 input planes (2N + 4 > 16)
+SHAPES = [(6, 61, 100), (8, 37, 300)]
+
+
+@pytest.mark.parametrize("N,H,W", SHAPES)
+def test_forward_layers_match_oracle(V, N, H, W):
     import torch
-    N, H, W = 6, 61, 100
     net, lay, theta, flow, *_ , T = _setup(V, N, H, W)
     try:
         rho = torch.zeros((H, W), device="cuda")
@@ -113,8 +119,8 @@ def test_forward_layers_match_oracle(V):
         V.vd_cnn_destroy(net)
 
 
-def test_loss_and_gradients_match_oracle(V):
-    N, H, W = 6, 61, 100
+@pytest.mark.parametrize("N,H,W", SHAPES)
+def test_loss_and_gradients_match_oracle(V, N, H, W):
     net, lay, theta, flow, rho_t, q_t, mask, T = _setup(V, N, H, W, seed=2)
     try:
         loss = V.vd_cnn_train_step(net, T(flow), T(rho_t), T(q_t), T(mask), RHO_MIN, RHO_MAX,
