@@ -130,8 +130,10 @@ def dist_setup(n):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if n > 1 else "gloo")
+        # one process per GPU over NCCL; gloo where there is no GPU (host tests)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         pg = dist
     return rank, world, local, pg
 
@@ -150,15 +152,34 @@ def max_over_ranks(pg, x, device):
     return float(t.item())
 
 
+def whole_job(pg, world, units_per_rank, local_ms, device):
+    """(slowest rank's time in ms, whole-job rate): every rank processes
+    units_per_rank units of its own (weak scaling, no data-path exchange);
+    the job ends when the slowest rank does."""
+    ms = max_over_ranks(pg, local_ms, device)
+    return ms, units_per_rank * world / (ms / 1e3)
+
+
+def rank_window_seeds(seed, rank, nb):
+    """Seeds of the nb windows rank `rank` runs: the first is seed + rank (the
+    single-window run's), the others distinct across ranks and windows."""
+    return [seed + rank] + [seed + 100 * (rank + 1) + i for i in range(1, nb)]
+
+
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(seconds_hint=20.0):
-    """Time the float64 oracle on a centred 608 x 184 crop of the same window
-    (1/4 of the pixels, same N, K, S): one EM iteration from a mid-EM state."""
+_ORACLE_WINDOW = []
+
+
+def oracle_sample(cw=WORK["W"] // 2, ch=WORK["H"] // 2):
+    """Time the float64 oracle on a centred cw x ch crop of the same window
+    (608 x 184 = 1/4 of the pixels by default, same N, K, S): one EM
+    iteration from a mid-EM state.  The window is generated once."""
     import synth
     from oracle import em as oem
     from oracle import model as omodel
-    win = synth.make_window(WORK["name"], WORK["seed"])
-    cw, ch = WORK["W"] // 2, WORK["H"] // 2
+    if not _ORACLE_WINDOW:
+        _ORACLE_WINDOW.append(synth.make_window(WORK["name"], WORK["seed"]))
+    win = _ORACLE_WINDOW[0]
     u0, v0 = (WORK["W"] - cw) // 2, (WORK["H"] - ch) // 2
     fx, fy, cx, cy = win.intrinsics
     P = omodel.Problem(cw, ch, WORK["N"], (fx, fy, cx - u0, cy - v0),
@@ -281,8 +302,8 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
     units_per_window = W * H * N * iters
     # ---- a batch of windows in one graph launch (the headline throughput)
     nb = max(1, args.batch)
-    bw = [win] + [synth.make_window(WORK["name"], WORK["seed"] + 100 * (rank + 1) + i)
-                  for i in range(1, nb)]
+    seeds = rank_window_seeds(WORK["seed"], rank, nb)
+    bw = [win] + [synth.make_window(WORK["name"], sd) for sd in seeds[1:]]
     b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in bw], params, sptr)
     for i, w in enumerate(bw):
         fl = torch.from_numpy(w.flow).to(dev)
@@ -304,8 +325,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
     clk = clocks.stop()
     barrier(pg)
     bstats = V.vd_batch_get_stats(b)
-    total_ms = max_over_ranks(pg, sum(tb), dev)
-    value = units_per_window * nb * args.steps * world / (total_ms / 1e3)
+    total_ms, value = whole_job(pg, world, units_per_window * nb * args.steps, sum(tb), dev)
 
     e2e = None
     if not args.no_e2e:
@@ -455,10 +475,13 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
+        # each timed step: one EM iteration of the oracle on the 608 x 184
+        # crop (10-20 s of CPU work); warm-up steps on a 304 x 92 crop (they
+        # only take the one-time costs: imports, the window, first touches)
+        for _ in range(max(args.warmup, 0)):
+            oracle_sample(WORK["W"] // 4, WORK["H"] // 4)
         units_s = []
         samples = []
-        for _ in range(max(args.warmup, 0) and 0):
-            pass
         for _ in range(args.steps):
             v, dt, desc = oracle_sample()
             units_s.append(v)
@@ -484,7 +507,7 @@ def main():
         return 0
     line = run_ours(args, rank, world, local, pg)
     if rank == 0:
-        if not args.no_cpu:
+        if not args.no_cpu and world == 1:   # the host baseline: rank 0 of a 1-GPU run only
             v, dt, desc = oracle_sample()
             line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cpu_cores_used(),
                                     "kind": "oracle", "sample": desc}

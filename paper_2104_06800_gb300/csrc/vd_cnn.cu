@@ -34,7 +34,10 @@
 #define CNN_TILE 128               // output pixels of a row per tile (the MMA's M)
 #define CNN_HALO_X (CNN_TILE + 2)
 #ifndef CNN_ROWS
-#define CNN_ROWS 4                 // output rows per CTA
+#define CNN_ROWS 4                 // output rows per tile
+#endif
+#ifndef CNN_STAGES
+#define CNN_STAGES 3               // halo tiles in flight per CTA
 #endif
 #define CNN_WAIT_LIMIT (1 << 22)   // mbarrier polls before a wait gives up
 
@@ -209,129 +212,200 @@ __host__ __device__ constexpr size_t vd_tile_index(int n, int k, int K) {
 
 __host__ __device__ constexpr uint32_t vd_round128(uint32_t b) { return (b + 127u) & ~127u; }
 
-template <int K, int N, int R>
+template <int K, int N, int R, int NS>
 struct VdConvShape {
   static constexpr int CIN = K / 9, G = CIN / 8;
   static constexpr uint32_t B_BYTES = (uint32_t)N * K * 2;
   static constexpr uint32_t BOX_BYTES = (uint32_t)(R + 2) * CNN_HALO_X * 16;
   static constexpr uint32_t GS = vd_round128(BOX_BYTES);   // stride between channel groups
+  static constexpr uint32_t STAGE = G * GS;                 // one halo tile
   static constexpr uint32_t A_OFF = vd_round128(B_BYTES);
-  static constexpr uint32_t TX_BYTES = B_BYTES + G * BOX_BYTES;
-  // tensor-memory columns: R accumulators of N, as a power of two >= 32
-  static constexpr uint32_t NCOLS = R * N <= 32 ? 32 : R * N <= 64 ? 64 : R * N <= 128 ? 128
-                                  : R * N <= 256 ? 256 : 512;
-  // shared memory: the tiles, 128 B of alignment slack, and at least enough
-  // that no more CTAs share an SM than its 512 tensor-memory columns hold
-  // (228 KB per SM, 1 KB reserved per CTA)
-  static constexpr uint32_t NEED = A_OFF + G * GS + 128;
+  static constexpr uint32_t ACC = (uint32_t)R * N;          // columns of one accumulator
+  // tensor-memory columns: two accumulators, as a power of two >= 32
+  static constexpr uint32_t NCOLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128
+                                  : 2 * ACC <= 256 ? 256 : 512;
+  // shared memory: weights, NS halo stages, 128 B of alignment slack, and
+  // at least enough that no more CTAs share an SM than its 512 tensor-memory
+  // columns hold (228 KB per SM, 1 KB reserved per CTA)
+  static constexpr uint32_t NEED = A_OFF + NS * STAGE + 128;
   static constexpr uint32_t FLOOR = 233472u / (512u / NCOLS + 1u) - 1024u + 16u;
   static constexpr uint32_t SMEM = NEED > FLOOR ? NEED : FLOOR;
 };
 
-template <int K, int N, int EPI, int R>
-__global__ void __launch_bounds__(CNN_TILE)
-k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg,
+// Bounded wait that also gives up once another role of the CTA has set
+// `abort` (checked every 256 polls).
+__device__ __forceinline__ bool vd_mbar_wait_or_abort(uint64_t* m, uint32_t phase,
+                                                      volatile int* abort) {
+  for (int i = 0; i < CNN_WAIT_LIMIT; ++i) {
+    if (vd_mbar_try_wait(m, phase)) return true;
+    if ((i & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+
+// Persistent, warp-specialised: CTA b takes tiles b, b + gridDim.x, ...
+// (tile = x-tile + tiles_x * row block).  Warp 4 loads halo tiles into a ring
+// of NS stages (the weights with the first); one thread of warp 5 issues a
+// tile's MMAs into one of two tensor-memory accumulators and commits them to
+// the stage's `empty` barrier and the accumulator's `full` barrier; warps
+// 0..3 (tensor-memory lanes 32 w .. 32 w + 31) run the epilogue and release
+// the accumulator.  So tile i + 1's MMAs run under tile i's epilogue and
+// the loads of the tiles after it.  Every wait is bounded; a role that gives
+// up flags the error and the abort, the others stop at their next wait, and
+// before the CTA ends the loads and MMAs it issued are waited for.
+template <int K, int N, int EPI, int R, int NS>
+__global__ void __launch_bounds__(192, 1)
+k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tiles_x, int n_tiles,
           const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
           void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int nout,
           int* __restrict__ err) {
-  using S = VdConvShape<K, N, R>;
+  using S = VdConvShape<K, N, R, NS>;
   static_assert(K % 144 == 0 && (N == 16 || N == 32), "shapes of this network");
-  static_assert(S::NCOLS <= 512 && R + 2 <= 256, "tile");
+  static_assert(S::NCOLS <= 512 && R + 2 <= 256 && NS >= 2, "tile");
   constexpr int CIN = S::CIN;
   extern __shared__ uint8_t smem[];
-  __shared__ uint64_t bar_load, bar_mma;
+  __shared__ uint64_t full[NS], empty[NS], accfull[2], accempty[2], fin;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
+  __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * CNN_TILE, y0 = blockIdx.y * R;
+  volatile int* abort = &s_abort;
   if (warp == 0) vd_tmem_alloc(&tmem_base, S::NCOLS);
-  if (tid == 0) {
-    vd_mbar_init(&bar_load, 1);
-    vd_mbar_init(&bar_mma, 1);
-    s_fail = 0;
+  if (tid == 32) {
+    for (int s = 0; s < NS; ++s) {
+      vd_mbar_init(&full[s], 1);
+      vd_mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      vd_mbar_init(&accfull[a], 1);
+      vd_mbar_init(&accempty[a], 4);
+    }
+    vd_mbar_init(&fin, 1);
+    s_abort = 0;
   }
   vd_tc_fence_before();
   __syncthreads();
   vd_tc_fence_after();
   const uint32_t dt = tmem_base;
-  if (tid == 0) {
-    const uint32_t sB = (vd_smem_u32(smem) + 127u) & ~127u, sA = sB + S::A_OFF;
-    vd_mbar_expect_tx(&bar_load, S::TX_BYTES);
-    vd_bulk_load(sB, Wt, S::B_BYTES, &bar_load);
+  const uint32_t sB = (vd_smem_u32(smem) + 127u) & ~127u, sA = sB + S::A_OFF;
+  const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (warp == 4) {
+    if (lane == 0) {   // producer
+      int issued = 0;
+      for (int i = 0; i < my_tiles && !*abort; ++i) {
+        const int s = i % NS;
+        if (i >= NS && !vd_mbar_wait_or_abort(&empty[s], ((i / NS) - 1) & 1, abort)) {
+          atomicExch(err, 1);
+          *abort = 1;
+          break;
+        }
+        const int tile = blockIdx.x + i * gridDim.x;
+        const int x0 = (tile % tiles_x) * CNN_TILE, y0 = (tile / tiles_x) * R;
+        vd_mbar_expect_tx(&full[s], S::G * S::BOX_BYTES + (i == 0 ? S::B_BYTES : 0u));
+        if (i == 0) vd_bulk_load(sB, Wt, S::B_BYTES, &full[0]);
 #pragma unroll
-    for (int g = 0; g < S::G; ++g)   // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128
-      vd_tma_load_3d(sA + g * S::GS, &xmap, 8 * g, x0 - 1, y0 - 1, &bar_load);
-    if (vd_mbar_wait_bounded(&bar_load, 0)) {
-      vd_tc_fence_after();
-      constexpr uint32_t idesc = vd_idesc_bf16(CNN_TILE, N);
-#pragma unroll 1
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-#pragma unroll
-          for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (two groups) per MMA
-            const uint32_t a = sA + 2 * j * S::GS + ((r + t / 3) * CNN_HALO_X + t % 3) * 16;
-            const uint32_t b = sB + ((t * CIN + 16 * j) >> 3) * 128;
-            vd_umma_bf16(dt + r * N, vd_umma_desc(a, S::GS, 128), vd_umma_desc(b, 128, K * 16),
-                         idesc, (t | j) ? 1u : 0u);
-          }
-      vd_umma_commit(&bar_mma);
-    } else {
-      atomicExch(err, 1);
-      s_fail = 1;
-      vd_mbar_wait_bounded(&bar_load, 0);   // let copies in flight land before the CTA ends
-      vd_mbar_arrive(&bar_mma);
+        for (int g = 0; g < S::G; ++g)   // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128
+          vd_tma_load_3d(sA + s * S::STAGE + g * S::GS, &xmap, 8 * g, x0 - 1, y0 - 1, &full[s]);
+        issued = i + 1;
+      }
+      // the loads in flight land before the CTA ends
+      for (int i = issued > NS ? issued - NS : 0; i < issued; ++i)
+        vd_mbar_wait_bounded(&full[i % NS], (i / NS) & 1);
     }
-  }
-  bool ok = vd_mbar_wait_bounded(&bar_mma, 0);
-  if (!ok) {
-    atomicExch(err, 1);
-    ok = vd_mbar_wait_bounded(&bar_mma, 0);   // a second bound before the memory is freed
-  }
-  vd_tc_fence_after();
-  ok = ok && !*(volatile int*)&s_fail;
-  const int x = x0 + warp * 32 + lane;       // accumulator lane = pixel of the row
-  const uint32_t tl = dt + ((uint32_t)(warp * 32) << 16);
-  if (ok) {
+  } else if (warp == 5) {
+    if (lane == 0) {   // MMA issuer
+      bool any = false;
+      constexpr uint32_t idesc = vd_idesc_bf16(CNN_TILE, N);
+      for (int i = 0; i < my_tiles && !*abort; ++i) {
+        const int s = i % NS, a = i & 1;
+        if (!vd_mbar_wait_or_abort(&full[s], (i / NS) & 1, abort) ||
+            (i >= 2 && !vd_mbar_wait_or_abort(&accempty[a], ((i >> 1) - 1) & 1, abort))) {
+          atomicExch(err, 1);
+          *abort = 1;
+          break;
+        }
+        vd_tc_fence_after();
+        const uint32_t a0 = sA + s * S::STAGE, d0 = dt + a * S::ACC;
 #pragma unroll 1
-    for (int r = 0; r < R; ++r) {
-      const int y = y0 + r;
-      if (y >= Himg) break;
-      float v[N];
-      if (N == 32)
-        vd_tmem_ld32(tl + r * N, v);
-      else
-        vd_tmem_ld16(tl + r * N, v);
-      if (x >= Wimg) continue;
-      const size_t p = (size_t)y * Wimg + x;
-      if (EPI == EPI_LAST) {
-        float* dst = reinterpret_cast<float*>(out) + p * 16;
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 16; c += 4)
-          *reinterpret_cast<float4*>(dst + c) =
-              make_float4(c + 0 < nout ? v[c + 0] + bias[c + 0] : 0.0f,
-                          c + 1 < nout ? v[c + 1] + bias[c + 1] : 0.0f,
-                          c + 2 < nout ? v[c + 2] + bias[c + 2] : 0.0f,
-                          c + 3 < nout ? v[c + 3] + bias[c + 3] : 0.0f);
-      } else {
-        __align__(16) __nv_bfloat16 o[N];
-        if (EPI == EPI_RELU) {
+          for (int t = 0; t < 9; ++t)
 #pragma unroll
-          for (int c = 0; c < N; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.0f));
+            for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (two groups) per MMA
+              const uint32_t aa = a0 + 2 * j * S::GS + ((r + t / 3) * CNN_HALO_X + t % 3) * 16;
+              const uint32_t bb = sB + ((t * CIN + 16 * j) >> 3) * 128;
+              vd_umma_bf16(d0 + r * N, vd_umma_desc(aa, S::GS, 128), vd_umma_desc(bb, 128, K * 16),
+                           idesc, (t | j) ? 1u : 0u);
+            }
+        vd_umma_commit(&empty[s]);     // the stage is free once these MMAs are done
+        vd_umma_commit(&accfull[a]);   // and the accumulator is ready
+        any = true;
+      }
+      if (any) {   // every MMA issued has finished before the memory is freed
+        vd_umma_commit(&fin);
+        vd_mbar_wait_bounded(&fin, 0);
+      }
+    }
+  } else {   // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31
+    const uint32_t tl = dt + ((uint32_t)(warp * 32) << 16);
+    for (int i = 0; i < my_tiles; ++i) {
+      const int a = i & 1;
+      int ok = 0;
+      if (lane == 0) ok = vd_mbar_wait_or_abort(&accfull[a], (i >> 1) & 1, abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(err, 1);
+          *abort = 1;
+        }
+        break;
+      }
+      vd_tc_fence_after();
+      const int tile = blockIdx.x + i * gridDim.x;
+      const int x = (tile % tiles_x) * CNN_TILE + warp * 32 + lane, y0 = (tile / tiles_x) * R;
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const int y = y0 + r;
+        if (y >= Himg) break;   // warp-uniform
+        float v[N];
+        if (N == 32)
+          vd_tmem_ld32(tl + a * S::ACC + r * N, v);
+        else
+          vd_tmem_ld16(tl + a * S::ACC + r * N, v);
+        if (x >= Wimg) continue;
+        const size_t p = (size_t)y * Wimg + x;
+        if (EPI == EPI_LAST) {
+          float* dst = reinterpret_cast<float*>(out) + p * 16;
+#pragma unroll
+          for (int c = 0; c < 16; c += 4)
+            *reinterpret_cast<float4*>(dst + c) =
+                make_float4(c + 0 < nout ? v[c + 0] + bias[c + 0] : 0.0f,
+                            c + 1 < nout ? v[c + 1] + bias[c + 1] : 0.0f,
+                            c + 2 < nout ? v[c + 2] + bias[c + 2] : 0.0f,
+                            c + 3 < nout ? v[c + 3] + bias[c + 3] : 0.0f);
         } else {
-          __align__(16) __nv_bfloat16 mk[N];
+          __align__(16) __nv_bfloat16 o[N];
+          if (EPI == EPI_RELU) {
+#pragma unroll
+            for (int c = 0; c < N; ++c) o[c] = __float2bfloat16_rn(fmaxf(v[c] + bias[c], 0.0f));
+          } else {
+            __align__(16) __nv_bfloat16 mk[N];
+#pragma unroll
+            for (int c = 0; c < N; c += 8)
+              *reinterpret_cast<uint4*>(mk + c) =
+                  *reinterpret_cast<const uint4*>(mask + p * N + c);
+#pragma unroll
+            for (int c = 0; c < N; ++c)
+              o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
+          }
+          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + p * N;
 #pragma unroll
           for (int c = 0; c < N; c += 8)
-            *reinterpret_cast<uint4*>(mk + c) = *reinterpret_cast<const uint4*>(mask + p * N + c);
-#pragma unroll
-          for (int c = 0; c < N; ++c)
-            o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
+            *reinterpret_cast<uint4*>(dst + c) = *reinterpret_cast<const uint4*>(o + c);
         }
-        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + p * N;
-#pragma unroll
-        for (int c = 0; c < N; c += 8)
-          *reinterpret_cast<uint4*>(dst + c) = *reinterpret_cast<const uint4*>(o + c);
       }
+      vd_tc_fence_before();
+      __syncwarp();
+      if (lane == 0) vd_mbar_arrive(&accempty[a]);
     }
   }
   vd_tc_fence_before();
@@ -736,17 +810,31 @@ template <int K, int N, int EPI>
 static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_bfloat16* Wt,
                                const float* b, void* out, const __nv_bfloat16* mask, int* err,
                                cudaStream_t s, int nout = N) {
-  constexpr int R = CNN_ROWS;
-  using S = VdConvShape<K, N, R>;
+  constexpr int R = CNN_ROWS, NS = CNN_STAGES;
+  using S = VdConvShape<K, N, R, NS>;
+  auto kern = k_conv_tc<K, N, EPI, R, NS>;
+  // persistent grid: every CTA that fits on the device at once (set up once)
+  static int slots = 0;
+  if (!slots) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, S::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    slots = sms * per_sm;
+  }
   CUtensorMap map;
   cudaError_t e = vd_halo_map(&map, X, K / 9, W, H, R);
   if (e != cudaSuccess) return e;
   if (reinterpret_cast<uintptr_t>(Wt) & 15u) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(k_conv_tc<K, N, EPI, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)S::SMEM);
-  if (e != cudaSuccess) return e;
-  const dim3 grid((W + CNN_TILE - 1) / CNN_TILE, (H + R - 1) / R);
-  k_conv_tc<K, N, EPI, R><<<grid, CNN_TILE, S::SMEM, s>>>(map, W, H, Wt, b, out, mask, nout, err);
+  const int tiles_x = (W + CNN_TILE - 1) / CNN_TILE;
+  const int n_tiles = tiles_x * ((H + R - 1) / R);
+  kern<<<min(n_tiles, slots), 192, S::SMEM, s>>>(map, W, H, tiles_x, n_tiles, Wt, b, out, mask,
+                                                 nout, err);
   return cudaGetLastError();
 }
 
