@@ -5,9 +5,10 @@
 //
 // Convolutions are implicit GEMMs on the 5th-generation tensor cores:
 // D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = (ky * 3 + kx) * C_in + c_in.
-// A CTA computes R image rows of 128 consecutive pixels.  It never builds
-// the im2col matrix: TMA loads the halo tile (R + 2 rows of 130 pixels,
-// zero outside the image) once, one box per group of 8 input channels,
+// Activations are stored channel-group planar, [C/8][H][W][8] bf16 (16
+// bytes per pixel and group).  A tile is R image rows of 128 consecutive
+// pixels.  No im2col matrix is built: one TMA box loads the tile's halo (R
+// + 2 rows of 130 pixels of every channel group, zero outside the image)
 // into [group][row][x][8 channels]; with 16 bytes per pixel and a stride of
 // 128 B between 8-pixel core matrices this is the canonical K-major layout
 // without swizzle, so tap (ky, kx) of output row r is the same tile with
@@ -140,14 +141,16 @@ __device__ __forceinline__ void vd_bulk_load(uint32_t dst, const void* src, uint
       : "memory");
 }
 
-// Tiled TMA load of one box of a rank-3 tensor map at (c0, c1, c2); c0 (the
-// innermost coordinate) must be a multiple of 16 bytes' worth of elements.
-__device__ __forceinline__ void vd_tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0,
-                                               int c1, int c2, uint64_t* m) {
+// Tiled TMA load of one box of a rank-4 tensor map at (c0, c1, c2, c3); c0
+// (the innermost coordinate) must be a multiple of 16 bytes' worth of
+// elements.
+__device__ __forceinline__ void vd_tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0,
+                                               int c1, int c2, int c3, uint64_t* m) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(vd_smem_u32(m))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(vd_smem_u32(m))
       : "memory");
 }
 
@@ -194,13 +197,13 @@ __device__ __forceinline__ void vd_tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ---------------------------------------------------------------------------
-// The convolution GEMM.  X (through the tensor map `xmap`): NHWC bf16 with
-// C_in = K / 9 channels (a multiple of 16), dims {C_in, W, H}, box
-// {8, 130, R + 2}.  Wt: the N x K weights pre-tiled (vd_tile_index).
-// Epilogues:
-//   EPI_RELU  out = bf16 NHWC [HW][N]: relu(D + bias)
+// The convolution GEMM.  X (through the tensor map `xmap`): bf16 planar
+// [C_in/8][H][W][8] with C_in = K / 9 channels (a multiple of 16), dims
+// {8, W, H, C_in/8}, box {8, 130, R + 2, C_in/8}.  Wt: the N x K weights
+// pre-tiled (vd_tile_index).  Epilogues:
+//   EPI_RELU  out = bf16 planar [N/8][HW][8]: relu(D + bias)
 //   EPI_LAST  out = f32 [HW][16]: D + bias for the nout real channels, 0 after
-//   EPI_DGRAD out = bf16 NHWC [HW][N]: D where mask[p][c] > 0, else 0
+//   EPI_DGRAD out = bf16 planar [N/8][HW][8]: D where mask (planar) > 0, else 0
 // ---------------------------------------------------------------------------
 enum { EPI_RELU = 0, EPI_LAST = 1, EPI_DGRAD = 2 };
 
@@ -216,9 +219,8 @@ template <int K, int N, int R, int NS>
 struct VdConvShape {
   static constexpr int CIN = K / 9, G = CIN / 8;
   static constexpr uint32_t B_BYTES = (uint32_t)N * K * 2;
-  static constexpr uint32_t BOX_BYTES = (uint32_t)(R + 2) * CNN_HALO_X * 16;
-  static constexpr uint32_t GS = vd_round128(BOX_BYTES);   // stride between channel groups
-  static constexpr uint32_t STAGE = G * GS;                 // one halo tile
+  static constexpr uint32_t GS = (uint32_t)(R + 2) * CNN_HALO_X * 16;   // one channel group
+  static constexpr uint32_t STAGE = vd_round128(G * GS);   // one halo tile (one TMA box)
   static constexpr uint32_t A_OFF = vd_round128(B_BYTES);
   static constexpr uint32_t ACC = (uint32_t)R * N;          // columns of one accumulator
   // tensor-memory columns: two accumulators, as a power of two >= 32
@@ -300,11 +302,10 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
         }
         const int tile = blockIdx.x + i * gridDim.x;
         const int x0 = (tile % tiles_x) * CNN_TILE, y0 = (tile / tiles_x) * R;
-        vd_mbar_expect_tx(&full[s], S::G * S::BOX_BYTES + (i == 0 ? S::B_BYTES : 0u));
+        vd_mbar_expect_tx(&full[s], S::G * S::GS + (i == 0 ? S::B_BYTES : 0u));
         if (i == 0) vd_bulk_load(sB, Wt, S::B_BYTES, &full[0]);
-#pragma unroll
-        for (int g = 0; g < S::G; ++g)   // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128
-          vd_tma_load_3d(sA + s * S::STAGE + g * S::GS, &xmap, 8 * g, x0 - 1, y0 - 1, &full[s]);
+        // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128, every group
+        vd_tma_load_4d(sA + s * S::STAGE, &xmap, 0, x0 - 1, y0 - 1, 0, &full[s]);
         issued = i + 1;
       }
       // the loads in flight land before the CTA ends
@@ -362,6 +363,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
       vd_tc_fence_after();
       const int tile = blockIdx.x + i * gridDim.x;
       const int x = (tile % tiles_x) * CNN_TILE + warp * 32 + lane, y0 = (tile / tiles_x) * R;
+      const size_t HW = (size_t)Wimg * Himg;
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
         const int y = y0 + r;
@@ -392,15 +394,16 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
 #pragma unroll
             for (int c = 0; c < N; c += 8)
               *reinterpret_cast<uint4*>(mk + c) =
-                  *reinterpret_cast<const uint4*>(mask + p * N + c);
+                  *reinterpret_cast<const uint4*>(mask + ((c >> 3) * HW + p) * 8);
 #pragma unroll
             for (int c = 0; c < N; ++c)
               o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
           }
-          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out) + p * N;
+          __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out);
 #pragma unroll
-          for (int c = 0; c < N; c += 8)
-            *reinterpret_cast<uint4*>(dst + c) = *reinterpret_cast<const uint4*>(o + c);
+          for (int c = 0; c < N; c += 8)   // group c / 8 of pixel p
+            *reinterpret_cast<uint4*>(dst + ((c >> 3) * HW + p) * 8) =
+                *reinterpret_cast<const uint4*>(o + c);
         }
       }
       vd_tc_fence_before();
@@ -414,7 +417,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
 }
 
 // ---------------------------------------------------------------------------
-// Input planes: flow [N][H][W][2] -> bf16 NHWC with C0 channels.
+// Input planes: flow [N][H][W][2] -> bf16 planar [C0/8][H][W][8].
 // ---------------------------------------------------------------------------
 // Geometry planes 2N .. 2N+3 (zero without a pose): the flow that the
 // rotation of T_1 alone gives pixel (u, v), and the extra flow of a point at
@@ -444,21 +447,27 @@ __global__ void k_cnn_input(const float2* __restrict__ flow, int N, int Wimg, in
       geo[3] = (y1 - y0) * (1.0f / 32.0f);
     }
   }
-  for (int c = 0; c < C0; ++c) {
-    float v = 0.0f;
-    if (c < 2 * N) {
-      const float2 f = flow[(size_t)(c >> 1) * HW + p];
-      v = ((c & 1) ? f.y : f.x) * (1.0f / 32.0f);
-    } else if (c < 2 * N + 4) {
-      v = geo[c - 2 * N];
+  for (int g = 0; g < C0 / 8; ++g) {   // planar: group g of pixel p, 16 bytes
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = 8 * g + k;
+      float v = 0.0f;
+      if (c < 2 * N) {
+        const float2 f = flow[(size_t)(c >> 1) * HW + p];
+        v = ((c & 1) ? f.y : f.x) * (1.0f / 32.0f);
+      } else if (c < 2 * N + 4) {
+        v = geo[c - 2 * N];
+      }
+      o[k] = __float2bfloat16_rn(v);
     }
-    a0[(size_t)p * C0 + c] = __float2bfloat16_rn(v);
+    *reinterpret_cast<uint4*>(a0 + ((size_t)g * HW + p) * 8) = *reinterpret_cast<uint4*>(o);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Heads, loss and dL/dz of the last layer (z: f32 [HW][16], channel 0 the
-// inverse depth, 1..N the rigidness of each flow; dz: bf16 [HW][16]).
+// inverse depth, 1..N the rigidness of each flow; dz: bf16 planar [2][HW][8]).
 // Per-block partial sums of the loss.
 // ---------------------------------------------------------------------------
 __global__ void k_cnn_heads(const float* __restrict__ z, int HW, int N, float rho_min,
@@ -498,8 +507,8 @@ __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
       o[1 + t] = __float2bfloat16_rn(wq_n * m * (s - qt) * inv_n);
     }
     l = (double)(m * (r * r + wq_n * bce));
-    *reinterpret_cast<uint4*>(dz + (size_t)p * 16) = *reinterpret_cast<uint4*>(o);
-    *reinterpret_cast<uint4*>(dz + (size_t)p * 16 + 8) = *reinterpret_cast<uint4*>(o + 8);
+    *reinterpret_cast<uint4*>(dz + (size_t)p * 8) = *reinterpret_cast<uint4*>(o);   // planar
+    *reinterpret_cast<uint4*>(dz + ((size_t)HW + p) * 8) = *reinterpret_cast<uint4*>(o + 8);
   }
   s_l[threadIdx.x] = l;
   __syncthreads();
@@ -543,7 +552,7 @@ __global__ void k_cnn_sum(const double* __restrict__ partial, int n, const int* 
 // ---------------------------------------------------------------------------
 // Weight gradient on the CUDA cores: dW[co][tap * CIN + ci] =
 // sum_p dz[p][co] X[p + offset(tap)][ci], db[co] = sum_p dz[p][co].  dz: bf16
-// [HW][DZC], COUT of its channels used; X: bf16 NHWC with CIN channels.
+// planar with (at least) COUT channels; X: bf16 planar with CIN channels.
 // The image is cut into tiles of WG_ROWS rows x WG_COLS pixels; block b
 // takes tiles b, b + gridDim.x, ... in order.  A block stages a tile's
 // input halo and dz in shared memory; thread (co8, ci) holds dW for 8
@@ -559,7 +568,7 @@ __global__ void k_cnn_sum(const double* __restrict__ partial, int n, const int* 
 #define WG_ROWS 4
 #define WG_COLS 64
 
-template <int CIN, int COUT, int DZC>
+template <int CIN, int COUT>
 __global__ void __launch_bounds__(COUT / 8 * CIN)
 k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ dz, int Wimg,
             int Himg, float* __restrict__ partial, float* __restrict__ partial_b) {
@@ -570,6 +579,7 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   const int tid = threadIdx.x, ci = tid % CIN, co8 = tid / CIN;
   const int tiles_x = (Wimg + WG_COLS - 1) / WG_COLS;
   const int n_tiles = tiles_x * ((Himg + WG_ROWS - 1) / WG_ROWS);
+  const size_t HW = (size_t)Wimg * Himg;
   float acc[8][9];
 #pragma unroll
   for (int c = 0; c < 8; ++c)
@@ -579,20 +589,20 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int y0 = tile / tiles_x * WG_ROWS, x0 = tile % tiles_x * WG_COLS;
     __syncthreads();   // the previous tile's values are no longer read
-    for (int i = tid; i < HR * HC * (CIN / 8); i += NT) {
-      const int g = i % (CIN / 8), px = i / (CIN / 8);
+    for (int i = tid; i < HR * HC * (CIN / 8); i += NT) {   // pixels fastest: coalesced
+      const int g = i / (HR * HC), px = i - g * (HR * HC);
       const int yy = y0 - 1 + px / HC, xx = x0 - 1 + px % HC;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * Wimg + xx) * CIN + 8 * g);
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)g * HW + (size_t)yy * Wimg + xx) * 8);
       *reinterpret_cast<uint4*>(sX + (size_t)px * CIN + 8 * g) = v;
     }
     for (int i = tid; i < WG_ROWS * WG_COLS * (COUT / 8); i += NT) {
-      const int g = i % (COUT / 8), px = i / (COUT / 8);
+      const int g = i / (WG_ROWS * WG_COLS), px = i - g * (WG_ROWS * WG_COLS);
       const int yy = y0 + px / WG_COLS, xx = x0 + px % WG_COLS;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (yy < Himg && xx < Wimg)
-        v = *reinterpret_cast<const uint4*>(dz + ((size_t)yy * Wimg + xx) * DZC + 8 * g);
+        v = *reinterpret_cast<const uint4*>(dz + ((size_t)g * HW + (size_t)yy * Wimg + xx) * 8);
       *reinterpret_cast<uint4*>(sD + (size_t)px * COUT + 8 * g) = v;
     }
     __syncthreads();
@@ -789,17 +799,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 vd_encode_tiled() {
   return fn;
 }
 
-// Tensor map of an NHWC bf16 image with cin channels: dims {cin, W, H},
-// box {8, 130, rows + 2}, zero fill outside the image.
+// Tensor map of a planar bf16 image with cin channels ([cin/8][H][W][8]):
+// dims {8, W, H, cin/8}, box {8, 130, rows + 2, cin/8}, zero fill outside
+// the image.
 static cudaError_t vd_halo_map(CUtensorMap* m, const void* X, int cin, int W, int H, int rows) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = vd_encode_tiled();
   if (!enc) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(X) & 15u) || cin % 16) return cudaErrorInvalidValue;
-  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H};
-  const cuuint64_t strides[2] = {(cuuint64_t)cin * 2, (cuuint64_t)W * cin * 2};
-  const cuuint32_t box[3] = {8, CNN_HALO_X, (cuuint32_t)rows + 2};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X), dims,
+  const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(cin / 8)};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
+  const cuuint32_t box[4] = {8, CNN_HALO_X, (cuuint32_t)rows + 2, (cuuint32_t)(cin / 8)};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(X), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -876,10 +887,10 @@ static cudaError_t cnn_forward(vd_cnn* n, const float* flow, int W, int H, cudaS
 // Gradients of the loss with respect to every parameter, after cnn_forward
 // on the same image; dz of the last layer comes from k_cnn_loss (in g0 with
 // 16 channels).
-template <int CIN, int COUT, int DZC>
+template <int CIN, int COUT>
 static cudaError_t launch_wgrad(vd_cnn* n, int l, const __nv_bfloat16* dz, int W, int H,
                                 cudaStream_t s) {
-  k_cnn_wgrad<CIN, COUT, DZC><<<WG_BLOCKS, COUT / 8 * CIN, 0, s>>>(n->act[l], dz, W, H,
+  k_cnn_wgrad<CIN, COUT><<<WG_BLOCKS, COUT / 8 * CIN, 0, s>>>(n->act[l], dz, W, H,
                                                                    n->wg_partial,
                                                                    n->wg_partial_b);
   cudaError_t e = cudaGetLastError();
@@ -897,11 +908,11 @@ static cudaError_t cnn_backward(vd_cnn* n, int W, int H, cudaStream_t s) {
   __nv_bfloat16* nxt = n->g1;
   for (int l = CNN_L - 1; l >= 0 && e == cudaSuccess; --l) {
     if (l == CNN_L - 1)
-      e = launch_wgrad<32, 16, 16>(n, l, dz, W, H, s);   // 1 + N of 16 rows used
+      e = launch_wgrad<32, 16>(n, l, dz, W, H, s);   // 1 + N of 16 rows used
     else if (l == 0 && n->cin[0] == 16)
-      e = launch_wgrad<16, 32, 32>(n, l, dz, W, H, s);   // 16 input planes (2N + 4 <= 16)
+      e = launch_wgrad<16, 32>(n, l, dz, W, H, s);   // 16 input planes (2N + 4 <= 16)
     else
-      e = launch_wgrad<32, 32, 32>(n, l, dz, W, H, s);
+      e = launch_wgrad<32, 32>(n, l, dz, W, H, s);
     if (e != cudaSuccess || l == 0) break;
     // dL/dz_{l-1} = (W_l^T * dL/dz_l) where a_l > 0
     if (l == CNN_L - 1)
@@ -1074,10 +1085,12 @@ extern "C" vd_status vd_cnn_get_activation(vd_cnn* n, int layer, float* out, int
     return VD_OK;
   }
   const int C = n->cin[layer];
-  std::vector<__nv_bfloat16> h(HW * C);
+  std::vector<__nv_bfloat16> h(HW * C);   // planar [C/8][HW][8] on the device
   VD_CU(cudaMemcpy(h.data(), n->act[layer], sizeof(__nv_bfloat16) * h.size(),
                    cudaMemcpyDeviceToHost));
-  for (size_t i = 0; i < h.size(); ++i) out[i] = __bfloat162float(h[i]);
+  for (size_t p = 0; p < HW; ++p)
+    for (int c = 0; c < C; ++c)
+      out[p * C + c] = __bfloat162float(h[((c >> 3) * HW + p) * 8 + (c & 7)]);
   return VD_OK;
 }
 
