@@ -278,9 +278,23 @@ def run_ours(args, rank, world, local, pg):
                 "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)",
                 "measured_in": "single-window run, kernel timed alone (CUDA events)"}
     stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
+    # the stride / keyframe score of the window just estimated (VC, Eq. 8):
+    # the call's time including its counter read-back, median of 20
+    vc_res = V.vd_vc_scores(ctx)
+    vc_ms = []
+    for _ in range(20):
+        t0 = time.perf_counter()
+        V.vd_vc_scores(ctx)
+        vc_ms.append(1e3 * (time.perf_counter() - t0))
+    vc_line = {"ms_per_call": round(statistics.median(vc_ms), 4),
+               "visibility": [round(x, 4) for x in vc_res["visibility"]],
+               "coverage": [round(x, 4) for x in vc_res["coverage"]],
+               "vc": [round(x, 4) for x in vc_res["vc"]],
+               "stride_at_tau_0.7": V.vd_vc_stride(vc_res["vc"], 0.7)}
     single = {"windows_per_s": round(1e3 / single_ms, 3), "ms_per_window": round(single_ms, 3),
               "value": round(units_per_window / (single_ms / 1e3), 1),
               "gpu_launches_per_window": int(prof["total_launches"] / args.steps),
+              "vc_scores": vc_line,
               "stage_ms_per_window": stages, "tune": tune}
     V.vd_destroy(ctx)
     if args.phase == "single":

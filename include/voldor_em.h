@@ -353,6 +353,44 @@ vd_status vd_eight_point(vd_ctx* ctx, double* T1_out /*host, 12*/);
  * have the context's N. */
 vd_status vd_bootstrap_learned(vd_ctx* ctx, vd_cnn* net);
 
+/* ---- Visibility-coverage score, VO stride and keyframe test ------------
+ * Sec. III-B "VO Stride and Keyframe Selection", Eq. 8.  The reference
+ * frame's depth pixels (finite rho > 0 of the context's current inverse
+ * depth) are projected into a frame of known pose T = [R | tau] (reference
+ * -> frame, 3x4 row-major): with r = ((u - cx)/fx, (v - cy)/fy, 1) and
+ * h = R r + rho tau, the point is in front when h_z > 1e-6 and lands at
+ * x = fx h_x/h_z + cx, y = fy h_y/h_z + cy; it is visible when in front and
+ * 0 <= x <= W-1, 0 <= y <= H-1, and covers the pixel cell
+ * (floor(x + 1/2), floor(y + 1/2)).  The projections are taken in float32,
+ * one rounding per operation in the order written (R, tau and the
+ * intrinsics rounded to float32 once), so the counts are exact integers.
+ * visibility = n_visible / n_depth (0 without depth pixels), coverage =
+ * n_covered / n_pixels, vc = 2 V C / (V + C) (0 when either is 0). */
+#define VD_VC_MAX_FRAMES 8
+typedef struct {
+  int n_frames;                              /* entries filled                 */
+  long long n_pixels;                        /* W * H                          */
+  long long n_depth;                         /* depth pixels                   */
+  long long n_visible[VD_VC_MAX_FRAMES];     /* depth pixels inside frame k    */
+  long long n_covered[VD_VC_MAX_FRAMES];     /* pixel cells of frame k covered */
+  double visibility[VD_VC_MAX_FRAMES];
+  double coverage[VD_VC_MAX_FRAMES];
+  double vc[VD_VC_MAX_FRAMES];
+} vd_vc;
+/* The reference depth in every frame t = 1..N of the window (entry t-1, the
+ * context's current poses).  Synchronises the context stream. */
+vd_status vd_vc_scores(vd_ctx* ctx, vd_vc* out);
+/* The reference depth in one frame of pose T (host, 12 doubles, reference ->
+ * frame): the keyframe test, with T the latest keyframe's pose relative to
+ * the reference frame.  Entry 0.  Synchronises the context stream. */
+vd_status vd_vc_pose(vd_ctx* ctx, const double* T, vd_vc* out);
+/* Host rules.  The next batch's reference: the first t (1-based) with
+ * vc[t-1] < tau_stride, n when there is none (0 for n < 1 or no vc).  The
+ * reference frame becomes a keyframe when its VC with the latest keyframe
+ * is below tau_keyframe (1) or not (0). */
+int vd_vc_stride(const double* vc, int n, double tau_stride);
+int vd_vc_is_keyframe(double vc, double tau_keyframe);
+
 /* State export/import for checkpoint and resume: a self-describing blob with
  * rho, q, q_hat, C, the poses, the iteration counter and the bootstrap flag.
  * Call export with blob = NULL to learn the size. */

@@ -222,7 +222,8 @@ extern "C" vd_status vd_destroy(vd_ctx* c) {
                   c->coarse, c->lam, c->flags, c->blk_counts, c->blk_offsets, c->n_rigid,
                   c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->partial,
                   c->root_energy, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
-                  c->ep_M, c->ep_E, c->ep_cand, c->ep_count, c->stat_partial, c->stat_out};
+                  c->ep_M, c->ep_E, c->ep_cand, c->ep_count, c->stat_partial, c->stat_out,
+                  c->vc_cover, c->vc_counts, c->vc_pose};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   prof_free(c);
@@ -314,6 +315,10 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(ep_count, 4);
   A(stat_partial, 2 * c->stat_blocks);
   A(stat_out, 2);
+  c->vc_stride = (np + 15) / 16 * 16;
+  A(vc_cover, (N + 1) * c->vc_stride);
+  A(vc_counts, 1 + 2 * (N + 1));
+  A(vc_pose, 12);
 #undef A
   (void)s;
   if (e != cudaSuccess) {

@@ -116,10 +116,6 @@ __device__ __forceinline__ bool vd_mbar_wait_bounded(uint64_t* m, uint32_t phase
   return false;
 }
 
-__device__ __forceinline__ void vd_fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 __device__ __forceinline__ void vd_mbar_expect_tx(uint64_t* m, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vd_smem_u32(m)),
                "r"(bytes)

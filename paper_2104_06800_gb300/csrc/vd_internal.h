@@ -129,6 +129,12 @@ struct vd_ctx {
   long long launches[VD_N_STAGES];
 
   // reductions for stats
+  // visibility-coverage scratch: N + 1 coverage maps of one byte per pixel
+  // cell (frames 1..N and a caller's pose), their counters, the caller's pose
+  unsigned char* vc_cover;        // [N + 1][vc_stride]
+  unsigned long long* vc_counts;  // [1 + 2 (N + 1)]
+  double* vc_pose;                // [12]
+  size_t vc_stride;               // npix rounded up to 16
   double* stat_partial;    // [blocks][2]
   double* stat_out;        // [2]
   int stat_blocks;

@@ -74,6 +74,16 @@ class vd_batch_stats(C.Structure):
 
 VD_BATCH_BOOTSTRAP = 1
 VD_BATCH_AUTOTUNE = 2
+VD_VC_MAX_FRAMES = 8
+
+
+class vd_vc(C.Structure):
+    _fields_ = [("n_frames", C.c_int), ("n_pixels", C.c_longlong), ("n_depth", C.c_longlong),
+                ("n_visible", C.c_longlong * VD_VC_MAX_FRAMES),
+                ("n_covered", C.c_longlong * VD_VC_MAX_FRAMES),
+                ("visibility", C.c_double * VD_VC_MAX_FRAMES),
+                ("coverage", C.c_double * VD_VC_MAX_FRAMES),
+                ("vc", C.c_double * VD_VC_MAX_FRAMES)]
 
 
 class VoldorError(RuntimeError):
@@ -136,6 +146,10 @@ _SIGS = {
                           C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                           C.POINTER(C.c_double), _P],
     "vd_eight_point": [_P, _P],
+    "vd_vc_scores": [_P, C.POINTER(vd_vc)],
+    "vd_vc_pose": [_P, _P, C.POINTER(vd_vc)],
+    "vd_vc_stride": [_P, C.c_int, C.c_double],
+    "vd_vc_is_keyframe": [C.c_double, C.c_double],
     "vd_bootstrap_learned": [_P, _P],
     "vd_export_state": [_P, _P, C.POINTER(C.c_size_t)],
     "vd_import_state": [_P, _P, C.c_size_t],
@@ -461,6 +475,39 @@ def vd_batch_get_stats(batch):
     _call("vd_batch_get_stats", batch, C.byref(st))
     return dict(windows=st.windows, captures=st.captures, replays=st.replays,
                 graph_nodes=st.graph_nodes, kernels_per_run=st.kernels_per_run)
+
+
+# ------------------------------------------------------------------ VC score
+def _vc_dict(s):
+    n = s.n_frames
+    return dict(n_frames=n, n_pixels=s.n_pixels, n_depth=s.n_depth,
+                n_visible=list(s.n_visible[:n]), n_covered=list(s.n_covered[:n]),
+                visibility=list(s.visibility[:n]), coverage=list(s.coverage[:n]),
+                vc=list(s.vc[:n]))
+
+
+def vd_vc_scores(ctx):
+    """Visibility, coverage and VC of the reference depth in frames 1..N."""
+    s = vd_vc()
+    _call("vd_vc_scores", ctx, C.byref(s))
+    return _vc_dict(s)
+
+
+def vd_vc_pose(ctx, T):
+    """The same in one frame of pose T (3x4, reference -> frame)."""
+    t = np.ascontiguousarray(np.asarray(T, np.float64).reshape(12))
+    s = vd_vc()
+    _call("vd_vc_pose", ctx, t.ctypes.data_as(C.c_void_p), C.byref(s))
+    return _vc_dict(s)
+
+
+def vd_vc_stride(vc, tau_stride):
+    a = np.ascontiguousarray(vc, np.float64)
+    return int(load().vd_vc_stride(a.ctypes.data_as(C.c_void_p), int(a.size), float(tau_stride)))
+
+
+def vd_vc_is_keyframe(vc, tau_keyframe):
+    return bool(load().vd_vc_is_keyframe(float(vc), float(tau_keyframe)))
 
 
 # ------------------------------------------------------------------ learned initialiser

@@ -4,6 +4,7 @@ No compute calls here (no GPU on this host)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -82,6 +83,27 @@ def test_tune_and_batch_structs_match_the_header():
     assert [f for f, _ in V.vd_tune._fields_] == _struct_fields(src, "} vd_tune;")
     assert [f for f, _ in V.vd_batch_stats._fields_] == _struct_fields(src, "} vd_batch_stats;")
     assert V.VD_BATCH_BOOTSTRAP == 1 and V.VD_BATCH_AUTOTUNE == 2
+
+
+def test_vc_struct_and_host_rules(lib):
+    """The VC result structure mirrors the header; the stride and keyframe
+    rules run on the host and agree with the oracle's."""
+    from paper_2104_06800_gb300 import voldor as V
+    from oracle import vc as ovc
+    src = open(os.path.join(ROOT, "include", "voldor_em.h")).read()
+    assert [f for f, _ in V.vd_vc._fields_] == _struct_fields(src, "} vd_vc;")
+    assert "#define VD_VC_MAX_FRAMES 8" in src and V.VD_VC_MAX_FRAMES == 8
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        n = int(rng.integers(1, 9))
+        vc = rng.uniform(0.3, 1.0, n)
+        tau = float(rng.uniform(0.3, 1.0))
+        assert V.vd_vc_stride(vc, tau) == ovc.stride(list(vc), tau)
+        assert V.vd_vc_is_keyframe(vc[0], tau) == ovc.is_keyframe(vc[0], tau)
+    assert lib.vd_vc_stride(None, 3, 0.5) == 0
+    s = V.vd_vc()
+    assert lib.vd_vc_scores(None, V.C.byref(s)) == V.VD_ERR_ARG
+    assert lib.vd_vc_pose(None, None, V.C.byref(s)) == V.VD_ERR_ARG
 
 
 def test_batch_and_tune_argument_checks(lib):
