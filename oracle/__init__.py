@@ -29,6 +29,9 @@ Modules and the passage each follows (Min & Dunn, "VOLDOR+SLAM", 2021):
   cnn      -- the learned initialiser (no counterpart in the paper): a small
               3x3 convolutional network from the flows to an initial inverse
               depth and rigidness, its backward pass, loss and Adam step.
+  posecov  -- the pose covariance from the P3P samples: iterative Gaussian
+              fit with 3-sigma rejection and an eigenvalue floor (Sec. III-A
+              "Uncertainty-aware Pose Estimation").
   vc       -- visibility, coverage and their harmonic mean (Eq. 8), the VO
               stride and keyframe test (Sec. III-B "VO Stride and Keyframe
               Selection").
