@@ -11,9 +11,13 @@ Readings fixed here (the paper names the steps, not these details):
   * the Gaussian lives in the tangent space at its mean mu: a sample's
     coordinates are d = log(mu^-1 T) in se(3) (rotation vector, then the
     translation part, the convention of geometry.se3_log).
-  * start: mu = the mean-shift mode; Sigma = the mean-shift kernel's
-    covariance there, diag(s_rot^2 x3, s_t^2 x3) with
-    s_t = s_rel |tau_mode| + s_abs.
+  * start: mu = the mean-shift mode; Sigma = a robust diagonal fit of all
+    the samples there, diag(s_i^2) with s_i = 1.4826 median_g |d_gi| (the
+    median absolute deviation from the mode, which equals sigma_i for a
+    Gaussian and ignores up to half of the samples as outliers).  The
+    mean-shift kernel's covariance is not a usable start: the P3P samples of
+    early iterations spread far wider than the kernel, and a 3-sigma window
+    of the kernel then holds only the mode's own sample.
   * one round: d for every sample; inliers: d^T Sigma^-1 d <= 9 (3 sigma);
     if the inlier set equals the previous round's, stop (converged); with
     fewer than 7 inliers (a 6-D covariance needs 7), stop and report the
@@ -36,9 +40,11 @@ MEAN_TOL = 1e-12
 MIN_INLIERS = 7
 
 
-def kernel_covariance(mode, sigma_rot, sigma_rel, sigma_abs):
-    st = sigma_rel * float(np.linalg.norm(mode[:, 3])) + sigma_abs
-    return np.diag([sigma_rot ** 2] * 3 + [st ** 2] * 3)
+def robust_start(samples, mode):
+    """diag((1.4826 median_g |d_gi|)^2), d_g = log(mode^-1 T_g)."""
+    d = _coords(np.asarray(mode, np.float64), samples)
+    s = 1.4826 * np.median(np.abs(d), axis=0)
+    return np.diag(s * s)
 
 
 def floor_eigenvalues(S, eps):
@@ -48,17 +54,22 @@ def floor_eigenvalues(S, eps):
 
 
 def _coords(mu, samples):
+    if not len(samples):
+        return np.zeros((0, 6))
     mi = geometry.inverse(mu)
     return np.array([geometry.se3_log(geometry.compose(mi, T)) for T in samples])
 
 
-def fit(samples, mode, sigma0, eps, max_rounds=MAX_ROUNDS):
-    """(mu, Sigma, n_inliers, rounds, degenerate) for the list of sample poses."""
+def fit(samples, mode, eps, sigma0=None, max_rounds=MAX_ROUNDS):
+    """(mu, Sigma, n_inliers, rounds, degenerate) for the list of sample
+    poses; sigma0 replaces the robust start when given."""
     mu = np.array(mode, np.float64)
-    S = floor_eigenvalues(np.array(sigma0, np.float64), eps)
     samples = [np.asarray(T, np.float64) for T in samples]
     if len(samples) < MIN_INLIERS:
-        return mu, S, len(samples), 0, True
+        S0 = np.zeros((6, 6)) if sigma0 is None else np.array(sigma0, np.float64)
+        return mu, floor_eigenvalues(S0, eps), len(samples), 0, True
+    S0 = robust_start(samples, mu) if sigma0 is None else np.array(sigma0, np.float64)
+    S = floor_eigenvalues(S0, eps)
     prev = None
     n_in = 0
     for r in range(1, max_rounds + 1):
