@@ -291,10 +291,22 @@ def run_ours(args, rank, world, local, pg):
                "coverage": [round(x, 4) for x in vc_res["coverage"]],
                "vc": [round(x, 4) for x in vc_res["vc"]],
                "stride_at_tau_0.7": V.vd_vc_stride(vc_res["vc"], 0.7)}
+    # the pose covariance of every frame (Sec. III-A): median call time of 10
+    pc = V.vd_pose_covariance(ctx, N, 1e-12)
+    pc_ms = []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        V.vd_pose_covariance(ctx, N, 1e-12)
+        pc_ms.append(1e3 * (time.perf_counter() - t0))
+    pc_line = {"ms_per_call": round(statistics.median(pc_ms), 4),
+               "n_inliers": [r["n_inliers"] for r in pc],
+               "rounds": [r["rounds"] for r in pc],
+               "sd_rot_rad": [round(float(np.sqrt(np.diag(r["cov"])[:3].mean())), 6) for r in pc],
+               "degenerate": [r["degenerate"] for r in pc]}
     single = {"windows_per_s": round(1e3 / single_ms, 3), "ms_per_window": round(single_ms, 3),
               "value": round(units_per_window / (single_ms / 1e3), 1),
               "gpu_launches_per_window": int(prof["total_launches"] / args.steps),
-              "vc_scores": vc_line,
+              "vc_scores": vc_line, "pose_covariance": pc_line,
               "stage_ms_per_window": stages, "tune": tune}
     V.vd_destroy(ctx)
     if args.phase == "single":

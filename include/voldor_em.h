@@ -169,7 +169,7 @@ vd_status vd_get_depth_candidates(vd_ctx* ctx, float* rho_star, float* e_star, v
  * current state (Eq. 5 criterion; H*W in, H*W out). */
 vd_status vd_eval_energy(vd_ctx* ctx, const float* rho, float* energy_out, vd_mem mem);
 
-/* Per-sample results of the last single-frame pose M-step: the kept root of
+/* Per-sample results of the last pose M-step of a frame: the kept root of
  * every sample (S x 12, absolute), its energy (S; +inf for a void sample) and
  * the rigid-set size.  Host memory. */
 vd_status vd_get_pose_samples(vd_ctx* ctx, double* poses, double* energies, int* n_rigid);
@@ -352,6 +352,32 @@ vd_status vd_eight_point(vd_ctx* ctx, double* T1_out /*host, 12*/);
  * rigidness is not used here (vd_cnn_forward gives it).  The network must
  * have the context's N. */
 vd_status vd_bootstrap_learned(vd_ctx* ctx, vd_cnn* net);
+
+/* ---- Pose covariance ----------------------------------------------------
+ * Sec. III-A "Uncertainty-aware Pose Estimation": the uncertainty of each
+ * camera pose from the samples of the last pose M-step (the kept root of
+ * every sample with one).  Starting from the mean-shift mode and the robust
+ * diagonal covariance diag((1.4826 median_g |d_gi|)^2) of the samples there,
+ * rounds of: the samples within 3 sigma (d^T Sigma^-1 d <= 9 with
+ * d = log(mean^-1 T) in se(3), rotation vector first), their Frechet mean,
+ * and the maximum-likelihood covariance of their d at that mean with every
+ * eigenvalue raised to eps; until the inlier set repeats (at most 50
+ * rounds).  Fewer than 7 samples or inliers leave the frame degenerate with
+ * its last fit (the mode and eps I without samples).  float64. */
+typedef struct {
+  double mean[12];   /* fitted mean pose (absolute, reference -> frame), 3x4 row-major */
+  double cov[36];    /* 6x6 row-major, tangent space at the mean                         */
+  int n_samples;     /* samples with a root                                             */
+  int n_inliers;     /* inliers of the last round                                       */
+  int rounds;
+  int degenerate;
+} vd_pose_cov;
+/* out: N entries, frame t at out[t-1].  Needs a pose M-step of every frame
+ * (VD_ERR_STATE otherwise).  Synchronises the context stream. */
+vd_status vd_pose_covariance(vd_ctx* ctx, double eps, vd_pose_cov* out);
+/* The samples of frame t's last pose M-step (S x 12 absolute poses, S
+ * energies, +inf for a sample without a root).  Host memory. */
+vd_status vd_get_frame_samples(vd_ctx* ctx, int t, double* poses, double* energies);
 
 /* ---- Visibility-coverage score, VO stride and keyframe test ------------
  * Sec. III-B "VO Stride and Keyframe Selection", Eq. 8.  The reference

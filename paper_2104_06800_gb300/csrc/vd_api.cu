@@ -223,7 +223,7 @@ extern "C" vd_status vd_destroy(vd_ctx* c) {
                   c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->partial,
                   c->root_energy, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
                   c->ep_M, c->ep_E, c->ep_cand, c->ep_count, c->stat_partial, c->stat_out,
-                  c->vc_cover, c->vc_counts, c->vc_pose};
+                  c->vc_cover, c->vc_counts, c->vc_pose, c->pc_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   prof_free(c);
@@ -305,8 +305,9 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(rootsf, (size_t)4 * S * 12);
   A(partial, (size_t)4 * S * c->nblk_score);
   A(root_energy, 4 * S);
-  A(sample_pose, 12 * S);
-  A(sample_energy, S);
+  A(sample_pose, 12 * S * N);
+  A(sample_energy, S * N);
+  A(pc_out, 52 * N);
   A(degenerate, 1);
   A(ep_partial, (size_t)45 * c->ep_blocks);
   A(ep_M, 45);
@@ -1153,12 +1154,13 @@ extern "C" vd_status vd_eval_energy(vd_ctx* c, const float* rho, float* out, vd_
 extern "C" vd_status vd_get_pose_samples(vd_ctx* c, double* poses, double* energies, int* n_rigid) {
   if (!c) return VD_ERR_ARG;
   const int S = c->prm.n_pose_samples;
+  const size_t f = c->last_pose_t > 0 ? (size_t)(c->last_pose_t - 1) * VD_MAX_SAMPLES : 0;
   if (poses)
-    VD_CU(cudaMemcpyAsync(poses, c->sample_pose, sizeof(double) * 12 * S, cudaMemcpyDeviceToHost,
-                          c->stream));
+    VD_CU(cudaMemcpyAsync(poses, c->sample_pose + 12 * f, sizeof(double) * 12 * S,
+                          cudaMemcpyDeviceToHost, c->stream));
   if (energies)
-    VD_CU(cudaMemcpyAsync(energies, c->sample_energy, sizeof(double) * S, cudaMemcpyDeviceToHost,
-                          c->stream));
+    VD_CU(cudaMemcpyAsync(energies, c->sample_energy + f, sizeof(double) * S,
+                          cudaMemcpyDeviceToHost, c->stream));
   if (n_rigid)
     VD_CU(cudaMemcpyAsync(n_rigid, c->n_rigid, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   VD_CU(cudaStreamSynchronize(c->stream));

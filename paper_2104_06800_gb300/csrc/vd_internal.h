@@ -100,8 +100,11 @@ struct vd_ctx {
   float* rootsf;           // [S*4][12]
   float* partial;          // [S*4][score blocks]
   double* root_energy;     // [S*4]
-  double* sample_pose;     // [S][12]
-  double* sample_energy;   // [S]
+  double* sample_pose;     // [N][S][12] kept root of every sample, per frame
+  double* sample_energy;   // [N][S] (+inf: no root)
+  int last_pose_t;         // frame of the last pose M-step (0: none)
+  unsigned samples_set;    // bit t-1: frame t's samples are from a pose M-step
+  double* pc_out;          // [N][52] pose covariance results (mean, cov, info)
   int* degenerate;         // [1] counter of kept poses
   int nblk_scan;
   int nblk_score;

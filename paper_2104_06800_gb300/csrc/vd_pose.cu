@@ -736,6 +736,9 @@ cudaError_t launch_pose_score_only(vd_ctx* c) {
 
 cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   const DevParams& P = c->dp;
+  c->last_pose_t = t;
+  c->samples_set |= 1u << (t - 1);
+  const size_t f = (size_t)(t - 1) * VD_MAX_SAMPLES;   // this frame's sample slots
   vd_prof_begin(c, VD_ST_RIGID);
   k_rigid_flags<<<c->nblk_scan, SCAN_BLOCK, 0, c->stream>>>(P, c->G, c->posef, c->rho, c->q, t,
                                                             c->flags, c->blk_counts);
@@ -756,8 +759,8 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   vd_prof_end(c, VD_ST_SCORE, 2);
   vd_prof_begin(c, VD_ST_SELECT);
   k_select_meanshift<<<1, 32, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
-                                               c->posef, c->sample_pose, c->sample_energy,
-                                               c->degenerate);
+                                               c->posef, c->sample_pose + 12 * f,
+                                               c->sample_energy + f, c->degenerate);
   vd_prof_end(c, VD_ST_SELECT, 1);
   return cudaGetLastError();
 }

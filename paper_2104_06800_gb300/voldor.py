@@ -77,6 +77,11 @@ VD_BATCH_AUTOTUNE = 2
 VD_VC_MAX_FRAMES = 8
 
 
+class vd_pose_cov(C.Structure):
+    _fields_ = [("mean", C.c_double * 12), ("cov", C.c_double * 36), ("n_samples", C.c_int),
+                ("n_inliers", C.c_int), ("rounds", C.c_int), ("degenerate", C.c_int)]
+
+
 class vd_vc(C.Structure):
     _fields_ = [("n_frames", C.c_int), ("n_pixels", C.c_longlong), ("n_depth", C.c_longlong),
                 ("n_visible", C.c_longlong * VD_VC_MAX_FRAMES),
@@ -147,6 +152,8 @@ _SIGS = {
                           C.POINTER(C.c_double), _P],
     "vd_eight_point": [_P, _P],
     "vd_vc_scores": [_P, C.POINTER(vd_vc)],
+    "vd_pose_covariance": [_P, C.c_double, _P],
+    "vd_get_frame_samples": [_P, C.c_int, _P, _P],
     "vd_vc_pose": [_P, _P, C.POINTER(vd_vc)],
     "vd_vc_stride": [_P, C.c_int, C.c_double],
     "vd_vc_is_keyframe": [C.c_double, C.c_double],
@@ -475,6 +482,26 @@ def vd_batch_get_stats(batch):
     _call("vd_batch_get_stats", batch, C.byref(st))
     return dict(windows=st.windows, captures=st.captures, replays=st.replays,
                 graph_nodes=st.graph_nodes, kernels_per_run=st.kernels_per_run)
+
+
+# ------------------------------------------------------------------ pose covariance
+def vd_pose_covariance(ctx, N, eps=1e-12):
+    """Per frame t = 1..N: dict(mean 3x4, cov 6x6, n_samples, n_inliers,
+    rounds, degenerate)."""
+    arr = (vd_pose_cov * N)()
+    _call("vd_pose_covariance", ctx, float(eps), C.cast(arr, C.c_void_p))
+    return [dict(mean=np.array(r.mean[:]).reshape(3, 4), cov=np.array(r.cov[:]).reshape(6, 6),
+                 n_samples=r.n_samples, n_inliers=r.n_inliers, rounds=r.rounds,
+                 degenerate=bool(r.degenerate)) for r in arr]
+
+
+def vd_get_frame_samples(ctx, t, S):
+    """(poses S x 3 x 4, energies S) of frame t's last pose M-step."""
+    poses = np.zeros((S, 3, 4), np.float64)
+    energies = np.zeros(S, np.float64)
+    _call("vd_get_frame_samples", ctx, int(t), poses.ctypes.data_as(C.c_void_p),
+          energies.ctypes.data_as(C.c_void_p))
+    return poses, energies
 
 
 # ------------------------------------------------------------------ VC score

@@ -106,6 +106,15 @@ def test_vc_struct_and_host_rules(lib):
     assert lib.vd_vc_pose(None, None, V.C.byref(s)) == V.VD_ERR_ARG
 
 
+def test_pose_cov_struct_and_argument_checks(lib):
+    from paper_2104_06800_gb300 import voldor as V
+    src = open(os.path.join(ROOT, "include", "voldor_em.h")).read()
+    assert [f for f, _ in V.vd_pose_cov._fields_] == _struct_fields(src, "} vd_pose_cov;")
+    out = (V.vd_pose_cov * 1)()
+    assert lib.vd_pose_covariance(None, 1e-12, out) == V.VD_ERR_ARG
+    assert lib.vd_get_frame_samples(None, 1, None, None) == V.VD_ERR_ARG
+
+
 def test_batch_and_tune_argument_checks(lib):
     """Argument validation of the batch and tuning calls needs no GPU."""
     from paper_2104_06800_gb300 import voldor as V
