@@ -32,6 +32,9 @@ Modules and the passage each follows (Min & Dunn, "VOLDOR+SLAM", 2021):
   posecov  -- the pose covariance from the P3P samples: iterative Gaussian
               fit with 3-sigma rejection and an eigenvalue floor (Sec. III-A
               "Uncertainty-aware Pose Estimation").
+  ka       -- keyframe alignment (Sec. III-C, Eq. 9-12): point-to-plane
+              registration of two depth maps in inverse-depth form with a
+              Cauchy kernel, Levenberg-Marquardt, covariance (J^T J)^-1.
   vc       -- visibility, coverage and their harmonic mean (Eq. 8), the VO
               stride and keyframe test (Sec. III-B "VO Stride and Keyframe
               Selection").

@@ -1,0 +1,140 @@
+"""Pins of the keyframe-alignment oracle (oracle/ka.py) on depth maps
+rendered analytically from a three-plane scene with a known relative pose
+and scale, plus finite-difference Jacobians and the kernel's closed form."""
+import numpy as np
+import pytest
+
+from oracle import geometry, ka
+
+W, H = 160, 120
+K = (120.0, 120.0, 80.0, 60.0)
+# planes n . X = d in keyframe-1 coordinates (y points down): floor, back
+# wall, left and right walls.  Three planes leave the scale unobservable (a
+# scaled set of three planes is a translated one: n_i . t = (s - 1) d_i has a
+# solution); the fourth, parallel to the third, fixes it.
+PLANES = [(np.array([0.0, 1.0, 0.0]), 1.2), (np.array([0.0, 0.0, 1.0]), 9.0),
+          (np.array([1.0, 0.0, 0.0]), -4.0), (np.array([1.0, 0.0, 0.0]), 3.0)]
+
+
+def render(T):
+    """Depth map of the camera whose coordinates map to keyframe 1's by T."""
+    R, t = T[:, :3], T[:, 3]
+    r = ka.rays(W, H, K)
+    theta = np.full((H, W), np.inf)
+    for n, d in PLANES:
+        nc, dc = R.T @ n, d - n @ t          # the plane in this camera's coordinates
+        den = r @ nc
+        with np.errstate(divide="ignore", invalid="ignore"):
+            th = np.where(den != 0, dc / den, np.inf)
+        th = np.where(th > 1e-6, th, np.inf)
+        theta = np.minimum(theta, th)
+    theta[~np.isfinite(theta)] = np.nan
+    return theta
+
+
+def _T_true():
+    return geometry.se3_exp(np.array([0.01, -0.025, 0.008, 0.2, -0.05, 0.4]))
+
+
+def _start(T, rng, rot=0.02, trans=0.05):
+    xi = np.concatenate([rng.normal(size=3) * rot, rng.normal(size=3) * trans])
+    return geometry.compose(geometry.se3_exp(xi), T)
+
+
+def _pose_err(A, B):
+    d = geometry.se3_log(geometry.compose(geometry.inverse(A), B))
+    return np.abs(d[:3]).max(), np.abs(d[3:]).max()
+
+
+def test_normals_of_a_plane_face_the_camera():
+    th = render(geometry.IDENTITY)
+    n, ok = ka.normals(th, K)
+    # back wall interior: pixels around the principal point
+    assert ok[60, 80] and np.allclose(n[60, 80], [0, 0, -1], atol=1e-12)
+    # floor: bottom rows
+    assert ok[115, 80] and np.allclose(n[115, 80], [0, -1, 0], atol=1e-12)
+    assert not ok[0].any() and not ok[:, 0].any()
+
+
+def test_zero_residual_at_the_true_pose_on_plane_interiors():
+    T = _T_true()
+    th1, th2 = render(geometry.IDENTITY), render(T)
+    n1, ok1 = ka.normals(th1, K)
+    r, C, _ = ka.residuals(th1, n1, ok1, th2, None, K, T, 1.0)
+    assert len(r) > 0.6 * W * H
+    assert np.median(np.abs(r)) < 1e-12 and np.mean(np.abs(r) < 1e-9) > 0.9
+
+
+def test_jacobian_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    T = _start(_T_true(), rng, 0.01, 0.02)
+    s = 1.1
+    th1, th2 = render(geometry.IDENTITY), render(_T_true())
+    n1, ok1 = ka.normals(th1, K)
+    a0 = []
+    r0, _, J = ka.residuals(th1, n1, ok1, th2, None, K, T, s, jac=True, assoc_out=a0)
+    h = 1e-6
+    for k in range(7):
+        e = np.zeros(7)
+        e[k] = h
+        vals = []
+        for sg in (1.0, -1.0):
+            Tk = geometry.compose(geometry.se3_exp(sg * e[:6]), T)
+            sk = s * np.exp(sg * e[6])
+            a = []
+            rk, _, _ = ka.residuals(th1, n1, ok1, th2, None, K, Tk, sk, assoc_out=a)
+            vals.append(dict(zip(zip(*a[0]), rk)))
+        same = [i for i, key in enumerate(zip(*a0[0])) if key in vals[0] and key in vals[1]]
+        assert len(same) > 0.9 * len(r0)
+        keys = list(zip(*a0[0]))
+        fd = np.array([(vals[0][keys[i]] - vals[1][keys[i]]) / (2 * h) for i in same])
+        assert np.allclose(J[same, k], fd, rtol=1e-5, atol=1e-7), k
+
+
+def test_cauchy_energy_and_weights():
+    r = np.array([0.0, 0.01, -0.03, 0.5])
+    c = 0.01
+    assert np.allclose(ka.cauchy(r, c), 0.5 * c * c * np.log(1 + (r / c) ** 2))
+    assert ka.cauchy(np.array([c]), c)[0] == pytest.approx(0.5 * c * c * np.log(2.0))
+
+
+def test_alignment_recovers_the_pose():
+    rng = np.random.default_rng(1)
+    T = _T_true()
+    th1, th2 = render(geometry.IDENTITY), render(T)
+    res = ka.align(th1, th2, K, _start(T, rng), fix_scale=True)
+    er, et = _pose_err(res["T"], T)
+    assert er < 1e-6 and et < 1e-6, (er, et, res["iterations"])
+    assert res["s"] == 1.0 and np.all(np.linalg.eigvalsh(res["cov"]) > 0)
+
+
+def test_alignment_recovers_the_scale():
+    rng = np.random.default_rng(2)
+    T = _T_true()
+    s_true = 1.7
+    th1 = render(geometry.IDENTITY) / s_true        # keyframe 1 in another depth gauge
+    th2 = render(T)
+    # from a start a keyframe alignment gets (the pose graph's estimate):
+    # scale within 10 %
+    res = ka.align(th1, th2, K, _start(T, rng), s0=s_true * 1.1, fix_scale=False)
+    er, et = _pose_err(res["T"], T)
+    assert er < 1e-6 and et < 1e-6 and abs(res["s"] - s_true) < 1e-6, (er, et, res["s"])
+
+
+def test_robust_kernel_downweights_corrupted_depth():
+    # 10 % of keyframe 2 pushed 1.5-3x farther (with confidence 0.2): the
+    # Cauchy kernel at c = 0.01 stays far closer to the truth than a
+    # practically quadratic one (c = 100) on the same data
+    rng = np.random.default_rng(3)
+    T = _T_true()
+    th1, th2 = render(geometry.IDENTITY), render(T)
+    bad = rng.uniform(size=th2.shape) < 0.1
+    th2 = th2.copy()
+    th2[bad] *= rng.uniform(1.5, 3.0, size=bad.sum())
+    conf = np.where(bad, 0.2, 1.0)
+    T0 = _start(T, rng)
+    robust = ka.align(th1, th2, K, T0, conf2=conf, fix_scale=True, c=0.01)
+    quad = ka.align(th1, th2, K, T0, conf2=conf, fix_scale=True, c=100.0)
+    er, et = _pose_err(robust["T"], T)
+    eq, tq = _pose_err(quad["T"], T)
+    assert er < 0.2 * eq and et < 0.2 * tq and er < 1e-2, (er, et, eq, tq)
