@@ -379,6 +379,42 @@ vd_status vd_pose_covariance(vd_ctx* ctx, double eps, vd_pose_cov* out);
  * energies, +inf for a sample without a root).  Host memory. */
 vd_status vd_get_frame_samples(vd_ctx* ctx, int t, double* poses, double* energies);
 
+/* ---- Keyframe alignment --------------------------------------------------
+ * Sec. III-C "Keyframe Alignment", Eq. 9-12: the motion T and scale s of
+ * two keyframes' depth maps theta_1, theta_2 (depth, not inverse depth;
+ * same size and intrinsics) minimising
+ *   E = sum_j C^j psi(<n_l, s theta_1^l r_l - P_j> / (s theta_1^l P_jz)),
+ * P_j = R theta_2^j r_j + t (keyframe 2's pixel j in keyframe-1
+ * coordinates), l the nearest pixel of its projection into keyframe 1
+ * (a pair counts when |P_jz - s theta_1^l| <= 0.2 s theta_1^l: occlusions),
+ * r = ((u - cx)/fx, (v - cy)/fy, 1), n_l the normal of depth map 1 (central
+ * differences of its points, towards the camera; none at the border, next
+ * to an invalid depth, or where a second difference of the points exceeds
+ * 0.2 of the central span: a depth edge or fold), psi(r) = (c^2/2)
+ * log(1 + r^2/c^2),
+ * C^j keyframe 2's confidence (1 without a map).  Valid depth: finite, > 0.
+ * Levenberg-Marquardt on a left increment of T in se(3) and log s (s fixed
+ * at 1 with fix_scale): the step solves (H + lambda diag H) delta = -g with
+ * H = sum w J J^T, g = sum w J r, w = C / (1 + r^2/c^2); taken when it
+ * lowers E (lambda /= 10), refused otherwise (lambda *= 10); lambda starts at
+ * 1e-3; stop after max_iters steps, a step below 1e-10, or lambda > 1e10.
+ * cov = the pose block of H^-1 (rotation first), NaN without a pixel.
+ * Device buffers; float64 arithmetic.  Synchronises the stream. */
+typedef struct {
+  double pose[12];   /* T; in: start, 3x4 keyframe-2 -> keyframe-1; out: estimate */
+  double s;          /* in: start (> 0); out: estimate                          */
+  double cauchy_c;   /* Cauchy kernel scale c (inverse-depth units, > 0)        */
+  int fix_scale;     /* 1: s = 1 (depth of absolute scale)                      */
+  int max_iters;     /* Levenberg-Marquardt steps at most (>= 0)                */
+  double cov[36];    /* out: 6x6 row-major                                      */
+  double energy;     /* out: E at the estimate                                  */
+  int iterations;    /* out                                                     */
+  long long n_valid; /* out: associated pixels at the estimate                  */
+} vd_ka;
+vd_status vd_ka_align(const float* depth1, const float* depth2, const float* conf2 /*nullable*/,
+                      int width, int height, const double* intrinsics /*fx fy cx cy*/, vd_ka* io,
+                      void* cuda_stream);
+
 /* ---- Visibility-coverage score, VO stride and keyframe test ------------
  * Sec. III-B "VO Stride and Keyframe Selection", Eq. 8.  The reference
  * frame's depth pixels (finite rho > 0 of the context's current inverse

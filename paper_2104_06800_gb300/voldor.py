@@ -77,6 +77,12 @@ VD_BATCH_AUTOTUNE = 2
 VD_VC_MAX_FRAMES = 8
 
 
+class vd_ka(C.Structure):
+    _fields_ = [("pose", C.c_double * 12), ("s", C.c_double), ("cauchy_c", C.c_double),
+                ("fix_scale", C.c_int), ("max_iters", C.c_int), ("cov", C.c_double * 36),
+                ("energy", C.c_double), ("iterations", C.c_int), ("n_valid", C.c_longlong)]
+
+
 class vd_pose_cov(C.Structure):
     _fields_ = [("mean", C.c_double * 12), ("cov", C.c_double * 36), ("n_samples", C.c_int),
                 ("n_inliers", C.c_int), ("rounds", C.c_int), ("degenerate", C.c_int)]
@@ -153,6 +159,7 @@ _SIGS = {
     "vd_eight_point": [_P, _P],
     "vd_vc_scores": [_P, C.POINTER(vd_vc)],
     "vd_pose_covariance": [_P, C.c_double, _P],
+    "vd_ka_align": [_P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(vd_ka), _P],
     "vd_get_frame_samples": [_P, C.c_int, _P, _P],
     "vd_vc_pose": [_P, _P, C.POINTER(vd_vc)],
     "vd_vc_stride": [_P, C.c_int, C.c_double],
@@ -502,6 +509,26 @@ def vd_get_frame_samples(ctx, t, S):
     _call("vd_get_frame_samples", ctx, int(t), poses.ctypes.data_as(C.c_void_p),
           energies.ctypes.data_as(C.c_void_p))
     return poses, energies
+
+
+# ------------------------------------------------------------------ keyframe alignment
+def vd_ka_align(depth1, depth2, K, T0, s0=1.0, conf2=None, c=0.01, fix_scale=False,
+                max_iters=50, stream=None):
+    """depth1, depth2 (and conf2): CUDA float32 tensors [H][W] of depth; K =
+    (fx, fy, cx, cy); T0: 3x4 keyframe-2 -> keyframe-1.  Returns dict(T, s,
+    cov 6x6, energy, iterations, n_valid)."""
+    H, W = depth1.shape
+    io = vd_ka()
+    for i, v in enumerate(np.asarray(T0, np.float64).reshape(12)):
+        io.pose[i] = float(v)
+    io.s, io.cauchy_c = float(s0), float(c)
+    io.fix_scale, io.max_iters = int(bool(fix_scale)), int(max_iters)
+    k = np.ascontiguousarray(K, np.float64)
+    _call("vd_ka_align", _dev(depth1), _dev(depth2), _dev(conf2) if conf2 is not None else None,
+          int(W), int(H), k.ctypes.data_as(C.c_void_p), C.byref(io),
+          stream if stream is not None else current_stream())
+    return dict(T=np.array(io.pose[:]).reshape(3, 4), s=io.s, cov=np.array(io.cov[:]).reshape(6, 6),
+                energy=io.energy, iterations=io.iterations, n_valid=io.n_valid)
 
 
 # ------------------------------------------------------------------ VC score

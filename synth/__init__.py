@@ -283,6 +283,44 @@ CONFIGS = {
 }
 
 
+def _config(name, rng, noisy, N, size):
+    """Scene, poses, flows and parameters of one window of config `name`."""
+    if name == "planes160":
+        return _cfg_planes(rng, noisy)
+    if name == "boxes640_stereo":
+        W, H = size or (640, 480)
+        return _cfg_boxes(rng, noisy, W, H, N or 5, 0.10 if noisy else 0.0)
+    if name == "driving1216":
+        W, H = size or (1216, 368)
+        return _cfg_driving(rng, noisy, W, H, N or 6)
+    if name == "rgbd_batch":
+        if size is None:
+            size = [(320, 240), (640, 480), (1216, 368)][rng.integers(0, 3)]
+        Nw = N or int(rng.integers(3, 9))
+        W, H = size
+        out = _cfg_boxes(rng, noisy, W, H, Nw, 0.05 if noisy else 0.0)
+        out[8]["n_iters"] = 5
+        return out
+    raise ValueError(f"unknown window config {name!r}")
+
+
+def keyframe_pair(name: str = "driving1216", seed: int = 0, t: int = 3,
+                  size: tuple[int, int] | None = None):
+    """Two keyframes of one window's scene: the true depth Z of the reference
+    frame and of frame t (float32 [H, W]), the pose that maps frame-t
+    coordinates to reference coordinates (G_0 G_t^-1, 3x4) and the
+    intrinsics (fx, fy, cx, cy)."""
+    rng = np.random.default_rng(seed)
+    W, H, _, K, sc, G, _, _, _ = _config(name, rng, False, None, size)
+    fx, fy, cx, cy = K
+    _, Z0 = sc.cast(G[0], W, H, fx, fy, cx, cy)
+    _, Zt = sc.cast(G[t], W, H, fx, fy, cx, cy)
+    Rt, taut = G[t][:, :3], G[t][:, 3]
+    inv = np.hstack([Rt.T, (-Rt.T @ taut)[:, None]])
+    T = _compose(G[0], inv)
+    return Z0.astype(np.float32), Zt.astype(np.float32), T, (fx, fy, cx, cy)
+
+
 def make_window(name: str, seed: int = 0, noisy: bool = True, N: int | None = None,
                 size: tuple[int, int] | None = None) -> Window:
     """Build one seeded synthetic window.
@@ -293,29 +331,8 @@ def make_window(name: str, seed: int = 0, noisy: bool = True, N: int | None = No
     N, size : optional overrides of the flow count and (W, H) (rgbd_batch and tests)."""
     rng = np.random.default_rng(seed)
     stereo = depth_prior = None
-    baseline = 0.0
-    if name == "planes160":
-        W, H, Nn, K, sc, G, flow, mv, prm = _cfg_planes(rng, noisy)
-    elif name == "boxes640_stereo":
-        W, H = size or (640, 480)
-        W, H, Nn, K, sc, G, flow, mv, prm = _cfg_boxes(rng, noisy, W, H, N or 5,
-                                                       0.10 if noisy else 0.0)
-        baseline = 0.25
-    elif name == "driving1216":
-        W, H = size or (1216, 368)
-        W, H, Nn, K, sc, G, flow, mv, prm = _cfg_driving(rng, noisy, W, H, N or 6)
-        if not noisy:
-            pass
-    elif name == "rgbd_batch":
-        if size is None:
-            size = [(320, 240), (640, 480), (1216, 368)][rng.integers(0, 3)]
-        Nw = N or int(rng.integers(3, 9))
-        W, H = size
-        W, H, Nn, K, sc, G, flow, mv, prm = _cfg_boxes(rng, noisy, W, H, Nw,
-                                                       0.05 if noisy else 0.0)
-        prm["n_iters"] = 5
-    else:
-        raise ValueError(f"unknown window config {name!r}")
+    baseline = 0.25 if name == "boxes640_stereo" else 0.0
+    W, H, Nn, K, sc, G, flow, mv, prm = _config(name, rng, noisy, N, size)
     fx, fy, cx, cy = K
     _, Z0 = sc.cast(G[0], W, H, fx, fy, cx, cy)
     if name == "boxes640_stereo":

@@ -115,6 +115,19 @@ def test_pose_cov_struct_and_argument_checks(lib):
     assert lib.vd_get_frame_samples(None, 1, None, None) == V.VD_ERR_ARG
 
 
+def test_ka_struct_and_argument_checks(lib):
+    from paper_2104_06800_gb300 import voldor as V
+    src = open(os.path.join(ROOT, "include", "voldor_em.h")).read()
+    assert [f for f, _ in V.vd_ka._fields_] == _struct_fields(src, "} vd_ka;")
+    io = V.vd_ka()
+    io.s, io.cauchy_c, io.max_iters = 1.0, 0.01, 10
+    k = (V.C.c_double * 4)(100.0, 100.0, 5.0, 5.0)
+    assert lib.vd_ka_align(None, None, None, 10, 10, k, V.C.byref(io), None) == V.VD_ERR_ARG
+    io.cauchy_c = 0.0
+    p = V.C.c_void_p(16)   # never dereferenced: the arguments are checked first
+    assert lib.vd_ka_align(p, p, None, 10, 10, k, V.C.byref(io), None) == V.VD_ERR_ARG
+
+
 def test_batch_and_tune_argument_checks(lib):
     """Argument validation of the batch and tuning calls needs no GPU."""
     from paper_2104_06800_gb300 import voldor as V

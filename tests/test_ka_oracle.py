@@ -4,47 +4,11 @@ and scale, plus finite-difference Jacobians and the kernel's closed form."""
 import numpy as np
 import pytest
 
+from ka_scene import H, K, W, render
+from ka_scene import T_true as _T_true
+from ka_scene import pose_err as _pose_err
+from ka_scene import start as _start
 from oracle import geometry, ka
-
-W, H = 160, 120
-K = (120.0, 120.0, 80.0, 60.0)
-# planes n . X = d in keyframe-1 coordinates (y points down): floor, back
-# wall, left and right walls.  Three planes leave the scale unobservable (a
-# scaled set of three planes is a translated one: n_i . t = (s - 1) d_i has a
-# solution); the fourth, parallel to the third, fixes it.
-PLANES = [(np.array([0.0, 1.0, 0.0]), 1.2), (np.array([0.0, 0.0, 1.0]), 9.0),
-          (np.array([1.0, 0.0, 0.0]), -4.0), (np.array([1.0, 0.0, 0.0]), 3.0)]
-
-
-def render(T):
-    """Depth map of the camera whose coordinates map to keyframe 1's by T."""
-    R, t = T[:, :3], T[:, 3]
-    r = ka.rays(W, H, K)
-    theta = np.full((H, W), np.inf)
-    for n, d in PLANES:
-        nc, dc = R.T @ n, d - n @ t          # the plane in this camera's coordinates
-        den = r @ nc
-        with np.errstate(divide="ignore", invalid="ignore"):
-            th = np.where(den != 0, dc / den, np.inf)
-        th = np.where(th > 1e-6, th, np.inf)
-        theta = np.minimum(theta, th)
-    theta[~np.isfinite(theta)] = np.nan
-    return theta
-
-
-def _T_true():
-    return geometry.se3_exp(np.array([0.01, -0.025, 0.008, 0.2, -0.05, 0.4]))
-
-
-def _start(T, rng, rot=0.02, trans=0.05):
-    xi = np.concatenate([rng.normal(size=3) * rot, rng.normal(size=3) * trans])
-    return geometry.compose(geometry.se3_exp(xi), T)
-
-
-def _pose_err(A, B):
-    d = geometry.se3_log(geometry.compose(geometry.inverse(A), B))
-    return np.abs(d[:3]).max(), np.abs(d[3:]).max()
-
 
 def test_normals_of_a_plane_face_the_camera():
     th = render(geometry.IDENTITY)
@@ -122,18 +86,18 @@ def test_alignment_recovers_the_scale():
 
 
 def test_robust_kernel_downweights_corrupted_depth():
-    # 10 % of keyframe 2 pushed 1.5-3x farther (with confidence 0.2): the
-    # Cauchy kernel at c = 0.01 stays far closer to the truth than a
-    # practically quadratic one (c = 100) on the same data
+    # 10 % of keyframe 2 pushed 8-18 % farther (inside the occlusion gate,
+    # confidence 0.2): the Cauchy kernel at c = 0.002 stays far closer to
+    # the truth than a practically quadratic one (c = 100) on the same data
     rng = np.random.default_rng(3)
     T = _T_true()
     th1, th2 = render(geometry.IDENTITY), render(T)
     bad = rng.uniform(size=th2.shape) < 0.1
     th2 = th2.copy()
-    th2[bad] *= rng.uniform(1.5, 3.0, size=bad.sum())
+    th2[bad] *= rng.uniform(1.08, 1.18, size=bad.sum())
     conf = np.where(bad, 0.2, 1.0)
     T0 = _start(T, rng)
-    robust = ka.align(th1, th2, K, T0, conf2=conf, fix_scale=True, c=0.01)
+    robust = ka.align(th1, th2, K, T0, conf2=conf, fix_scale=True, c=0.002)
     quad = ka.align(th1, th2, K, T0, conf2=conf, fix_scale=True, c=100.0)
     er, et = _pose_err(robust["T"], T)
     eq, tq = _pose_err(quad["T"], T)
