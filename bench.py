@@ -33,7 +33,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the float64 oracle (cpu_baseline, --impl reference) runs on one host core:
+# no BLAS thread pool (set before numpy loads its BLAS)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
