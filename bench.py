@@ -43,8 +43,7 @@ import numpy as np  # noqa: E402
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] \
-    if os.path.exists(os.path.join(ROOT, "BASELINE.json")) else "EM pixel*frame*iters/s"
+METRIC = "EM pixel\u00b7frame\u00b7iters/s and windows/s at 1216x368 N=6; plain vs learned-init at \u22641% err"
 UNIT = "pixel*frame*iter/s"
 WORK = dict(name="driving1216", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2000)
 
