@@ -86,3 +86,12 @@ def test_full_size_alignment_and_argument_checks(V):
         V.vd_ka_align(_dev(th1), _dev(th2), Kf, T0, c=0.0)
     with pytest.raises(V.VoldorError):
         V.vd_ka_align(_dev(th1), _dev(th2), Kf, np.full((3, 4), np.nan))
+
+
+def test_no_valid_pixel_is_reported_not_an_error(V):
+    th = np.full((H, W), np.nan, np.float32)
+    got = V.vd_ka_align(_dev(th), _dev(th), K, T_true(), fix_scale=True)
+    ref = ka.align(th, th, K, T_true(), fix_scale=True)
+    assert got["n_valid"] == ref["n_valid"] == 0 and got["iterations"] == ref["iterations"] == 0
+    assert np.all(np.isnan(got["cov"])) and got["energy"] == 0.0
+    assert np.array_equal(got["T"], T_true())

@@ -60,3 +60,17 @@ def test_covariance_matches_oracle(V, name, seed, size, iters):
         _compare(V, ctx, w, params, 1e-8)           # a floor that binds
     finally:
         V.vd_destroy(ctx)
+
+
+def test_many_samples_per_lane(V):
+    """200 samples per frame: every lane owns up to 7 samples."""
+    w = window("planes160", 0)
+    ctx, _, _ = make_ctx(V, w, n_pose_samples=200)
+    params = V.vd_params_default(**params_for(w, n_pose_samples=200))
+    try:
+        V.vd_bootstrap(ctx)
+        V.vd_run_em(ctx, 2)
+        res = _compare(V, ctx, w, params, 1e-12)
+        assert all(r["n_samples"] > 64 for r in res)
+    finally:
+        V.vd_destroy(ctx)

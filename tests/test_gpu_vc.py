@@ -112,3 +112,22 @@ def test_full_size_after_the_em(V):
             assert V.vd_vc_stride(vc, tau) == ovc.stride(vc, tau)
     finally:
         V.vd_destroy(ctx)
+
+
+def test_tiny_window_one_flow(V):
+    """A 3 x 2 window with one flow: a single partial warp."""
+    rng = np.random.default_rng(11)
+    K = (2.0, 2.0, 1.0, 0.5)
+    ctx = V.vd_create(3, 2, 1, K, V.vd_params_default())
+    try:
+        rho = rng.uniform(0.2, 1.0, (2, 3)).astype(np.float32)
+        rho[0, 1] = np.nan
+        from oracle import geometry as ogeo
+        G = np.stack([np.hstack([np.eye(3), np.zeros((3, 1))]),
+                      ogeo.se3_exp(np.array([0.0, 0.02, 0.0, 0.3, 0.0, 0.1]))])
+        V.vd_set_poses(ctx, G.reshape(-1, 12))
+        V.vd_set_state(ctx, rho)
+        res = V.vd_vc_scores(ctx)
+        _check(res, rho, K, [G[1]], 3, 2)
+    finally:
+        V.vd_destroy(ctx)
