@@ -373,7 +373,9 @@ typedef struct {
   int degenerate;
 } vd_pose_cov;
 /* out: N entries, frame t at out[t-1].  Needs a pose M-step of every frame
- * (VD_ERR_STATE otherwise).  Synchronises the context stream. */
+ * since the last vd_bootstrap, vd_set_poses, vd_set_state or
+ * vd_import_state (VD_ERR_STATE otherwise).  Synchronises the context
+ * stream. */
 vd_status vd_pose_covariance(vd_ctx* ctx, double eps, vd_pose_cov* out);
 /* The samples of frame t's last pose M-step (S x 12 absolute poses, S
  * energies, +inf for a sample without a root).  Host memory. */

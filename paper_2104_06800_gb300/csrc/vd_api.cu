@@ -498,6 +498,7 @@ extern "C" vd_status vd_set_poses(vd_ctx* c, const double* poses, vd_pose_kind k
   VD_CU(launch_posef(c));
   VD_CU(cudaStreamSynchronize(c->stream));
   c->poses_set = 1;
+  c->samples_set = 0;   // the pose samples no longer belong to the state
   ++c->cfg_version;
   return VD_OK;
 }
@@ -533,6 +534,7 @@ extern "C" vd_status vd_set_state(vd_ctx* c, const float* rho, const float* q, c
   else VD_CU(launch_fill(c->qhat, 1.0f, c->npix, c->stream));
   VD_CU(cudaStreamSynchronize(c->stream));
   c->bootstrapped = 1;
+  c->samples_set = 0;   // the pose samples no longer belong to the state
   return VD_OK;
 }
 
@@ -588,6 +590,7 @@ static cudaError_t pose_step(vd_ctx* c, int iter, int t) {
 // The bootstrap is a function of the inputs alone: it starts from the initial
 // poses (identity, or those of vd_set_poses), not from a previous run's.
 static cudaError_t bootstrap(vd_ctx* c) {
+  c->samples_set = 0;   // a bootstrap with given poses runs no pose step
   vd_prof_begin(c, VD_ST_OTHER);
   cudaError_t e = cudaMemcpyAsync(c->G, c->G_init, sizeof(double) * 12 * (c->N + 1),
                                   cudaMemcpyDeviceToDevice, c->stream);
@@ -1241,6 +1244,7 @@ extern "C" vd_status vd_import_state(vd_ctx* c, const void* blob, size_t bytes) 
   VD_CU(cudaStreamSynchronize(c->stream));
   c->iter = h.iter;
   c->bootstrapped = h.bootstrapped;
+  c->samples_set = 0;   // the blob holds no pose samples
   c->poses_set = h.poses_set;
   ++c->cfg_version;
   return VD_OK;

@@ -58,6 +58,10 @@ def test_covariance_matches_oracle(V, name, seed, size, iters):
             res = _compare(V, ctx, w, params, 1e-12)
         assert any(r["n_inliers"] >= 7 and not r["degenerate"] for r in res)
         _compare(V, ctx, w, params, 1e-8)           # a floor that binds
+        # new poses: the samples no longer belong to the state
+        V.vd_set_poses(ctx, V.vd_get_poses(ctx, w.N).reshape(-1, 12))
+        with pytest.raises(V.VoldorError):
+            V.vd_pose_covariance(ctx, w.N)
     finally:
         V.vd_destroy(ctx)
 
