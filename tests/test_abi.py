@@ -142,3 +142,20 @@ def test_batch_and_tune_argument_checks(lib):
     t = V.vd_tune()
     assert lib.vd_set_tune(None, V.C.byref(t)) == V.VD_ERR_ARG
     assert lib.vd_autotune(None, None) == V.VD_ERR_ARG
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/voldor_em.h compiles as C99 with warnings as errors (a C ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "voldor_em.h"\n'
+                   "int main(void) { vd_params p; vd_vc v; vd_pose_cov c; vd_ka k;\n"
+                   "  (void)v; (void)c; (void)k; return vd_params_default(&p) == VD_OK ? 0 : 1; }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                        str(tmp_path / "use.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
