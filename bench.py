@@ -60,6 +60,16 @@ K1_TRAFFIC_BYTES = 32.4e6
 SM_MAX_MHZ = 2070.0
 
 
+def workload_config(nb, world):
+    """The headline workload (both arms report it)."""
+    return {"workload": f"driving1216 x {nb} windows per step: 1216x368, N=6 flows, "
+                        "K=128 hypotheses, 8 EM iterations, S=64 P3P samples, "
+                        "monocular bootstrap; all windows in one CUDA-graph launch",
+            "windows_per_step_per_gpu": nb,
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{world}"}
+
+
 def fp32_per_pixel_hyp(N):
     return FP32_T1 + (N - 1) * FP32_TN
 
@@ -391,12 +401,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
             "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"driving1216 x {nb} windows per step: 1216x368, N=6 flows, "
-                                   "K=128 hypotheses, 8 EM iterations, S=64 P3P samples, "
-                                   "monocular bootstrap; all windows in one CUDA-graph launch",
-                       "windows_per_step_per_gpu": nb,
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(nb, world),
             "windows_per_s": round(nb * args.steps * world / (total_ms / 1e3), 3),
             "single_window": single, "batch": bstats,
             "roofline": roofline, "stage_ms_per_window": stages,
@@ -590,7 +595,7 @@ def main():
                 "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1e3 * statistics.median(samples), 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": "driving1216 crop (oracle sample)"},
+                "data": "synthetic", "config": workload_config(args.batch, 1),
                 "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cpu_cores_used(),
                                  "kind": "oracle", "sample": desc},
                 "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
