@@ -371,29 +371,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
 
     e2e = None
     if not args.no_e2e:
-        host = [torch.from_numpy(w.flow).pin_memory() for w in bw]
-        host_rho = torch.empty((H, W), dtype=torch.float32).pin_memory()
-        n_e2e = max(2, min(args.steps, 5))
-        torch.cuda.synchronize()
-        barrier(pg)
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            for i in range(nb):
-                c = V.vd_batch_window(b, i)
-                for t in range(N):
-                    V.vd_push_flow(c, t + 1, host[i][t].numpy())
-            V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
-            for i in range(nb):
-                c = V.vd_batch_window(b, i)
-                V.vd_get_inv_depth(c, host_rho.numpy())
-                V.vd_get_poses(c, N)
-        torch.cuda.synchronize()
-        dt = max_over_ranks(pg, time.perf_counter() - t0, dev)
-        e2e = {"value": round(units_per_window * nb * n_e2e * world / dt, 1), "unit": UNIT,
-               "h2d_bytes_per_step": int(sum(w.flow.nbytes for w in bw)),
-               "d2h_bytes_per_step": int(nb * (W * H * 4 + (N + 1) * 12 * 8)), "steps": n_e2e,
-               "path": "vd_push_flow from pinned host memory, vd_batch_run, vd_get_inv_depth + "
-                       "vd_get_poses per window"}
+        e2e = run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, world)
 
     V.vd_batch_destroy(b)
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -409,6 +387,78 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
             "e2e": e2e}
     return line
 
+
+
+def run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, world):
+    """End-to-end throughput through the C ABI with host buffers: every step
+    pushes one batch of flows from pinned host memory, runs the batch and
+    reads every window's inverse depth and poses back.  Two batches on
+    independent streams alternate, so that a helper thread pushes the next
+    batch's flows and reads back the previous batch's results while the
+    current batch runs (vd_batch_run blocks the calling thread; ctypes drops
+    the interpreter lock around it).  Every copy is inside the timed region."""
+    import concurrent.futures
+    import torch
+    N, W, H = bw[0].N, bw[0].W, bw[0].H
+    nb = len(bw)
+    side = torch.cuda.Stream(device=dev)
+    b2 = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in bw], params,
+                           V.C.c_void_p(side.cuda_stream))
+    try:
+        for i in range(nb):
+            t = V.vd_get_tune(V.vd_batch_window(b, i))
+            V.vd_set_tune(V.vd_batch_window(b2, i), t["k1_warps"], t["score_blocks_per_sm"],
+                          t["score_threads"])
+        host = [torch.from_numpy(w.flow).pin_memory() for w in bw]
+        host_rho = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        bufs = (b, b2)
+
+        def stage(x):
+            for i in range(nb):
+                c = V.vd_batch_window(x, i)
+                for t in range(N):
+                    V.vd_push_flow(c, t + 1, host[i][t].numpy())
+
+        def drain(x):
+            for i in range(nb):
+                c = V.vd_batch_window(x, i)
+                V.vd_get_inv_depth(c, host_rho.numpy())
+                V.vd_get_poses(c, N)
+
+        # one untimed pass through both batches (graph capture of the second)
+        for x in bufs:
+            stage(x)
+            V.vd_batch_run(x, iters, V.VD_BATCH_BOOTSTRAP)
+            drain(x)
+        n_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier(pg)
+        with concurrent.futures.ThreadPoolExecutor(max_workers=1) as pool:
+            t0 = time.perf_counter()
+            stage(bufs[0])
+            for k in range(n_e2e):
+                cur, other = bufs[k % 2], bufs[(k + 1) % 2]
+
+                def side_work(k=k, other=other):
+                    if k > 0:
+                        drain(other)
+                    if k + 1 < n_e2e:
+                        stage(other)
+
+                fut = pool.submit(side_work)
+                V.vd_batch_run(cur, iters, V.VD_BATCH_BOOTSTRAP)
+                fut.result()
+            drain(bufs[(n_e2e - 1) % 2])
+            torch.cuda.synchronize()
+            dt = max_over_ranks(pg, time.perf_counter() - t0, dev)
+    finally:
+        V.vd_batch_destroy(b2)
+    return {"value": round(units_per_window * nb * n_e2e * world / dt, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(w.flow.nbytes for w in bw)),
+            "d2h_bytes_per_step": int(nb * (W * H * 4 + (N + 1) * 12 * 8)), "steps": n_e2e,
+            "path": "vd_push_flow from pinned host memory, vd_batch_run, vd_get_inv_depth + "
+                    "vd_get_poses per window; two batches alternate so that one batch's "
+                    "copies overlap the other's run"}
 
 def run_rgbd64(args, rank, world, local, pg):
     """64 windows with an RGB-D prior, sizes drawn from 320x240 / 640x480 /
