@@ -372,17 +372,23 @@ __global__ void k_roots_float(DevParams P, const double* __restrict__ roots,
 // registers and loops over the roots (broadcast from shared memory); warp
 // sums go to per-warp shared slots, summed in fixed order at the end.
 // ---------------------------------------------------------------------------
+// One pixel's term under one root, without branches, so that the unrolled
+// terms of a thread's pixels form one block the compiler can interleave.
+// FAST: beta = 2 and alpha1 = 0 (closed form; obs.z unused).  A point behind
+// the camera gives the constant term (its projection is computed from a
+// denominator of 1 and discarded).
+template <bool FAST>
 __device__ __forceinline__ float vd_score_term(const DevParams& P, const float* Mr, float4 pt,
                                                float4 ob) {
   const float hx = fmaf(Mr[0], pt.x, fmaf(Mr[1], pt.y, fmaf(Mr[2], pt.z, Mr[9])));
   const float hy = fmaf(Mr[3], pt.x, fmaf(Mr[4], pt.y, fmaf(Mr[5], pt.z, Mr[10])));
   const float hz = fmaf(Mr[6], pt.x, fmaf(Mr[7], pt.y, fmaf(Mr[8], pt.z, Mr[11])));
-  if (!(hz > VD_Z_EPS)) return pt.w * VD_L_BEHIND;
-  const float iz = __fdividef(1.0f, hz);
+  const bool front = hz > VD_Z_EPS;
+  const float iz = __fdividef(1.0f, front ? hz : 1.0f);
   const float dx = ob.x - hx * iz, dy = ob.y - hy * iz;
   const float r2 = fmaf(dx, dx, dy * dy);
-  const float l2 = P.fast_beta2 ? vd_l2_beta2(P, r2) : vd_l2_general(P, r2, ob.z);
-  return pt.w * VD_LN2 * l2;
+  const float l2 = FAST ? vd_l2_beta2(P, r2) : vd_l2_general(P, r2, ob.z);
+  return front ? pt.w * VD_LN2 * l2 : pt.w * VD_L_BEHIND;
 }
 
 // Dynamic shared memory of k_pose_score<THREADS> for M roots.
@@ -390,7 +396,7 @@ static inline size_t vd_score_smem(int M, int threads) {
   return sizeof(float) * (size_t)M * (12 + threads / 32) + sizeof(int) * (size_t)(M + 1);
 }
 
-template <int THREADS>
+template <int THREADS, bool FAST = false>
 __global__ void __launch_bounds__(THREADS)
 k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restrict__ robs,
              const int* __restrict__ n_ptr, int n_host, const float* __restrict__ rootsf,
@@ -444,7 +450,7 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
       float acc = 0.0f;
 #pragma unroll
       for (int k = 0; k < SCORE_PPT; ++k)
-        if (k < kact) acc += vd_score_term(P, Mr, pt[k], ob[k]);
+        if (k < kact) acc += vd_score_term<FAST>(P, Mr, pt[k], ob[k]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) sAcc[wid * M + r] += acc;
@@ -709,11 +715,12 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
 // stream capture, has to change a function attribute.
 cudaError_t vd_pose_prepare(void) {
   const int M = 4 * VD_MAX_SAMPLES;
-  cudaError_t e = cudaFuncSetAttribute(k_pose_score<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)vd_score_smem(M, 256));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pose_score<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)vd_score_smem(M, 512));
+  const int s256 = (int)vd_score_smem(M, 256), s512 = (int)vd_score_smem(M, 512);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_pose_score<256, false>, a, s256);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pose_score<256, true>, a, s256);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pose_score<512, false>, a, s512);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pose_score<512, true>, a, s512);
   return e;
 }
 
@@ -723,12 +730,17 @@ cudaError_t launch_pose_score_only(vd_ctx* c) {
   const DevParams& P = c->dp;
   const int M = 4 * P.S;
   const int nblk = c->score_bps * c->num_sms;
-  if (c->score_threads == 512)
-    k_pose_score<512><<<nblk, 512, vd_score_smem(M, 512), c->stream>>>(
-        P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
-  else
-    k_pose_score<256><<<nblk, 256, vd_score_smem(M, 256), c->stream>>>(
-        P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial);
+#define VD_SCORE_LAUNCH(TH, FAST)                                                     \
+  k_pose_score<TH, FAST><<<nblk, TH, vd_score_smem(M, TH), c->stream>>>(                   \
+      P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial)
+  if (c->score_threads == 512) {
+    if (P.fast_beta2) VD_SCORE_LAUNCH(512, true);
+    else VD_SCORE_LAUNCH(512, false);
+  } else {
+    if (P.fast_beta2) VD_SCORE_LAUNCH(256, true);
+    else VD_SCORE_LAUNCH(256, false);
+  }
+#undef VD_SCORE_LAUNCH
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_root_energy(c->partial, nblk, M, c->root_count, c->root_energy, c->stream);
