@@ -367,6 +367,8 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
     clk = clocks.stop()
     barrier(pg)
     bstats = V.vd_batch_get_stats(b)
+    bt = V.vd_get_tune(V.vd_batch_window(b, 0))
+    bstats["tune"] = {k: bt[k] for k in ("k1_warps", "score_threads", "score_blocks_per_sm")}
     total_ms, value = whole_job(pg, world, units_per_window * nb * args.steps, sum(tb), dev)
 
     e2e = None

@@ -266,7 +266,11 @@ vd_status vd_get_tune(vd_ctx* ctx, vd_tune* out);
  *   - flags: VD_BATCH_BOOTSTRAP re-bootstraps every window first (a new
  *     batch of flows); VD_BATCH_AUTOTUNE (with BOOTSTRAP) first tunes one
  *     window of every distinct (size, N, K, S, prior) and gives its choice to
- *     the others.
+ *     the others, then times whole-batch runs (bootstrap and up to two
+ *     iterations) of every pose-scoring shape that was within 25 % of the
+ *     best alone for every group and gives the fastest to every window
+ *     (the windows' kernels share the SMs; the trials' results are replaced
+ *     by the run itself).
  *   - degenerate: optional int[n] receiving each window's count of frames
  *     whose pose step kept the previous pose; the status is
  *     VD_WARN_DEGENERATE if any is non-zero.

@@ -954,14 +954,57 @@ extern "C" vd_status vd_batch_get_stats(vd_batch* b, vd_batch_stats* out) {
 
 // Tune one window of every distinct launch configuration and hand its
 // choice to the windows that share it.
-static vd_status batch_autotune(vd_batch* b) {
+static vd_status batch_capture(vd_batch* b, int n_iters, bool boot);
+
+// Scoring shapes whose time alone is within this factor of the best shape of
+// every window group take part in the whole-batch trial.
+static const float kBatchTrialMargin = 1.25f;
+
+// Time of one run of the captured batch graph (the second of two launches,
+// so that the graph's upload is not counted).
+static cudaError_t batch_time_run(vd_batch* b, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+static void batch_set_score_shape(vd_batch* b, int threads, int bps) {
+  for (vd_ctx* o : b->win) {
+    if (o->score_threads == threads && o->score_bps == bps) continue;
+    o->score_threads = threads;
+    o->score_bps = bps;
+    ++o->cfg_version;
+  }
+}
+
+// Tuning of a batch.  (1) One window of every distinct (size, N, K, S,
+// prior) is tuned alone (vd_autotune) and its choice given to the others.
+// (2) The windows' kernels share the SMs, so the scoring shape that is
+// fastest alone is not always the fastest among the other windows' launches
+// (one 512-thread block of ~90 registers per SM leaves little room beside
+// it).  Every shape within kBatchTrialMargin of the best time alone of every
+// group is therefore timed on whole-batch runs (the bootstrap and up to two
+// iterations) and the fastest one is given to every window.  A trial leaves
+// no state behind: the run that follows bootstraps again.
+static vd_status batch_autotune(vd_batch* b, int n_iters) {
   const int n = (int)b->win.size();
   std::vector<int> done(n, 0);
+  std::vector<vd_ctx*> leaders;
   for (int i = 0; i < n; ++i) {
     if (done[i]) continue;
     vd_ctx* c = b->win[i];
     const vd_status s = vd_autotune(c, nullptr);
     if (s < 0) return s;
+    leaders.push_back(c);
     for (int k = i; k < n; ++k) {
       vd_ctx* o = b->win[k];
       if (o->W == c->W && o->H == c->H && o->N == c->N && o->dp.K == c->dp.K &&
@@ -977,6 +1020,41 @@ static vd_status batch_autotune(vd_batch* b) {
       }
     }
   }
+  if (n < 2 || n_iters < 1) return VD_OK;
+  std::vector<std::pair<int, int>> cand;   // (threads, blocks per SM)
+  for (int ti = 0; ti < 2; ++ti)
+    for (int bps = 1; bps <= VD_SCORE_BPS_MAX; ++bps) {
+      bool ok = true;
+      for (vd_ctx* c : leaders) {
+        float best = INFINITY;
+        for (int a = 0; a < 2; ++a)
+          for (int q = 0; q < VD_SCORE_BPS_MAX; ++q) best = fminf(best, c->tune_meas.score_ms[a][q]);
+        ok = ok && c->tune_meas.score_ms[ti][bps - 1] <= kBatchTrialMargin * best;
+      }
+      if (ok) cand.push_back({ti ? 512 : 256, bps});
+    }
+  if (cand.size() < 2) return VD_OK;
+  const int trial_iters = n_iters < 2 ? n_iters : 2;
+  float best = INFINITY;
+  std::pair<int, int> pick = cand[0];
+  for (const auto& cs : cand) {
+    batch_set_score_shape(b, cs.first, cs.second);
+    vd_status s = batch_capture(b, trial_iters, true);
+    if (s < 0) return s;
+    float ms = 0.0f;
+    const cudaError_t e = batch_time_run(b, &ms);
+    if (e != cudaSuccess) {
+      b->key.clear();
+      vd_set_error(cudaGetErrorString(e));
+      return VD_ERR_CUDA;
+    }
+    if (ms < best) {
+      best = ms;
+      pick = cs;
+    }
+  }
+  b->key.clear();                     // the run that follows captures its own graph
+  batch_set_score_shape(b, pick.first, pick.second);
   return VD_OK;
 }
 
@@ -1053,7 +1131,7 @@ extern "C" vd_status vd_batch_run(vd_batch* b, int n_iters, int flags, int* dege
     if (!flows_ready(c)) return VD_ERR_STATE;
   const bool boot = (flags & VD_BATCH_BOOTSTRAP) != 0;
   if (flags & VD_BATCH_AUTOTUNE) {
-    const vd_status s = batch_autotune(b);
+    const vd_status s = batch_autotune(b, n_iters);
     if (s < 0) return s;
   }
   // signature of the launches this run issues
