@@ -391,6 +391,27 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
 
 
 
+def pipelined_steps(n, bufs, stage, run, drain, submit):
+    """n steps over two alternating buffers: step k runs bufs[k % 2] on the
+    calling thread while submit() (a one-worker pool) drains the previous
+    step's buffer and stages the next step's into it.  Every step is staged
+    before its run and drained after it, exactly once; a buffer is staged
+    again only after its previous step was drained."""
+    stage(bufs[0])
+    for k in range(n):
+        cur, other = bufs[k % 2], bufs[(k + 1) % 2]
+
+        def side_work(k=k, other=other):
+            if k > 0:
+                drain(other)
+            if k + 1 < n:
+                stage(other)
+
+        fut = submit(side_work)
+        run(cur)
+        fut.result()
+    drain(bufs[(n - 1) % 2])
+
 def run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, world):
     """End-to-end throughput through the C ABI with host buffers: every step
     pushes one batch of flows from pinned host memory, runs the batch and
@@ -437,20 +458,9 @@ def run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, worl
         barrier(pg)
         with concurrent.futures.ThreadPoolExecutor(max_workers=1) as pool:
             t0 = time.perf_counter()
-            stage(bufs[0])
-            for k in range(n_e2e):
-                cur, other = bufs[k % 2], bufs[(k + 1) % 2]
-
-                def side_work(k=k, other=other):
-                    if k > 0:
-                        drain(other)
-                    if k + 1 < n_e2e:
-                        stage(other)
-
-                fut = pool.submit(side_work)
-                V.vd_batch_run(cur, iters, V.VD_BATCH_BOOTSTRAP)
-                fut.result()
-            drain(bufs[(n_e2e - 1) % 2])
+            pipelined_steps(n_e2e, bufs, stage,
+                            lambda x: V.vd_batch_run(x, iters, V.VD_BATCH_BOOTSTRAP),
+                            drain, pool.submit)
             torch.cuda.synchronize()
             dt = max_over_ranks(pg, time.perf_counter() - t0, dev)
     finally:
