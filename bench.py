@@ -472,6 +472,7 @@ def run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, worl
                     "vd_get_poses per window; two batches alternate so that one batch's "
                     "copies overlap the other's run"}
 
+
 def run_rgbd64(args, rank, world, local, pg):
     """64 windows with an RGB-D prior, sizes drawn from 320x240 / 640x480 /
     1216x368 and N from 3..8 (seeds 5000..5063), 5 EM iterations each: one
