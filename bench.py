@@ -221,6 +221,24 @@ def cpu_cores_used():
     return 1
 
 
+def host_cpu():
+    """The host the oracle ran on: its CPU model (or part number) and core count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                k, _, v = ln.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    model = v.strip()
+                    if k.strip() != "CPU part":
+                        break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 # ------------------------------------------------------------------ our arm
 def _timed(stream, flush, fn, steps):
     """CUDA-event time of `steps` calls of fn on `stream`, L2 flushed before each."""
@@ -660,6 +678,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": workload_config(args.batch, 1),
                 "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cpu_cores_used(),
+                                 "host": host_cpu(),
                                  "kind": "oracle", "sample": desc},
                 "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -678,6 +697,7 @@ def main():
         if not args.no_cpu and world == 1:   # the host baseline: rank 0 of a 1-GPU run only
             v, dt, desc = oracle_sample()
             line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cpu_cores_used(),
+                                    "host": host_cpu(),
                                     "kind": "oracle", "sample": desc}
         print(json.dumps(line))
     if pg is not None:
