@@ -94,6 +94,21 @@ def test_se3_exp_log_roundtrip_and_compose():
     assert np.allclose(R @ [1, 0, 0], [0, 1, 0], atol=1e-15)
 
 
+def test_se3_exp_equals_the_matrix_exponential():
+    """exp of the 4x4 twist matrix [[w^, v], [0, 0]] (a library routine, not
+    the closed form the oracle uses), from the series branch to large angles."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(5)
+    for mag in [1e-7, 1e-4, 0.3, 1.5, 3.0]:
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        w, v = ax * mag, rng.normal(size=3)
+        Xi = np.zeros((4, 4))
+        Xi[:3, :3] = [[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]]
+        Xi[:3, 3] = v
+        assert np.allclose(geometry.se3_exp(np.concatenate([w, v])), expm(Xi)[:3], atol=1e-12)
+
+
 def test_bilinear_reproduces_affine_fields_and_grid_values():
     H, W = 7, 9
     v, u = np.mgrid[0:H, 0:W]

@@ -45,6 +45,17 @@ def test_sideways_translation_over_a_plane(shift):
     assert v == c == s == (W - abs(shift)) / W
 
 
+def test_two_projections_in_one_nearest_pixel_cell():
+    # tau_x = 1/fx moves a point by rho pixels: pixel 3 (rho 5/8) lands on
+    # x = 3.625 and pixel 4 (rho 1/4) on x = 4.25, both nearest to pixel 4:
+    # two visible depth pixels, one covered cell
+    rho = np.full((H, W), np.nan, np.float32)
+    rho[5, 3], rho[5, 4] = 0.625, 0.25
+    x, y, inside = vc.project_f32(rho, K, _pose(t=(1.0 / K[0], 0, 0)), W, H)
+    assert x[5, 3] == 3.625 and x[5, 4] == 4.25 and y[5, 3] == 5.0
+    assert vc.counts(rho, K, _pose(t=(1.0 / K[0], 0, 0)), W, H) == (2, 2, 1)
+
+
 def test_camera_past_the_plane_sees_nothing():
     # h_z = 1 + rho tau_z = 1 - 2 < 0 for every pixel
     assert vc.counts(_plane(0.25), K, _pose(t=(0, 0, -8.0)), W, H) == (W * H, 0, 0)
@@ -113,6 +124,7 @@ def test_harmonic_mean_stride_and_keyframe():
     assert vc.stride([0.95, 0.81, 0.62, 0.4], 0.7) == 3
     assert vc.stride([0.95, 0.81], 0.7) == 2            # none below: the last frame
     assert vc.stride([0.5, 0.9], 0.7) == 1
+    assert vc.stride([0.9, 0.7, 0.5], 0.7) == 3       # equal is not below
     assert vc.is_keyframe(0.49, 0.5) and not vc.is_keyframe(0.5, 0.5)
 
 
