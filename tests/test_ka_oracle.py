@@ -29,6 +29,25 @@ def test_zero_residual_at_the_true_pose_on_plane_interiors():
     assert np.median(np.abs(r)) < 1e-12 and np.mean(np.abs(r) < 1e-9) > 0.9
 
 
+def test_hidden_points_are_not_paired_with_the_occluder():
+    # keyframe 1 sees a near patch (depth 3) in front of the back wall (depth
+    # ~9); keyframe 2, without the patch, sees the wall there.  Its wall
+    # points land on the patch with three times the patch's depth: hidden in
+    # keyframe 1, they must not be paired with the occluder
+    T = _T_true()
+    th1, th2 = render(geometry.IDENTITY), render(T)
+    patch = np.zeros(th1.shape, bool)
+    patch[40:70, 60:100] = True
+    th1 = th1.copy()
+    th1[patch] = 3.0
+    n1, ok1 = ka.normals(th1, K)
+    assert ok1[55, 80]                    # the patch interior has normals
+    a = []
+    r, _, _ = ka.residuals(th1, n1, ok1, th2, None, K, T, 1.0, assoc_out=a)
+    assert not patch.ravel()[a[0][1]].any()
+    assert len(r) > 0.5 * W * H and np.median(np.abs(r)) < 1e-12
+
+
 def test_jacobian_matches_finite_differences():
     rng = np.random.default_rng(0)
     T = _start(_T_true(), rng, 0.01, 0.02)

@@ -202,6 +202,13 @@ MUTANTS = [
      [(KA, "test_alignment_recovers_the_pose", ())]),
     ("ka-scale-dropped", "ka", "D = s * t1", "D = t1",
      [(KA, "test_alignment_recovers_the_scale", ())]),
+    ("ka-kink-test-dropped", "ka", "ok_d[1:-1, 1:-1] & (nrm > 0) & smooth)",
+     "ok_d[1:-1, 1:-1] & (nrm > 0))",
+     [(KA, "test_alignment_recovers_the_pose", ()),
+      (KA, "test_zero_residual_at_the_true_pose_on_plane_interiors", ())]),
+    ("ka-occlusion-gate-dropped", "ka", "assoc = inside & ok1[li, lj] & valid_depth(th1) & agree",
+     "assoc = inside & ok1[li, lj] & valid_depth(th1)",
+     [(KA, "test_hidden_points_are_not_paired_with_the_occluder", ())]),
     ("ka-cauchy-weight", "ka", "w = C / (1.0 + (r / c) ** 2)", "w = C / (1.0 + np.abs(r / c))",
      [(KA, "test_robust_kernel_downweights_corrupted_depth", ()),
       (KA, "test_alignment_recovers_the_pose", ())]),
