@@ -14,7 +14,9 @@ A change that leaves the defined result unchanged is not a slip and is not
 listed: for example the side on which the mean-shift step is applied moves
 the iterates but not the fixed point (the weighted mean of the tangent
 coordinates is zero), and a different tie rule between equal energies picks
-an equal value.
+an equal value.  Nor are choices the paper leaves open and that no closed
+form decides (the order of the chain directions over the iterations): the
+oracle fixes them and the GPU parity replays them.
 
 The mistakes are planted in the oracle only, on the CPU; nothing here runs
 the CUDA path.
@@ -125,6 +127,14 @@ MUTANTS = [
     ("model-rgbd-uniform-density", "model", "e0 = 1.0 / (p.prior_w_uniform * rhat)",
      "e0 = 1.0 / p.prior_w_uniform",
      [(PINS, "test_rgbd_prior_closed_forms", ())]),
+    ("model-behind-camera-free", "model", "np.where(obs, fisk.L_BEHIND, 0.0)", "np.where(obs, 0.0, 0.0)",
+     [(PINS, "test_behind_camera_and_unobserved_terms", ())]),
+    ("model-unobserved-emission", "model", "np.where(obs, 0.0, p.outlier_density)",
+     "np.where(obs, 0.0, 0.0)",
+     [(PINS, "test_behind_camera_and_unobserved_terms", ())]),
+    ("hmm-prior-rigidness-inverted", "hmm", "qh = np.where(valid, e1h / (e1h + e0h), 0.0)",
+     "qh = np.where(valid, e0h / (e1h + e0h), 0.0)",
+     [(PINS, "test_prior_rigidness_at_a_perfect_prior", ())]),
     # ---- depth M-step
     ("depth-perturbation-scale", "depth", "0.5 * 2.0 ** (-it)", "0.5 * 2.0 ** (it)",
      [(PINS, "test_hypotheses_distribution_and_sharing", ())]),
@@ -135,6 +145,8 @@ MUTANTS = [
     ("depth-propagated-value-not-written", "depth", "        new[v, u] = cur\n",
      "        new[v, u] = rho_star[v, u]\n",
      [(PINS, "test_split_propagation_equals_naive_sequential", (0,))]),
+    ("depth-hierarchical-coarse-test", "depth", "take = E_up < E_star", "take = E_up > E_star",
+     [(PINS, "test_propagation_never_raises_a_pixels_energy", (0,))]),
     ("depth-argmin-keeps-first-slot", "depth", "best = np.where(take, cands[k], best)",
      "best = np.where(take & (k == 0), cands[k], best)",
      [(PINS, "test_argmin_finds_true_depth_among_candidates", ()),
@@ -143,6 +155,8 @@ MUTANTS = [
     ("pose-meanshift-weight-sign", "pose", "w = np.exp(-0.5 * np.sum(d * d * inv_var, axis=1))",
      "w = np.exp(0.5 * np.sum(d * d * inv_var, axis=1))",
      [(PINS, "test_meanshift_cases", ())]),
+    ("pose-triplet-duplicates", "pose", "if len(set(idx)) == 3:", "if True:",
+     [(PINS, "test_sample_triplets_are_distinct_indices", ())]),
     ("pose-rigid-threshold", "pose", "(S.q[t - 1] > np.float32(0.5))", "(S.q[t - 1] >= np.float32(0.0))",
      [(PINS, "test_pose_step_skips_degenerate_frame", ())]),
     ("pose-bearing-principal-point", "pose", "(xo[:, 0] - cx) / fx", "(xo[:, 0] - cy) / fx",

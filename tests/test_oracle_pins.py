@@ -269,6 +269,33 @@ def test_energy_minimum_at_true_depth_noise_free():
     assert np.allclose(E_star, model.energy(P, S, iu, iv, rho_star, p1), rtol=0, atol=0)
 
 
+def test_behind_camera_and_unobserved_terms():
+    """The three cases of a flow term: observed and in front (Fisk energy),
+    observed but behind camera t (the constant L_BEHIND, rigid emission 0),
+    not observed because x_{t-1} left the image (energy 0, both emissions
+    P0)."""
+    win = synth.make_window("planes160", 0, noisy=False)
+    P = model.problem_from_window(win)
+    p = _params(win)
+    G = np.stack([geometry.IDENTITY] * (P.N + 1))
+    iu, iv = model.pixel_grid(P)
+    rho = np.full((P.H, P.W), 0.5)
+    # camera 1 moves 10 units forward: z = 1 + 0.5 * (-10) < 0 for every pixel
+    G[1] = geometry.IDENTITY.copy()
+    G[1][2, 3] = -10.0
+    ell, e1, ok = model.flow_terms(P, G, iu, iv, rho, p)
+    assert not ok[0].any()
+    assert np.all(ell[0] == fisk.L_BEHIND) and np.all(e1[0] == 0.0)
+    # frame 1 behind: flow 2 has no observation at x_1
+    assert np.all(ell[1] == 0.0) and np.all(e1[1] == p.outlier_density)
+    # camera 1 shifted sideways by 1000 px: x_1 leaves the image, flow 2 unobserved
+    G[1] = geometry.IDENTITY.copy()
+    G[1][0, 3] = 1000.0 / (P.K[0] * 0.5)
+    ell, e1, ok = model.flow_terms(P, G, iu, iv, rho, p)
+    assert np.all(ok[0]) and np.all(ell[0] > 0)
+    assert np.all(ell[1] == 0.0) and np.all(e1[1] == p.outlier_density)
+
+
 def test_argmin_finds_true_depth_among_candidates():
     win = synth.make_window("planes160", 1, noisy=False)
     P = model.problem_from_window(win)
@@ -363,6 +390,28 @@ def test_hierarchical_with_window_covering_chain_and_scale1_reduces():
         assert np.array_equal(full, hier)
 
 
+@pytest.mark.parametrize("direction", [0, 1])
+def test_propagation_never_raises_a_pixels_energy(direction):
+    """Every pass takes a value only when it lowers the pixel's energy, so
+    after the full and the hierarchical propagation (coarse cells of 4,
+    windows of 5) no pixel's energy is above its own candidate's."""
+    win = synth.make_window("planes160", 5, noisy=True)
+    P0 = model.problem_from_window(win)
+    P = model.Problem(24, 16, P0.N, P0.K, np.ascontiguousarray(P0.flow[:, :16, :24]))
+    S = model.State(rho=np.full((16, 24), 0.05, np.float32), q=np.ones((P.N, 16, 24), np.float32),
+                    qhat=np.zeros((16, 24), np.float32), G=_truth_state(win, P0).G)
+    p = _params(win, n_hyp=4, hierarchical=1, hier_scale=4, hier_window=5)
+    c = depth.hypotheses(P, S.rho, 0, p)
+    rho_star, E_star, _ = depth.argmin_candidates(P, S, c, p)
+    iu, iv = model.pixel_grid(P)
+    for fn in (depth.propagate, depth.hierarchical):
+        new, E_new = fn(P, S, rho_star, E_star, direction, p)
+        E = model.energy(P, S, iu, iv, new, p)
+        assert np.array_equal(E, E_new)
+        assert np.all(E <= E_star)
+        assert np.any(E < E_star)        # the pass did propagate something
+
+
 # ---------------------------------------------------------------- E-step
 def test_estep_moving_blobs_get_low_rigidness():
     win = synth.make_window("boxes640_stereo", 7, noisy=True, size=(160, 120), N=3)
@@ -396,6 +445,24 @@ def test_stereo_prior_optimum_is_the_prior():
     assert np.allclose(rhat, win.stereo_disp / np.float32(P.K[0] * 0.25), rtol=1e-7)
     l0 = fisk.inlier_energy(0.0, p.fisk_alpha0, 2.0, p.outlier_density)
     assert np.allclose(E0, l0, rtol=1e-5)
+
+
+def test_prior_rigidness_at_a_perfect_prior():
+    """q_hat is the isolated posterior p1 / (p1 + P0) at the new depth: at the
+    prior's own value (residual 0) and beta = 2, p1(0) = 1 / (pi alpha^2)."""
+    win = synth.make_window("boxes640_stereo", 1, noisy=False, size=(128, 96), N=2)
+    P = model.problem_from_window(win)
+    S = model.State(rho=(1.0 / win.depth0).astype(np.float32), q=np.ones((P.N, P.H, P.W), np.float32),
+                    qhat=np.ones((P.H, P.W), np.float32), G=win.G.copy())
+    p = _params(win)
+    rhat = P.prior_rho()
+    _, qhat, C = hmm.rigidness_estep(P, S, rhat.astype(np.float64), 0, p)
+    a = p.fisk_alpha0
+    want = 1.0 / (1.0 + p.outlier_density * math.pi * a * a)
+    valid = np.isfinite(rhat)
+    assert valid.mean() > 0.5
+    assert np.allclose(qhat[valid], want, rtol=1e-6)
+    assert np.all(qhat[~valid] == 0.0)
 
 
 def test_rgbd_prior_closed_forms():
@@ -453,6 +520,25 @@ def test_pose_step_recovers_first_pose_from_true_depth():
     # rigid-set ordering and the sample draws are deterministic
     rs = pose.rigid_set(P, S, 1, p)
     assert np.all(np.diff(rs["j"]) > 0)
+
+
+def test_sample_triplets_are_distinct_indices():
+    """A P3P sample is three different rigid pixels: for a set of 3 every
+    drawn triplet is a permutation of {0, 1, 2} (or the sample is void after
+    the retries); larger sets give distinct in-range indices."""
+    p = model.Params()
+    for n in (3, 4, 50):
+        void = 0
+        for g in range(200):
+            tri = pose.draw_triplet(n, g, 1, 0, p)
+            if tri is None:
+                void += 1
+                continue
+            assert len(set(tri)) == 3 and all(0 <= i < n for i in tri)
+        # a draw is distinct with probability n (n-1) (n-2) / n^3; 8 tries
+        p_void = (1 - n * (n - 1) * (n - 2) / n ** 3) ** 8
+        assert abs(void - 200 * p_void) <= 4 * math.sqrt(200 * p_void * (1 - p_void)) + 1
+    assert pose.draw_triplet(3, 7, 2, 1, p) == pose.draw_triplet(3, 7, 2, 1, p)
 
 
 def test_pose_step_skips_degenerate_frame():
