@@ -269,7 +269,7 @@ def _cfg_driving(rng, noisy, W=1216, H=368, N=6):
         T = np.concatenate([R, d[:, None]], axis=1)
         G.append(_compose(T, G[-1]))
     G = np.stack(G)
-    flow, mv = _flows(rng, sc, G, W, H, N, K, 1.0, 2.0, 0.05, noisy, (8, 40))
+    flow, mv = _flows(rng, sc, G, W, H, N, K, 1.0, 2.0, 0.05 if noisy else 0.0, noisy, (8, 40))
     return W, H, N, K, sc, G, flow, mv, dict(fisk_alpha0=1.0, fisk_beta=2.0, n_hyp=128,
                                               n_iters=8, dmin=2.0, dmax=80.0)
 
