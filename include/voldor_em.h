@@ -320,6 +320,13 @@ vd_status vd_batch_get_stats(vd_batch* b, vd_batch_stats* out);
  * a tensor-core wait that gives up returns VD_ERR_TIMEOUT. */
 typedef struct vd_cnn vd_cnn;
 #define VD_CNN_LAYERS 6
+/* Self-test of the failure path of the tensor-core kernels' waits: one
+ * thread waits on an mbarrier that nothing completes, with the bounded wait
+ * the convolution's roles use (`polls` polls, 1..2^20), gives up, sets the
+ * error flag and returns; the host reads the flag.  Returns VD_ERR_TIMEOUT,
+ * the status of a convolution whose wait ran out (VD_ERR_ARG for polls out
+ * of range); the device stays usable.  Synchronises `cuda_stream`. */
+vd_status vd_check_bounded_wait(int polls, void* cuda_stream);
 typedef struct {
   double fx, fy, cx, cy;    /* intrinsics of the window                     */
   double T1[12];            /* pose of flow 1, [R | tau] row-major           */

@@ -233,12 +233,25 @@ struct VdConvShape {
 // Bounded wait that also gives up once another role of the CTA has set
 // `abort` (checked every 256 polls).
 __device__ __forceinline__ bool vd_mbar_wait_or_abort(uint64_t* m, uint32_t phase,
-                                                      volatile int* abort) {
-  for (int i = 0; i < CNN_WAIT_LIMIT; ++i) {
+                                                      volatile int* abort,
+                                                      int limit = CNN_WAIT_LIMIT) {
+  for (int i = 0; i < limit; ++i) {
     if (vd_mbar_try_wait(m, phase)) return true;
     if ((i & 255) == 255 && *abort) return false;
   }
   return false;
+}
+
+// Self-test of that failure path: one thread waits on a barrier that
+// nothing completes, gives up after `polls` polls and sets the error flag,
+// as a role of the convolution does; the host reads the flag.
+__global__ void k_wait_probe(int polls, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort;
+  if (threadIdx.x != 0) return;
+  abort = 0;
+  vd_mbar_init(&bar, 1);
+  if (!vd_mbar_wait_or_abort(&bar, 0, &abort, polls)) *err = 1;
 }
 
 // Persistent, warp-specialised: CTA b takes tiles b, b + gridDim.x, ...
@@ -940,6 +953,32 @@ static vd_status cnn_check_err(vd_cnn* n, cudaStream_t s) {
   int h = 0;
   VD_CU(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   VD_CU(cudaStreamSynchronize(s));
+  if (h) {
+    vd_set_error("a tensor-core wait gave up");
+    return VD_ERR_TIMEOUT;
+  }
+  return VD_OK;
+}
+
+extern "C" vd_status vd_check_bounded_wait(int polls, void* cuda_stream) {
+  if (polls < 1 || polls > (1 << 20)) return VD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  int h = 0;
+  cudaError_t e = cudaMallocAsync((void**)&d, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_probe<<<1, 32, 0, s>>>(polls, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (d) cudaFreeAsync(d, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
   if (h) {
     vd_set_error("a tensor-core wait gave up");
     return VD_ERR_TIMEOUT;

@@ -144,6 +144,7 @@ _SIGS = {
     "vd_batch_window": [_P, C.c_int, C.POINTER(_P)],
     "vd_batch_run": [_P, C.c_int, C.c_int, _P],
     "vd_batch_get_stats": [_P, C.POINTER(vd_batch_stats)],
+    "vd_check_bounded_wait": [C.c_int, _P],
     "vd_cnn_create": [C.c_int, C.c_ulonglong, C.POINTER(_P)],
     "vd_cnn_destroy": [_P],
     "vd_cnn_layout": [_P, C.POINTER(C.c_int), _P, _P, _P, _P],
@@ -579,6 +580,11 @@ def vd_cnn_create(n_flows, seed=0):
     h = C.c_void_p()
     _call("vd_cnn_create", int(n_flows), int(seed), C.byref(h))
     return h
+
+
+def vd_check_bounded_wait(polls, stream=None):
+    """Raises VoldorError with status VD_ERR_TIMEOUT: the bounded wait gave up."""
+    _call("vd_check_bounded_wait", int(polls), stream)
 
 
 def vd_cnn_destroy(net):

@@ -203,3 +203,19 @@ def test_learned_bootstrap_runs_the_em(V):
     finally:
         V.vd_destroy(ctx)
         V.vd_cnn_destroy(net)
+
+
+def test_a_wait_that_runs_out_reports_timeout_and_the_device_stays_usable(V):
+    """The failure path of the tensor-core waits, made to run out on purpose
+    by a barrier nothing completes: the kernel gives up after the poll
+    budget, the host reads VD_ERR_TIMEOUT, and the device keeps working."""
+    import torch
+    for polls in (1, 256, 4096):
+        with pytest.raises(V.VoldorError) as e:
+            V.vd_check_bounded_wait(polls)
+        assert e.value.status == V.VD_ERR_TIMEOUT
+    with pytest.raises(V.VoldorError) as e:
+        V.vd_check_bounded_wait(0)
+    assert e.value.status == V.VD_ERR_ARG
+    x = torch.arange(1024, device="cuda", dtype=torch.float32)
+    assert float(x.sum()) == 1023 * 1024 / 2
