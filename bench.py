@@ -91,6 +91,9 @@ def parse():
                     help="keep the default launch shapes (no vd_autotune; for profiling)")
     ap.add_argument("--phase", default="both", choices=["both", "single", "batch"],
                     help="single: only the one-window run (for profiling); batch: skip it")
+    ap.add_argument("--hierarchical", action="store_true",
+                    help="hierarchical depth propagation (coarse cells of 4 px, windows of "
+                         "32 px) instead of full chains")
     return ap.parse_args()
 
 
@@ -271,7 +274,8 @@ def run_ours(args, rank, world, local, pg):
     pr = win.params
     params = V.vd_params_default(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"],
                                  rho_max=pr["rho_max"], n_hyp=WORK["K"],
-                                 n_pose_samples=WORK["S"], seed=WORK["seed"] + rank)
+                                 n_pose_samples=WORK["S"], seed=WORK["seed"] + rank,
+                                 hierarchical=1 if args.hierarchical else 0)
     W, H, N, iters = win.W, win.H, win.N, WORK["iters"]
     units_per_window = W * H * N * iters
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -348,7 +352,9 @@ def run_ours(args, rank, world, local, pg):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(single_ms, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "phase": "single",
-                "config": {"workload": "driving1216: one window per step"},
+                "config": {"workload": "driving1216: one window per step",
+                           "propagation": "hierarchical (cells 4, windows 32)"
+                           if args.hierarchical else "full chains"},
                 "single_window": single, "roofline": roofline,
                 "gpu_launches": int(prof["total_launches"])}
     return run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream, flush, dev,
@@ -399,7 +405,9 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
             "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": workload_config(nb, world),
+            "config": dict(workload_config(nb, world),
+                           **({"propagation": "hierarchical (cells 4, windows 32)"}
+                              if args.hierarchical else {})),
             "windows_per_s": round(nb * args.steps * world / (total_ms / 1e3), 3),
             "single_window": single, "batch": bstats,
             "roofline": roofline, "stage_ms_per_window": stages,
