@@ -101,6 +101,29 @@ def test_adam_first_step_closed_form():
     assert np.allclose(th, 1 - 5 * 0.01 * g / (np.abs(g) + cnn.ADAM_EPS), atol=1e-12)
 
 
+def test_heads_and_loss_closed_forms():
+    """z_0 = 0 gives the geometric centre of the range, z_0 = ln 2 twice it,
+    and the rigidness is the logistic function of its channel; the depth
+    loss is the mean squared log ratio of the head's depth to the target,
+    zero (with a zero gradient) where they agree."""
+    rmin, rmax = 0.05, 2.0
+    rc = np.sqrt(rmin * rmax)
+    z = np.zeros((3, 2, 2))
+    z[0, 0, 1] = np.log(2.0)
+    z[1] = [[0.0, np.log(3.0)], [-np.log(3.0), 0.0]]
+    rho, q = cnn.heads(z, rmin, rmax)
+    assert np.allclose(rho, [[rc, 2 * rc], [rc, rc]], rtol=1e-15)
+    assert np.allclose(q[0], [[0.5, 0.75], [0.25, 0.5]], rtol=1e-15)
+    # targets equal to the heads' depth: zero depth loss and gradient
+    q_t = np.full((2, 2, 2), 0.5)
+    mask = np.ones((2, 2))
+    L, dz = cnn.loss_and_grad(z, rho, q_t, mask, rmin, rmax, 0.0)
+    assert abs(L) < 1e-28 and np.abs(dz[0]).max() < 1e-14
+    # targets a factor e off everywhere: loss 1
+    L, _ = cnn.loss_and_grad(z, rho * np.e, q_t, mask, rmin, rmax, 0.0)
+    assert L == pytest.approx(1.0, rel=1e-12)
+
+
 def test_shapes_and_input_planes():
     assert cnn.in_channels(6) == 16 and cnn.in_channels(3) == 16 and cnn.in_channels(8) == 32
     assert cnn.layer_shapes(6) == [(16, 32)] + [(32, 32)] * 4 + [(32, 7)]

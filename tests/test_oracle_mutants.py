@@ -135,6 +135,9 @@ MUTANTS = [
     ("hmm-prior-rigidness-inverted", "hmm", "qh = np.where(valid, e1h / (e1h + e0h), 0.0)",
      "qh = np.where(valid, e0h / (e1h + e0h), 0.0)",
      [(PINS, "test_prior_rigidness_at_a_perfect_prior", ())]),
+    ("em-initial-range", "em", "rho = rmin + np.float32(u * np.float32(rmax - rmin))",
+     "rho = rmin + np.float32(u * rmax)",
+     [(PINS, "test_initial_inverse_depth_is_uniform_in_range_or_the_prior", ())]),
     # ---- depth M-step
     ("depth-perturbation-scale", "depth", "0.5 * 2.0 ** (-it)", "0.5 * 2.0 ** (it)",
      [(PINS, "test_hypotheses_distribution_and_sharing", ())]),
@@ -178,6 +181,8 @@ MUTANTS = [
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
     ("eightpoint-second-rotation", "eightpoint", "R2 = U @ WMAT.T @ Vt", "R2 = U @ WMAT @ Vt",
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
+    ("eightpoint-translation-column", "eightpoint", "t = U[:, 2]", "t = Vt[2]",
+     [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
     ("eightpoint-cheirality-sign", "eightpoint", "m12 = -np.sum(Ra * b, 1)", "m12 = np.sum(Ra * b, 1)",
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
     # ---- pose covariance
@@ -188,6 +193,9 @@ MUTANTS = [
      [(PC, "test_robust_start_is_the_gaussian_scale_and_ignores_outliers", ())]),
     ("posecov-unbiased-normalisation", "posecov", "dn.T @ dn / n_in", "dn.T @ dn / (n_in - 1)",
      [(PC, "test_symmetric_star_closed_form", ())]),
+    ("posecov-start-mean", "posecov", "s = 1.4826 * np.median(np.abs(d), axis=0)",
+     "s = 1.4826 * np.mean(np.abs(d), axis=0)",
+     [(PC, "test_robust_start_is_the_gaussian_scale_and_ignores_outliers", ())]),
     ("posecov-floor-min", "posecov", "np.maximum(w, eps)", "np.minimum(w, eps)",
      [(PC, "test_eigenvalue_floor_and_symmetry", ())]),
     ("posecov-coordinates-side", "posecov", "geometry.compose(mi, T)", "geometry.compose(T, mi)",
@@ -200,6 +208,8 @@ MUTANTS = [
      [(VC, "test_harmonic_mean_stride_and_keyframe", ())]),
     ("vc-stride-boundary", "vc", "if s < tau_stride:", "if s <= tau_stride:",
      [(VC, "test_harmonic_mean_stride_and_keyframe", ())]),
+    ("vc-coverage-over-depth-pixels", "vc", "c = n_cov / (W * H)", "c = n_cov / n_depth if n_depth else 0.0",
+     [(VC, "test_coverage_is_a_fraction_of_the_image_not_of_the_depth_pixels", ())]),
     ("vc-invalid-depth-counted", "vc", "vis = valid & inside", "vis = inside",
      [(VC, "test_invalid_depths_are_not_depth_pixels", ())]),
     ("vc-inside-one-past", "vc", "(x <= f32(W - 1))", "(x <= f32(W))",
@@ -237,6 +247,12 @@ MUTANTS = [
      [(CNN, "test_adam_first_step_closed_form", ())]),
     ("cnn-bf16-truncation", "cnn", "(u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u & 0xFFFF0000",
      [(CNN, "test_bf16_rounding_matches_torch_and_known_values", ())]),
+    ("cnn-depth-head-sign", "cnn", "rho = np.clip(rho_c * np.exp(z[0]), rho_min, rho_max)",
+     "rho = np.clip(rho_c * np.exp(-z[0]), rho_min, rho_max)",
+     [(CNN, "test_heads_and_loss_closed_forms", ())]),
+    ("cnn-loss-centre-sign", "cnn", "e = z[0] + 0.5 * np.log(rho_min * rho_max) - np.log(rho_t)",
+     "e = z[0] - 0.5 * np.log(rho_min * rho_max) - np.log(rho_t)",
+     [(CNN, "test_heads_and_loss_closed_forms", ())]),
     ("cnn-bce-gradient-sign", "cnn", "dz[1:] = w_q * m * (q - q_t) / (nq * nm)",
      "dz[1:] = w_q * m * (q_t - q) / (nq * nm)",
      [(CNN, "test_backward_matches_finite_differences", ())]),

@@ -412,6 +412,25 @@ def test_propagation_never_raises_a_pixels_energy(direction):
         assert np.any(E < E_star)        # the pass did propagate something
 
 
+def test_initial_inverse_depth_is_uniform_in_range_or_the_prior():
+    from scipy import stats
+    win = synth.make_window("planes160", 0, noisy=False)
+    P = model.problem_from_window(win)
+    p = _params(win, rho_min=0.1, rho_max=0.5)
+    rho = em.initial_rho(P, p)
+    assert rho.dtype == np.float32
+    assert np.all((rho >= np.float32(0.1)) & (rho <= np.float32(0.5)))
+    assert stats.kstest((rho.ravel().astype(np.float64) - 0.1) / 0.4, "uniform").statistic < 0.02
+    # with a prior: its inverse depth (clamped) where valid, the draw at holes
+    win = synth.make_window("boxes640_stereo", 1, noisy=True, size=(128, 96), N=2)
+    P = model.problem_from_window(win)
+    p = _params(win)
+    rho = em.initial_rho(P, p)
+    pr = P.prior_rho()
+    ok = np.isfinite(pr)
+    assert 0 < (~ok).sum() and np.array_equal(rho[ok], np.clip(pr[ok], p.f32("rho_min"), p.f32("rho_max")))
+
+
 # ---------------------------------------------------------------- E-step
 def test_estep_moving_blobs_get_low_rigidness():
     win = synth.make_window("boxes640_stereo", 7, noisy=True, size=(160, 120), N=3)

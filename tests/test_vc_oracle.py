@@ -74,6 +74,14 @@ def test_invalid_depths_are_not_depth_pixels():
     assert vc.scores(np.full((H, W), np.nan, np.float32), K, _pose(), W, H) == (0.0, 0.0, 0.0)
 
 
+def test_coverage_is_a_fraction_of_the_image_not_of_the_depth_pixels():
+    # only the left half has depth: all of it is visible and covers half of
+    # the second image (V = 1, C = 1/2, VC = 2/3)
+    rho = np.full((H, W), np.nan, np.float32)
+    rho[:, :W // 2] = 0.25
+    assert vc.scores(rho, K, _pose(), W, H) == (1.0, 0.5, pytest.approx(2.0 / 3.0))
+
+
 def test_receding_camera_contracts_the_image():
     # tau_z = +2 on a plane at depth 4: h = (r, 1.5); every point lands at
     # c + (p - c) / 1.5.  Coverage counted with exact rationals (no ties:
