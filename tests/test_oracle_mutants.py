@@ -75,6 +75,8 @@ MUTANTS = [
     ("hmm-initial-distribution", "hmm", "x0, x1 = 0.5 * e0[0], 0.5 * e1[0]",
      "x0, x1 = 0.5 * e0[0], 0.25 * e1[0]",
      [(PINS, "test_forward_backward_matches_enumeration", (5,))]),
+    ("hmm-transition-swapped", "hmm", "g, h = gamma, 1.0 - gamma", "g, h = 1.0 - gamma, gamma",
+     [(PINS, "test_forward_backward_matches_enumeration", (5,))]),
     ("hmm-confidence-denominator", "hmm",
      "C = q.astype(np.float64).sum(0) / P.N", "C = q.astype(np.float64).sum(0) / (P.N + 1)",
      [(PINS, "test_estep_moving_blobs_get_low_rigidness", ())]),
@@ -124,6 +126,10 @@ MUTANTS = [
      [(PINS, "test_stereo_prior_optimum_is_the_prior", ())]),
     ("model-rgbd-sigma-unscaled", "model", "sig = p.prior_c_sigma * rhat", "sig = p.prior_c_sigma",
      [(PINS, "test_rgbd_prior_closed_forms", ())]),
+    ("model-rgbd-normaliser", "model",
+     "logk = math.log(math.sqrt(2 * math.pi) * p.prior_c_sigma / p.prior_w_uniform)",
+     "logk = math.log(2 * math.pi * p.prior_c_sigma / p.prior_w_uniform)",
+     [(PINS, "test_rgbd_prior_closed_forms", ())]),
     ("model-rgbd-uniform-density", "model", "e0 = 1.0 / (p.prior_w_uniform * rhat)",
      "e0 = 1.0 / p.prior_w_uniform",
      [(PINS, "test_rgbd_prior_closed_forms", ())]),
@@ -140,6 +146,9 @@ MUTANTS = [
      [(PINS, "test_initial_inverse_depth_is_uniform_in_range_or_the_prior", ())]),
     # ---- depth M-step
     ("depth-perturbation-scale", "depth", "0.5 * 2.0 ** (-it)", "0.5 * 2.0 ** (it)",
+     [(PINS, "test_hypotheses_distribution_and_sharing", ())]),
+    ("depth-perturbation-one-sided", "depth",
+     "a = np.float32(np.float32(2.0) * u) - np.float32(1.0)", "a = u",
      [(PINS, "test_hypotheses_distribution_and_sharing", ())]),
     ("depth-uniform-range", "depth", "c = rmin + np.float32(u * rng)", "c = rmin + np.float32(u * rmax)",
      [(PINS, "test_hypotheses_distribution_and_sharing", ())]),
@@ -160,6 +169,10 @@ MUTANTS = [
      [(PINS, "test_meanshift_cases", ())]),
     ("pose-triplet-duplicates", "pose", "if len(set(idx)) == 3:", "if True:",
      [(PINS, "test_sample_triplets_are_distinct_indices", ())]),
+    ("pose-kernel-widths-swapped", "pose",
+     "inv_var = np.array([1 / p.pose_sigma_rot ** 2] * 3 + [1 / st ** 2] * 3)",
+     "inv_var = np.array([1 / st ** 2] * 3 + [1 / p.pose_sigma_rot ** 2] * 3)",
+     [(PINS, "test_meanshift_mode_on_one_rotation_axis_solves_the_scalar_equation", ())]),
     ("pose-rigid-threshold", "pose", "(S.q[t - 1] > np.float32(0.5))", "(S.q[t - 1] >= np.float32(0.0))",
      [(PINS, "test_pose_step_skips_degenerate_frame", ())]),
     ("pose-bearing-principal-point", "pose", "(xo[:, 0] - cx) / fx", "(xo[:, 0] - cy) / fx",
@@ -196,6 +209,8 @@ MUTANTS = [
     ("posecov-start-mean", "posecov", "s = 1.4826 * np.median(np.abs(d), axis=0)",
      "s = 1.4826 * np.mean(np.abs(d), axis=0)",
      [(PC, "test_robust_start_is_the_gaussian_scale_and_ignores_outliers", ())]),
+    ("posecov-six-samples", "posecov", "MIN_INLIERS = 7", "MIN_INLIERS = 6",
+     [(PC, "test_six_samples_cannot_give_a_covariance", ())]),
     ("posecov-floor-min", "posecov", "np.maximum(w, eps)", "np.minimum(w, eps)",
      [(PC, "test_eigenvalue_floor_and_symmetry", ())]),
     ("posecov-coordinates-side", "posecov", "geometry.compose(mi, T)", "geometry.compose(T, mi)",
@@ -253,6 +268,13 @@ MUTANTS = [
     ("cnn-loss-centre-sign", "cnn", "e = z[0] + 0.5 * np.log(rho_min * rho_max) - np.log(rho_t)",
      "e = z[0] - 0.5 * np.log(rho_min * rho_max) - np.log(rho_t)",
      [(CNN, "test_heads_and_loss_closed_forms", ())]),
+    ("cnn-bias-dropped", "cnn",
+     "z = np.broadcast_to(np.asarray(b, np.float64)[:, None, None], (W.shape[0], H, Wd)).copy()",
+     "z = np.zeros((W.shape[0], H, Wd))",
+     [(CNN, "test_conv_equals_channel_sum_of_library_correlation", ())]),
+    ("cnn-adam-second-moment", "cnn", "v = ADAM_B2 * v + (1 - ADAM_B2) * g * g",
+     "v = ADAM_B2 * v + (1 - ADAM_B2) * np.abs(g)",
+     [(CNN, "test_adam_first_step_closed_form", ())]),
     ("cnn-bce-gradient-sign", "cnn", "dz[1:] = w_q * m * (q - q_t) / (nq * nm)",
      "dz[1:] = w_q * m * (q_t - q) / (nq * nm)",
      [(CNN, "test_backward_matches_finite_differences", ())]),

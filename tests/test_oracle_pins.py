@@ -522,6 +522,25 @@ def test_meanshift_cases():
     assert np.abs(geometry.se3_log(geometry.compose(geometry.inverse(far), x))).max() < 1e-12
 
 
+def test_meanshift_mode_on_one_rotation_axis_solves_the_scalar_equation():
+    """Samples T, T and T exp(a e_x) (a rotation about one body axis): every
+    iterate stays on that axis, the tangent coordinates are (a_g - m) e_x
+    exactly, and the mode is the root of sum_g w_g (a_g - m) = 0 with
+    w_g = exp(-(a_g - m)^2 / (2 sigma_rot^2)) nearest the start m = 0."""
+    from scipy import optimize
+    p = model.Params()
+    T = geometry.se3_exp(np.array([0.2, -0.1, 0.3, 2.0, -1.5, 1.0]))   # |tau| ~ 2.7
+    a = 1.5 * p.pose_sigma_rot
+    samples = [T, T, geometry.compose(T, geometry.se3_exp(np.array([a, 0, 0, 0, 0, 0])))]
+    x, _ = pose.meanshift(samples, T, p)
+    d = geometry.se3_log(geometry.compose(geometry.inverse(T), x))
+    assert np.abs(d[1:]).max() < 1e-12
+    ag = np.array([0.0, 0.0, a])
+    f = lambda m: np.sum(np.exp(-0.5 * ((ag - m) / p.pose_sigma_rot) ** 2) * (ag - m))
+    m = optimize.brentq(f, 0.0, a / 2, xtol=1e-15)
+    assert abs(d[0] - m) < 1e-10 and 0 < m < a / 3
+
+
 def test_pose_step_recovers_first_pose_from_true_depth():
     win = synth.make_window("planes160", 4, noisy=False)
     P = model.problem_from_window(win)

@@ -117,6 +117,16 @@ def test_few_samples_are_degenerate_and_the_fit_is_a_fixed_point():
     assert np.allclose(m2, m, atol=1e-12) and np.allclose(S2, S, rtol=1e-9, atol=1e-20)
 
 
+def test_six_samples_cannot_give_a_covariance():
+    # a 6-D covariance needs 7 samples: 6 (however spread) are degenerate
+    mu = _mu(np.random.default_rng(8))
+    a = 1e-3
+    six = [geometry.compose(mu, geometry.se3_exp(sg * a * np.eye(6)[k]))
+           for k in range(3) for sg in (1.0, -1.0)]
+    m, S, n_in, rounds, deg = posecov.fit(six, mu, EPS, sigma0=a * a * np.eye(6))
+    assert deg and n_in == 6 and rounds == 0
+
+
 def test_robust_start_is_the_gaussian_scale_and_ignores_outliers():
     # median |x| of N(0, s^2) is 0.67449 s, so 1.4826 median |x| = s
     rng = np.random.default_rng(7)
