@@ -99,3 +99,14 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 2
     assert line["value"] == 1.0e5 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the contract's keys, the same metric, unit and workload as our arm's line
+    import bench
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["scaling"] == "weak"
+    assert line["vs_baseline"] is None and line["data"] == "synthetic" and line["n_gpus"] == 1
+    assert line["config"] == bench.workload_config(8, 1)
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["unit"] == line["unit"]
+    assert line["e2e"]["d2h_bytes_per_step"] == 0
+    cb = line["cpu_baseline"]
+    assert cb["value"] == line["value"] and cb["cores"] == 1 and cb["host"]["nproc"] >= 1
+    assert "608x184" in cb["sample"] and line["ms_per_step"] > 0
