@@ -196,6 +196,12 @@ MUTANTS = [
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
     ("eightpoint-translation-column", "eightpoint", "t = U[:, 2]", "t = Vt[2]",
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
+    ("eightpoint-one-depth-test", "eightpoint", "return int(np.sum((la > 0) & (lb > 0)))",
+     "return int(np.sum(la > 0))",
+     [(PINS, "test_essential_decomposition_and_cheirality", ())]),
+    ("eightpoint-improper-rotation", "eightpoint", "    if np.linalg.det(U) < 0:\n        U = -U\n",
+     "",
+     [(PINS, "test_essential_decomposition_and_cheirality", ())]),
     ("eightpoint-cheirality-sign", "eightpoint", "m12 = -np.sum(Ra * b, 1)", "m12 = np.sum(Ra * b, 1)",
      [(PINS, "test_eight_point_noise_free_two_planes_is_exact", ())]),
     # ---- pose covariance
@@ -211,6 +217,9 @@ MUTANTS = [
      [(PC, "test_robust_start_is_the_gaussian_scale_and_ignores_outliers", ())]),
     ("posecov-six-samples", "posecov", "MIN_INLIERS = 7", "MIN_INLIERS = 6",
      [(PC, "test_six_samples_cannot_give_a_covariance", ())]),
+    ("posecov-no-convergence-test", "posecov",
+     "if prev is not None and np.array_equal(inl, prev):", "if False:",
+     [(PC, "test_symmetric_star_closed_form", ())]),
     ("posecov-floor-min", "posecov", "np.maximum(w, eps)", "np.minimum(w, eps)",
      [(PC, "test_eigenvalue_floor_and_symmetry", ())]),
     ("posecov-coordinates-side", "posecov", "geometry.compose(mi, T)", "geometry.compose(T, mi)",

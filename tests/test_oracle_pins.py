@@ -205,6 +205,28 @@ def test_eight_point_noise_free_two_planes_is_exact():
     assert min(np.abs(E - Et).max(), np.abs(E + Et).max()) < 1e-7
 
 
+def test_essential_decomposition_and_cheirality():
+    """Every candidate of E = [t]x R is a proper rotation and one of them is
+    (R, t/|t|) up to the sign of t, whatever signs the SVD picks; on the
+    noise-free two-plane flow only the true motion puts the points in front
+    of both cameras (the other three fail for at least half of them)."""
+    rng = np.random.default_rng(9)
+    for _ in range(60):
+        R = geometry.so3_exp(rng.normal(size=3) * 0.3)
+        t = rng.normal(size=3)
+        t /= np.linalg.norm(t)
+        E = geometry.hat(t) @ R * rng.choice([-1.0, 1.0])
+        cands = eightpoint.candidates(E)
+        assert all(abs(np.linalg.det(Rc) - 1.0) < 1e-12 for Rc, _ in cands)
+        assert min(np.abs(Rc - R).max() + min(np.abs(tc - t).max(), np.abs(tc + t).max())
+                   for Rc, tc in cands) < 1e-9
+    win = synth.make_window("planes160", 0, noisy=False)
+    P = model.problem_from_window(win)
+    G1, counts = eightpoint.bootstrap_pose(P, 0.5)
+    c = sorted(counts)
+    assert c[-1] == P.W * P.H and c[-2] <= 0.5 * P.W * P.H
+
+
 def test_eight_point_single_plane_is_degenerate():
     win = synth.make_window("planes160", 0, noisy=False)
     # replace the scene by one fronto-parallel plane at 4 m: a homography, E is not unique
