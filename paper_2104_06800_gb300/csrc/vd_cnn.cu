@@ -794,7 +794,7 @@ static cudaError_t cnn_reserve(vd_cnn* n, int HW) {
   return e;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once.
+// cuTensorMapEncodeTiled from the CUDA driver API (libcuda), looked up once.
 static PFN_cuTensorMapEncodeTiled_v12000 vd_encode_tiled() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
