@@ -247,7 +247,10 @@ def _cfg_boxes(rng, noisy, W=640, H=480, N=5, moving=0.10, dmax=40.0):
                                               n_iters=5, dmin=1.0, dmax=dmax)
 
 
-def _cfg_driving(rng, noisy, W=1216, H=368, N=6):
+def _cfg_driving(rng, noisy, W=1216, H=368, N=6, kerb=False):
+    """kerb: the car boxes stand at the kerbs (|x| >= 2.5 m), leaving the
+    camera's lane clear; otherwise anywhere across the street, so that the
+    camera passes close to some of them."""
     K = (720.0, 720.0, W / 2.0, H / 2.0)
     sc = _Scene()
     cam_h = 1.65
@@ -258,7 +261,10 @@ def _cfg_driving(rng, noisy, W=1216, H=368, N=6):
     sc.planes.append((np.array([-1.0, 0, 0]), -xr))        # right facade x = +xr
     for _ in range(12):
         z = rng.uniform(6.0, 60.0)
-        x = rng.uniform(-xl + 1, xr - 1)
+        if kerb:
+            x = -rng.uniform(2.5, xl - 1) if rng.uniform() < 0.5 else rng.uniform(2.5, xr - 1)
+        else:
+            x = rng.uniform(-xl + 1, xr - 1)
         lo = np.array([x - 0.9, cam_h - 1.5, z - 2.0])
         hi = np.array([x + 0.9, cam_h, z + 2.0])
         sc.boxes.append((lo, hi))
@@ -279,6 +285,7 @@ CONFIGS = {
     "planes160": "160x120 N=3, two random planes 2-10 m, small random motion, Fisk noise 0.5 px",
     "boxes640_stereo": "640x480 N=5, ground + 20 boxes 1-40 m, 10% moving blobs, stereo prior",
     "driving1216": "1216x368 N=6, road + facades + boxes 2-80 m, forward 1-1.5 m/frame, 5% moving",
+    "driving1216_kerb": "driving1216 with the car boxes at the kerbs (the camera's lane clear)",
     "rgbd_batch": "320x240 / 640x480 / 1216x368, N 3..8, RGB-D prior 1% noise 10% holes",
 }
 
@@ -290,9 +297,9 @@ def _config(name, rng, noisy, N, size):
     if name == "boxes640_stereo":
         W, H = size or (640, 480)
         return _cfg_boxes(rng, noisy, W, H, N or 5, 0.10 if noisy else 0.0)
-    if name == "driving1216":
+    if name in ("driving1216", "driving1216_kerb"):
         W, H = size or (1216, 368)
-        return _cfg_driving(rng, noisy, W, H, N or 6)
+        return _cfg_driving(rng, noisy, W, H, N or 6, kerb=name.endswith("_kerb"))
     if name == "rgbd_batch":
         if size is None:
             size = [(320, 240), (640, 480), (1216, 368)][rng.integers(0, 3)]

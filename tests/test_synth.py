@@ -138,3 +138,13 @@ def test_keyframe_pair_depths_agree_under_the_pose():
     # nearest-pixel lookup on smooth surfaces: most agree closely (occlusion
     # and depth edges make the rest)
     assert np.median(rel) < 0.01
+
+
+def test_kerb_variant_keeps_the_lane_clear():
+    # the car boxes at the kerbs: no frame pair passes close to one, so
+    # every pair's flows stay within a street sequence's few hundred px
+    w = synth.make_window("driving1216_kerb", 2000)
+    assert (w.W, w.H, w.N) == (1216, 368, 6)
+    mag = np.hypot(w.flow[..., 0], w.flow[..., 1])
+    for t in range(w.N):
+        assert np.percentile(mag[t], 99.9) < 400 and (mag[t] > 400).mean() < 1e-4
