@@ -6,7 +6,8 @@ KITTI-like driving workload (1216 x 368, N = 6 flows, K = 128 hypotheses,
 8 EM iterations, S = 64 P3P samples per frame): per window the monocular
 bootstrap plus 8 iterations of depth M-step, rigidness E-step and pose
 M-step, all windows in one CUDA-graph launch (vd_batch_run).  Inputs are
-synthetic (synth.make_window("driving1216", ...)) and resident in HBM; L2 is
+synthetic (synth.make_window("driving1216_kerb", ...): road, facades, car
+boxes at the kerbs, 1-1.5 m per frame) and resident in HBM; L2 is
 flushed before every timed step.
 
 value  = pixel*frame*iterations per second over all ranks (W*H*N*8 per window)
@@ -45,7 +46,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EM pixel\u00b7frame\u00b7iters/s and windows/s at 1216x368 N=6; plain vs learned-init at \u22641% err"
 UNIT = "pixel*frame*iter/s"
-WORK = dict(name="driving1216", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2000)
+WORK = dict(name="driving1216_kerb", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2000)
 
 # Algorithmic FP32 instructions of one hypothesis evaluation against one flow
 # (projection 3 FMA + 2 MUL, residual 4 ADD + 2 FMA/MUL, energy 5, view tests 1
@@ -62,7 +63,7 @@ SM_MAX_MHZ = 2070.0
 
 def workload_config(nb, world):
     """The headline workload (both arms report it)."""
-    return {"workload": f"driving1216 x {nb} windows per step: 1216x368, N=6 flows, "
+    return {"workload": f"{WORK['name']} x {nb} windows per step: 1216x368, N=6 flows, "
                         "K=128 hypotheses, 8 EM iterations, S=64 P3P samples, "
                         "monocular bootstrap; all windows in one CUDA-graph launch",
             "windows_per_step_per_gpu": nb,
@@ -83,8 +84,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=8, help="windows per step (one graph launch)")
-    ap.add_argument("--workload", default="driving1216",
-                    choices=["driving1216", "rgbd_batch64", "ka1216"],
+    ap.add_argument("--workload", default="driving1216_kerb",
+                    choices=["driving1216_kerb", "driving1216", "rgbd_batch64", "ka1216"],
                     help="rgbd_batch64: 64 RGB-D windows of uneven size and N, plain vs "
                          "batched; ka1216: keyframe alignment of two 1216x368 depth maps")
     ap.add_argument("--no-tune", action="store_true",
@@ -352,7 +353,7 @@ def run_ours(args, rank, world, local, pg):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(single_ms, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "phase": "single",
-                "config": {"workload": "driving1216: one window per step",
+                "config": {"workload": f"{WORK['name']}: one window per step",
                            "propagation": "hierarchical (cells 4, windows 32)"
                            if args.hierarchical else "full chains"},
                 "single_window": single, "roofline": roofline,
@@ -700,6 +701,8 @@ def main():
         if pg is not None:
             pg.destroy_process_group()
         return 0
+    if args.workload.startswith("driving1216"):
+        WORK["name"] = args.workload
     line = run_ours(args, rank, world, local, pg)
     if rank == 0:
         if not args.no_cpu and world == 1:   # the host baseline: rank 0 of a 1-GPU run only

@@ -50,7 +50,8 @@ typedef enum {
   VD_ERR_CUDA = -2,        /* a CUDA call failed, see vd_last_error()         */
   VD_ERR_OOM = -3,         /* device allocation failed                        */
   VD_ERR_STATE = -4,       /* call out of order (e.g. EM before every flow)   */
-  VD_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up         */
+  VD_ERR_TIMEOUT = -5,     /* a bounded device wait gave up (tensor-core
+                              kernels, vd_check_bounded_wait)                 */
   VD_ERR_NUMERIC = -6      /* non-finite value detected in the state          */
 } vd_status;
 
@@ -152,7 +153,10 @@ vd_status vd_bootstrap(vd_ctx* ctx);
 vd_status vd_run_em(vd_ctx* ctx, int n_iters, vd_stats* stats);
 
 /* Single steps (for staged use and testing).  `iter` selects the random
- * streams (-1 = the bootstrap streams) and `direction` the chains. */
+ * streams (-1 = the bootstrap streams) and `direction` the chains.  On a
+ * context without a prior, vd_depth_mstep with iter = -1 is the monocular
+ * bootstrap's depth step: it weighs X_1 alone (the other flows' rigidness is
+ * not read), exactly as vd_bootstrap does. */
 vd_status vd_depth_mstep(vd_ctx* ctx, int iter, int direction);
 vd_status vd_rigidness_estep(vd_ctx* ctx, int direction);
 /* Pose M-step of frame t (1..N), or of every frame in order for t = 0. */

@@ -1168,7 +1168,8 @@ extern "C" vd_status vd_batch_run(vd_batch* b, int n_iters, int flags, int* dege
 extern "C" vd_status vd_depth_mstep(vd_ctx* c, int iter, int direction) {
   if (!c || direction < 0 || direction > 3 || iter < -1) return VD_ERR_ARG;
   if (!flows_ready(c)) return VD_ERR_STATE;
-  VD_CU(depth_step(c, iter, direction));
+  // iter -1 without a prior is the monocular bootstrap's own depth step (X_1 alone)
+  VD_CU(depth_step(c, iter, direction, iter < 0 && c->prior_kind == VD_PRIOR_NONE));
   VD_CU(cudaStreamSynchronize(c->stream));
   return VD_OK;
 }

@@ -248,9 +248,10 @@ def _cfg_boxes(rng, noisy, W=640, H=480, N=5, moving=0.10, dmax=40.0):
 
 
 def _cfg_driving(rng, noisy, W=1216, H=368, N=6, kerb=False):
-    """kerb: the car boxes stand at the kerbs (|x| >= 2.5 m), leaving the
-    camera's lane clear; otherwise anywhere across the street, so that the
-    camera passes close to some of them."""
+    """kerb: the car boxes stand at the kerbs (|x| >= 2.5 m) and at least
+    12 m ahead, beyond the camera's travel over the window (at most 9 m), so
+    that the camera passes none of them; otherwise anywhere across the street
+    from 6 m on, so that the camera passes close to some of them."""
     K = (720.0, 720.0, W / 2.0, H / 2.0)
     sc = _Scene()
     cam_h = 1.65
@@ -260,7 +261,7 @@ def _cfg_driving(rng, noisy, W=1216, H=368, N=6, kerb=False):
     sc.planes.append((np.array([1.0, 0, 0]), -xl))         # left facade x = -xl
     sc.planes.append((np.array([-1.0, 0, 0]), -xr))        # right facade x = +xr
     for _ in range(12):
-        z = rng.uniform(6.0, 60.0)
+        z = rng.uniform(12.0 if kerb else 6.0, 60.0)
         if kerb:
             x = -rng.uniform(2.5, xl - 1) if rng.uniform() < 0.5 else rng.uniform(2.5, xr - 1)
         else:
@@ -285,7 +286,7 @@ CONFIGS = {
     "planes160": "160x120 N=3, two random planes 2-10 m, small random motion, Fisk noise 0.5 px",
     "boxes640_stereo": "640x480 N=5, ground + 20 boxes 1-40 m, 10% moving blobs, stereo prior",
     "driving1216": "1216x368 N=6, road + facades + boxes 2-80 m, forward 1-1.5 m/frame, 5% moving",
-    "driving1216_kerb": "driving1216 with the car boxes at the kerbs (the camera's lane clear)",
+    "driving1216_kerb": "driving1216 with the car boxes at the kerbs, 12-60 m ahead (none passed)",
     "rgbd_batch": "320x240 / 640x480 / 1216x368, N 3..8, RGB-D prior 1% noise 10% holes",
 }
 

@@ -140,11 +140,16 @@ def test_keyframe_pair_depths_agree_under_the_pose():
     assert np.median(rel) < 0.01
 
 
-def test_kerb_variant_keeps_the_lane_clear():
-    # the car boxes at the kerbs: no frame pair passes close to one, so
-    # every pair's flows stay within a street sequence's few hundred px
-    w = synth.make_window("driving1216_kerb", 2000)
+@pytest.mark.parametrize("seed", [2000, 2001])
+def test_kerb_variant_keeps_the_lane_clear(seed):
+    # the car boxes at the kerbs and beyond the camera's travel: no frame
+    # pair passes close to one, so the rigid flows stay at a street
+    # sequence's magnitudes (the road's bottom corners move most, ~200 px
+    # at 1.5 m per frame)
+    w = synth.make_window("driving1216_kerb", seed)
     assert (w.W, w.H, w.N) == (1216, 368, 6)
     mag = np.hypot(w.flow[..., 0], w.flow[..., 1])
     for t in range(w.N):
-        assert np.percentile(mag[t], 99.9) < 400 and (mag[t] > 400).mean() < 1e-4
+        m = mag[t][~w.moving[t]]
+        assert np.percentile(m, 99) < 250 and np.percentile(m, 99.9) < 300, t
+        assert (m > 400).mean() < 1e-4
