@@ -7,8 +7,8 @@ KITTI-like driving workload (1216 x 368, N = 6 flows, K = 128 hypotheses,
 bootstrap plus 8 iterations of depth M-step, rigidness E-step and pose
 M-step, all windows in one CUDA-graph launch (vd_batch_run).  Inputs are
 synthetic (synth.make_window("driving1216_kerb", ...): road, facades, car
-boxes at the kerbs, 1-1.5 m per frame) and resident in HBM; L2 is
-flushed before every timed step.
+boxes at the kerbs, 1-1.5 m per frame) and resident in HBM; L2 is flushed
+before every timed step.
 
 value  = pixel*frame*iterations per second over all ranks (W*H*N*8 per window)
 single_window = the same for one window at a time (vd_bootstrap + vd_run_em),
@@ -16,11 +16,17 @@ single_window = the same for one window at a time (vd_bootstrap + vd_run_em),
 e2e    = the batched metric through the C ABI with host buffers: flows pushed
          from pinned host memory, inverse depth and poses read back, every step.
 roofline = the depth-sampling kernel (the dominant kernel), FP32-issue bound:
-         algorithmic FP32 instructions per launch / its CUDA-event time in the
-         single-window run.
-cpu_baseline = the float64 oracle on a bounded crop of the same window.
+         algorithmic FP32 operations per launch (counted below) over its
+         CUDA-event time in the single-window run, against the FFMA
+         throughput measured on the same GPU by the library's probe.
+configs = the other workloads on one GPU: the small two-plane window, the
+         stereo 640 x 480 window, the 64-window RGB-D batch (plain vs batched).
+cpu_baseline = the float64 oracle on the host: one iteration of the whole
+         window over every core (row bands in spawned processes), one
+         iteration of a crop on one core, and the small workload in full.
 
---impl reference times the oracle (the CPU definition of the method) instead.
+--impl reference times the oracle (the CPU definition of the method) instead:
+every step one iteration of the whole window over every host core.
 """
 from __future__ import annotations
 
@@ -48,17 +54,81 @@ METRIC = "EM pixel\u00b7frame\u00b7iters/s and windows/s at 1216x368 N=6; plain 
 UNIT = "pixel*frame*iter/s"
 WORK = dict(name="driving1216_kerb", W=1216, H=368, N=6, iters=8, K=128, S=64, seed=2000)
 
-# Algorithmic FP32 instructions of one hypothesis evaluation against one flow
-# (projection 3 FMA + 2 MUL, residual 4 ADD + 2 FMA/MUL, energy 5, view tests 1
-# for t = 1; plus 12 for the bilinear sample and 4 bound tests for t >= 2) and
-# MUFU operations (one reciprocal, one log2).
-FP32_T1, FP32_TN, MUFU_PER_EVAL = 17, 33, 2
-SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+# Algorithmic FP32 work of one hypothesis evaluation against one flow term
+# (Eq. 5 with the beta = 2 closed form), counted operation by operation:
+#   candidate projection hx, hy, hz = A + c B            3 FFMA
+#   x = hx / hz, y = hy / hz (1 / hz on the MUFU)        2 FMUL
+#   residual F - (x - x_prev), both coordinates          4 FADD
+#   r^2                                                  1 FMUL + 1 FFMA
+#   s = 1 + r^2 / alpha^2, y = c0 s^2                    1 FFMA + 2 FMUL
+#   log(1 + y) (log2 on the MUFU)                        1 FADD
+#   q_t-weighted sum                                     1 FFMA
+#   camera-plane test                                    1 FSETP
+# = 17 for X_1, read at the pixel itself.  A gathered flow (t >= 2) adds the
+# inside-image test (4 FSETP), the tap position and weights (2 floor,
+# 2 FADD) and the bilinear sample (2 x (2 FADD + 2 FFMA) per row pair, then
+# 2 FADD + 2 FFMA) = 20: 37.  MUFU: one reciprocal and one log2 per term.
+FP32_T1, FP32_TN, MUFU_PER_EVAL = 17, 37, 2
+# One root against one rigid pixel in the pose scoring (same closed form):
+# projection 9 FFMA, 2 FMUL, residual 2 FADD, r^2 2, s and y 3, log 1 FADD,
+# weighted sum 1 FFMA, camera-plane test 1 FSETP = 21 FP32 + 2 MUFU.
+FP32_SCORE, MUFU_SCORE = 21, 2
 # DRAM bytes (read + write) per launch of k_depth_sample_q on this workload,
 # from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of three launches); re-measure when it changes.
 K1_TRAFFIC_BYTES = 32.4e6
 SM_MAX_MHZ = 2070.0
+
+
+def measure_peaks(V, stream, sms):
+    """FP32 FFMA and MUFU throughput of this GPU, measured with the
+    library's probes (independent chains, 8 blocks of 256 threads per SM):
+    thread-level operations per second, best of five CUDA-event timings of
+    launches of a few ms."""
+    import torch
+    sptr = V.C.c_void_p(stream.cuda_stream)
+    out = {}
+    for name, kind, iters in (("fp32_ffma_per_s", V.VD_PROBE_FP32, 4000),
+                              ("mufu_per_s", V.VD_PROBE_MUFU, 500)):
+        blocks = 8 * sms
+        for _ in range(2):
+            V.vd_probe_pipe(kind, blocks, iters, sptr)
+        best = 0.0
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = V.vd_probe_pipe(kind, blocks, iters, sptr)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) / 1e3))
+        out[name] = best
+    out["fp32_per_sm_per_clk_at_max"] = round(out["fp32_ffma_per_s"] / (sms * SM_MAX_MHZ * 1e6), 2)
+    out["mufu_per_sm_per_clk_at_max"] = round(out["mufu_per_s"] / (sms * SM_MAX_MHZ * 1e6), 2)
+    out["sms"] = sms
+    out["how"] = ("vd_probe_pipe: 8 blocks x 256 threads per SM, 8 independent chains per "
+                  "thread of FFMA (4000 x 128 each) or MUFU log2 (500 x 128 each); best of 5 "
+                  "CUDA-event timings")
+    return out
+
+
+def alu_roofline(kernel, evals, fp32_per_eval, mufu_per_eval, launch_ms, peaks, traffic, how):
+    """Roofline entry of an FP32-issue-bound kernel: algorithmic FP32
+    operations per launch over its CUDA-event time, against the measured
+    FFMA throughput (the MUFU time is reported beside it)."""
+    fp32 = evals * fp32_per_eval
+    achieved = fp32 / (launch_ms / 1e3) / 1e12
+    peak = peaks["fp32_ffma_per_s"] / 1e12
+    t_fp32 = fp32 / peaks["fp32_ffma_per_s"]
+    t_mufu = evals * mufu_per_eval / peaks["mufu_per_s"]
+    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
+            "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic, "traffic_unit": "B per launch", "launch_ms": round(launch_ms, 4),
+            "evals_per_launch": int(evals), "fp32_per_eval": fp32_per_eval,
+            "mufu_per_eval": mufu_per_eval,
+            "roofline_ms": {"fp32": round(1e3 * t_fp32, 4), "mufu": round(1e3 * t_mufu, 4)},
+            "peak_basis": "measured FFMA throughput of this GPU (vd_probe_pipe, of measured)",
+            "measured_in": how}
 
 
 def workload_config(nb, world):
@@ -75,6 +145,11 @@ def fp32_per_pixel_hyp(N):
     return FP32_T1 + (N - 1) * FP32_TN
 
 
+def fp32_per_eval(N):
+    """Mean algorithmic FP32 operations per (pixel, flow, hypothesis)."""
+    return fp32_per_pixel_hyp(N) / N
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,6 +158,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads' measurements (small, stereo, RGB-D batch)")
     ap.add_argument("--batch", type=int, default=8, help="windows per step (one graph launch)")
     ap.add_argument("--workload", default="driving1216_kerb",
                     choices=["driving1216_kerb", "driving1216", "rgbd_batch64", "ka1216"],
@@ -190,39 +267,112 @@ def rank_window_seeds(seed, rank, nb):
 _ORACLE_WINDOW = []
 
 
-def oracle_sample(cw=WORK["W"] // 2, ch=WORK["H"] // 2):
-    """Time the float64 oracle on a centred cw x ch crop of the same window
-    (608 x 184 = 1/4 of the pixels by default, same N, K, S): one EM
-    iteration from a mid-EM state.  The window is generated once."""
+def _oracle_window():
     import synth
-    from oracle import em as oem
-    from oracle import model as omodel
     if not _ORACLE_WINDOW:
         _ORACLE_WINDOW.append(synth.make_window(WORK["name"], WORK["seed"]))
-    win = _ORACLE_WINDOW[0]
-    u0, v0 = (WORK["W"] - cw) // 2, (WORK["H"] - ch) // 2
-    fx, fy, cx, cy = win.intrinsics
-    P = omodel.Problem(cw, ch, WORK["N"], (fx, fy, cx - u0, cy - v0),
-                       np.ascontiguousarray(win.flow[:, v0:v0 + ch, u0:u0 + cw]))
+    return _ORACLE_WINDOW[0]
+
+
+def _oracle_band(args):
+    """One EM iteration of the float64 oracle on a sub-window (run in a
+    worker process): returns (pixel*frames, seconds)."""
+    flow, K, rho, G, prm, u0, v0 = args
+    from oracle import em as oem
+    from oracle import model as omodel
+    N, ch, cw = flow.shape[0], flow.shape[1], flow.shape[2]
+    fx, fy, cx, cy = K
+    P = omodel.Problem(cw, ch, N, (fx, fy, cx - u0, cy - v0), np.ascontiguousarray(flow))
+    p = omodel.Params(**prm)
+    S = omodel.State(rho=rho, q=np.ones((N, ch, cw), np.float32),
+                     qhat=np.zeros((ch, cw), np.float32), G=G)
+    t0 = time.perf_counter()
+    oem.iteration(P, S, 0, p)
+    return cw * ch * N, time.perf_counter() - t0
+
+
+def _oracle_inputs(u0, v0, cw, ch):
+    """The oracle's start on a cw x ch sub-window at (u0, v0): the scene's
+    true inverse depth (in |tau_1| units) and poses, rigidness 1 -- not a
+    mid-EM state, and no bootstrap (the oracle's per-iteration work does not
+    depend on the state: it evaluates every candidate in full)."""
+    win = _oracle_window()
     pr = win.params
-    p = omodel.Params(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"], rho_max=pr["rho_max"],
-                      n_hyp=WORK["K"], n_pose_samples=WORK["S"])
+    prm = dict(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"], rho_max=pr["rho_max"],
+               n_hyp=WORK["K"], n_pose_samples=WORK["S"])
     s = pr["scale"]
     G = win.G.copy()
     G[:, :, 3] /= s
     rho = (s / win.depth0[v0:v0 + ch, u0:u0 + cw]).astype(np.float32)
-    S = omodel.State(rho=rho, q=np.ones((P.N, ch, cw), np.float32),
-                     qhat=np.zeros((ch, cw), np.float32), G=G)
+    flow = win.flow[:, v0:v0 + ch, u0:u0 + cw]
+    return flow, win.intrinsics, rho, G, prm, u0, v0
+
+
+def oracle_sample(cw=WORK["W"] // 2, ch=WORK["H"] // 2):
+    """Time the float64 oracle on one host core: one EM iteration (depth
+    M-step, E-step, pose M-step of every frame) on the centred cw x ch crop
+    of the workload's first window (608 x 184 = 1/4 of its pixels by
+    default; same N, K, S), from the start of _oracle_inputs."""
+    u0, v0 = (WORK["W"] - cw) // 2, (WORK["H"] - ch) // 2
+    units, dt = _oracle_band(_oracle_inputs(u0, v0, cw, ch))
+    return units / dt, dt, (f"one EM iteration (no bootstrap; start: true depth and poses, "
+                            f"rigidness 1) of the float64 oracle on a centred {cw}x{ch} crop of "
+                            f"{WORK['name']} seed {WORK['seed']} (N={WORK['N']}, K={WORK['K']}, "
+                            f"S={WORK['S']}) on one core, {dt:.1f} s")
+
+
+def oracle_all_cores():
+    """The oracle on every host core: the whole 1216 x 368 window cut into
+    one row band per core, each band one EM iteration in its own process
+    (spawned: this process has used the GPU), from the start of
+    _oracle_inputs.  Bands run the method on their own pixels (a pose step
+    scores the band's rigid pixels), so the work is the window's, split.
+    Wall time from the pool's first task to its last result."""
+    import concurrent.futures
+    import multiprocessing
+    ncores = os.cpu_count() or 1
+    H, W = WORK["H"], WORK["W"]
+    edges = np.linspace(0, H, ncores + 1).astype(int)
+    tasks = [_oracle_inputs(0, int(edges[i]), W, int(edges[i + 1] - edges[i]))
+             for i in range(ncores) if edges[i + 1] > edges[i]]
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=len(tasks), mp_context=ctx) as ex:
+        list(ex.map(_oracle_warm, range(len(tasks))))      # imports in every worker
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_band, tasks))
+        dt = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    return units / dt, dt, len(tasks), (
+        f"one EM iteration (no bootstrap; start: true depth and poses, rigidness 1) of the "
+        f"float64 oracle on the whole {W}x{H} window of {WORK['name']} seed {WORK['seed']} "
+        f"(N={WORK['N']}, K={WORK['K']}, S={WORK['S']}), {len(tasks)} row bands in {len(tasks)} "
+        f"processes, {dt:.1f} s wall")
+
+
+def _oracle_warm(_):
+    from oracle import em  # noqa: F401
+    return os.getpid()
+
+
+def oracle_small_full():
+    """The oracle's whole run of the small workload (planes160 seed 0:
+    160 x 120, N = 3, K = 64, monocular bootstrap and 3 EM iterations) on one
+    core: windows/s and pixel*frame*iter/s."""
+    import synth
+    from oracle import em as oem
+    from oracle import model as omodel
+    win = synth.make_window("planes160", 0)
+    pr = win.params
+    P = omodel.problem_from_window(win)
+    p = omodel.Params(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"],
+                      rho_max=pr["rho_max"], n_hyp=pr["n_hyp"])
     t0 = time.perf_counter()
-    oem.iteration(P, S, 0, p)
+    oem.run(P, p, pr["n_iters"])
     dt = time.perf_counter() - t0
-    units = cw * ch * WORK["N"] * 1
-    return units / dt, dt, f"one EM iteration of the float64 oracle on a centred {cw}x{ch} crop " \
-                           f"(N={WORK['N']}, K={WORK['K']}, S={WORK['S']}), {dt:.1f} s"
-
-
-def cpu_cores_used():
-    return 1
+    return {"windows_per_s": round(1.0 / dt, 5),
+            "value": round(win.W * win.H * win.N * pr["n_iters"] / dt, 1), "unit": UNIT,
+            "cores": 1, "seconds": round(dt, 2),
+            "sample": "planes160 seed 0 in full: monocular bootstrap + 3 EM iterations, K=64"}
 
 
 def host_cpu():
@@ -306,16 +456,12 @@ def run_ours(args, rank, world, local, pg):
     single_ms = statistics.median(t1)
     smp = prof["depth_sample"]
     launch_ms = smp["ms"] / max(smp["calls"], 1)
-    fp32 = W * H * WORK["K"] * fp32_per_pixel_hyp(N)
-    achieved = fp32 / (launch_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_depth_sample_q", "achieved": round(achieved, 3),
-                "peak": round(peak, 3), "unit": "TFP32-inst/s", "frac": round(achieved / peak, 4),
-                "traffic": K1_TRAFFIC_BYTES, "traffic_unit": "B per launch",
-                "launch_ms": round(launch_ms, 4),
-                "evals_per_s": round(W * H * N * WORK["K"] / (launch_ms / 1e3), 1),
-                "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (max SM clock)",
-                "measured_in": "single-window run, kernel timed alone (CUDA events)"}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measure_peaks(V, stream, sms)
+    roofline = alu_roofline("k_depth_sample_q", W * H * N * WORK["K"], fp32_per_eval(N),
+                            MUFU_PER_EVAL, launch_ms, peaks, K1_TRAFFIC_BYTES,
+                            "single-window run, kernel timed alone (CUDA events per stage)")
+    roofline["peaks_measured"] = peaks
     stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
     # the stride / keyframe score of the window just estimated (VC, Eq. 8):
     # the call's time including its counter read-back, median of 20
@@ -370,7 +516,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
     # ---- a batch of windows in one graph launch (the headline throughput)
     nb = max(1, args.batch)
     seeds = rank_window_seeds(WORK["seed"], rank, nb)
-    bw = [win] + [synth.make_window(WORK["name"], sd) for sd in seeds[1:]]
+    bw = [win] + make_windows([(WORK["name"], sd, {}) for sd in seeds[1:]])
     b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in bw], params, sptr)
     for i, w in enumerate(bw):
         fl = torch.from_numpy(w.flow).to(dev)
@@ -401,6 +547,14 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
         e2e = run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, world)
 
     V.vd_batch_destroy(b)
+    configs = None
+    if world == 1 and not args.no_configs:
+        # the other workloads, one line: small, stereo, the RGB-D batch
+        configs = {
+            "planes160": single_config(V, dev, stream, sptr, flush, "planes160", 0, {}, "none"),
+            "boxes640_stereo": single_config(V, dev, stream, sptr, flush, "boxes640_stereo", 1000,
+                                             {}, "stereo", steps=10, warmup=3),
+            "rgbd_batch64": rgbd64_measure(V, dev, stream, sptr, flush, 3, 1, rank, pg)}
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3),
@@ -413,7 +567,7 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
             "single_window": single, "batch": bstats,
             "roofline": roofline, "stage_ms_per_window": stages,
             "gpu_launches": int(bstats["kernels_per_run"] * args.steps), "clocks": clk,
-            "e2e": e2e}
+            "e2e": e2e, "configs": configs}
     return line
 
 
@@ -500,28 +654,37 @@ def run_batch_e2e(args, pg, V, b, bw, params, dev, iters, units_per_window, worl
                     "copies overlap the other's run"}
 
 
-def run_rgbd64(args, rank, world, local, pg):
+def _make_window(spec):
+    import synth
+    name, seed, kw = spec
+    return synth.make_window(name, seed, **kw)
+
+
+def make_windows(specs):
+    """synth windows for [(name, seed, kwargs)], generated in parallel by
+    spawned worker processes (this process may already hold a GPU context)."""
+    import concurrent.futures
+    import multiprocessing
+    if len(specs) <= 1:
+        return [_make_window(sp) for sp in specs]
+    n = min(len(specs), os.cpu_count() or 1)
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=n, mp_context=ctx) as ex:
+        return list(ex.map(_make_window, specs))
+
+
+def rgbd64_measure(V, dev, stream, sptr, flush, steps, warmup, rank, pg):
     """64 windows with an RGB-D prior, sizes drawn from 320x240 / 640x480 /
     1216x368 and N from 3..8 (seeds 5000..5063), 5 EM iterations each: one
     window at a time (vd_bootstrap + vd_run_em per window) versus all of them
     in one graph launch (vd_batch_run).  Both give bit-identical results."""
     import torch
-    from paper_2104_06800_gb300 import build as B
-    from paper_2104_06800_gb300 import voldor as V
-    import synth
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    B.build()
-    V.load()
-    stream = torch.cuda.current_stream(dev)
-    sptr = V.C.c_void_p(stream.cuda_stream)
     nw, iters = 64, 5
-    wins = [synth.make_window("rgbd_batch", 5000 + 64 * rank + i) for i in range(nw)]
+    wins = make_windows([("rgbd_batch", 5000 + 64 * rank + i, {}) for i in range(nw)])
     prms = [V.vd_params_default(fisk_alpha0=w.params["fisk_alpha0"], rho_min=w.params["rho_min"],
                                 rho_max=w.params["rho_max"], n_hyp=w.params["n_hyp"],
                                 n_pose_samples=64) for w in wins]
     units = sum(w.W * w.H * w.N * iters for w in wins)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def push(ctx, w):
         for t in range(1, w.N + 1):
@@ -540,21 +703,21 @@ def run_rgbd64(args, rank, world, local, pg):
             V.vd_bootstrap(c)
             V.vd_run_em(c, iters, stats=False)
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         plain()
     torch.cuda.synchronize()
-    tp = _timed(stream, flush, plain, args.steps)
+    tp = _timed(stream, flush, plain, steps)
     # the same windows as one batch
     b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in wins], prms, sptr)
     for i, w in enumerate(wins):
         push(V.vd_batch_window(b, i), w)
     V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP | V.VD_BATCH_AUTOTUNE)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP)
     torch.cuda.synchronize()
-    clocks = Clocks(local)
+    clocks = Clocks(dev.index or 0)
     clocks.start()
-    tb = _timed(stream, flush, lambda: V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP), args.steps)
+    tb = _timed(stream, flush, lambda: V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP), steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     # accuracy against the scenes' true depth (metric: the prior fixes the scale)
@@ -571,29 +734,90 @@ def run_rgbd64(args, rank, world, local, pg):
     V.vd_batch_destroy(b)
     for c in ctxs:
         V.vd_destroy(c)
+    world = 1 if pg is None else pg.get_world_size()
     tot_b = max_over_ranks(pg, sum(tb), dev)
     tot_p = max_over_ranks(pg, sum(tp), dev)
     sizes = {}
     for w in wins:
         sizes[f"{w.W}x{w.H}"] = sizes.get(f"{w.W}x{w.H}", 0) + 1
-    return {"metric": METRIC, "value": round(units * args.steps * world / (tot_b / 1e3), 1),
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(tot_b / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"rgbd_batch64: {nw} windows, RGB-D prior (1% noise, 10% holes), "
-                                   f"{iters} EM iterations, K=64, S=64; sizes {sizes}, "
-                                   f"N {min(w.N for w in wins)}..{max(w.N for w in wins)}",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
-            "windows_per_s": round(nw * args.steps * world / (tot_b / 1e3), 3),
-            "plain": {"windows_per_s": round(nw * args.steps * world / (tot_p / 1e3), 3),
-                      "value": round(units * args.steps * world / (tot_p / 1e3), 1),
-                      "ms_per_step": round(tot_p / args.steps, 3)},
+    return {"value": round(units * steps * world / (tot_b / 1e3), 1), "unit": UNIT,
+            "windows_per_s": round(nw * steps * world / (tot_b / 1e3), 3),
+            "ms_per_step": round(tot_b / steps, 3),
+            "workload": f"rgbd_batch64: {nw} windows, RGB-D prior (1% noise, 10% holes), "
+                        f"{iters} EM iterations, K=64, S=64; sizes {sizes}, "
+                        f"N {min(w.N for w in wins)}..{max(w.N for w in wins)}",
+            "plain": {"windows_per_s": round(nw * steps * world / (tot_p / 1e3), 3),
+                      "value": round(units * steps * world / (tot_p / 1e3), 1),
+                      "ms_per_step": round(tot_p / steps, 3)},
             "batched_equals_plain": same,
             "median_depth_rel_err": {"median_over_windows": round(float(np.median(errs)), 5),
                                      "max_over_windows": round(float(np.max(errs)), 5)},
-            "batch": bstats, "gpu_launches": int(bstats["kernels_per_run"] * args.steps),
-            "clocks": clk, "e2e": None}
+            "batch": bstats, "gpu_launches": int(bstats["kernels_per_run"] * steps),
+            "clocks": clk, "steps": steps}
+
+
+def single_config(V, dev, stream, sptr, flush, name, seed, kw, prior, steps=20, warmup=5):
+    """windows/s of one window at a time (vd_bootstrap + vd_run_em) for one of
+    the smaller workloads, median of `steps` CUDA-event timings."""
+    import torch
+    w = make_windows([(name, seed, kw)])[0]
+    pr = w.params
+    params = V.vd_params_default(fisk_alpha0=pr["fisk_alpha0"], rho_min=pr["rho_min"],
+                                 rho_max=pr["rho_max"], n_hyp=pr["n_hyp"], n_pose_samples=64)
+    ctx = V.vd_create(w.W, w.H, w.N, w.intrinsics, params, sptr)
+    try:
+        for t in range(1, w.N + 1):
+            V.vd_push_flow(ctx, t, w.flow[t - 1])
+        if prior == "stereo":
+            V.vd_push_stereo_prior(ctx, w.stereo_disp, w.stereo_baseline)
+        iters = pr["n_iters"]
+
+        def step():
+            V.vd_bootstrap(ctx)
+            V.vd_run_em(ctx, iters, stats=False)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ms = statistics.median(_timed(stream, flush, step, steps))
+        rho = np.empty((w.H, w.W), np.float32)
+        V.vd_get_inv_depth(ctx, rho)
+    finally:
+        V.vd_destroy(ctx)
+    d = 1.0 / np.maximum(rho, 1e-9)
+    scale = float(np.median(w.depth0 / d)) if prior == "none" else 1.0
+    return {"windows_per_s": round(1e3 / ms, 2), "ms_per_window": round(ms, 4),
+            "value": round(w.W * w.H * w.N * iters / (ms / 1e3), 1), "unit": UNIT,
+            "workload": f"{name} seed {seed}: {w.W}x{w.H}, N={w.N}, K={pr['n_hyp']}, "
+                        f"{iters} EM iterations, prior {prior}, one window per call",
+            "median_depth_rel_err_vs_truth": round(
+                float(np.median(np.abs(d * scale - w.depth0) / w.depth0)), 5)}
+
+
+def run_rgbd64(args, rank, world, local, pg):
+    """--workload rgbd_batch64: the 64-window RGB-D batch as the line's workload."""
+    import torch
+    from paper_2104_06800_gb300 import build as B
+    from paper_2104_06800_gb300 import voldor as V
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    V.load()
+    stream = torch.cuda.current_stream(dev)
+    sptr = V.C.c_void_p(stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    r = rgbd64_measure(V, dev, stream, sptr, flush, args.steps, args.warmup, rank, pg)
+    return {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": r["workload"],
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "windows_per_s": r["windows_per_s"], "plain": r["plain"],
+            "batched_equals_plain": r["batched_equals_plain"],
+            "median_depth_rel_err": r["median_depth_rel_err"], "batch": r["batch"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": None}
 
 
 def run_ka(args, rank, world, local, pg):
@@ -663,32 +887,46 @@ def run_ka(args, rank, world, local, pg):
             "e2e": None}
 
 
+def cpu_baselines(small=True):
+    """The oracle on the host: every core (the reported baseline), one core,
+    and the small workload in full on one core."""
+    v1, dt1, desc1 = oracle_sample()
+    va, dta, ncores, desca = oracle_all_cores()
+    out = {"value": round(va, 1), "unit": UNIT, "cores": ncores, "host": host_cpu(),
+           "kind": "oracle", "sample": desca,
+           "single_core": {"value": round(v1, 1), "unit": UNIT, "cores": 1, "sample": desc1}}
+    if small:
+        out["planes160_full"] = oracle_small_full()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         if rank != 0:
             return 0
-        # each timed step: one EM iteration of the oracle on the 608 x 184
-        # crop (10-20 s of CPU work); warm-up steps on a 304 x 92 crop (they
+        # each timed step: one EM iteration of the oracle over the whole
+        # window, one row band per host core (a few s of wall time);
+        # warm-up steps one iteration on a 304 x 92 crop on one core (they
         # only take the one-time costs: imports, the window, first touches)
         for _ in range(max(args.warmup, 0)):
             oracle_sample(WORK["W"] // 4, WORK["H"] // 4)
-        units_s = []
-        samples = []
+        units_s, samples = [], []
         for _ in range(args.steps):
-            v, dt, desc = oracle_sample()
+            v, dt, ncores, desc = oracle_all_cores()
             units_s.append(v)
             samples.append(dt)
         value = statistics.median(units_s)
+        cfg = dict(workload_config(args.batch, 1))
+        cfg["reference_step"] = desc
         line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
                 "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1e3 * statistics.median(samples), 1),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": workload_config(args.batch, 1),
-                "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cpu_cores_used(),
-                                 "host": host_cpu(),
-                                 "kind": "oracle", "sample": desc},
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": ncores,
+                                 "host": host_cpu(), "kind": "oracle", "sample": desc},
                 "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -706,10 +944,7 @@ def main():
     line = run_ours(args, rank, world, local, pg)
     if rank == 0:
         if not args.no_cpu and world == 1:   # the host baseline: rank 0 of a 1-GPU run only
-            v, dt, desc = oracle_sample()
-            line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": cpu_cores_used(),
-                                    "host": host_cpu(),
-                                    "kind": "oracle", "sample": desc}
+            line["cpu_baseline"] = cpu_baselines(small=not args.no_configs)
         print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()

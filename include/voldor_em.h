@@ -185,7 +185,8 @@ vd_status vd_get_pose_samples(vd_ctx* ctx, double* poses, double* energies, int*
  * l the Fisk maximum-inlier energy with shape beta and outlier density p0,
  * and a large constant for points behind the camera.  energies: m float64.
  * Allocates its own scratch for the block partial sums; runs on cuda_stream
- * and synchronises it.  n >= 0, 1 <= m <= 1024. */
+ * and synchronises it.  n >= 0 (points and obs may be NULL when n = 0, which
+ * gives zero energies), 1 <= m <= 1024. */
 vd_status vd_score_poses(const float* points, const float* obs, int n, const double* poses, int m,
                          const double* intrinsics, float beta, float p0, double* energies,
                          void* cuda_stream);
@@ -213,11 +214,15 @@ vd_status vd_get_profile(vd_ctx* ctx, vd_profile* out);
  * cudaMalloc (which can synchronise the device and can fail under memory
  * pressure) is not allowed.  Same arguments and result as vd_score_poses, but
  * the block partial sums live in a fixed array of the library's device code
- * (VD_NOALLOC_MAX_POSES x (12 + 304) floats, about 324 KB, held by every GPU
+ * (VD_NOALLOC_MAX_POSES x (12 + 512) floats, about 0.5 MB, held by every GPU
  * that loads the library until the process exits).
- *   - m must be in 1..VD_NOALLOC_MAX_POSES, else VD_ERR_ARG (see vd_last_error).
+ *   - m must be in 1..VD_NOALLOC_MAX_POSES, else VD_ERR_ARG (see vd_last_error);
+ *     n = 0 gives zero energies.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address; make that first call before any stream capture.
+ *     array's device address and the device's SM count; make that first call
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after a cudaDeviceReset of that device it is stale, and the
+ *     call must not be used again in that process.
  *   - All calls share the one array: calls that may overlap on the GPU (other
  *     streams, other host threads) race and must be serialised by the caller.
  *     Every scratch value a call reads is written earlier in the same call.
@@ -331,6 +336,19 @@ typedef struct vd_cnn vd_cnn;
  * the status of a convolution whose wait ran out (VD_ERR_ARG for polls out
  * of range); the device stays usable.  Synchronises `cuda_stream`. */
 vd_status vd_check_bounded_wait(int polls, void* cuda_stream);
+
+/* ---- Pipe throughput probes (measurement; the paper has none) ------------
+ * Launch `blocks` blocks of 256 threads that run only independent chains of
+ * FP32 fused multiply-adds (VD_PROBE_FP32) or of MUFU log2 operations
+ * (VD_PROBE_MUFU), `iters` x 128 per thread, on cuda_stream, without
+ * synchronising; *ops_out receives the number of thread-level operations
+ * launched.  Timed with CUDA events around the call, ops / time is the
+ * pipe's measured throughput, the denominator of the roofline fractions of
+ * the depth sampling and pose scoring kernels.  blocks and iters in
+ * 1..2^20, else VD_ERR_ARG. */
+#define VD_PROBE_FP32 0
+#define VD_PROBE_MUFU 1
+vd_status vd_probe_pipe(int kind, int blocks, int iters, double* ops_out, void* cuda_stream);
 typedef struct {
   double fx, fy, cx, cy;    /* intrinsics of the window                     */
   double T1[12];            /* pose of flow 1, [R | tau] row-major           */

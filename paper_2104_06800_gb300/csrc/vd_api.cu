@@ -271,8 +271,8 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   c->score_bps = 2;
   c->score_threads = 256;
   c->nblk_score = VD_SCORE_BPS_MAX * c->num_sms;   // capacity of the partial sums
-  c->ep_blocks = 2 * 152;
-  c->stat_blocks = 152;
+  c->ep_blocks = 2 * c->num_sms;
+  c->stat_blocks = c->num_sms;
   const int s = p.hier_scale;
   cudaError_t e = cudaSuccess;
 #define A(ptr, n) if (e == cudaSuccess) e = dalloc(&c->ptr, (n))

@@ -2,6 +2,7 @@
 // pose is approximated by S P3P samples drawn from the rigid pixels; every
 // root is scored against all rigid pixels, each sample keeps its best root,
 // and the pose is the mean-shift mode of the samples in se(3).
+#include <algorithm>
 #include <mutex>
 
 #include "vd_device.cuh"
@@ -798,30 +799,37 @@ __global__ void k_poses_float(DevParams P, const double* __restrict__ poses, int
 // K R | K tau of every pose, then the per-block partial sums) lives in this
 // fixed device array instead of memory allocated per call.
 // ---------------------------------------------------------------------------
-#define VD_NOALLOC_BLOCKS (2 * 152)
-#define VD_NOALLOC_FLOATS (VD_NOALLOC_MAX_POSES * (12 + VD_NOALLOC_BLOCKS))
+#define VD_NOALLOC_MAX_BLOCKS 512
+#define VD_NOALLOC_FLOATS (VD_NOALLOC_MAX_POSES * (12 + VD_NOALLOC_MAX_BLOCKS))
 static __device__ __align__(256) float g_noalloc_scratch[VD_NOALLOC_FLOATS];
 
 #define VD_NOALLOC_MAX_DEVICES 64
 static float* g_noalloc_ptr[VD_NOALLOC_MAX_DEVICES];
+static int g_noalloc_blocks[VD_NOALLOC_MAX_DEVICES];
 static std::mutex g_noalloc_mu;
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current; host code must not use the symbol
-// itself, which is only a host-side stand-in).
-static cudaError_t noalloc_scratch(float** out) {
+// Device address of the scratch array on the current device and the block
+// count of its scoring launch (two per SM, at most VD_NOALLOC_MAX_BLOCKS),
+// looked up once per device with that device current (host code must not
+// use the symbol itself, which is only a host-side stand-in).
+static cudaError_t noalloc_scratch(float** out, int* nblk) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= VD_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    g_noalloc_blocks[dev] = std::max(1, std::min(2 * sms, VD_NOALLOC_MAX_BLOCKS));
     g_noalloc_ptr[dev] = (float*)p;
   }
   *out = g_noalloc_ptr[dev];
+  *nblk = g_noalloc_blocks[dev];
   return cudaSuccess;
 }
 
@@ -829,8 +837,8 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
                                             const double* poses, int m, const double* intrinsics,
                                             float beta, float p0, double* energies,
                                             void* cuda_stream) {
-  if (!points || !obs || !poses || !intrinsics || !energies || n < 0 || !(beta > 0.0f) ||
-      !(p0 > 0.0f))
+  if ((n > 0 && (!points || !obs)) || !poses || !intrinsics || !energies || n < 0 ||
+      !(beta > 0.0f) || !(p0 > 0.0f))
     return VD_ERR_ARG;
   if (m < 1 || m > VD_NOALLOC_MAX_POSES) {
     vd_set_error("vd_score_poses_noalloc: m must be between 1 and VD_NOALLOC_MAX_POSES (256)");
@@ -838,7 +846,8 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   float* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  int nblk = 0;
+  cudaError_t e = noalloc_scratch(&scratch, &nblk);
   double K[4];
   if (e == cudaSuccess) e = cudaMemcpy(K, intrinsics, sizeof K, cudaMemcpyDefault);
   if (e != cudaSuccess) {
@@ -851,13 +860,13 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
   P.p0 = p0;
   P.fast_beta2 = 0;           // the per-point scale rides in obs.z
   P.cgen = p0 * 2.0f * 3.14159265358979f / beta;
-  float* rootsf = scratch;                          // m x 12
-  float* partial = scratch + 12 * VD_NOALLOC_MAX_POSES;   // m x VD_NOALLOC_BLOCKS
+  float* rootsf = scratch;                                  // m x 12
+  float* partial = scratch + 12 * VD_NOALLOC_MAX_POSES;     // m x nblk
   k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
   const size_t smem = vd_score_smem(m, SCORE_THREADS);
-  k_pose_score<SCORE_THREADS><<<VD_NOALLOC_BLOCKS, SCORE_THREADS, smem, s>>>(
+  k_pose_score<SCORE_THREADS><<<nblk, SCORE_THREADS, smem, s>>>(
       P, (const float4*)points, (const float4*)obs, nullptr, n, rootsf, nullptr, m, partial);
-  launch_root_energy(partial, VD_NOALLOC_BLOCKS, m, nullptr, energies, s);
+  launch_root_energy(partial, nblk, m, nullptr, energies, s);
   e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
@@ -871,8 +880,8 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
 extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n, const double* poses,
                                     int m, const double* intrinsics, float beta, float p0,
                                     double* energies, void* cuda_stream) {
-  if (!points || !obs || !poses || !intrinsics || !energies || n < 0 || m < 1 || m > 1024 ||
-      !(beta > 0.0f) || !(p0 > 0.0f))
+  if ((n > 0 && (!points || !obs)) || !poses || !intrinsics || !energies || n < 0 || m < 1 ||
+      m > 1024 || !(beta > 0.0f) || !(p0 > 0.0f))
     return VD_ERR_ARG;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   double K[4];
@@ -886,7 +895,13 @@ extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n
   P.p0 = p0;
   P.fast_beta2 = 0;           // the per-point scale rides in obs.z
   P.cgen = p0 * 2.0f * 3.14159265358979f / beta;
-  const int nblk = 2 * 152;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(cudaGetLastError()));
+    return VD_ERR_CUDA;
+  }
+  const int nblk = 2 * std::max(sms, 1);
   float* rootsf = nullptr;
   float* partial = nullptr;
   cudaError_t e = cudaMallocAsync(&rootsf, sizeof(float) * 12 * m, s);

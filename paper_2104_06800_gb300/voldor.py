@@ -145,6 +145,7 @@ _SIGS = {
     "vd_batch_run": [_P, C.c_int, C.c_int, _P],
     "vd_batch_get_stats": [_P, C.POINTER(vd_batch_stats)],
     "vd_check_bounded_wait": [C.c_int, _P],
+    "vd_probe_pipe": [C.c_int, C.c_int, C.c_int, _P, _P],
     "vd_cnn_create": [C.c_int, C.c_ulonglong, C.POINTER(_P)],
     "vd_cnn_destroy": [_P],
     "vd_cnn_layout": [_P, C.POINTER(C.c_int), _P, _P, _P, _P],
@@ -585,6 +586,18 @@ def vd_cnn_create(n_flows, seed=0):
 def vd_check_bounded_wait(polls, stream=None):
     """Raises VoldorError with status VD_ERR_TIMEOUT: the bounded wait gave up."""
     _call("vd_check_bounded_wait", int(polls), stream)
+
+
+VD_PROBE_FP32, VD_PROBE_MUFU = 0, 1
+
+
+def vd_probe_pipe(kind, blocks, iters, stream=None):
+    """Launch a pipe throughput probe (no synchronisation); returns the number
+    of thread-level operations launched."""
+    ops = C.c_double(0.0)
+    _call("vd_probe_pipe", int(kind), int(blocks), int(iters), C.byref(ops),
+          stream if stream is not None else current_stream())
+    return ops.value
 
 
 def vd_cnn_destroy(net):

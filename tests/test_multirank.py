@@ -53,7 +53,12 @@ def _reference_rank(rank, world, port, out_dir):
         calls.append((cw, ch))
         return 1.0e5, 2.0, f"fake sample {cw}x{ch}"
 
+    def fake_all_cores():              # the signature of bench.oracle_all_cores
+        calls.append(("all", 16))
+        return 1.0e5, 2.0, 16, "fake all-cores step 1216x368"
+
     bench.oracle_sample = fake_sample
+    bench.oracle_all_cores = fake_all_cores
     out = os.path.join(out_dir, f"ref{rank}.txt")
     sys.argv = ["bench.py", "--impl", "reference", "--gpus", str(world), "--steps", "3",
                 "--warmup", "2"]
@@ -91,7 +96,8 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     r1 = json.load(open(tmp_path / "ref1.calls.json"))
     assert r0["rc"] == 0 and r1["rc"] == 0
     assert len(r0["calls"]) == 2 + 3 and r1["calls"] == []    # warm-up + timed steps, rank 0 only
-    assert r0["calls"][2:] == [[608, 184]] * 3                # the timed steps on the full crop
+    assert r0["calls"][:2] == [[304, 92]] * 2                 # warm-up on the small crop
+    assert r0["calls"][2:] == [["all", 16]] * 3               # the timed steps on every core
     assert open(tmp_path / "ref1.txt").read() == ""
     lines = open(tmp_path / "ref0.txt").read().strip().splitlines()
     assert len(lines) == 1
@@ -104,9 +110,11 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["scaling"] == "weak"
     assert line["vs_baseline"] is None and line["data"] == "synthetic" and line["n_gpus"] == 1
-    assert line["config"] == bench.workload_config(8, 1)
+    cfg = dict(line["config"])
+    assert cfg.pop("reference_step") == "fake all-cores step 1216x368"
+    assert cfg == bench.workload_config(8, 1)
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["unit"] == line["unit"]
     assert line["e2e"]["d2h_bytes_per_step"] == 0
     cb = line["cpu_baseline"]
-    assert cb["value"] == line["value"] and cb["cores"] == 1 and cb["host"]["nproc"] >= 1
-    assert "608x184" in cb["sample"] and line["ms_per_step"] > 0
+    assert cb["value"] == line["value"] and cb["cores"] == 16 and cb["host"]["nproc"] >= 1
+    assert "1216x368" in cb["sample"] and line["ms_per_step"] > 0

@@ -59,6 +59,30 @@ def test_noalloc_matches_allocating_entry_point_twice(V):
         assert np.allclose(g, r, rtol=1e-4, atol=0)
 
 
+def test_noalloc_matches_the_oracle_at_its_limits(V):
+    """Against the float64 oracle's pose score (Eq. 7 scoring), at the
+    largest pose count the fixed array holds and with no points at all."""
+    import torch
+    from oracle import model as omodel
+    from oracle import pose as opose
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(11)
+    n, m = 3000, V.VD_NOALLOC_MAX_POSES
+    pts, obs, poses, K = _problem(rng, n, m, dev)
+    got = torch.full((m,), -1.0, dtype=torch.float64, device=dev)
+    V.vd_score_poses_noalloc(pts, obs, poses, K, 2.0, 1e-3, got)
+    P = omodel.Problem(10, 10, 1, tuple(K.cpu().numpy()), np.zeros((1, 10, 10, 2), np.float32))
+    p = omodel.Params(fisk_beta=2.0, outlier_density=1e-3)
+    pn, on = pts.cpu().numpy().astype(np.float64), obs.cpu().numpy().astype(np.float64)
+    rs = dict(X=pn[:, :3], w=pn[:, 3], xobs=on[:, :2], alpha=on[:, 2])
+    want = np.array([opose.score(P, G, rs, p) for G in poses.cpu().numpy().reshape(m, 3, 4)])
+    assert np.allclose(got.cpu().numpy(), want, rtol=1e-4, atol=0)
+    # no points: every energy is zero (and the array's last contents are not read)
+    zero = torch.full((5,), -1.0, dtype=torch.float64, device=dev)
+    V.vd_score_poses_noalloc(pts[:0], obs[:0], poses[:5], K, 2.0, 1e-3, zero)
+    assert np.array_equal(zero.cpu().numpy(), np.zeros(5))
+
+
 def test_noalloc_rejects_too_many_poses(V):
     import torch
     dev = torch.device("cuda")
