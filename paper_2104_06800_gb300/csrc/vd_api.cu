@@ -204,6 +204,12 @@ static void fill_devparams(vd_ctx* c) {
   d.ms_sig_rot = p.pose_sigma_rot;
   d.ms_sig_rel = p.pose_sigma_trans_rel;
   d.ms_sig_abs = p.pose_sigma_trans_abs;
+  const double kv[6] = {c->desc.fx, c->desc.fy, c->desc.cx, c->desc.cy, 1.0 / c->desc.fx,
+                        1.0 / c->desc.fy};
+  for (int i = 0; i < 6; ++i) {
+    d.kdf[2 * i] = (float)kv[i];
+    d.kdf[2 * i + 1] = (float)(kv[i] - (double)d.kdf[2 * i]);
+  }
 }
 
 template <typename T>

@@ -168,7 +168,11 @@ VD_HD __forceinline__ double vd_poly_eval(const double* c, int deg, double x) {
 // search first runs in float32 to about 1e-6 and then continues in float64
 // from there inside the float64 bracket, so the float64 phase needs only a
 // few steps; the bracket keeps the result a root of the float64 polynomial.
-static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, double hi) {
+// fp64_steps caps the float64 phase: 0 returns the float32 estimate (enough
+// for a split point between roots), a few steps polish a simple root to
+// float64 precision (Newton doubles the correct digits per step).
+static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, double hi,
+                                           int fp64_steps = 40) {
   double d[4];
   for (int i = 1; i <= deg; ++i) d[i - 1] = c[i] * i;
   double flo = vd_poly_eval(c, deg, lo);
@@ -202,7 +206,7 @@ static VD_HD double vd_poly_bracketed_root(const double* c, int deg, double lo, 
   // float64 phase: Newton converges quadratically from the float32 estimate
   // for a simple root (two or three steps); clustered roots converge
   // linearly, hence the cap.  Stops at a 4-ulp step.
-  for (int it = 0; it < 40; ++it) {
+  for (int it = 0; it < fp64_steps; ++it) {
     const double f = vd_poly_eval(c, deg, x);
     if (f == 0.0) return x;
     if ((f < 0.0) == (flo < 0.0)) {
@@ -249,7 +253,7 @@ VD_HD __forceinline__ double vd_root_bound(const double* c, int deg) {
 // roots of its derivative): one root per interval with a sign change.
 // Writes at most ncrit + 1 roots.
 VD_HD __forceinline__ int vd_roots_between(const double* c, int deg, const double* crit,
-                                                int ncrit, double* out) {
+                                                int ncrit, double* out, int fp64_steps = 40) {
   const double bound = vd_root_bound(c, deg);
   double lo = -bound;
   double flo = vd_poly_eval(c, deg, lo);
@@ -261,12 +265,32 @@ VD_HD __forceinline__ int vd_roots_between(const double* c, int deg, const doubl
     if (flo == 0.0) {
       out[n++] = lo;
     } else if ((flo < 0.0) != (fhi < 0.0) && fhi != 0.0) {
-      out[n++] = vd_poly_bracketed_root(c, deg, lo, hi);
+      out[n++] = vd_poly_bracketed_root(c, deg, lo, hi, fp64_steps);
     }
     lo = hi;
     flo = fhi;
   }
   return n;
+}
+
+// Cap of the float64 Newton steps that polish a quartic's root found by the
+// float32 phase (two or three for a simple root; the loop stops at a 4-ulp
+// step).  The split-point stages need no float64 digits.
+#define VD_P3P_POLISH_STEPS 40
+
+// Real roots of a quartic with a non-negligible leading coefficient, as
+// vd_poly_real_roots isolates them (second derivative, first derivative,
+// quartic), with float32 split points and the float64 phase on the roots
+// of the quartic itself only.
+static VD_HD int vd_quartic_real_roots_fast(const double* c, double* out) {
+  const double q[3] = {c[2] * 2.0, c[3] * 6.0, c[4] * 12.0};
+  const double split = -q[1] / (2.0 * q[2]);
+  double r2[2];
+  const int n2 = vd_roots_between(q, 2, &split, 1, r2, 0);
+  const double cc[4] = {c[1], c[2] * 2.0, c[3] * 3.0, c[4] * 4.0};
+  double r3[3];
+  const int n3 = vd_roots_between(cc, 3, r2, n2, r3, 0);
+  return vd_roots_between(c, 4, r3, n3, out, VD_P3P_POLISH_STEPS);
 }
 
 // All real roots of sum_{i<=deg} c[i] x^i for deg <= 4, ascending.  Real
@@ -448,11 +472,11 @@ static VD_HD bool vd_p3p_pose(const VdP3P& g, const double* X, double v, double*
   const double qq0 = b2 * v * v - a2 * (1.0 + v * v - 2.0 * v * cb);
   const double den = b2 * (2.0 * b2 * cg) + b2 * qq1;
   if (fabs(den) < 1e-300) return false;
-  const double u = (-b2 * qq0 - b2 * pp0) / den;
+  const double u = (-b2 * qq0 - b2 * pp0) * vd_rcp64(den);
   if (!(u > 0.0)) return false;
   const double dd = 1.0 + v * v - 2.0 * v * cb;
   if (!(dd > 0.0)) return false;
-  const double s1 = sqrt(b2 / dd);
+  const double s1 = b2 * vd_rsqrt64(b2 * dd);      // sqrt(b2 / dd)
   const double* f = g.f;
   const double Q[9] = {s1 * f[0], s1 * f[1], s1 * f[2],
                        u * s1 * f[3], u * s1 * f[4], u * s1 * f[5],

@@ -48,6 +48,8 @@ struct DevParams {
   float c_sigma, w_unif, logk;   // RGB-D prior: logk = log(sqrt(2 pi) c_sigma / w)
   double fx_d, fy_d, cx_d, cy_d;
   double ms_sig_rot, ms_sig_rel, ms_sig_abs;
+  // fx, fy, cx, cy, 1/fx, 1/fy as double-float (hi, lo) pairs
+  float kdf[12];
 };
 
 struct vd_ctx {

@@ -7,6 +7,7 @@
 
 #include "vd_device.cuh"
 #include "vd_geom64.cuh"
+#include "vd_p3p_df.cuh"
 
 #define SCAN_BLOCK 256
 #define SCORE_THREADS 256
@@ -168,108 +169,188 @@ k_rigid_scatter(DevParams P, const float* __restrict__ posef, const float2* __re
 }
 
 // ---------------------------------------------------------------------------
-// One thread per sample: three distinct indices into the rigid set, float64
-// correspondences, P3P, roots ordered by (rotation vector, translation).
+// P3P sampling in double-float (vd_p3p_df.cuh): on this GPU a float64
+// instruction costs a warp 64 cycles, a float32 one about 1.3.
 // ---------------------------------------------------------------------------
-__device__ void vd_correspondence64(const DevParams& P, const double* __restrict__ G,
-                                    const float2* __restrict__ flow, const float* __restrict__ rho,
-                                    int t, int j, double* X, double* bearing) {
+// Correspondence of rigid pixel j in double-float: the point X = r_j / rho_j
+// of the reference frame and the bearing K^-1 x_obs of its observation in
+// frame t, x_obs = x_{t-1} + X_t(x_{t-1}) (x_0 = j; for t >= 2, x_{t-1} is
+// the projection by G_{t-1}, given as 12 double-float values in g).
+__device__ void vd_correspondence_df(const DevParams& P, const vd_df* g,
+                                     const float2* __restrict__ flow, const float* __restrict__ rho,
+                                     int t, int j, vd_df* X, vd_df* bearing) {
   const int v = j / P.W, u = j - v * P.W;
-  const double c = (double)rho[j];
-  const double rx = ((double)u - P.cx_d) / P.fx_d, ry = ((double)v - P.cy_d) / P.fy_d;
-  X[0] = rx / c;
-  X[1] = ry / c;
-  X[2] = 1.0 / c;
+  const vd_df fx = vd_df_make(P.kdf[0], P.kdf[1]), fy = vd_df_make(P.kdf[2], P.kdf[3]);
+  const vd_df cx = vd_df_make(P.kdf[4], P.kdf[5]), cy = vd_df_make(P.kdf[6], P.kdf[7]);
+  const vd_df ifx = vd_df_make(P.kdf[8], P.kdf[9]), ify = vd_df_make(P.kdf[10], P.kdf[11]);
+  const float c = rho[j];
+  const vd_df rx = vd_df_mul(vd_df_sub(vd_df_make((float)u), cx), ifx);
+  const vd_df ry = vd_df_mul(vd_df_sub(vd_df_make((float)v), cy), ify);
+  const vd_df th = vd_df_rcp(vd_df_make(c));
+  X[0] = vd_df_mul(rx, th);
+  X[1] = vd_df_mul(ry, th);
+  X[2] = th;
   const size_t npix = (size_t)P.W * P.H;
-  double xp, yp, fx, fy;
-  if (t == 1) {
-    xp = u;
-    yp = v;
-    const float2 F = flow[j];
-    fx = F.x;
-    fy = F.y;
-  } else {
-    xp = 0.0;
-    yp = 0.0;
-    vd_track64(P, G + 12 * (t - 1), u, v, c, &xp, &yp);
+  vd_df xp = vd_df_make((float)u), yp = vd_df_make((float)v);
+  float2 F0 = flow[j];
+  vd_df Fx = vd_df_make(F0.x), Fy = vd_df_make(F0.y);
+  if (t >= 2) {
+    const vd_df cc = vd_df_make(c);
+    const vd_df Xc = vd_df_add(vd_df_add(vd_df_mul(g[0], rx), vd_df_mul(g[1], ry)),
+                               vd_df_add(g[2], vd_df_mul(cc, g[3])));
+    const vd_df Yc = vd_df_add(vd_df_add(vd_df_mul(g[4], rx), vd_df_mul(g[5], ry)),
+                               vd_df_add(g[6], vd_df_mul(cc, g[7])));
+    const vd_df Zc = vd_df_add(vd_df_add(vd_df_mul(g[8], rx), vd_df_mul(g[9], ry)),
+                               vd_df_add(g[10], vd_df_mul(cc, g[11])));
+    if (Zc.hi > VD_Z_EPS) {
+      const vd_df iz = vd_df_rcp(Zc);
+      xp = vd_df_mul(vd_df_add(vd_df_mul(fx, Xc), vd_df_mul(cx, Zc)), iz);
+      yp = vd_df_mul(vd_df_add(vd_df_mul(fy, Yc), vd_df_mul(cy, Zc)), iz);
+    }
     // members of the rigid set are inside the image; the clamp only guards
-    // the gather against a non-finite position
-    xp = fmin(fmax(xp, 0.0), (double)(P.W - 1));
-    yp = fmin(fmax(yp, 0.0), (double)(P.H - 1));
-    if (!(xp == xp)) xp = 0.0;
-    if (!(yp == yp)) yp = 0.0;
-    vd_bilinear64(flow + (size_t)(t - 1) * npix, P.W, P.H, xp, yp, &fx, &fy);
+    // the gather against a position at or beyond the border
+    const float wmax = (float)(P.W - 1), hmax = (float)(P.H - 1);
+    if (!(xp.hi >= 0.0f)) xp = vd_df_make(0.0f);
+    if (!(xp.hi <= wmax)) xp = vd_df_make(wmax);
+    if (!(yp.hi >= 0.0f)) yp = vd_df_make(0.0f);
+    if (!(yp.hi <= hmax)) yp = vd_df_make(hmax);
+    // bilinear taps (x0, y0) .. (x0 + 1, y0 + 1), x0 = min(floor(x), W - 2)
+    float x0 = floorf(xp.hi), y0 = floorf(yp.hi);
+    if (xp.hi == x0 && xp.lo < 0.0f) x0 -= 1.0f;
+    if (yp.hi == y0 && yp.lo < 0.0f) y0 -= 1.0f;
+    x0 = fminf(fmaxf(x0, 0.0f), (float)(P.W - 2));
+    y0 = fminf(fmaxf(y0, 0.0f), (float)(P.H - 2));
+    const vd_df ax = vd_df_sub(xp, vd_df_make(x0)), ay = vd_df_sub(yp, vd_df_make(y0));
+    const float2* q = flow + (size_t)(t - 1) * npix + (size_t)y0 * P.W + (int)x0;
+    const float2 f00 = q[0], f01 = q[1], f10 = q[P.W], f11 = q[P.W + 1];
+    // F = t + ay (b - t), t = f00 + ax (f01 - f00), b = f10 + ax (f11 - f10)
+    const vd_df tx = vd_df_add(vd_df_make(f00.x), vd_df_mul(ax, vd_two_sum(f01.x, -f00.x)));
+    const vd_df ty = vd_df_add(vd_df_make(f00.y), vd_df_mul(ax, vd_two_sum(f01.y, -f00.y)));
+    const vd_df bx = vd_df_add(vd_df_make(f10.x), vd_df_mul(ax, vd_two_sum(f11.x, -f10.x)));
+    const vd_df by = vd_df_add(vd_df_make(f10.y), vd_df_mul(ax, vd_two_sum(f11.y, -f10.y)));
+    Fx = vd_df_add(tx, vd_df_mul(ay, vd_df_sub(bx, tx)));
+    Fy = vd_df_add(ty, vd_df_mul(ay, vd_df_sub(by, ty)));
   }
-  const double xo = xp + fx, yo = yp + fy;
-  bearing[0] = (xo - P.cx_d) / P.fx_d;
-  bearing[1] = (yo - P.cy_d) / P.fy_d;
-  bearing[2] = 1.0;
+  bearing[0] = vd_df_mul(vd_df_sub(vd_df_add(xp, Fx), cx), ifx);
+  bearing[1] = vd_df_mul(vd_df_sub(vd_df_add(yp, Fy), cy), ify);
+  bearing[2] = vd_df_make(1.0f);
 }
 
-// Real roots of a polynomial of exact degree `deg` split by the sorted points
-// `crit`, with the interval searches spread over the lanes of a warp: the
-// intervals and the bracketed search are those of vd_roots_between, so the
-// roots are bitwise the same; every lane receives all roots.
-__device__ int vd_roots_between_warp(const double* c, int deg, const double* crit, int ncrit,
-                                     double* out, int lane) {
-  const double bound = vd_root_bound(c, deg);
-  double lo = -bound;
-  double flo = vd_poly_eval(c, deg, lo);
-  double mlo = 0.0, mhi = 0.0;      // this lane's interval
-  int mkind = 0;                    // 0 none, 1 root at lo, 2 search
-  int kinds = 0;                    // 2 bits per interval
-  int ni = 0;
+__device__ __forceinline__ vd_df vd_shfl_df(vd_df x, int src) {
+  return vd_df{__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
+}
+
+// vd_split_rootsf with the interval searches in parallel lanes (the same
+// intervals and searches; every lane receives all roots).
+__device__ int vd_split_rootsf_warp(const float* c, int deg, const float* crit, int ncrit,
+                                    float* out, int lane) {
+  const float bound = vd_root_boundf(c, deg);
+  float lo = -bound, flo = vd_polyf(c, deg, lo);
+  float mlo = 0.0f, mhi = 0.0f;
+  bool mneg = false;
+  int mkind = 0, kinds = 0, ni = 0;
   for (int i = 0; i <= ncrit; ++i) {
-    const double hi = i < ncrit ? fmin(fmax(crit[i], -bound), bound) : bound;
+    const float hi = i < ncrit ? fminf(fmaxf(crit[i], -bound), bound) : bound;
     if (!(hi > lo)) continue;
-    const double fhi = vd_poly_eval(c, deg, hi);
-    const int kind = flo == 0.0 ? 1 : (((flo < 0.0) != (fhi < 0.0) && fhi != 0.0) ? 2 : 0);
+    const float fhi = vd_polyf(c, deg, hi);
+    const int kind = flo == 0.0f ? 1 : (((flo < 0.0f) != (fhi < 0.0f) && fhi != 0.0f) ? 2 : 0);
     kinds |= kind << (2 * ni);
     if (ni == lane) {
       mlo = lo;
       mhi = hi;
       mkind = kind;
+      mneg = flo < 0.0f;
     }
     ++ni;
     lo = hi;
     flo = fhi;
   }
-  const double mine = mkind == 2 ? vd_poly_bracketed_root(c, deg, mlo, mhi) : mlo;
+  const float mine = mkind == 2 ? vd_bracketed_rootf(c, deg, mlo, mhi, mneg) : mlo;
   int n = 0;
-  for (int k = 0; k < 5; ++k) {
-    const double r = __shfl_sync(0xffffffffu, mine, k);
+  for (int k = 0; k < 4; ++k) {
+    const float r = __shfl_sync(0xffffffffu, mine, k);
     if (k < ni && ((kinds >> (2 * k)) & 3)) out[n++] = r;
   }
   return n;
 }
 
-// The real roots of the P3P quartic as vd_poly_real_roots finds them
-// (second derivative, first derivative, quartic), each stage's interval
-// searches in parallel lanes.
-__device__ int vd_quartic_roots_warp(const double* cin, double* out, int lane) {
-  double mx = 0.0;
-  for (int i = 0; i <= 4; ++i) mx = fmax(mx, fabs(cin[i]));
-  if (mx == 0.0) return 0;
-  if (fabs(cin[4]) <= 1e-14 * mx) return vd_poly_real_roots(cin, 4, out);   // lower degree
-  const double q[3] = {cin[2] * 2.0, cin[3] * 6.0, cin[4] * 12.0};
-  const double split = -q[1] / (2.0 * q[2]);
-  double r2[2];
-  const int n2 = vd_roots_between_warp(q, 2, &split, 1, r2, lane);
-  const double cc[4] = {cin[1], cin[2] * 2.0, cin[3] * 3.0, cin[4] * 4.0};
-  double r3[3];
-  const int n3 = vd_roots_between_warp(cc, 3, r2, n2, r3, lane);
-  return vd_roots_between_warp(cin, 4, r3, n3, out, lane);
+// vd_p3p_df_roots with the shifted quartic's interval searches and
+// double-float polish in parallel lanes; every lane receives all roots
+// (ascending).  A
+// quartic whose leading coefficient is negligible takes the float64 search
+// of vd_geom64.cuh (lower degree), as the float64 solver does.
+__device__ int vd_p3p_df_roots_warp(const VdP3Pdf& g, const vd_df* res, vd_df* out, int lane) {
+  float mx = 0.0f;
+  for (int i = 0; i <= 4; ++i) mx = fmaxf(mx, fabsf(res[i].hi));
+  if (!(mx > 0.0f)) return 0;
+  if (!(fabsf(res[4].hi) > 1e-7f * mx)) {
+    double rd[5], vd[4];
+    for (int i = 0; i <= 4; ++i) rd[i] = vd_df_to(res[i]);
+    const int n = vd_poly_real_roots(rd, 4, vd);
+    for (int i = 0; i < n; ++i) out[i] = vd_df_from(vd[i]);
+    return n;
+  }
+  vd_df d[5];
+  const vd_df m = vd_df_taylor_shift(res, d);
+  float cf[5];
+  float dm = 0.0f;
+  for (int i = 0; i <= 4; ++i) dm = fmaxf(dm, fabsf(d[i].hi));
+  const float s = 1.0f / dm;
+  for (int i = 0; i <= 4; ++i) cf[i] = d[i].hi * s;
+  const float q[3] = {cf[2] * 2.0f, cf[3] * 6.0f, cf[4] * 12.0f};
+  const float split = -q[1] / (2.0f * q[2]);
+  float r2[2], r3[3];
+  const int n2 = vd_split_rootsf_warp(q, 2, &split, 1, r2, lane);
+  const float cc[4] = {cf[1], cf[2] * 2.0f, cf[3] * 3.0f, cf[4] * 4.0f};
+  const int n3 = vd_split_rootsf_warp(cc, 3, r2, n2, r3, lane);
+  // the quartic's sign at the ends of the intervals, in double-float: lane
+  // k < n3 + 2 evaluates end k (-bound, the split points, +bound)
+  const float bound = vd_root_boundf(cf, 4);
+  float e = -bound;
+  if (lane >= 1 && lane <= n3) e = fminf(fmaxf(r3[lane - 1], -bound), bound);
+  else if (lane == n3 + 1) e = bound;
+  const vd_df fe = vd_df_poly(d, 4, vd_df_make(e));
+  const int sgn = (fe.hi == 0.0f && fe.lo == 0.0f) ? 0 : (vd_df_lt0(fe) ? -1 : 1);
+  // interval k = [end k, end k + 1] on lane k
+  float mlo = 0.0f, mhi = 0.0f;
+  int kind = 0;
+  bool mneg = false;
+  {
+    const float ehi = __shfl_sync(0xffffffffu, e, lane < 31 ? lane + 1 : 0);
+    const int shi = __shfl_sync(0xffffffffu, sgn, lane < 31 ? lane + 1 : 0);
+    if (lane <= n3 && ehi > e) {
+      mlo = e;
+      mhi = ehi;
+      mneg = sgn < 0;
+      kind = sgn == 0 ? 1 : ((sgn != shi && shi != 0) ? 2 : 0);
+    }
+  }
+  vd_df mine = vd_df_make(mlo);
+  mine = vd_df_add(mine, m);        // back from the shifted variable
+  if (kind == 2) {    // no warp-wide operation inside: lanes may diverge here
+    const float x0 = vd_bracketed_rootf(cf, 4, mlo, mhi, mneg);
+    mine = vd_p3p_df_polish(g, m, x0, mlo, mhi);
+  }
+  int n = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int kk = __shfl_sync(0xffffffffu, kind, k);
+    const vd_df r = vd_shfl_df(mine, k);
+    if (k <= n3 && kk) out[n++] = r;
+  }
+  return n;
 }
 
-// One warp per sample (samples spread over the SMs: the float64 pipe is
-// narrow, so the solve is latency-bound per warp).  Lanes 0-2 build the three
-// correspondences, every lane forms the quartic, lanes 0-3 turn one root each
-// into a pose and its ordering key; each lane then finds its rank.
+// One warp per sample (samples spread over the SMs).  Lanes 0-2 build the
+// three correspondences, every lane forms the quartic, the root searches
+// run in parallel lanes, lanes 0-3 turn one root each into a pose and its
+// ordering key; each lane then finds its rank.  Writes the roots (float64,
+// ordered by rotation vector, then translation), their count and their
+// float K R | K tau for the dense scoring.
 __global__ void __launch_bounds__(32)
 k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restrict__ flow,
               const float* __restrict__ rho, const int* __restrict__ idx,
               const int* __restrict__ n_rigid, int t, uint32_t itcode, double* __restrict__ roots,
-              int* __restrict__ root_count) {
+              int* __restrict__ root_count, float* __restrict__ rootsf) {
   const int g = blockIdx.x;
   const int lane = threadIdx.x;
   if (g >= P.S) return;
@@ -288,52 +369,56 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
   }
   if (!ok) {
     if (lane == 0) root_count[g] = 0;
+    if (lane < 4)
+      for (int i = 0; i < 12; ++i) rootsf[48 * g + 12 * lane + i] = 0.0f;
     return;
   }
-  double Xl[3] = {0, 0, 0}, fl[3] = {0, 0, 1};
-  if (lane < 3)
-    vd_correspondence64(P, G, flow, rho, t, idx[pick[lane < 3 ? lane : 0]], Xl, fl);
-  double X[9], f[9];
+  // G_{t-1} as double-float, one value per lane
+  vd_df gl = vd_df_make(0.0f);
+  if (t >= 2 && lane < 12) gl = vd_df_from(G[12 * (t - 1) + lane]);
+  vd_df gt[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) gt[i] = vd_shfl_df(gl, i);
+  vd_df Xl[3] = {vd_df_make(0.0f), vd_df_make(0.0f), vd_df_make(0.0f)};
+  vd_df fl[3] = {vd_df_make(0.0f), vd_df_make(0.0f), vd_df_make(1.0f)};
+  if (lane < 3) vd_correspondence_df(P, gt, flow, rho, t, idx[pick[lane]], Xl, fl);
+  vd_df X[9], f[9];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      X[3 * k + c] = __shfl_sync(0xffffffffu, Xl[c], k);
-      f[3 * k + c] = __shfl_sync(0xffffffffu, fl[c], k);
+      X[3 * k + c] = vd_shfl_df(Xl[c], k);
+      f[3 * k + c] = vd_shfl_df(fl[c], k);
     }
-  VdP3P geo;
-  double v[4], res[5];
-  const int nr = vd_p3p_quartic(f, X, &geo, res) < 0 ? 0 : vd_quartic_roots_warp(res, v, lane);
-  double T[12];
+  VdP3Pdf geo;
+  vd_df res[5], v[4];
+  const int nr = vd_p3p_df_quartic(f, X, &geo, res) ? vd_p3p_df_roots_warp(geo, res, v, lane) : 0;
+  vd_df T[12];
   bool valid = false;
-  if (lane < 4 && lane < nr) valid = vd_p3p_pose(geo, X, v[lane], T);
-  double key[6] = {0, 0, 0, 0, 0, 0};
+  if (lane < 4 && lane < nr) valid = vd_p3p_df_pose(geo, X, v[lane], T);
+  float key[6] = {0, 0, 0, 0, 0, 0};
   if (valid) {
     // ordering key: rotation vector (float32 is plenty to order distinct
-    // roots; the float64 logarithm near a half turn), then the translation
-    const float cf = 0.5f * ((float)T[0] + (float)T[5] + (float)T[10] - 1.0f);
-    if (cf < -0.9f) {
-      vd_so3_log(T, key);
-    } else {
-      const float vx = 0.5f * (float)(T[9] - T[6]), vy = 0.5f * (float)(T[2] - T[8]);
-      const float vz = 0.5f * (float)(T[4] - T[1]);
-      const float s = sqrtf(vx * vx + vy * vy + vz * vz);
-      const float th = atan2f(s, cf);
-      const float fk = s < 1e-6f ? 1.0f + th * th * (1.0f / 6.0f) : th / s;
-      key[0] = vx * fk;
-      key[1] = vy * fk;
-      key[2] = vz * fk;
-    }
-    key[3] = T[3];
-    key[4] = T[7];
-    key[5] = T[11];
+    // roots), then the translation
+    const float cf = 0.5f * (T[0].hi + T[5].hi + T[10].hi - 1.0f);
+    const float vx = 0.5f * (T[9].hi - T[6].hi), vy = 0.5f * (T[2].hi - T[8].hi);
+    const float vz = 0.5f * (T[4].hi - T[1].hi);
+    const float sn = sqrtf(vx * vx + vy * vy + vz * vz);
+    const float th = atan2f(sn, cf);
+    const float fk = sn < 1e-6f ? 1.0f + th * th * (1.0f / 6.0f) : th / sn;
+    key[0] = vx * fk;
+    key[1] = vy * fk;
+    key[2] = vz * fk;
+    key[3] = T[3].hi;
+    key[4] = T[7].hi;
+    key[5] = T[11].hi;
   }
   // rank among the valid roots by (rotation vector, translation), ties by lane
   int rank = 0, count = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const bool vk = __shfl_sync(0xffffffffu, valid, k);
-    double kk[6];
+    float kk[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) kk[i] = __shfl_sync(0xffffffffu, key[i], k);
     if (!vk) continue;
@@ -343,28 +428,22 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
     for (int i = 0; i < 6 && cmp == 0; ++i) cmp = kk[i] < key[i] ? -1 : (kk[i] > key[i] ? 1 : 0);
     if (cmp < 0 || (cmp == 0 && k < lane)) ++rank;
   }
-  double* out = roots + (size_t)g * 48;
-  if (valid)
-    for (int i = 0; i < 12; ++i) out[12 * rank + i] = T[i];
+  if (valid) {
+    double* out = roots + (size_t)g * 48 + 12 * rank;
+    for (int i = 0; i < 12; ++i) out[i] = vd_df_to(T[i]);
+    // float K R | K tau of the root, for the dense scoring
+    const float fxf = P.kdf[0], fyf = P.kdf[2], cxf = P.kdf[4], cyf = P.kdf[6];
+    float* o = rootsf + 48 * g + 12 * rank;
+    for (int i = 0; i < 4; ++i) {
+      const float r0 = T[i].hi, r1 = T[4 + i].hi, r2 = T[8 + i].hi;
+      o[i < 3 ? i : 9] = fmaf(fxf, r0, cxf * r2);
+      o[i < 3 ? 3 + i : 10] = fmaf(fyf, r1, cyf * r2);
+      o[i < 3 ? 6 + i : 11] = r2;
+    }
+  }
+  if (lane < 4 && lane >= count)      // slots without a root
+    for (int i = 0; i < 12; ++i) rootsf[48 * g + 12 * lane + i] = 0.0f;
   if (lane == 0) root_count[g] = count;
-}
-
-// float K R | K tau of every root slot (invalid slots: zero).
-__global__ void k_roots_float(DevParams P, const double* __restrict__ roots,
-                              const int* __restrict__ root_count, float* __restrict__ rootsf) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= 4 * P.S) return;
-  float* o = rootsf + 12 * r;
-  if ((r & 3) >= root_count[r >> 2]) {
-    for (int i = 0; i < 12; ++i) o[i] = 0.0f;
-    return;
-  }
-  const double* g = roots + 12 * r;
-  for (int i = 0; i < 4; ++i) {
-    o[i < 3 ? i : 9] = (float)(P.fx_d * g[i] + P.cx_d * g[8 + i]);
-    o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
-    o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -762,11 +841,9 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   vd_prof_end(c, VD_ST_RIGID, 3);
   vd_prof_begin(c, VD_ST_P3P);
   k_p3p_samples<<<P.S, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
-                                                       c->n_rigid, t, itcode, c->roots,
-                                                       c->root_count);
-  const int M = 4 * P.S;
-  k_roots_float<<<(M + 127) / 128, 128, 0, c->stream>>>(P, c->roots, c->root_count, c->rootsf);
-  vd_prof_end(c, VD_ST_P3P, 2);
+                                            c->n_rigid, t, itcode, c->roots, c->root_count,
+                                            c->rootsf);
+  vd_prof_end(c, VD_ST_P3P, 1);
   vd_prof_begin(c, VD_ST_SCORE);
   launch_pose_score_only(c);
   vd_prof_end(c, VD_ST_SCORE, 2);
