@@ -225,8 +225,8 @@ extern "C" vd_status vd_destroy(vd_ctx* c) {
   }
   void* ptrs[] = {c->flow, c->prior_val, c->prior_rho, c->prior_conf, c->rho, c->q, c->qhat,
                   c->conf, c->G, c->G_init, c->posef, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
-                  c->coarse, c->lam, c->flags, c->blk_counts, c->blk_offsets, c->n_rigid,
-                  c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->partial,
+                  c->coarse, c->lam, c->flags, c->blk_counts, c->n_rigid,
+                  c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->rootsr, c->partial,
                   c->root_energy, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
                   c->ep_M, c->ep_E, c->ep_cand, c->ep_count, c->stat_partial, c->stat_out,
                   c->vc_cover, c->vc_counts, c->vc_pose, c->pc_out};
@@ -301,7 +301,6 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(lam, N * np);
   A(flags, np);
   A(blk_counts, c->nblk_scan);
-  A(blk_offsets, c->nblk_scan);
   A(n_rigid, 1);
   A(rigid_idx, np);
   A(rpts, np);
@@ -309,6 +308,7 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(roots, (size_t)S * 48);
   A(root_count, S);
   A(rootsf, (size_t)4 * S * 12);
+  A(rootsr, (size_t)4 * S * 12);
   A(partial, (size_t)4 * S * c->nblk_score);
   A(root_energy, 4 * S);
   A(sample_pose, 12 * S * N);

@@ -5,6 +5,7 @@
 // robust to the heavy-tailed Fisk noise by iterative re-weighting with the
 // weight 1 / (1 + (d / alpha0)^2) of the Sampson distance d.
 #include "vd_device.cuh"
+#include "vd_df64.cuh"
 #include "vd_geom64.cuh"
 
 #define EP_THREADS 256
@@ -39,17 +40,11 @@ cudaError_t launch_initial_rho(vd_ctx* c) {
 // sums in float64.
 // ---------------------------------------------------------------------------
 
-// Double-float arithmetic (value = hi + lo, |lo| <= ulp(hi) / 2; Dekker 1971,
-// Knuth's TwoSum): about 2^-44 per operation on the float32 pipes, which
-// are 64 times wider than the float64 pipe of this GPU.
-struct VdDF {
-  float hi, lo;
-};
-__device__ __forceinline__ VdDF vd_df(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ VdDF vd_df_mul(VdDF a, VdDF b) {
+// Accumulation in double-float (vd_df64.cuh): a product with its exact
+// error, and a sum whose error term is carried along (the "sloppy" form:
+// one TwoSum of the leading parts, the trailing parts added in float32),
+// about 2^-44 per operation.
+__device__ __forceinline__ vd_df ep_df_mul(vd_df a, vd_df b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);          // exact error of the product
   e = fmaf(a.hi, b.lo, e);
@@ -57,7 +52,7 @@ __device__ __forceinline__ VdDF vd_df_mul(VdDF a, VdDF b) {
   const float s = p + e;
   return {s, e - (s - p)};
 }
-__device__ __forceinline__ VdDF vd_df_add(VdDF a, VdDF b) {
+__device__ __forceinline__ vd_df ep_df_add(vd_df a, vd_df b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
   float err = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum
@@ -66,11 +61,29 @@ __device__ __forceinline__ VdDF vd_df_add(VdDF a, VdDF b) {
   return {t, err - (t - s)};
 }
 
+// Calibrated rays of pixel (u, v) and of its flow end point, in
+// double-float from the float32 inputs (no float64 instruction per pixel:
+// on this GPU one costs a warp 64 cycles).
+__device__ __forceinline__ void ep_rays(const DevParams& P, int u, int v, float2 F, vd_df* a0,
+                                        vd_df* a1, vd_df* b0, vd_df* b1) {
+  const vd_df cx = vd_df_make(P.kdf[4], P.kdf[5]), cy = vd_df_make(P.kdf[6], P.kdf[7]);
+  const vd_df ifx = vd_df_make(P.kdf[8], P.kdf[9]), ify = vd_df_make(P.kdf[10], P.kdf[11]);
+  const vd_df uu = vd_df_make((float)u), vv = vd_df_make((float)v);
+  *a0 = vd_df_mul(vd_df_sub(uu, cx), ifx);
+  *a1 = vd_df_mul(vd_df_sub(vv, cy), ify);
+  *b0 = vd_df_mul(vd_df_sub(vd_two_sum((float)u, F.x), cx), ifx);
+  *b1 = vd_df_mul(vd_df_sub(vd_two_sum((float)v, F.y), cy), ify);
+}
+
+__device__ __forceinline__ vd_df ep_shfl_xor(vd_df x, int o) {
+  return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
 __global__ void __launch_bounds__(EP_THREADS)
 k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restrict__ Eprev,
-            int weighted, double* __restrict__ partial) {
-  __shared__ double sW[EP_THREADS / 32][45];
-  VdDF acc[45];
+            int weighted, float2* __restrict__ partial) {
+  __shared__ vd_df sW[EP_THREADS / 32][45];
+  vd_df acc[45];
 #pragma unroll
   for (int i = 0; i < 45; ++i) acc[i] = {0.0f, 0.0f};
   // the IRLS weight needs no extended precision: on noise-free flow every
@@ -78,20 +91,18 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
   // relative weight error moves E far below the pose tolerance
   float Ef[9];
   for (int i = 0; i < 9; ++i) Ef[i] = weighted ? (float)Eprev[i] : 0.0f;
-  const float ff = (float)sqrt(P.fx_d * P.fy_d);
+  const float ff = sqrtf(P.fx * P.fy);
   const float ia = 1.0f / P.alpha0;
-  const double ifx = 1.0 / P.fx_d, ify = 1.0 / P.fy_d;
   const size_t npix = (size_t)P.W * P.H;
   for (size_t j = (size_t)blockIdx.x * EP_THREADS + threadIdx.x; j < npix;
        j += (size_t)gridDim.x * EP_THREADS) {
     const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
     const float2 F = flow[j];
-    const double a0 = ((double)u - P.cx_d) * ifx, a1 = ((double)v - P.cy_d) * ify;
-    const double b0 = ((double)u + (double)F.x - P.cx_d) * ifx;
-    const double b1 = ((double)v + (double)F.y - P.cy_d) * ify;
+    vd_df A0, A1, B0, B1;
+    ep_rays(P, u, v, F, &A0, &A1, &B0, &B1);
     float w = 1.0f;
     if (weighted) {
-      const float af[3] = {(float)a0, (float)a1, 1.0f}, bf[3] = {(float)b0, (float)b1, 1.0f};
+      const float af[3] = {A0.hi, A1.hi, 1.0f}, bf[3] = {B0.hi, B1.hi, 1.0f};
       float Ea[3], Etb[3];
       for (int i = 0; i < 3; ++i) {
         Ea[i] = Ef[3 * i] * af[0] + Ef[3 * i + 1] * af[1] + Ef[3 * i + 2] * af[2];
@@ -103,31 +114,31 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
       w = 1.0f / (1.0f + d * d);
     }
     // r = b (x) a with a2 = b2 = 1
-    const VdDF A0 = vd_df(a0), A1 = vd_df(a1), B0 = vd_df(b0), B1 = vd_df(b1);
-    const VdDF one = {1.0f, 0.0f};
-    VdDF r[9] = {vd_df_mul(B0, A0), vd_df_mul(B0, A1), B0,
-                 vd_df_mul(B1, A0), vd_df_mul(B1, A1), B1,
-                 A0,                A1,                one};
+    const vd_df one = {1.0f, 0.0f};
+    vd_df r[9] = {ep_df_mul(B0, A0), ep_df_mul(B0, A1), B0,
+                  ep_df_mul(B1, A0), ep_df_mul(B1, A1), B1,
+                  A0,                A1,                one};
     int k = 0;
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-      const VdDF wr = vd_df_mul(r[p], {w, 0.0f});
+      const vd_df wr = ep_df_mul(r[p], {w, 0.0f});
 #pragma unroll
-      for (int q = p; q < 9; ++q) acc[k] = vd_df_add(acc[k], vd_df_mul(wr, r[q])), ++k;
+      for (int q = p; q < 9; ++q) acc[k] = ep_df_add(acc[k], ep_df_mul(wr, r[q])), ++k;
     }
   }
+  // warp and block sums in double-float, fixed order; one partial per block
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 45; ++i) {
-    double x = (double)acc[i].hi + (double)acc[i].lo;
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    vd_df x = acc[i];
+    for (int o = 16; o > 0; o >>= 1) x = vd_df_add(x, ep_shfl_xor(x, o));
     if (lane == 0) sW[wid][i] = x;
   }
   __syncthreads();
   if (threadIdx.x < 45) {
-    double s = 0.0;
-    for (int w = 0; w < EP_THREADS / 32; ++w) s += sW[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * 45 + threadIdx.x] = s;
+    vd_df s = sW[0][threadIdx.x];
+    for (int w = 1; w < EP_THREADS / 32; ++w) s = vd_df_add(s, sW[w][threadIdx.x]);
+    partial[(size_t)blockIdx.x * 45 + threadIdx.x] = make_float2(s.hi, s.lo);
   }
 }
 
@@ -138,46 +149,61 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
 // inverse, then every step x <- (M + d I)^-1 x / |x| is a 9-lane
 // matrix-vector product, until the iterate stops moving.  `warm` starts from
 // the previous round's E, else from (1, ..., 1) / 3.
-__global__ void __launch_bounds__(64)
-k_ep_solve(const double* __restrict__ partial, int nblk, double* __restrict__ Mout,
+__global__ void __launch_bounds__(512)
+k_ep_solve(const float2* __restrict__ partial, int nblk, double* __restrict__ Mout,
            double* __restrict__ Eio, int warm) {
   __shared__ double sM[45];
   __shared__ double sA[81];   // L (lower triangle)
   __shared__ double sRd[9];   // 1 / L_jj
   __shared__ double sI[81];   // (M + d I)^-1, column-major by solving lane
   const int tid = threadIdx.x;
-  if (tid < 45) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * 45 + tid];
-    sM[tid] = s;
-    Mout[tid] = s;
-  }
-  __syncthreads();
-  if (tid >= 32) return;
-  if (tid == 0) {
-    double tr = 0.0;
-    int k = 0;
-    for (int p = 0; p < 9; ++p)
-      for (int q = p; q < 9; ++q) {
-        sA[9 * q + p] = sM[k];   // lower triangle, row q column p
-        if (p == q) tr += sM[k];
-        ++k;
+  {
+    // entry e by warp e % 16 (lanes: strided blocks), double-float sums in
+    // fixed order, then one conversion to float64
+    const int lane = tid & 31, wp = tid >> 5;
+    for (int e = wp; e < 45; e += 16) {
+      vd_df s = {0.0f, 0.0f};
+      for (int b = lane; b < nblk; b += 32) {
+        const float2 x = partial[(size_t)b * 45 + e];
+        s = vd_df_add(s, vd_df_make(x.x, x.y));
       }
-    const double shift = 1e-14 * tr + 1e-300;
-    for (int j = 0; j < 9; ++j) {
-      double d = sA[10 * j] + shift;
-      for (int m = 0; m < j; ++m) d -= sA[9 * j + m] * sA[9 * j + m];
-      d = fmax(d, shift);
-      const double r = vd_rsqrt64(d);
-      sRd[j] = r;
-      for (int i = j + 1; i < 9; ++i) {
-        double s = sA[9 * i + j];
-        for (int m = 0; m < j; ++m) s -= sA[9 * i + m] * sA[9 * j + m];
-        sA[9 * i + j] = s * r;
+      for (int o = 16; o > 0; o >>= 1) s = vd_df_add(s, ep_shfl_xor(s, o));
+      if (lane == 0) {
+        const double d = vd_df_to(s);
+        sM[e] = d;
+        Mout[e] = d;
       }
     }
   }
+  __syncthreads();
+  if (tid >= 32) return;
+  if (tid < 9) {
+    // lane q copies column q of the upper triangle into row q's lower part
+    int k = 0;
+    for (int p = 0; p < 9; ++p)
+      for (int q = p; q < 9; ++q, ++k)
+        if (q == tid) sA[9 * q + p] = sM[k];   // lower triangle, row q column p
+  }
   __syncwarp();
+  double tr = 0.0;
+  for (int p = 0; p < 9; ++p) tr += sA[10 * p];
+  const double shift = 1e-14 * tr + 1e-300;
+  // Cholesky by columns: every lane forms the pivot of column j, lane i > j
+  // its entry of the column (the same operations in the same order as the
+  // row-by-row form, spread over lanes)
+  for (int j = 0; j < 9; ++j) {
+    double d = sA[10 * j] + shift;
+    for (int m = 0; m < j; ++m) d -= sA[9 * j + m] * sA[9 * j + m];
+    d = fmax(d, shift);
+    const double r = vd_rsqrt64(d);
+    if (tid == 0) sRd[j] = r;
+    if (tid > j && tid < 9) {
+      double s = sA[9 * tid + j];
+      for (int m = 0; m < j; ++m) s -= sA[9 * tid + m] * sA[9 * j + m];
+      sA[9 * tid + j] = s * r;
+    }
+    __syncwarp();
+  }
   if (tid < 9) {   // column tid of the inverse: L L^T z = e_tid
     double y[9];
 #pragma unroll
@@ -287,37 +313,43 @@ __global__ void k_ep_decompose(const double* __restrict__ Ein, double* __restric
 }
 
 // Pixels whose least-squares triangulation lam_b b = lam_a R a + t has both
-// depths positive, for each of the four candidate motions.
+// depths positive, for each of the four candidate motions.  A vote: taken
+// in float32 (a pixel within rounding of a zero depth may count on either
+// side; the winner is ahead by thousands of pixels), with the signs of the
+// depths read from their numerators and the common determinant (no
+// division).
 __global__ void __launch_bounds__(EP_THREADS)
 k_ep_cheirality(DevParams P, const float2* __restrict__ flow, const double* __restrict__ cand,
                 int* __restrict__ counts) {
-  __shared__ double sC[48];
-  if (threadIdx.x < 48) sC[threadIdx.x] = cand[threadIdx.x];
+  __shared__ float sC[48];
+  if (threadIdx.x < 48) sC[threadIdx.x] = (float)cand[threadIdx.x];
   __syncthreads();
   int cnt[4] = {0, 0, 0, 0};
   const size_t npix = (size_t)P.W * P.H;
+  const float ifx = P.kdf[8], ify = P.kdf[10];
   for (size_t j = (size_t)blockIdx.x * EP_THREADS + threadIdx.x; j < npix;
        j += (size_t)gridDim.x * EP_THREADS) {
     const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
     const float2 F = flow[j];
-    const double a[3] = {((double)u - P.cx_d) / P.fx_d, ((double)v - P.cy_d) / P.fy_d, 1.0};
-    const double b[3] = {((double)u + (double)F.x - P.cx_d) / P.fx_d,
-                         ((double)v + (double)F.y - P.cy_d) / P.fy_d, 1.0};
+    const float a[3] = {((float)u - P.cx) * ifx, ((float)v - P.cy) * ify, 1.0f};
+    const float b[3] = {((float)u + F.x - P.cx) * ifx, ((float)v + F.y - P.cy) * ify, 1.0f};
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double* T = sC + 12 * k;
-      const double Ra[3] = {T[0] * a[0] + T[1] * a[1] + T[2] * a[2],
-                            T[4] * a[0] + T[5] * a[1] + T[6] * a[2],
-                            T[8] * a[0] + T[9] * a[1] + T[10] * a[2]};
-      const double t[3] = {T[3], T[7], T[11]};
-      const double m11 = Ra[0] * Ra[0] + Ra[1] * Ra[1] + Ra[2] * Ra[2];
-      const double m12 = -(Ra[0] * b[0] + Ra[1] * b[1] + Ra[2] * b[2]);
-      const double m22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-      const double r1 = -(Ra[0] * t[0] + Ra[1] * t[1] + Ra[2] * t[2]);
-      const double r2 = b[0] * t[0] + b[1] * t[1] + b[2] * t[2];
-      const double det = m11 * m22 - m12 * m12;
-      const double la = (m22 * r1 - m12 * r2) / det;
-      const double lb = (m11 * r2 - m12 * r1) / det;
-      cnt[k] += (la > 0.0 && lb > 0.0) ? 1 : 0;
+      const float* T = sC + 12 * k;
+      const float Ra[3] = {T[0] * a[0] + T[1] * a[1] + T[2] * a[2],
+                           T[4] * a[0] + T[5] * a[1] + T[6] * a[2],
+                           T[8] * a[0] + T[9] * a[1] + T[10] * a[2]};
+      const float t[3] = {T[3], T[7], T[11]};
+      const float m11 = Ra[0] * Ra[0] + Ra[1] * Ra[1] + Ra[2] * Ra[2];
+      const float m12 = -(Ra[0] * b[0] + Ra[1] * b[1] + Ra[2] * b[2]);
+      const float m22 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+      const float r1 = -(Ra[0] * t[0] + Ra[1] * t[1] + Ra[2] * t[2]);
+      const float r2 = b[0] * t[0] + b[1] * t[1] + b[2] * t[2];
+      const float det = m11 * m22 - m12 * m12;
+      const float na = m22 * r1 - m12 * r2, nb = m11 * r2 - m12 * r1;
+      const bool pos = det > 0.0f ? (na > 0.0f && nb > 0.0f)
+                                  : (det < 0.0f && na < 0.0f && nb < 0.0f);
+      cnt[k] += pos ? 1 : 0;
     }
   }
   for (int k = 0; k < 4; ++k) {
@@ -367,7 +399,7 @@ cudaError_t launch_eight_point(vd_ctx* c) {
   for (int r = 0; r < VD_IRLS_ITERS; ++r) {
     k_ep_normal<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_E, r > 0 ? 1 : 0,
                                                             c->ep_partial);
-    k_ep_solve<<<1, 64, 0, c->stream>>>(c->ep_partial, c->ep_blocks, c->ep_M, c->ep_E, r > 0);
+    k_ep_solve<<<1, 512, 0, c->stream>>>(c->ep_partial, c->ep_blocks, c->ep_M, c->ep_E, r > 0);
   }
   k_ep_decompose<<<1, 32, 0, c->stream>>>(c->ep_E, c->ep_cand, c->ep_count);
   k_ep_cheirality<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_cand,

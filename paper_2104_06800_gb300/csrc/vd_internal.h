@@ -92,14 +92,14 @@ struct vd_ctx {
   // pose step scratch
   unsigned char* flags;    // [H*W]
   int* blk_counts;         // [nblk_scan]
-  int* blk_offsets;        // [nblk_scan]
   int* n_rigid;            // [1]
   int* rigid_idx;          // [H*W]
   float4* rpts;            // [H*W] (X, Y, Z, w)
   float4* robs;            // [H*W] (x_obs, y_obs, alpha, 0)
   double* roots;           // [S][4][12]
   int* root_count;         // [S]
-  float* rootsf;           // [S*4][12]
+  float* rootsf;           // [S*4][12] float K R | K tau of every root slot
+  float* rootsr;           // [S*4][12] float R | tau of every root slot
   float* partial;          // [S*4][score blocks]
   double* root_energy;     // [S*4]
   double* sample_pose;     // [N][S][12] kept root of every sample, per frame
@@ -112,7 +112,7 @@ struct vd_ctx {
   int nblk_score;
 
   // bootstrap scratch
-  double* ep_partial;      // [blocks][45]
+  float2* ep_partial;      // [blocks][45] double-float partial sums of the normal matrix
   double* ep_M;            // [45]
   double* ep_E;            // [9] current essential matrix (row-major)
   double* ep_cand;         // [4][12]

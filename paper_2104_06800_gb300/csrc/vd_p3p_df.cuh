@@ -20,6 +20,14 @@
 
 #include "vd_df64.cuh"
 
+// The solver's steps are inlined on the device: out-of-line calls (arrays
+// passed through local memory) measured 1.4x slower per P3P launch.
+#ifdef __CUDA_ARCH__
+#define VD_DF_CALL __forceinline__
+#else
+#define VD_DF_CALL inline
+#endif
+
 struct VdP3Pdf {
   vd_df f[9];                      // unit bearings
   vd_df a2, b2, c2, ca, cb, cg;
@@ -53,7 +61,7 @@ VD_HD __forceinline__ vd_df vd_df_dist2(const vd_df* X, int i, int k) {
 
 // The instance and its quartic res[0..4] (low order first); false for a
 // degenerate triangle (a side of length 0).
-VD_HD __forceinline__ bool vd_p3p_df_quartic(const vd_df* fin, const vd_df* X, VdP3Pdf* g,
+VD_HD VD_DF_CALL bool vd_p3p_df_quartic(const vd_df* fin, const vd_df* X, VdP3Pdf* g,
                                             vd_df* res) {
   for (int i = 0; i < 9; ++i) g->f[i] = fin[i];
   vd_df_normalize3(g->f);
@@ -127,7 +135,7 @@ VD_HD __forceinline__ float vd_polyf(const float* c, int deg, float x) {
 // A bracketed root of a float32 polynomial that changes sign on [lo, hi]
 // (neg_lo: its sign at lo): Newton steps, a bisection step where Newton
 // leaves the bracket; at most 40 steps, stops at a 1e-6 relative step.
-VD_HD __forceinline__ float vd_bracketed_rootf(const float* c, int deg, float lo, float hi,
+VD_HD VD_DF_CALL float vd_bracketed_rootf(const float* c, int deg, float lo, float hi,
                                                bool neg_lo) {
   float d[4];
   for (int i = 1; i <= deg; ++i) d[i - 1] = c[i] * (float)i;
@@ -152,7 +160,7 @@ VD_HD __forceinline__ float vd_bracketed_rootf(const float* c, int deg, float lo
 }
 
 // Bound on the magnitude of every root of a float32 polynomial (Fujiwara).
-VD_HD __forceinline__ float vd_root_boundf(const float* c, int deg) {
+VD_HD VD_DF_CALL float vd_root_boundf(const float* c, int deg) {
   float b = 0.0f;
   for (int i = 0; i < deg; ++i) {
     float r = fabsf(c[i] / c[deg]);
@@ -166,7 +174,7 @@ VD_HD __forceinline__ float vd_root_boundf(const float* c, int deg) {
 
 // Float32 roots of a polynomial of degree `deg` on the intervals cut by the
 // sorted split points (one per sign change), ascending; at most ncrit + 1.
-VD_HD __forceinline__ int vd_split_rootsf(const float* c, int deg, const float* crit, int ncrit,
+VD_HD VD_DF_CALL int vd_split_rootsf(const float* c, int deg, const float* crit, int ncrit,
                                           float* out) {
   const float bound = vd_root_boundf(c, deg);
   float lo = -bound, flo = vd_polyf(c, deg, lo);
@@ -188,7 +196,7 @@ VD_HD __forceinline__ int vd_split_rootsf(const float* c, int deg, const float* 
 // A(v)^2 - B(v) C(v): near a root A^2 and B C cancel, and the expanded
 // quartic's coefficients cancel far more (to many digits on an
 // ill-conditioned instance), so the polish evaluates the factors.
-VD_HD __forceinline__ void vd_p3p_df_resultant(const VdP3Pdf& g, vd_df v, vd_df* r, vd_df* dr) {
+VD_HD VD_DF_CALL void vd_p3p_df_resultant(const VdP3Pdf& g, vd_df v, vd_df* r, vd_df* dr) {
   const vd_df a = vd_df_add(vd_df_mul(vd_df_add(vd_df_mul(g.A[2], v), g.A[1]), v), g.A[0]);
   const vd_df da = vd_df_add(vd_df_mulf(vd_df_mul(g.A[2], v), 2.0f), g.A[1]);
   const vd_df b = vd_df_add(vd_df_mul(g.B[1], v), g.B[0]);
@@ -206,7 +214,7 @@ VD_HD __forceinline__ void vd_p3p_df_resultant(const VdP3Pdf& g, vd_df v, vd_df*
 // resultant inside a double-float bracket, a bisection step where Newton
 // leaves it or gains less than a halving (clustered roots converge
 // linearly); stops at a 2^-44 relative step or bracket, at most 80 steps.
-VD_HD __forceinline__ vd_df vd_p3p_df_polish(const VdP3Pdf& g, vd_df m, float x0, float lo_f,
+VD_HD VD_DF_CALL vd_df vd_p3p_df_polish(const VdP3Pdf& g, vd_df m, float x0, float lo_f,
                                              float hi_f) {
   vd_df lo = vd_df_add(vd_df_make(lo_f), m), hi = vd_df_add(vd_df_make(hi_f), m);
   vd_df r, dr;
@@ -247,7 +255,7 @@ VD_HD __forceinline__ vd_df vd_p3p_df_polish(const VdP3Pdf& g, vd_df m, float x0
 // instance, the coefficients of res cancelling to many digits) become small
 // roots of d, whose coefficients keep their own magnitudes, so a float32
 // search on d's leading digits still separates them.
-VD_HD __forceinline__ vd_df vd_df_taylor_shift(const vd_df* res, vd_df* d) {
+VD_HD VD_DF_CALL vd_df vd_df_taylor_shift(const vd_df* res, vd_df* d) {
   const vd_df m = vd_df_neg(vd_df_div(res[3], vd_df_mulf(res[4], 4.0f)));
   for (int i = 0; i <= 4; ++i) d[i] = res[i];
   for (int i = 0; i < 4; ++i)
@@ -300,7 +308,7 @@ VD_HD __forceinline__ int vd_p3p_df_roots(const VdP3Pdf& g, const vd_df* res, vd
 }
 
 // Triad of a triangle: columns e1 (p1 -> p2), e2 = e3 x e1, e3 (normal).
-VD_HD __forceinline__ void vd_df_triad(const vd_df* p, vd_df* F) {
+VD_HD VD_DF_CALL void vd_df_triad(const vd_df* p, vd_df* F) {
   vd_df e1[3], d[3], e3[3], e2[3];
   for (int i = 0; i < 3; ++i) {
     e1[i] = vd_df_sub(p[3 + i], p[i]);
@@ -319,7 +327,7 @@ VD_HD __forceinline__ void vd_df_triad(const vd_df* p, vd_df* F) {
 
 // Pose (world -> camera, 3x4 row-major) of the root v; false if v gives no
 // valid triangle (v <= 0, u <= 0 or a vanishing distance).
-VD_HD __forceinline__ bool vd_p3p_df_pose(const VdP3Pdf& g, const vd_df* X, vd_df v, vd_df* T) {
+VD_HD VD_DF_CALL bool vd_p3p_df_pose(const VdP3Pdf& g, const vd_df* X, vd_df v, vd_df* T) {
   if (!vd_df_gt0(v)) return false;
   const vd_df one = vd_df_make(1.0f);
   const vd_df v2 = vd_df_mul(v, v);

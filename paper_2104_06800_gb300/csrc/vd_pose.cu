@@ -95,52 +95,44 @@ k_rigid_flags(DevParams P, const double* __restrict__ G, const float* __restrict
   if (threadIdx.x == 0) blk_counts[blockIdx.x] = cnt;
 }
 
-// Exclusive scan of the block counts by one block; total into n_out.
-__global__ void k_scan_counts(const int* __restrict__ counts, int nblk, int* __restrict__ offsets,
-                              int* __restrict__ n_out) {
-  __shared__ int s[1024];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < nblk; base += 1024) {
-    const int i = base + threadIdx.x;
-    const int x = i < nblk ? counts[i] : 0;
-    s[threadIdx.x] = x;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      const int y = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
-      __syncthreads();
-      s[threadIdx.x] += y;
-      __syncthreads();
-    }
-    if (i < nblk) offsets[i] = carry + s[threadIdx.x] - x;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += s[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *n_out = carry;
-}
-
 // Scatter the rigid pixels in row-major order with their float32 scoring data:
 // X = r_j / rho_j (reference frame), x_obs = x_{t-1} + X_t(x_{t-1}), w = q_t.
+// Each block adds up the counts of the blocks before it (a few thousand
+// integers from L2, instead of a separate scan launch); the last block
+// writes the total.
 __global__ void __launch_bounds__(SCAN_BLOCK)
 k_rigid_scatter(DevParams P, const float* __restrict__ posef, const float2* __restrict__ flow,
                 const float* __restrict__ rho, const float* __restrict__ q, int t,
-                const unsigned char* __restrict__ flags, const int* __restrict__ offsets,
-                int* __restrict__ idx, float4* __restrict__ rpts, float4* __restrict__ robs) {
+                const unsigned char* __restrict__ flags, const int* __restrict__ counts,
+                int* __restrict__ n_out, int* __restrict__ idx, float4* __restrict__ rpts,
+                float4* __restrict__ robs) {
   __shared__ int warp_tot[SCAN_BLOCK / 32];
+  __shared__ int warp_pre[SCAN_BLOCK / 32];
   const size_t npix = (size_t)P.W * P.H;
   const size_t j = (size_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
   const int f = (j < npix) ? flags[j] : 0;
   const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // counts of the blocks before this one, a fixed-order integer sum
+  int pre = 0;
+  for (unsigned k = threadIdx.x; k < blockIdx.x; k += SCAN_BLOCK) pre += counts[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
   const unsigned bal = __ballot_sync(0xffffffffu, f);
-  if (lane == 0) warp_tot[wid] = __popc(bal);
+  if (lane == 0) {
+    warp_tot[wid] = __popc(bal);
+    warp_pre[wid] = pre;
+  }
   __syncthreads();
-  int before = 0;
-  for (unsigned w = 0; w < wid; ++w) before += warp_tot[w];
+  int offset = 0, before = 0, total = 0;
+  for (unsigned w = 0; w < SCAN_BLOCK / 32; ++w) {
+    offset += warp_pre[w];
+    total += warp_tot[w];
+    if (w < wid) before += warp_tot[w];
+  }
   before += __popc(bal & ((1u << lane) - 1u));
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = offset + total;
   if (!f) return;
-  const int pos = offsets[blockIdx.x] + before;
+  const int pos = offset + before;
   const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
   const float c = rho[j];
   const float rx = ((float)u - P.cx) / P.fx, ry = ((float)v - P.cy) / P.fy;
@@ -176,7 +168,7 @@ k_rigid_scatter(DevParams P, const float* __restrict__ posef, const float2* __re
 // of the reference frame and the bearing K^-1 x_obs of its observation in
 // frame t, x_obs = x_{t-1} + X_t(x_{t-1}) (x_0 = j; for t >= 2, x_{t-1} is
 // the projection by G_{t-1}, given as 12 double-float values in g).
-__device__ void vd_correspondence_df(const DevParams& P, const vd_df* g,
+__device__ __forceinline__ void vd_correspondence_df(const DevParams& P, const vd_df* g,
                                      const float2* __restrict__ flow, const float* __restrict__ rho,
                                      int t, int j, vd_df* X, vd_df* bearing) {
   const int v = j / P.W, u = j - v * P.W;
@@ -350,7 +342,8 @@ __global__ void __launch_bounds__(32)
 k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restrict__ flow,
               const float* __restrict__ rho, const int* __restrict__ idx,
               const int* __restrict__ n_rigid, int t, uint32_t itcode, double* __restrict__ roots,
-              int* __restrict__ root_count, float* __restrict__ rootsf) {
+              int* __restrict__ root_count, float* __restrict__ rootsf,
+              float* __restrict__ rootsr) {
   const int g = blockIdx.x;
   const int lane = threadIdx.x;
   if (g >= P.S) return;
@@ -431,6 +424,8 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
   if (valid) {
     double* out = roots + (size_t)g * 48 + 12 * rank;
     for (int i = 0; i < 12; ++i) out[i] = vd_df_to(T[i]);
+    float* orr = rootsr + 48 * g + 12 * rank;      // float R | tau (the mean-shift's)
+    for (int i = 0; i < 12; ++i) orr[i] = T[i].hi;
     // float K R | K tau of the root, for the dense scoring
     const float fxf = P.kdf[0], fyf = P.kdf[2], cxf = P.kdf[4], cyf = P.kdf[6];
     float* o = rootsf + 48 * g + 12 * rank;
@@ -447,33 +442,69 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Dense scoring: every root against every rigid pixel.  Each block owns a
-// contiguous range of rigid pixels, keeps SCORE_PPT of them per thread in
-// registers and loops over the roots (broadcast from shared memory); warp
-// sums go to per-warp shared slots, summed in fixed order at the end.
+// Dense scoring: every root against every rigid pixel.  Each warp takes
+// passes of 32 x SCORE_PPT consecutive rigid pixels of its block's range
+// (pixels in registers) and, 32 roots at a time, accumulates one sum per
+// root in every lane; a butterfly reduce-scatter (31 shuffles) then leaves
+// lane L holding the warp's sum of root 32 g + L.  Warp sums are added in
+// fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-// One pixel's term under one root, without branches, so that the unrolled
-// terms of a thread's pixels form one block the compiler can interleave.
-// FAST: beta = 2 and alpha1 = 0 (closed form; obs.z unused).  A point behind
-// the camera gives the constant term (its projection is computed from a
-// denominator of 1 and discarded).
+#undef SCORE_PPT
+#define SCORE_PPT 4
+
+// One pixel's term under one root in log2 units (the caller scales by ln 2),
+// without branches.  FAST: beta = 2 and alpha1 = 0 (closed form; obs.z
+// unused) with one MUFU log2: log2(1 + y) below y = 2^24, log2 y = log2 c0 +
+// 2 log2 s above (equal to float32 precision there, and no overflow), the
+// series of ln(1 + y) below y = 1/32.  A point behind the camera gives the
+// constant term (its projection uses a denominator of 1 and is discarded).
 template <bool FAST>
-__device__ __forceinline__ float vd_score_term(const DevParams& P, const float* Mr, float4 pt,
-                                               float4 ob) {
+__device__ __forceinline__ float vd_score_term2(const DevParams& P, const float* Mr, float4 pt,
+                                                float4 ob) {
   const float hx = fmaf(Mr[0], pt.x, fmaf(Mr[1], pt.y, fmaf(Mr[2], pt.z, Mr[9])));
   const float hy = fmaf(Mr[3], pt.x, fmaf(Mr[4], pt.y, fmaf(Mr[5], pt.z, Mr[10])));
   const float hz = fmaf(Mr[6], pt.x, fmaf(Mr[7], pt.y, fmaf(Mr[8], pt.z, Mr[11])));
   const bool front = hz > VD_Z_EPS;
   const float iz = __fdividef(1.0f, front ? hz : 1.0f);
-  const float dx = ob.x - hx * iz, dy = ob.y - hy * iz;
+  const float dx = fmaf(-hx, iz, ob.x), dy = fmaf(-hy, iz, ob.y);
   const float r2 = fmaf(dx, dx, dy * dy);
-  const float l2 = FAST ? vd_l2_beta2(P, r2) : vd_l2_general(P, r2, ob.z);
-  return front ? pt.w * VD_LN2 * l2 : pt.w * VD_L_BEHIND;
+  float l2;
+  if (FAST) {
+    const float sq = fmaf(r2, P.inv_a2, 1.0f);
+    const float y = P.c0 * sq * sq;
+    const bool mid = y < 16777216.0f;
+    const float L = __log2f(mid ? 1.0f + y : sq);
+    const float big = mid ? L : fmaf(2.0f, L, P.log2c0);
+    // log2(1 + y) = y (1 - y/2 + y^2/3 - y^3/4 + y^4/5) / ln 2 (below 1/32)
+    const float ser = y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, 0.28853901f, -0.36067376f),
+                                                0.48089835f), -0.72134752f), 1.44269504f);
+    l2 = y < 0.03125f ? ser : big;
+  } else {
+    l2 = vd_l2_general(P, r2, ob.z);
+  }
+  return front ? l2 : VD_L_BEHIND / VD_LN2;
 }
 
 // Dynamic shared memory of k_pose_score<THREADS> for M roots.
 static inline size_t vd_score_smem(int M, int threads) {
   return sizeof(float) * (size_t)M * (12 + threads / 32) + sizeof(int) * (size_t)(M + 1);
+}
+
+// acc[0..31] of every lane -> lane L returns the sum over the warp's lanes
+// of acc[L] (recursive halving: each step keeps the half of the entries
+// selected by one lane bit and adds the partner's copy of that half).
+__device__ __forceinline__ float vd_reduce_scatter32(float* acc, int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = upper ? acc[i] : acc[i + s];
+      const float keep = upper ? acc[i + s] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return acc[0];
 }
 
 template <int THREADS, bool FAST = false>
@@ -483,6 +514,7 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
              const int* __restrict__ root_count, int M, float* __restrict__ partial) {
   extern __shared__ float smem[];
   constexpr int nwarp = THREADS / 32;
+  constexpr int PASS = 32 * SCORE_PPT;
   float* sRoot = smem;                       // M * 12
   float* sAcc = smem + 12 * M;               // nwarp * M
   int* sList = (int*)(sAcc + nwarp * M);     // the real roots, in index order
@@ -504,18 +536,18 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
   }
   __syncthreads();
   const int nroot = *sNum;
+  const int ngroup = (nroot + 31) >> 5;
+  float* wAcc = sAcc + wid * M;              // this warp's sum per root
   const int n = n_ptr ? *n_ptr : n_host;
-  // contiguous ranges of whole warps, so that only the last warp is ragged
-  const int per = (((n + gridDim.x - 1) / gridDim.x) + 31) & ~31;
+  // contiguous block ranges of whole passes; passes go to the warps in turn
+  const int per = ((n + gridDim.x - 1) / gridDim.x + PASS - 1) / PASS * PASS;
   const int beg = min(n, blockIdx.x * per);
   const int end = min(n, beg + per);
-  for (int base = beg; base < end; base += THREADS * SCORE_PPT) {
-    // passes of this tile that hold at least one pixel (block-uniform)
-    const int kact = min(SCORE_PPT, (end - base + THREADS - 1) / THREADS);
+  for (int base = beg + wid * PASS; base < end; base += nwarp * PASS) {
     float4 pt[SCORE_PPT], ob[SCORE_PPT];
 #pragma unroll
     for (int k = 0; k < SCORE_PPT; ++k) {
-      const int i = base + k * THREADS + threadIdx.x;
+      const int i = base + 32 * k + lane;
       if (i < end) {
         pt[k] = rpts[i];
         ob[k] = robs[i];
@@ -524,24 +556,32 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
         ob[k] = make_float4(0.f, 0.f, 1.f, 0.f);
       }
     }
-    for (int m = 0; m < nroot; ++m) {
-      const int r = sList[m];
-      const float* Mr = sRoot + 12 * r;
-      float acc = 0.0f;
+#pragma unroll 1
+    for (int g = 0; g < ngroup; ++g) {
+      float acc[32];
 #pragma unroll
-      for (int k = 0; k < SCORE_PPT; ++k)
-        if (k < kact) acc += vd_score_term<FAST>(P, Mr, pt[k], ob[k]);
+      for (int k = 0; k < 32; ++k) {
+        acc[k] = 0.0f;
+        const int m = 32 * g + k;
+        if (m < nroot) {                    // warp-uniform
+          const float* Mr = sRoot + 12 * sList[m];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) sAcc[wid * M + r] += acc;
+          for (int q = 0; q < SCORE_PPT; ++q)
+            acc[k] = fmaf(pt[q].w, vd_score_term2<FAST>(P, Mr, pt[q], ob[q]), acc[k]);
+        }
+      }
+      const float v = vd_reduce_scatter32(acc, lane);
+      const int m = 32 * g + lane;
+      if (m < nroot) wAcc[sList[m]] += v;
     }
   }
+  // the block's sum per root, warps in fixed order
   __syncthreads();
   for (int m = threadIdx.x; m < nroot; m += THREADS) {
     const int r = sList[m];
     float s = 0.0f;
     for (int w = 0; w < nwarp; ++w) s += sAcc[w * M + r];
-    partial[(size_t)r * gridDim.x + blockIdx.x] = s;
+    partial[(size_t)r * gridDim.x + blockIdx.x] = VD_LN2 * s;
   }
 }
 
@@ -608,6 +648,38 @@ __device__ __forceinline__ bool vd_se3_log_f(const float* T, float* xi) {
   return true;
 }
 
+// vd_se3_log_f for the mean-shift's samples when the rotation kernel is
+// narrow: a sample whose rotation part alone has Mahalanobis distance
+// s^2 ivr >= 210 (s = sin of its angle) has weight exp(-m / 2) <= e^-105,
+// which is 0 in float32: it returns false with no logarithm.  Near samples
+// (angle below 14.5 sigma, cos > 0) take the angle asin(s) and the
+// coefficient e of the translation part from their series (truncation below
+// 1e-10 relative at that angle), without atan2f or sincosf.
+__device__ __forceinline__ bool vd_se3_log_near_f(const float* T, float* xi, float ivr) {
+  const float c = 0.5f * (T[0] + T[5] + T[10] - 1.0f);
+  const float vx = 0.5f * (T[9] - T[6]), vy = 0.5f * (T[2] - T[8]), vz = 0.5f * (T[4] - T[1]);
+  const float s2 = vx * vx + vy * vy + vz * vz;
+  if (!(c > 0.0f) || s2 * ivr >= 210.0f) return false;
+  // th / s = asin(s) / s = 1 + s^2/6 + 3 s^4/40 + 5 s^6/112 + 35 s^8/1152
+  const float f = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 35.0f / 1152.0f, 5.0f / 112.0f),
+                                         3.0f / 40.0f), 1.0f / 6.0f), 1.0f);
+  const float wx = vx * f, wy = vy * f, wz = vz * f;
+  const float th2 = wx * wx + wy * wy + wz * wz;
+  // e = (1 - (th/2) cot(th/2)) / th^2 = 1/12 + th^2/720 + th^4/30240 + th^6/1209600
+  const float e = fmaf(th2, fmaf(th2, fmaf(th2, 1.0f / 1209600.0f, 1.0f / 30240.0f),
+                                 1.0f / 720.0f), 1.0f / 12.0f);
+  const float t0 = T[3], t1 = T[7], t2 = T[11];
+  const float k0 = wy * t2 - wz * t1, k1 = wz * t0 - wx * t2, k2 = wx * t1 - wy * t0;
+  const float q0 = wy * k2 - wz * k1, q1 = wz * k0 - wx * k2, q2 = wx * k1 - wy * k0;
+  xi[0] = wx;
+  xi[1] = wy;
+  xi[2] = wz;
+  xi[3] = t0 - 0.5f * k0 + e * q0;
+  xi[4] = t1 - 0.5f * k1 + e * q1;
+  xi[5] = t2 - 0.5f * k2 + e * q2;
+  return true;
+}
+
 __device__ __forceinline__ void vd_se3_exp_f(const float* xi, float* T) {
   const float wx = xi[0], wy = xi[1], wz = xi[2];
   const float th2 = wx * wx + wy * wy + wz * wz;
@@ -649,37 +721,42 @@ __device__ __forceinline__ void vd_se3_exp_f(const float* xi, float* T) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32)
 k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __restrict__ root_count,
-                   const double* __restrict__ root_energy, int t, double* __restrict__ G,
-                   float* __restrict__ posef, double* __restrict__ sample_pose,
-                   double* __restrict__ sample_energy, int* __restrict__ degenerate) {
+                   const float* __restrict__ roots_r, const double* __restrict__ root_energy,
+                   int t, double* __restrict__ G, float* __restrict__ posef,
+                   double* __restrict__ sample_pose, double* __restrict__ sample_energy,
+                   int* __restrict__ degenerate) {
   // one warp; lane l owns samples l, l + 32, ...
   __shared__ float sT[VD_MAX_SAMPLES][12];
   __shared__ unsigned char sValid[VD_MAX_SAMPLES];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
-  double bestE = INFINITY;
+  // Energies are sums of non-negative terms (or +inf for a missing root): as
+  // bit patterns they order like the numbers, so the comparisons run on the
+  // integer pipe instead of the float64 one.
+  const long long INF_BITS = __double_as_longlong(INFINITY);
+  long long bestE = INF_BITS;
   int bestS = 0x7fffffff;
   for (int g = lane; g < P.S; g += 32) {
     // the sample's lowest-energy root (ties: lower index in the sorted order)
     const int nr = root_count[g];
     int best = -1;
-    double Eg = INFINITY;
+    long long Eg = INF_BITS;
     for (int r = 0; r < nr; ++r) {
-      const double e = root_energy[4 * g + r];
+      const long long e = __double_as_longlong(root_energy[4 * g + r]);
       if (best < 0 || e < Eg) {
         Eg = e;
         best = r;
       }
     }
     const double* src = roots + (size_t)48 * g + 12 * (best < 0 ? 0 : best);
+    const float* srf = roots_r + (size_t)48 * g + 12 * (best < 0 ? 0 : best);
     for (int i = 0; i < 12; ++i) {
-      const double v = best >= 0 ? src[i] : 0.0;
-      sample_pose[12 * g + i] = v;
-      sT[g][i] = (float)v;
+      sample_pose[12 * g + i] = best >= 0 ? src[i] : 0.0;
+      sT[g][i] = best >= 0 ? srf[i] : 0.0f;
     }
-    if (best < 0) Eg = INFINITY;
-    sample_energy[g] = Eg;
-    sValid[g] = Eg < INFINITY;
+    if (best < 0) Eg = INF_BITS;
+    sample_energy[g] = __longlong_as_double(Eg);
+    sValid[g] = Eg < INF_BITS;
     if (Eg < bestE) {           // g ascends per lane: ties keep the lower index
       bestE = Eg;
       bestS = g;
@@ -689,7 +766,7 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   // every lane ends with the same pair
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double oE = __shfl_xor_sync(FULL, bestE, o);
+    const long long oE = __shfl_xor_sync(FULL, bestE, o);
     const int oS = __shfl_xor_sync(FULL, bestS, o);
     if (oE < bestE || (oE == bestE && oS < bestS)) {
       bestE = oE;
@@ -697,7 +774,7 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
     }
   }
   __syncwarp();
-  if (!(bestE < INFINITY)) {
+  if (!(bestE < INF_BITS)) {
     if (lane == 0) atomicAdd(degenerate, 1);
     return;
   }
@@ -710,6 +787,9 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   // the float32 iterations stop at this step norm (the float32 floor of the
   // relative poses); the float64 definition stops at 1e-12
   const float tol = (float)(VD_MS_TOL_F32 * (1.0 + (double)tn));
+  // the narrow-kernel path of the logarithm applies while 14.5 sigma of
+  // rotation stays below 0.2 rad (the default sigma is 0.01 rad)
+  const bool near_log = 210.0f / ivr < 0.04f;
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
     float acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int g = lane; g < P.S; g += 32) {
@@ -726,7 +806,7 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
         rel[4 * r + 3] = x[r] * (Tg[3] - x[3]) + x[4 + r] * (Tg[7] - x[7]) +
                          x[8 + r] * (Tg[11] - x[11]);
       }
-      if (vd_se3_log_f(rel, d)) {
+      if (near_log ? vd_se3_log_near_f(rel, d, ivr) : vd_se3_log_f(rel, d)) {
         const float m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
                         (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
         const float w = __expf(-0.5f * m);
@@ -834,21 +914,22 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   vd_prof_begin(c, VD_ST_RIGID);
   k_rigid_flags<<<c->nblk_scan, SCAN_BLOCK, 0, c->stream>>>(P, c->G, c->posef, c->rho, c->q, t,
                                                             c->flags, c->blk_counts);
-  k_scan_counts<<<1, 1024, 0, c->stream>>>(c->blk_counts, c->nblk_scan, c->blk_offsets, c->n_rigid);
   k_rigid_scatter<<<c->nblk_scan, SCAN_BLOCK, 0, c->stream>>>(P, c->posef, c->flow, c->rho, c->q, t,
-                                                              c->flags, c->blk_offsets,
-                                                              c->rigid_idx, c->rpts, c->robs);
-  vd_prof_end(c, VD_ST_RIGID, 3);
+                                                              c->flags, c->blk_counts,
+                                                              c->n_rigid, c->rigid_idx, c->rpts,
+                                                              c->robs);
+  vd_prof_end(c, VD_ST_RIGID, 2);
   vd_prof_begin(c, VD_ST_P3P);
   k_p3p_samples<<<P.S, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
                                             c->n_rigid, t, itcode, c->roots, c->root_count,
-                                            c->rootsf);
+                                            c->rootsf, c->rootsr);
   vd_prof_end(c, VD_ST_P3P, 1);
   vd_prof_begin(c, VD_ST_SCORE);
   launch_pose_score_only(c);
   vd_prof_end(c, VD_ST_SCORE, 2);
   vd_prof_begin(c, VD_ST_SELECT);
-  k_select_meanshift<<<1, 32, 0, c->stream>>>(P, c->roots, c->root_count, c->root_energy, t, c->G,
+  k_select_meanshift<<<1, 32, 0, c->stream>>>(P, c->roots, c->root_count, c->rootsr,
+                                               c->root_energy, t, c->G,
                                                c->posef, c->sample_pose + 12 * f,
                                                c->sample_energy + f, c->degenerate);
   vd_prof_end(c, VD_ST_SELECT, 1);
