@@ -5,11 +5,14 @@ of uneven size, flow count and prior as one CUDA graph.  Each window's
 kernels, inputs and order are those of the window run alone, so its results
 must be bit-identical to vd_bootstrap + vd_run_em on that window; parity of
 the single-window path with the float64 oracle is covered by
-test_gpu_parity.py.  The depth-sampling launch shapes the tuner chooses
-between must not change a single output bit either."""
+test_gpu_parity.py and test_gpu_chained.py, and the windows of a mixed
+RGB-D batch are replayed stage by stage against the oracle here.  The
+depth-sampling launch shapes the tuner chooses between must not change a
+single output bit either."""
 import numpy as np
 import pytest
 
+import chained
 from gpu_common import noisy_state, params_for, push_state, window
 
 pytestmark = pytest.mark.gpu
@@ -195,3 +198,33 @@ def test_bootstrap_restarts_from_the_initial_poses(V):
             assert _same(runs[0], runs[1]), w.name
         finally:
             V.vd_destroy(ctx)
+
+
+def test_batch_windows_are_the_chained_oracle_replay(V):
+    """A mixed RGB-D batch of the batched workload's kind (uneven size and
+    N, the prior with 1 % noise and 10 % holes): every window's bootstrap
+    and 3 iterations replayed stage by stage against the float64 oracle at
+    the method's bounds (chained.py), and the batch's graph launch gives
+    each window bit for bit the replay's depth, rigidness and poses."""
+    from oracle import model as omodel
+    specs = [((96, 72), 3), ((128, 80), 5), ((80, 64), 4)]
+    wins = [window("rgbd_batch", 5300 + i, size=sz, N=n) for i, (sz, n) in enumerate(specs)]
+    iters = 3
+    b = V.vd_batch_create([(w.W, w.H, w.N, w.intrinsics) for w in wins],
+                          [V.vd_params_default(**params_for(w)) for w in wins])
+    try:
+        for i, w in enumerate(wins):
+            _push(V, V.vd_batch_window(b, i), w)
+        V.vd_batch_run(b, iters, V.VD_BATCH_BOOTSTRAP, len(wins))
+        for i, w in enumerate(wins):
+            P = omodel.problem_from_window(w, prior="rgbd")
+            assert P.prior_kind == "rgbd"
+            rep = chained.replay(V, lambda w=w: _alone(V, w), P, omodel.Params(**params_for(w)),
+                                 iters, f"batch window {i} {w.W}x{w.H} N={w.N}")
+            print(rep.summary())
+            rho, q, G = _results(V, V.vd_batch_window(b, i), w)
+            assert np.array_equal(rho, rep.final.rho), i
+            assert np.array_equal(q, rep.final.q), i
+            assert np.array_equal(np.asarray(G), rep.final.G), i
+    finally:
+        V.vd_batch_destroy(b)
