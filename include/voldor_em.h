@@ -235,8 +235,10 @@ vd_status vd_score_poses_noalloc(const float* points, const float* obs, int n,
 /* ---- Launch tuning (the paper has none: GPU launch shapes) ---------------
  * Three launch shapes are tunable per context: the warps per block of the
  * depth-sampling kernel (1, 2 or 4; default 4), and the threads per block
- * (256 or 512; default 256) and blocks per SM (1..4; default 2) of the dense
- * pose scoring.  None changes any result bit except the float32 summation
+ * (256 or 512; default 256) and the blocks setting b (1..4; default 2) of
+ * the dense pose scoring, which launches b x SMs / 2 blocks of rigid pixels
+ * for every group of 32 roots.  None changes any result bit except the
+ * float32 summation
  * grouping of the pose scores (a rounding-level change).  vd_autotune times
  * every variant on this window and keeps the fastest: it needs all flows
  * pushed, and it OVERWRITES the EM state (it runs the bootstrap and one
@@ -245,7 +247,7 @@ vd_status vd_score_poses_noalloc(const float* points, const float* obs, int n,
 typedef struct {
   int k1_warps;                 /* 1, 2 or 4                                  */
   int score_threads;            /* 256 or 512                                 */
-  int score_blocks_per_sm;      /* 1..4                                       */
+  int score_blocks_per_sm;      /* 1..4 (pixel blocks: this x SMs / 2)        */
   float k1_ms[3];               /* measured, for 1, 2, 4 warps (0 if unset)   */
   float score_ms[2][4];         /* measured, [256, 512 threads][1..4 per SM]  */
 } vd_tune;

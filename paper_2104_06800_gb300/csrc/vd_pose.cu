@@ -487,15 +487,15 @@ __device__ __forceinline__ float vd_score_term2(const DevParams& P, const float*
 
 // Dynamic shared memory of k_pose_score<THREADS> for M roots.
 static inline size_t vd_score_smem(int M, int threads) {
-  return sizeof(float) * (size_t)M * (12 + threads / 32) + sizeof(int) * (size_t)(M + 1);
+  return sizeof(float) * (size_t)32 * (12 + threads / 32) + sizeof(int) * (size_t)(M + 1);
 }
 
-// acc[0..31] of every lane -> lane L returns the sum over the warp's lanes
-// of acc[L] (recursive halving: each step keeps the half of the entries
-// selected by one lane bit and adds the partner's copy of that half).
-__device__ __forceinline__ float vd_reduce_scatter32(float* acc, int lane) {
+// acc[0..7] of every lane -> lanes with L % 8 == k return the warp's sum of
+// acc[k] (recursive halving over lane bits 2, 1, 0, then the four copies
+// summed over lane bits 3 and 4).
+__device__ __forceinline__ float vd_reduce_scatter8(float* acc, int lane) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
+  for (int s = 4; s >= 1; s >>= 1) {
     const bool upper = (lane & s) != 0;
 #pragma unroll
     for (int i = 0; i < s; ++i) {
@@ -504,9 +504,19 @@ __device__ __forceinline__ float vd_reduce_scatter32(float* acc, int lane) {
       acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
-  return acc[0];
+  float v = acc[0];
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  return v;
 }
 
+// Grid (pixel blocks, root groups of 32): block (b, g) scores the group's
+// roots against pixel block b's contiguous range of rigid pixels; warps
+// take passes of 32 x SCORE_PPT pixels in turn (pixels in registers), and
+// per pass the roots eight at a time: every lane accumulates one sum per
+// root over its pixels, then a reduce-scatter gives lane k < 8 the warp's
+// sum of root k.  Warp sums are added in fixed order, so the result does
+// not depend on scheduling.
 template <int THREADS, bool FAST = false>
 __global__ void __launch_bounds__(THREADS)
 k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restrict__ robs,
@@ -515,12 +525,10 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
   extern __shared__ float smem[];
   constexpr int nwarp = THREADS / 32;
   constexpr int PASS = 32 * SCORE_PPT;
-  float* sRoot = smem;                       // M * 12
-  float* sAcc = smem + 12 * M;               // nwarp * M
-  int* sList = (int*)(sAcc + nwarp * M);     // the real roots, in index order
+  float* sRoot = smem;                       // 32 * 12: this group's roots
+  float* sAcc = smem + 32 * 12;              // nwarp * 32
+  int* sList = (int*)(sAcc + nwarp * 32);    // the real roots, in index order
   int* sNum = sList + M;
-  for (int i = threadIdx.x; i < 12 * M; i += THREADS) sRoot[i] = rootsf[i];
-  for (int i = threadIdx.x; i < nwarp * M; i += THREADS) sAcc[i] = 0.0f;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid == 0) {
     // compact the roots that exist (slot r & 3 below its sample's root count)
@@ -534,15 +542,21 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
     }
     if (lane == 0) *sNum = cnt;
   }
+  for (int i = threadIdx.x; i < nwarp * 32; i += THREADS) sAcc[i] = 0.0f;
   __syncthreads();
   const int nroot = *sNum;
-  const int ngroup = (nroot + 31) >> 5;
-  float* wAcc = sAcc + wid * M;              // this warp's sum per root
+  const int g0 = 32 * blockIdx.y;
+  if (g0 >= nroot) return;                   // whole block: no root in this group
+  const int ng = min(32, nroot - g0);
+  for (int i = threadIdx.x; i < 12 * ng; i += THREADS)
+    sRoot[i] = rootsf[12 * sList[g0 + i / 12] + i % 12];
+  __syncthreads();
   const int n = n_ptr ? *n_ptr : n_host;
-  // contiguous block ranges of whole passes; passes go to the warps in turn
+  // contiguous pixel-block ranges of whole passes; passes go to the warps in turn
   const int per = ((n + gridDim.x - 1) / gridDim.x + PASS - 1) / PASS * PASS;
   const int beg = min(n, blockIdx.x * per);
   const int end = min(n, beg + per);
+  float* wAcc = sAcc + wid * 32;             // this warp's sum per root of the group
   for (int base = beg + wid * PASS; base < end; base += nwarp * PASS) {
     float4 pt[SCORE_PPT], ob[SCORE_PPT];
 #pragma unroll
@@ -557,31 +571,28 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
       }
     }
 #pragma unroll 1
-    for (int g = 0; g < ngroup; ++g) {
-      float acc[32];
+    for (int r0 = 0; r0 < ng; r0 += 8) {
+      float acc[8];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
+      for (int k = 0; k < 8; ++k) {
         acc[k] = 0.0f;
-        const int m = 32 * g + k;
-        if (m < nroot) {                    // warp-uniform
-          const float* Mr = sRoot + 12 * sList[m];
+        if (r0 + k < ng) {                    // warp-uniform
+          const float* Mr = sRoot + 12 * (r0 + k);
 #pragma unroll
           for (int q = 0; q < SCORE_PPT; ++q)
             acc[k] = fmaf(pt[q].w, vd_score_term2<FAST>(P, Mr, pt[q], ob[q]), acc[k]);
         }
       }
-      const float v = vd_reduce_scatter32(acc, lane);
-      const int m = 32 * g + lane;
-      if (m < nroot) wAcc[sList[m]] += v;
+      const float v = vd_reduce_scatter8(acc, lane);
+      if (lane < 8 && r0 + lane < ng) wAcc[r0 + lane] += v;
     }
   }
   // the block's sum per root, warps in fixed order
   __syncthreads();
-  for (int m = threadIdx.x; m < nroot; m += THREADS) {
-    const int r = sList[m];
+  if (threadIdx.x < ng) {
     float s = 0.0f;
-    for (int w = 0; w < nwarp; ++w) s += sAcc[w * M + r];
-    partial[(size_t)r * gridDim.x + blockIdx.x] = VD_LN2 * s;
+    for (int w = 0; w < nwarp; ++w) s += sAcc[w * 32 + threadIdx.x];
+    partial[(size_t)sList[g0 + threadIdx.x] * gridDim.x + blockIdx.x] = VD_LN2 * s;
   }
 }
 
@@ -889,9 +900,12 @@ cudaError_t vd_pose_prepare(void) {
 cudaError_t launch_pose_score_only(vd_ctx* c) {
   const DevParams& P = c->dp;
   const int M = 4 * P.S;
-  const int nblk = c->score_bps * c->num_sms;
+  // pixel blocks: half an SM's worth per unit of score_bps; the grid's
+  // second dimension covers the root groups of 32 (those without a root exit)
+  const int nblk = std::max(1, c->score_bps * c->num_sms / 2);
+  const dim3 grid(nblk, (M + 31) / 32);
 #define VD_SCORE_LAUNCH(TH, FAST)                                                     \
-  k_pose_score<TH, FAST><<<nblk, TH, vd_score_smem(M, TH), c->stream>>>(                   \
+  k_pose_score<TH, FAST><<<grid, TH, vd_score_smem(M, TH), c->stream>>>(                   \
       P, c->rpts, c->robs, c->n_rigid, 0, c->rootsf, c->root_count, M, c->partial)
   if (c->score_threads == 512) {
     if (P.fast_beta2) VD_SCORE_LAUNCH(512, true);
@@ -1022,7 +1036,7 @@ extern "C" vd_status vd_score_poses_noalloc(const float* points, const float* ob
   float* partial = scratch + 12 * VD_NOALLOC_MAX_POSES;     // m x nblk
   k_poses_float<<<(m + 127) / 128, 128, 0, s>>>(P, poses, m, rootsf);
   const size_t smem = vd_score_smem(m, SCORE_THREADS);
-  k_pose_score<SCORE_THREADS><<<nblk, SCORE_THREADS, smem, s>>>(
+  k_pose_score<SCORE_THREADS><<<dim3(nblk, (m + 31) / 32), SCORE_THREADS, smem, s>>>(
       P, (const float4*)points, (const float4*)obs, nullptr, n, rootsf, nullptr, m, partial);
   launch_root_energy(partial, nblk, m, nullptr, energies, s);
   e = cudaGetLastError();
@@ -1074,8 +1088,8 @@ extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_pose_score<SCORE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-  k_pose_score<SCORE_THREADS><<<nblk, SCORE_THREADS, smem, s>>>(P, (const float4*)points, (const float4*)obs,
-                                                 nullptr, n, rootsf, nullptr, m, partial);
+  k_pose_score<SCORE_THREADS><<<dim3(nblk, (m + 31) / 32), SCORE_THREADS, smem, s>>>(
+      P, (const float4*)points, (const float4*)obs, nullptr, n, rootsf, nullptr, m, partial);
   launch_root_energy(partial, nblk, m, nullptr, energies, s);
   e = cudaGetLastError();
   cudaFreeAsync(rootsf, s);
