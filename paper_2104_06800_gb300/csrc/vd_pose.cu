@@ -801,6 +801,15 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   // the narrow-kernel path of the logarithm applies while 14.5 sigma of
   // rotation stays below 0.2 rad (the default sigma is 0.01 rad)
   const bool near_log = 210.0f / ivr < 0.04f;
+  // Aitken extrapolation: where two successive plain steps point the same
+  // way (cosine above 0.9) and shrink by a ratio r in (0.05, 0.95), the
+  // iteration converges linearly along them and the remaining distance is
+  // about step r / (1 - r); the next step is then taken 1 / (1 - r) times
+  // as long (at most one kernel width), and the one after it is plain
+  // again.  The fixed point is that of the plain iteration, which also
+  // decides convergence: a plain step below the tolerance ends the loop.
+  float prev[6] = {0, 0, 0, 0, 0, 0};
+  bool have_prev = false;
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
     float acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int g = lane; g < P.S; g += 32) {
@@ -834,10 +843,36 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
       for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(FULL, acc[i], o);
     if (!(acc[0] > 0.0f)) break;
     float step[6], nrm = 0.0f;
+    const float iw = 1.0f / acc[0];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      step[i] = acc[1 + i] / acc[0];
+      step[i] = acc[1 + i] * iw;
       nrm += step[i] * step[i];
+    }
+    const bool converged = sqrtf(nrm) < tol;
+    float scale = 1.0f;
+    if (have_prev && !converged) {
+      float dot = 0.0f, pn = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        dot += step[i] * prev[i];
+        pn += prev[i] * prev[i];
+      }
+      const float r = dot / pn;
+      if (r > 0.05f && r < 0.95f && dot > 0.9f * sqrtf(nrm * pn)) {
+        const float mh = (step[0] * step[0] + step[1] * step[1] + step[2] * step[2]) * ivr +
+                         (step[3] * step[3] + step[4] * step[4] + step[5] * step[5]) * ivt;
+        scale = fmaxf(1.0f, fminf(1.0f / (1.0f - r), rsqrtf(fmaxf(mh, 1e-30f))));
+      }
+    }
+    if (scale > 1.0f) {
+      have_prev = false;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) step[i] *= scale;
+    } else {
+      have_prev = true;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) prev[i] = step[i];
     }
     float E[12], xn[12];
     vd_se3_exp_f(step, E);
@@ -850,7 +885,7 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
     }
 #pragma unroll
     for (int i = 0; i < 12; ++i) x[i] = xn[i];
-    if (sqrtf(nrm) < tol) break;
+    if (converged) break;
   }
   if (lane != 0) return;
   // re-orthonormalise the rotation in float64 (Gram-Schmidt on the rows,
