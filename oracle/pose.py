@@ -23,8 +23,12 @@ Reading fixed here:
     (roots ordered by (rotation vector, translation) first; ties: first).
   * mean-shift starts at the lowest-energy sample and iterates
     x <- x exp(sum_g w_g d_g / sum_g w_g), d_g = log(x^-1 T_g),
-    w_g = exp(-d_g^T Sigma^-1 d_g / 2), until |step| < 1e-12 or 100 steps.
-    Sigma = diag(s_r^2 (x3), s_t^2 (x3)), s_t = rel |tau_start| + abs.
+    w_g = exp(-d_g^T Sigma^-1 d_g / 2), until |step| < 1e-12: the pose is
+    the mode of the approximated posterior (Sec. III-A, the paragraph after
+    Eq. 7), the iteration's fixed point, so it runs to convergence; the
+    linear rate approaches 1 where the mode is flat (a few samples in the
+    kernel's reach, as after the bootstrap), and MS_MAX_ITERS is only a
+    safeguard.  Sigma = diag(s_r^2 (x3), s_t^2 (x3)), s_t = rel |tau_start| + abs.
   * fewer than 3 rigid pixels, or no valid sample: the pose is kept and the
     step reports a degenerate frame.
 """
@@ -37,7 +41,7 @@ import numpy as np
 from . import fisk, geometry, model, p3p, philox
 
 MS_TOL = 1e-12
-MS_MAX_ITERS = 100
+MS_MAX_ITERS = 100000
 MAX_ATTEMPTS = 8
 
 

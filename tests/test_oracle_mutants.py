@@ -167,6 +167,8 @@ MUTANTS = [
     ("pose-meanshift-weight-sign", "pose", "w = np.exp(-0.5 * np.sum(d * d * inv_var, axis=1))",
      "w = np.exp(0.5 * np.sum(d * d * inv_var, axis=1))",
      [(PINS, "test_meanshift_cases", ())]),
+    ("pose-meanshift-stops-at-100-steps", "pose", "MS_MAX_ITERS = 100000", "MS_MAX_ITERS = 100",
+     [(PINS, "test_meanshift_runs_to_the_mode_where_it_converges_slowly", ())]),
     ("pose-triplet-duplicates", "pose", "if len(set(idx)) == 3:", "if True:",
      [(PINS, "test_sample_triplets_are_distinct_indices", ())]),
     ("pose-kernel-widths-swapped", "pose",

@@ -544,6 +544,23 @@ def test_meanshift_cases():
     assert np.abs(geometry.se3_log(geometry.compose(geometry.inverse(far), x))).max() < 1e-12
 
 
+def test_meanshift_runs_to_the_mode_where_it_converges_slowly():
+    """Two samples at +-a on one rotation axis around T with a just below the
+    kernel's sigma: the density has one mode, the midpoint T, and the
+    iteration approaches it at the linear rate (a / sigma)^2 = 0.98 -- after
+    100 steps still 1e-3 rad away.  The pose is the mode, so the oracle must
+    reach T to float64 precision."""
+    p = model.Params()
+    T = geometry.se3_exp(np.array([0.05, 0.1, -0.2, 0.5, -1.0, 2.0]))
+    a = 0.99 * p.pose_sigma_rot
+    A = geometry.compose(T, geometry.se3_exp(np.array([a, 0, 0, 0, 0, 0])))
+    B = geometry.compose(T, geometry.se3_exp(np.array([-a, 0, 0, 0, 0, 0])))
+    x, n = pose.meanshift([A, B], A, p)
+    d = geometry.se3_log(geometry.compose(geometry.inverse(T), x))
+    assert np.abs(d).max() < 1e-10
+    assert n > 500           # a step below 1e-12 takes several hundred
+
+
 def test_meanshift_mode_on_one_rotation_axis_solves_the_scalar_equation():
     """Samples T, T and T exp(a e_x) (a rotation about one body axis): every
     iterate stays on that axis, the tangent coordinates are (a_g - m) e_x
