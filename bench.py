@@ -20,7 +20,8 @@ roofline = the depth-sampling kernel (the dominant kernel), FP32-issue bound:
          CUDA-event time in the single-window run, against the FFMA
          throughput measured on the same GPU by the library's probe.
 configs = the other workloads on one GPU: the small two-plane window, the
-         stereo 640 x 480 window, the 64-window RGB-D batch (plain vs batched).
+         stereo 640 x 480 window, the 64-window RGB-D batch (plain vs batched),
+         and plain vs learned-initialised EM at equal accuracy.
 cpu_baseline = the float64 oracle on the host: one iteration of the whole
          window over every core (row bands in spawned processes), one
          iteration of a crop on one core, and the small workload in full.
@@ -75,8 +76,9 @@ FP32_T1, FP32_TN, MUFU_PER_EVAL = 17, 37, 2
 FP32_SCORE, MUFU_SCORE = 21, 2
 # DRAM bytes (read + write) per launch of k_depth_sample_q on this workload,
 # from one ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of three launches); re-measure when it changes.
-K1_TRAFFIC_BYTES = 32.4e6
+# dram__bytes_write.sum, one launch on the kerb-side driving window); re-measure
+# when it changes.
+K1_TRAFFIC_BYTES = 34.04e6
 SM_MAX_MHZ = 2070.0
 
 
@@ -462,6 +464,13 @@ def run_ours(args, rank, world, local, pg):
                             MUFU_PER_EVAL, launch_ms, peaks, K1_TRAFFIC_BYTES,
                             "single-window run, kernel timed alone (CUDA events per stage)")
     roofline["peaks_measured"] = peaks
+    # the dense pose scoring (K5, Eq. 7): every (rigid pixel, root) pair of
+    # the timed steps, counted by the device, over the stage's event time
+    sc = prof["pose_score"]
+    roofline_score = alu_roofline("k_pose_score", prof["score_evals"] / max(sc["calls"], 1),
+                                  FP32_SCORE, MUFU_SCORE, sc["ms"] / max(sc["calls"], 1), peaks,
+                                  None, "single-window run, kernel timed alone (CUDA events "
+                                  "per stage); evals = rigid pixels x roots of each launch")
     stages = {k: round(v["ms"] / args.steps, 4) for k, v in prof.items() if isinstance(v, dict)}
     # the stride / keyframe score of the window just estimated (VC, Eq. 8):
     # the call's time including its counter read-back, median of 20
@@ -492,7 +501,8 @@ def run_ours(args, rank, world, local, pg):
               "value": round(units_per_window / (single_ms / 1e3), 1),
               "gpu_launches_per_window": int(prof["total_launches"] / args.steps),
               "vc_scores": vc_line, "pose_covariance": pc_line,
-              "stage_ms_per_window": stages, "tune": tune}
+              "stage_ms_per_window": stages, "tune": tune,
+              "roofline_pose_score": roofline_score}
     V.vd_destroy(ctx)
     if args.phase == "single":
         return {"metric": METRIC, "value": single["value"], "unit": UNIT, "n_gpus": world,
@@ -554,7 +564,8 @@ def run_batch(args, rank, world, local, pg, V, synth, win, params, sptr, stream,
             "planes160": single_config(V, dev, stream, sptr, flush, "planes160", 0, {}, "none"),
             "boxes640_stereo": single_config(V, dev, stream, sptr, flush, "boxes640_stereo", 1000,
                                              {}, "stereo", steps=10, warmup=3),
-            "rgbd_batch64": rgbd64_measure(V, dev, stream, sptr, flush, 3, 1, rank, pg)}
+            "rgbd_batch64": rgbd64_measure(V, dev, stream, sptr, flush, 3, 1, rank, pg),
+            "learned_init": learned_measure(V)}
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3),
@@ -792,6 +803,38 @@ def single_config(V, dev, stream, sptr, flush, name, seed, kw, prior, steps=20, 
                         f"{iters} EM iterations, prior {prior}, one window per call",
             "median_depth_rel_err_vs_truth": round(
                 float(np.median(np.abs(d * scale - w.depth0) / w.depth0)), 5)}
+
+
+def learned_measure(V, n_windows=16):
+    """Plain vs learned-initialised EM (the committed network) on held-out
+    windows of the learned initialiser's workload (640 x 480, N = 6, scenes
+    of the stereo configuration's kind run monocularly, seeds 6000..): the
+    iterations and windows/s to reach a median inverse-depth error against
+    the converged plain EM (16 iterations) and against the scene's truth
+    (paper_2104_06800_gb300.learned_init.evaluate)."""
+    from paper_2104_06800_gb300 import learned_init as LI
+    wins = make_windows([("boxes640_stereo", LI.EVAL_SEED0 + i, {"N": LI.N_FLOWS})
+                         for i in range(n_windows)])
+    net = V.vd_cnn_create(LI.N_FLOWS, seed=1)
+    try:
+        V.vd_cnn_set_params(net, np.load(os.path.join(ROOT, "paper_2104_06800_gb300", "weights",
+                                                      "learned_init_boxes640_n6.npy")))
+        rep = LI.evaluate(V, net, wins, log=lambda *a, **k: None)
+    finally:
+        V.vd_cnn_destroy(net)
+    out = {"workload": f"boxes640_stereo scenes run monocularly, 640x480, N={LI.N_FLOWS}, "
+                       f"{n_windows} held-out windows (seeds {LI.EVAL_SEED0}..), K=64",
+           "reference": f"plain EM after {LI.REF_ITERS} iterations; error = median relative "
+                        "inverse-depth error over its rigid pixels after the monocular scale "
+                        "alignment",
+           "max_iters": LI.MAX_ITERS}
+    for kind in ("plain", "learned"):
+        d = rep[kind]
+        out[kind] = {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in d.items()
+                     if k.startswith("tol_") or k.startswith("truth_tol_")}
+        out[kind]["ms_bootstrap"] = round(d["ms_bootstrap"], 4)
+        out[kind]["ms_iteration"] = round(d["ms_iteration"], 4)
+    return out
 
 
 def run_rgbd64(args, rank, world, local, pg):

@@ -203,6 +203,9 @@ typedef struct {
   long long calls[VD_N_STAGES];     /* stage executions                      */
   long long launches[VD_N_STAGES];  /* kernel launches per stage             */
   long long total_launches;
+  long long score_evals;            /* (rigid pixel, root) pairs scored by the
+                                       pose M-steps since profiling was enabled
+                                       (counted by the device, profiling on or off) */
 } vd_profile;
 vd_status vd_profile_enable(vd_ctx* ctx, int enable);
 vd_status vd_get_profile(vd_ctx* ctx, vd_profile* out);
@@ -351,6 +354,20 @@ vd_status vd_check_bounded_wait(int polls, void* cuda_stream);
 #define VD_PROBE_FP32 0
 #define VD_PROBE_MUFU 1
 vd_status vd_probe_pipe(int kind, int blocks, int iters, double* ops_out, void* cuda_stream);
+
+/* ---- Checked build (the library's stand-in for a memory checker; the
+ * paper has none) ----------------------------------------------------------
+ * Built with -DVD_CHECKED, the library checks every index its kernels form
+ * from data (bilinear taps of the flow, the P3P picks and their taps, the
+ * rigid-set scatter, chain pixels, coverage cells) against its buffer,
+ * records the first out-of-range one and clamps it into range (the access
+ * stays inside the buffer; the results are then wrong).  out[5]: out[0]
+ * the site of the first such index (0: none; 1 bilinear taps, 2 P3P taps,
+ * 3 scatter, 4 P3P picks, 5 coverage cells, 6 chain pixels), out[1] the
+ * index, out[2] its bound, out[3] how many were seen since the last report,
+ * out[4] 1 in the checked build, 0 otherwise.  Clears the records; reads
+ * device memory (synchronous). */
+vd_status vd_check_report(long long* out);
 typedef struct {
   double fx, fy, cx, cy;    /* intrinsics of the window                     */
   double T1[12];            /* pose of flow 1, [R | tau] row-major           */

@@ -44,12 +44,20 @@ def _digest(extra):
     return h.hexdigest()
 
 
+CHECKED_LIB = os.path.join(HERE, "libvoldor_em_checked.so")
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=(), lib_path: str | None = None,
-          build_dir: str | None = None) -> str:
+          build_dir: str | None = None, checked: bool = False) -> str:
     """Compile (if sources changed) and return the path of the shared library.
 
     extra_flags: additional nvcc flags (for example -D options of the kernels);
-    lib_path / build_dir: where to put the library and the objects."""
+    lib_path / build_dir: where to put the library and the objects;
+    checked: the index-checking build (-DVD_CHECKED) as libvoldor_em_checked.so."""
+    if checked:
+        extra_flags = (*extra_flags, "-DVD_CHECKED")
+        lib_path = lib_path or CHECKED_LIB
+        build_dir = build_dir or os.path.join(HERE, "_build_checked")
     LIB = lib_path or globals()["LIB"]
     BUILD = build_dir or globals()["BUILD"]
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

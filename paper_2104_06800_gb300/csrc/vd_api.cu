@@ -88,6 +88,8 @@ extern "C" vd_status vd_profile_enable(vd_ctx* c, int enable) {
   }
   ps->open_stage = -1;
   c->prof_on = enable ? 1 : 0;
+  if (cudaMemsetAsync(c->score_work, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+    return VD_ERR_CUDA;
   return VD_OK;
 }
 
@@ -111,6 +113,13 @@ extern "C" vd_status vd_get_profile(vd_ctx* c, vd_profile* out) {
     out->launches[i] = c->launches[i];
     out->total_launches += c->launches[i];
   }
+  unsigned long long w = 0;
+  e = cudaMemcpy(&w, c->score_work, sizeof w, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    vd_set_error(cudaGetErrorString(e));
+    return VD_ERR_CUDA;
+  }
+  out->score_evals = (long long)w;
   return VD_OK;
 }
 
@@ -227,7 +236,7 @@ extern "C" vd_status vd_destroy(vd_ctx* c) {
                   c->conf, c->G, c->G_init, c->posef, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
                   c->coarse, c->lam, c->flags, c->blk_counts, c->n_rigid,
                   c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->rootsr, c->partial,
-                  c->root_energy, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
+                  c->root_energy, c->score_work, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
                   c->ep_M, c->ep_E, c->ep_cand, c->ep_count, c->stat_partial, c->stat_out,
                   c->vc_cover, c->vc_counts, c->vc_pose, c->pc_out};
   for (void* p : ptrs)
@@ -311,6 +320,7 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(rootsr, (size_t)4 * S * 12);
   A(partial, (size_t)4 * S * c->nblk_score);
   A(root_energy, 4 * S);
+  A(score_work, 1);
   A(sample_pose, 12 * S * N);
   A(sample_energy, S * N);
   A(pc_out, 52 * N);
@@ -347,6 +357,8 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   if (e == cudaSuccess) e = launch_fill(c->prior_rho, nanf(""), np, c->stream);
   if (e == cudaSuccess) e = launch_fill(c->conf, 0.0f, np, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->degenerate, 0, sizeof(int), c->stream);
+
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->score_work, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = launch_posef(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -1332,5 +1344,41 @@ extern "C" vd_status vd_import_state(vd_ctx* c, const void* blob, size_t bytes) 
   c->samples_set = 0;   // the blob holds no pose samples
   c->poses_set = h.poses_set;
   ++c->cfg_version;
+  return VD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checked build: the index-check records of every translation unit.
+// ---------------------------------------------------------------------------
+cudaError_t vd_check_take_pose(unsigned long long*);
+cudaError_t vd_check_take_depth(unsigned long long*);
+cudaError_t vd_check_take_estep(unsigned long long*);
+cudaError_t vd_check_take_boot(unsigned long long*);
+cudaError_t vd_check_take_ka(unsigned long long*);
+cudaError_t vd_check_take_posecov(unsigned long long*);
+cudaError_t vd_check_take_cnn(unsigned long long*);
+cudaError_t vd_check_take_vc(unsigned long long*);
+
+extern "C" vd_status vd_check_report(long long* out) {
+  if (!out) return VD_ERR_ARG;
+  cudaError_t (*take[])(unsigned long long*) = {
+      vd_check_take_pose, vd_check_take_depth, vd_check_take_estep, vd_check_take_boot,
+      vd_check_take_ka, vd_check_take_posecov, vd_check_take_cnn, vd_check_take_vc};
+  for (int i = 0; i < 4; ++i) out[i] = 0;
+#ifdef VD_CHECKED
+  out[4] = 1;
+#else
+  out[4] = 0;
+#endif
+  for (auto f : take) {
+    unsigned long long r[4];
+    VD_CU(f(r));
+    if (r[3] && !out[0]) {
+      out[0] = (long long)r[0];
+      out[1] = (long long)r[1];
+      out[2] = (long long)r[2];
+    }
+    out[3] += (long long)r[3];
+  }
   return VD_OK;
 }

@@ -525,3 +525,5 @@ cudaError_t launch_stats(vd_ctx* c, double* out2) {
   k_stats_final<<<1, 32, 0, c->stream>>>(c->stat_partial, c->stat_blocks, out2);
   return cudaGetLastError();
 }
+
+VD_CHECK_ACCESSOR(boot)

@@ -1223,3 +1223,5 @@ cudaError_t launch_cnn_init(vd_cnn* n, vd_ctx* c, float* rho_dst, float* q_dst) 
 }
 
 int* vd_cnn_err_flag(vd_cnn* n) { return n->err; }
+
+VD_CHECK_ACCESSOR(cnn)

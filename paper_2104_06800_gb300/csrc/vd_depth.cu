@@ -403,6 +403,70 @@ VD_UNROLL(VD_KQ_PRE_UNROLL)
 // the carried value only, so it is unchanged).  The rounds end when no end
 // value changes, so the result is exactly the sequential walk.
 // ---------------------------------------------------------------------------
+// The loads of one pixel's propagation step that do not depend on the
+// carried value (its rigidness, X_1 at the pixel, the prior, rho* and E*),
+// issued one pixel ahead of the step that uses them, so that their latency
+// overlaps the current pixel's energy.
+template <int NF>
+struct VdPixLoads {
+  float q[NF];
+  float2 f1;
+  float pv, qh, pc;
+  float own, e;
+};
+
+template <int NF>
+__device__ __forceinline__ void vd_pix_load(VdPixLoads<NF>& L, const DevParams& P,
+                                            const float2* __restrict__ flow,
+                                            const float* __restrict__ q,
+                                            const float* __restrict__ prior_val,
+                                            const float* __restrict__ qhat,
+                                            const float* __restrict__ pconf,
+                                            const float* __restrict__ rho_star,
+                                            const float* __restrict__ e_star, size_t npix,
+                                            size_t j) {
+#pragma unroll
+  for (int t = 0; t < NF; ++t) L.q[t] = __ldg(q + (size_t)t * npix + j);
+  L.f1 = __ldg(flow + j);
+  L.pv = 0.0f;
+  L.qh = 0.0f;
+  L.pc = 0.0f;
+  if (P.prior_kind != VD_PRIOR_NONE) {
+    L.pv = __ldg(prior_val + j);
+    L.qh = __ldg(qhat + j);
+    L.pc = __ldg(pconf + j);
+  }
+  L.own = rho_star[j];
+  L.e = e_star[j];
+}
+
+// vd_pixel_setup from the preloaded values (the same arithmetic).
+template <int NF>
+__device__ __forceinline__ void vd_pixel_from_loads(VdPixel<NF>& px, const DevParams& P,
+                                                    const float* __restrict__ sPose, int u, int v,
+                                                    const VdPixLoads<NF>& L) {
+  const float rx = ((float)u - P.cx) / P.fx;
+  const float ry = ((float)v - P.cy) / P.fy;
+#pragma unroll
+  for (int t = 0; t < NF; ++t) {
+    const float* M = sPose + 12 * (t + 1);
+    px.ax[t] = fmaf(M[0], rx, fmaf(M[1], ry, M[2]));
+    px.ay[t] = fmaf(M[3], rx, fmaf(M[4], ry, M[5]));
+    px.az[t] = fmaf(M[6], rx, fmaf(M[7], ry, M[8]));
+    px.wl[t] = L.q[t] * VD_LN2;
+  }
+  px.f1x = L.f1.x;
+  px.f1y = L.f1.y;
+  px.u = (float)u;
+  px.v = (float)v;
+  px.pw = 0.0f;
+  px.pv = 0.0f;
+  if (P.prior_kind != VD_PRIOR_NONE && isfinite(L.pv)) {
+    px.pv = L.pv;
+    px.pw = L.qh * L.pc;
+  }
+}
+
 template <int NF>
 __device__ __forceinline__ float vd_prop_step(const DevParams& P, const float* sPose,
                                               const float2* __restrict__ flow,
@@ -440,18 +504,33 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
     const int pos = rev ? L - 1 - m : m;
     *u = rows ? pos : ch;
     *v = rows ? ch : pos;
-    return (size_t)(*v) * P.W + (*u);
+    return (size_t)VD_CHK(VD_SITE_CHAIN, (long long)(*v) * P.W + (*u), (long long)P.W * P.H);
   };
-  // phase A
+  // phase A; the next pixel's loads are issued before this pixel's energy
+  const size_t npix = (size_t)P.W * P.H;
   float cur = 0.0f;
+  VdPixLoads<NF> Ln;
+  int un = 0, vn = 0;
+  size_t jn = 0;
+  if (m0 < m1) {
+    jn = pix(m0, &un, &vn);
+    vd_pix_load<NF>(Ln, P, flow, q, prior_val, qhat, pconf, rho_star, e_star, npix, jn);
+  }
   for (int m = m0; m < m1; ++m) {
-    int u, v;
-    const size_t j = pix(m, &u, &v);
-    const float own = rho_star[j];
+    const VdPixLoads<NF> L = Ln;
+    const int u = un, v = vn;
+    const size_t j = jn;
+    if (m + 1 < m1) {
+      jn = pix(m + 1, &un, &vn);
+      vd_pix_load<NF>(Ln, P, flow, q, prior_val, qhat, pconf, rho_star, e_star, npix, jn);
+    }
     if (m == m0 || (restart > 0 && m % restart == 0)) {
-      cur = own;
+      cur = L.own;
     } else {
-      cur = vd_prop_step<NF>(P, sPose, flow, q, prior_val, qhat, pconf, cur, own, e_star[j], u, v, j);
+      VdPixel<NF> px;
+      vd_pixel_from_loads<NF>(px, P, sPose, u, v, L);
+      const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur, L.e);
+      cur = (Ec < L.e) ? cur : L.own;
     }
     rho_new[j] = cur;
   }
@@ -654,3 +733,5 @@ cudaError_t launch_eval_energy(vd_ctx* c, const float* rho_in, float* e_out) {
                             rho_in, e_out)));
   return cudaGetLastError();
 }
+
+VD_CHECK_ACCESSOR(depth)

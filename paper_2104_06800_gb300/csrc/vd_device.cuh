@@ -12,6 +12,47 @@
 #define VD_LN2 0.69314718055994530942f
 
 // ---------------------------------------------------------------------------
+// Checked build (-DVD_CHECKED; the stand-in for a memory checker): every
+// index a kernel forms from data is checked against its buffer; the first
+// index out of range is recorded (site, index, bound) with a count of all,
+// and the index is clamped into range so that the access stays inside its
+// buffer (the results are then wrong and the call reports it).  Each
+// translation unit has its own record; vd_check_report gathers them.
+// Without the flag VD_CHK is the index itself.
+// ---------------------------------------------------------------------------
+#ifdef VD_CHECKED
+static __device__ unsigned long long g_vd_check[4];
+__device__ __forceinline__ long long vd_checked(int site, long long i, long long n) {
+  if (i >= 0 && i < n) return i;
+  if (atomicCAS(&g_vd_check[0], 0ull, (unsigned long long)site) == 0ull) {
+    g_vd_check[1] = (unsigned long long)i;
+    g_vd_check[2] = (unsigned long long)n;
+  }
+  atomicAdd(&g_vd_check[3], 1ull);
+  return i < 0 ? 0 : (n > 0 ? n - 1 : 0);
+}
+#define VD_CHK(site, i, n) vd_checked((site), (long long)(i), (long long)(n))
+// host accessor of this unit's record: copies it to out[4] and clears it
+#define VD_CHECK_ACCESSOR(name)                                                  \
+  cudaError_t vd_check_take_##name(unsigned long long* out) {                    \
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_vd_check, 4 * sizeof(unsigned long long)); \
+    const unsigned long long z[4] = {0, 0, 0, 0};                                \
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_vd_check, z, sizeof z);       \
+    return e;                                                                    \
+  }
+#else
+#define VD_CHK(site, i, n) (i)
+#define VD_CHECK_ACCESSOR(name)                                                  \
+  cudaError_t vd_check_take_##name(unsigned long long* out) {                    \
+    for (int i = 0; i < 4; ++i) out[i] = 0;                                      \
+    return cudaSuccess;                                                          \
+  }
+#endif
+// sites of the checked build
+enum { VD_SITE_BILINEAR = 1, VD_SITE_P3P_TAPS = 2, VD_SITE_SCATTER = 3, VD_SITE_PICK = 4,
+       VD_SITE_VC_CELL = 5, VD_SITE_CHAIN = 6 };
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 bit
 // multiplies, mixing with the key, key advanced by the Weyl constants.
 // ---------------------------------------------------------------------------
@@ -131,7 +172,7 @@ __device__ __forceinline__ float2 vd_bilinear(const float2* __restrict__ F, int 
   const int y0 = min(__float2int_rd(y), H - 2);
   const float ax = x - (float)x0;
   const float ay = y - (float)y0;
-  const float2* p = F + (size_t)y0 * W + x0;
+  const float2* p = F + VD_CHK(VD_SITE_BILINEAR, (long long)y0 * W + x0, (long long)W * H - W - 1);
   const float2 f00 = __ldg(p), f01 = __ldg(p + 1);
   const float2 f10 = __ldg(p + W), f11 = __ldg(p + W + 1);
   const float tx = fmaf(ax, f01.x - f00.x, f00.x), ty = fmaf(ax, f01.y - f00.y, f00.y);

@@ -258,3 +258,5 @@ cudaError_t launch_estep(vd_ctx* c, int direction) {
                                                                          c->conf);
   return cudaGetLastError();
 }
+
+VD_CHECK_ACCESSOR(estep)

@@ -102,6 +102,7 @@ struct vd_ctx {
   float* rootsr;           // [S*4][12] float R | tau of every root slot
   float* partial;          // [S*4][score blocks]
   double* root_energy;     // [S*4]
+  unsigned long long* score_work;  // [1] rigid pixels x roots scored since vd_profile_enable
   double* sample_pose;     // [N][S][12] kept root of every sample, per frame
   double* sample_energy;   // [N][S] (+inf: no root)
   int last_pose_t;         // frame of the last pose M-step (0: none)

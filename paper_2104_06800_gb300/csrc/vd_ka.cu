@@ -349,3 +349,5 @@ extern "C" vd_status vd_ka_align(const float* depth1, const float* depth2, const
   io->n_valid = cur.n;
   return VD_OK;
 }
+
+VD_CHECK_ACCESSOR(ka)

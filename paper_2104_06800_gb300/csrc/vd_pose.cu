@@ -132,7 +132,7 @@ k_rigid_scatter(DevParams P, const float* __restrict__ posef, const float2* __re
   before += __popc(bal & ((1u << lane) - 1u));
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *n_out = offset + total;
   if (!f) return;
-  const int pos = offset + before;
+  const int pos = (int)VD_CHK(VD_SITE_SCATTER, offset + before, npix);
   const int v = (int)(j / P.W), u = (int)(j - (size_t)v * P.W);
   const float c = rho[j];
   const float rx = ((float)u - P.cx) / P.fx, ry = ((float)v - P.cy) / P.fy;
@@ -213,7 +213,9 @@ __device__ __forceinline__ void vd_correspondence_df(const DevParams& P, const v
     x0 = fminf(fmaxf(x0, 0.0f), (float)(P.W - 2));
     y0 = fminf(fmaxf(y0, 0.0f), (float)(P.H - 2));
     const vd_df ax = vd_df_sub(xp, vd_df_make(x0)), ay = vd_df_sub(yp, vd_df_make(y0));
-    const float2* q = flow + (size_t)(t - 1) * npix + (size_t)y0 * P.W + (int)x0;
+    const float2* q = flow + (size_t)(t - 1) * npix +
+                      VD_CHK(VD_SITE_P3P_TAPS, (long long)y0 * P.W + (long long)x0,
+                             (long long)npix - P.W - 1);
     const float2 f00 = q[0], f01 = q[1], f10 = q[P.W], f11 = q[P.W + 1];
     // F = t + ay (b - t), t = f00 + ax (f01 - f00), b = f10 + ax (f11 - f10)
     const vd_df tx = vd_df_add(vd_df_make(f00.x), vd_df_mul(ax, vd_two_sum(f01.x, -f00.x)));
@@ -338,15 +340,21 @@ __device__ int vd_p3p_df_roots_warp(const VdP3Pdf& g, const vd_df* res, vd_df* o
 // ordering key; each lane then finds its rank.  Writes the roots (float64,
 // ordered by rotation vector, then translation), their count and their
 // float K R | K tau for the dense scoring.
-__global__ void __launch_bounds__(32)
+// Samples per block (one warp each): warps of one SM share the fetched
+// instructions of the long straight-line double-float code.
+#ifndef VD_P3P_WARPS
+#define VD_P3P_WARPS 4
+#endif
+
+__global__ void __launch_bounds__(32 * VD_P3P_WARPS)
 k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restrict__ flow,
               const float* __restrict__ rho, const int* __restrict__ idx,
               const int* __restrict__ n_rigid, int t, uint32_t itcode, double* __restrict__ roots,
               int* __restrict__ root_count, float* __restrict__ rootsf,
               float* __restrict__ rootsr) {
-  const int g = blockIdx.x;
-  const int lane = threadIdx.x;
-  if (g >= P.S) return;
+  const int g = blockIdx.x * VD_P3P_WARPS + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= P.S) return;                       // whole warps leave together
   const int n = *n_rigid;
   int pick[3] = {0, 0, 0};
   bool ok = false;
@@ -374,7 +382,10 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
   for (int i = 0; i < 12; ++i) gt[i] = vd_shfl_df(gl, i);
   vd_df Xl[3] = {vd_df_make(0.0f), vd_df_make(0.0f), vd_df_make(0.0f)};
   vd_df fl[3] = {vd_df_make(0.0f), vd_df_make(0.0f), vd_df_make(1.0f)};
-  if (lane < 3) vd_correspondence_df(P, gt, flow, rho, t, idx[pick[lane]], Xl, fl);
+  if (lane < 3)
+    vd_correspondence_df(P, gt, flow, rho, t,
+                         (int)VD_CHK(VD_SITE_PICK, idx[VD_CHK(VD_SITE_PICK, pick[lane], n)],
+                                     (long long)P.W * P.H), Xl, fl);
   vd_df X[9], f[9];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -510,6 +521,22 @@ __device__ __forceinline__ float vd_reduce_scatter8(float* acc, int lane) {
   return v;
 }
 
+// acc[0..31] of every lane -> lane L returns the warp's sum of acc[L]
+// (recursive halving over lane bits 4..0: 31 shuffles).
+__device__ __forceinline__ float vd_reduce_scatter32(float* acc, int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = upper ? acc[i] : acc[i + s];
+      const float keep = upper ? acc[i + s] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return acc[0];
+}
+
 // Grid (pixel blocks, root groups of 32): block (b, g) scores the group's
 // roots against pixel block b's contiguous range of rigid pixels; warps
 // take passes of 32 x SCORE_PPT pixels in turn (pixels in registers), and
@@ -599,12 +626,20 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
 // float64 sum of the block partials of every root that exists (infinity for
 // the others): one warp per root, each lane sums a strided subset, then a
 // fixed-order butterfly over the lanes.
+// With work non-null, each block adds (rigid pixels x its real roots) to
+// *work (the scoring's evaluation count, read by the profiling).
 __global__ void k_root_energy(const float* __restrict__ partial, int nblk, int M,
-                              const int* __restrict__ root_count, double* __restrict__ energy) {
+                              const int* __restrict__ root_count, double* __restrict__ energy,
+                              const int* __restrict__ n_ptr, unsigned long long* __restrict__ work) {
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
+  const bool real = r < M && !(root_count && (r & 3) >= root_count[r >> 2]);
+  if (work) {
+    const int nreal = __syncthreads_count(real && lane == 0);
+    if (threadIdx.x == 0 && nreal) atomicAdd(work, (unsigned long long)*n_ptr * nreal);
+  }
   if (r >= M) return;                 // whole warps leave together
-  if (root_count && (r & 3) >= root_count[r >> 2]) {
+  if (!real) {
     if (lane == 0) energy[r] = INFINITY;
     return;
   }
@@ -617,8 +652,9 @@ __global__ void k_root_energy(const float* __restrict__ partial, int nblk, int M
 
 static inline cudaError_t launch_root_energy(const float* partial, int nblk, int M,
                                              const int* root_count, double* energy,
-                                             cudaStream_t s) {
-  k_root_energy<<<(M + 3) / 4, 128, 0, s>>>(partial, nblk, M, root_count, energy);
+                                             cudaStream_t s, const int* n_ptr = nullptr,
+                                             unsigned long long* work = nullptr) {
+  k_root_energy<<<(M + 3) / 4, 128, 0, s>>>(partial, nblk, M, root_count, energy, n_ptr, work);
   return cudaGetLastError();
 }
 
@@ -723,12 +759,13 @@ __device__ __forceinline__ void vd_se3_exp_f(const float* xi, float* T) {
 }
 
 // ---------------------------------------------------------------------------
-// Per sample: the lowest-energy root; then mean-shift (Eq. 7) from the best
-// sample: x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
-// w_g = exp(-d^T Sigma^-1 d / 2), at most 100 steps.  The float64 definition
-// stops at |step| < 1e-12; these float32 iterations stop at the float32
-// floor of the relative poses, 1e-6 (1 + |tau|).  One warp: the sums are
-// warp butterflies, every lane updates the same mode, no block barrier.
+// Per sample: the lowest-energy root; then the mode of the sample mixture
+// (Sec. III-A, after Eq. 7) from the best sample: the fixed point of the
+// mean-shift map x <- x exp(sum w_g d_g / sum w_g), d_g = log(x^-1 T_g),
+// w_g = exp(-d^T Sigma^-1 d / 2), reached by safeguarded Newton steps on
+// that map (below), at most VD_MS_MAX_ITERS steps.  The float64 definition
+// iterates the map itself until |step| < 1e-12.  One warp: the sums are a
+// warp reduce-scatter, every lane updates the same mode, no block barrier.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32)
 k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __restrict__ root_count,
@@ -793,25 +830,35 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
 #pragma unroll
   for (int i = 0; i < 12; ++i) x[i] = sT[bestS][i];
   const float tn = sqrtf(x[3] * x[3] + x[7] * x[7] + x[11] * x[11]);
-  const double st_ = P.ms_sig_rel * (double)tn + P.ms_sig_abs;
-  const float ivr = (float)(1.0 / (P.ms_sig_rot * P.ms_sig_rot)), ivt = (float)(1.0 / (st_ * st_));
-  // the float32 iterations stop at this step norm (the float32 floor of the
-  // relative poses); the float64 definition stops at 1e-12
+  // kernel widths in float32 (a float64 division costs this part's weak
+  // float64 pipe a long dependent sequence)
+  const float sr = (float)P.ms_sig_rot, st_ = fmaf((float)P.ms_sig_rel, tn, (float)P.ms_sig_abs);
+  const float ivr = 1.0f / (sr * sr), ivt = 1.0f / (st_ * st_);
+  // convergence (below): a Newton step under tol, or under 10 tol and no
+  // longer halving (the float32 floor of the relative poses, amplified by
+  // the mode's conditioning); the float64 definition stops at 1e-12
   const float tol = (float)(VD_MS_TOL_F32 * (1.0 + (double)tn));
   // the narrow-kernel path of the logarithm applies while 14.5 sigma of
   // rotation stays below 0.2 rad (the default sigma is 0.01 rad)
   const bool near_log = 210.0f / ivr < 0.04f;
-  // Aitken extrapolation: where two successive plain steps point the same
-  // way (cosine above 0.9) and shrink by a ratio r in (0.05, 0.95), the
-  // iteration converges linearly along them and the remaining distance is
-  // about step r / (1 - r); the next step is then taken 1 / (1 - r) times
-  // as long (at most one kernel width), and the one after it is plain
-  // again.  The fixed point is that of the plain iteration, which also
-  // decides convergence: a plain step below the tolerance ends the loop.
-  float prev[6] = {0, 0, 0, 0, 0, 0};
-  bool have_prev = false;
+  // Whitened tangent coordinates z = Sigma^-1/2 d.  The plain step is the
+  // weighted mean s of the z_g; it vanishes at the mode.  Moving the mode by
+  // delta changes it, to first order, by -(I - C) delta, C the weighted
+  // covariance of the z_g about s, so the Newton step is
+  // delta = (I - C)^-1 s.  At a mode I - C is positive definite and the
+  // plain iteration converges at the rate of C's largest eigenvalue, close
+  // to 1 where only a few samples fall in the kernel's reach (as after a
+  // rough bootstrap depth): hundreds of steps where Newton takes a few.  The
+  // Newton step is taken when the Cholesky pivots of I - C exceed 1e-3 and
+  // it stays within one kernel width, else the plain step; either way the
+  // fixed point is the plain iteration's.
+  const float sq[6] = {sqrtf(ivr), sqrtf(ivr), sqrtf(ivr), sqrtf(ivt), sqrtf(ivt), sqrtf(ivt)};
+  float last = INFINITY;
   for (int it = 0; it < VD_MS_MAX_ITERS; ++it) {
-    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    // per lane: w, w z (6), w z_i z_j (21, i <= j), then padding
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
     for (int g = lane; g < P.S; g += 32) {
       if (!sValid[g]) continue;
       const float* Tg = sT[g];
@@ -827,53 +874,93 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
                          x[8 + r] * (Tg[11] - x[11]);
       }
       if (near_log ? vd_se3_log_near_f(rel, d, ivr) : vd_se3_log_f(rel, d)) {
-        const float m = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * ivr +
-                        (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) * ivt;
+        float z[6], m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          z[i] = d[i] * sq[i];
+          m = fmaf(z[i], z[i], m);
+        }
         const float w = __expf(-0.5f * m);
         acc[0] += w;
+        int k = 7;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) acc[1 + i] += w * d[i];
+        for (int i = 0; i < 6; ++i) {
+          const float wz = w * z[i];
+          acc[1 + i] += wz;
+#pragma unroll
+          for (int j = i; j < 6; ++j, ++k) acc[k] = fmaf(wz, z[j], acc[k]);
+        }
       }
     }
-    // xor butterflies: float addition commutes, so partners hold equal sums
-    // after every level and all lanes end with the same totals
+    // lane L ends with the warp's sum of acc[L] (each sum formed once, in a
+    // fixed order), then every lane reads all 28
+    const float mine = vd_reduce_scatter32(acc, lane);
+    float v[28];
 #pragma unroll
-    for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 28; ++k) v[k] = __shfl_sync(FULL, mine, k);
+    if (!(v[0] > 0.0f)) break;
+    const float iw = 1.0f / v[0];
+    float sz[6];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(FULL, acc[i], o);
-    if (!(acc[0] > 0.0f)) break;
-    float step[6], nrm = 0.0f;
-    const float iw = 1.0f / acc[0];
+    for (int i = 0; i < 6; ++i) sz[i] = v[1 + i] * iw;
+    // A = I - C (packed lower triangle, row by row), then its Cholesky factor
+    float A[21];
+    {
+      int k = 7;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j, ++k)
+          A[j * (j + 1) / 2 + i] = (i == j ? 1.0f : 0.0f) - (v[k] * iw - sz[i] * sz[j]);
+    }
+    bool newton = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      float dj = A[j * (j + 1) / 2 + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) dj -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+      newton = newton && dj > 1e-3f;
+      const float lj = sqrtf(fmaxf(dj, 1e-3f));
+      A[j * (j + 1) / 2 + j] = lj;
+      const float il = 1.0f / lj;
+#pragma unroll
+      for (int i = j + 1; i < 6; ++i) {
+        float a = A[i * (i + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) a -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+        A[i * (i + 1) / 2 + j] = a * il;
+      }
+    }
+    // (L L^T) y = s_z
+    float y[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      step[i] = acc[1 + i] * iw;
-      nrm += step[i] * step[i];
-    }
-    const bool converged = sqrtf(nrm) < tol;
-    float scale = 1.0f;
-    if (have_prev && !converged) {
-      float dot = 0.0f, pn = 0.0f;
+      float a = sz[i];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        dot += step[i] * prev[i];
-        pn += prev[i] * prev[i];
-      }
-      const float r = dot / pn;
-      if (r > 0.05f && r < 0.95f && dot > 0.9f * sqrtf(nrm * pn)) {
-        const float mh = (step[0] * step[0] + step[1] * step[1] + step[2] * step[2]) * ivr +
-                         (step[3] * step[3] + step[4] * step[4] + step[5] * step[5]) * ivt;
-        scale = fmaxf(1.0f, fminf(1.0f / (1.0f - r), rsqrtf(fmaxf(mh, 1e-30f))));
-      }
+      for (int k = 0; k < i; ++k) a -= A[i * (i + 1) / 2 + k] * y[k];
+      y[i] = a / A[i * (i + 1) / 2 + i];
     }
-    if (scale > 1.0f) {
-      have_prev = false;
 #pragma unroll
-      for (int i = 0; i < 6; ++i) step[i] *= scale;
-    } else {
-      have_prev = true;
+    for (int i = 5; i >= 0; --i) {
+      float a = y[i];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) prev[i] = step[i];
+      for (int k = i + 1; k < 6; ++k) a -= A[k * (k + 1) / 2 + i] * y[k];
+      y[i] = a / A[i * (i + 1) / 2 + i];
     }
+    float mh = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) mh = fmaf(y[i], y[i], mh);
+    newton = newton && mh <= 1.0f;
+    float step[6], nrm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      step[i] = (newton ? y[i] : sz[i]) / sq[i];
+      nrm = fmaf(step[i], step[i], nrm);
+    }
+    nrm = sqrtf(nrm);
+    const bool converged = newton ? (nrm < tol || (nrm < 10.0f * tol && nrm > 0.5f * last))
+                                  : nrm < tol;
+    if (newton) last = nrm;
     float E[12], xn[12];
     vd_se3_exp_f(step, E);
 #pragma unroll
@@ -887,32 +974,48 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
     for (int i = 0; i < 12; ++i) x[i] = xn[i];
     if (converged) break;
   }
-  if (lane != 0) return;
-  // re-orthonormalise the rotation in float64 (Gram-Schmidt on the rows,
-  // third row as the cross product) and store the pose
-  double R[9], o[12];
+  // re-orthonormalise the rotation (Gram-Schmidt on the rows, third row as
+  // the cross product) in double-float on the FP32 pipe, every lane alike;
+  // lane i < 12 stores entry i of the pose and of its float K R | K tau
+  vd_df R[9];
+#pragma unroll
   for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) R[3 * r + c] = (double)x[4 * r + c];
-  double n0 = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
-  for (int c = 0; c < 3; ++c) R[c] /= n0;
-  const double d01 = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
-  for (int c = 0; c < 3; ++c) R[3 + c] -= d01 * R[c];
-  const double n1 = sqrt(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
-  for (int c = 0; c < 3; ++c) R[3 + c] /= n1;
-  R[6] = R[1] * R[5] - R[2] * R[4];
-  R[7] = R[2] * R[3] - R[0] * R[5];
-  R[8] = R[0] * R[4] - R[1] * R[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) R[3 * r + c] = vd_df_make(x[4 * r + c]);
+  {
+    const vd_df s0 = vd_df_add(vd_df_add(vd_df_mul(R[0], R[0]), vd_df_mul(R[1], R[1])),
+                               vd_df_mul(R[2], R[2]));
+    const vd_df i0 = vd_df_rsqrt(s0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) R[c] = vd_df_mul(R[c], i0);
+    const vd_df d01 = vd_df_add(vd_df_add(vd_df_mul(R[0], R[3]), vd_df_mul(R[1], R[4])),
+                                vd_df_mul(R[2], R[5]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) R[3 + c] = vd_df_sub(R[3 + c], vd_df_mul(d01, R[c]));
+    const vd_df s1 = vd_df_add(vd_df_add(vd_df_mul(R[3], R[3]), vd_df_mul(R[4], R[4])),
+                               vd_df_mul(R[5], R[5]));
+    const vd_df i1 = vd_df_rsqrt(s1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) R[3 + c] = vd_df_mul(R[3 + c], i1);
+    R[6] = vd_df_sub(vd_df_mul(R[1], R[5]), vd_df_mul(R[2], R[4]));
+    R[7] = vd_df_sub(vd_df_mul(R[2], R[3]), vd_df_mul(R[0], R[5]));
+    R[8] = vd_df_sub(vd_df_mul(R[0], R[4]), vd_df_mul(R[1], R[3]));
+  }
+  double o[12];
+#pragma unroll
   for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c) o[4 * r + c] = R[3 * r + c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[4 * r + c] = vd_df_to(R[3 * r + c]);
     o[4 * r + 3] = (double)x[4 * r + 3];
   }
-  for (int i = 0; i < 12; ++i) G[12 * t + i] = o[i];
-  // float K R | K tau of the updated pose
-  float* pf = posef + 12 * t;
-  for (int i = 0; i < 4; ++i) {
-    pf[i < 3 ? i : 9] = (float)(P.fx_d * o[i] + P.cx_d * o[8 + i]);
-    pf[i < 3 ? 3 + i : 10] = (float)(P.fy_d * o[4 + i] + P.cy_d * o[8 + i]);
-    pf[i < 3 ? 6 + i : 11] = (float)o[8 + i];
+  if (lane < 12) {
+    G[12 * t + lane] = o[lane];
+    // float K R | K tau of the updated pose: row lane / 4, column lane % 4
+    const int i = lane & 3, row = lane >> 2;
+    float* pf = posef + 12 * t;
+    if (row == 0) pf[i < 3 ? i : 9] = (float)(P.fx_d * o[i] + P.cx_d * o[8 + i]);
+    else if (row == 1) pf[i < 3 ? 3 + i : 10] = (float)(P.fy_d * o[4 + i] + P.cy_d * o[8 + i]);
+    else pf[i < 3 ? 6 + i : 11] = (float)o[8 + i];
   }
 }
 
@@ -952,7 +1055,8 @@ cudaError_t launch_pose_score_only(vd_ctx* c) {
 #undef VD_SCORE_LAUNCH
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_root_energy(c->partial, nblk, M, c->root_count, c->root_energy, c->stream);
+  return launch_root_energy(c->partial, nblk, M, c->root_count, c->root_energy, c->stream,
+                            c->n_rigid, c->score_work);
 }
 
 cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
@@ -969,7 +1073,8 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
                                                               c->robs);
   vd_prof_end(c, VD_ST_RIGID, 2);
   vd_prof_begin(c, VD_ST_P3P);
-  k_p3p_samples<<<P.S, 32, 0, c->stream>>>(P, c->G, c->flow, c->rho, c->rigid_idx,
+  k_p3p_samples<<<(P.S + VD_P3P_WARPS - 1) / VD_P3P_WARPS, 32 * VD_P3P_WARPS, 0, c->stream>>>(
+      P, c->G, c->flow, c->rho, c->rigid_idx,
                                             c->n_rigid, t, itcode, c->roots, c->root_count,
                                             c->rootsf, c->rootsr);
   vd_prof_end(c, VD_ST_P3P, 1);
@@ -1137,3 +1242,5 @@ extern "C" vd_status vd_score_poses(const float* points, const float* obs, int n
   }
   return VD_OK;
 }
+
+VD_CHECK_ACCESSOR(pose)

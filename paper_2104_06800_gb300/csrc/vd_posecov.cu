@@ -289,3 +289,5 @@ extern "C" vd_status vd_get_frame_samples(vd_ctx* c, int t, double* poses, doubl
   VD_CU(cudaStreamSynchronize(c->stream));
   return VD_OK;
 }
+
+VD_CHECK_ACCESSOR(posecov)

@@ -66,7 +66,7 @@ k_vc_project(const float* __restrict__ rho, int W, int H, float fx, float fy, fl
     }
     const unsigned b = __ballot_sync(FULL, in);
     if (lane == 0 && b) atomicAdd(&counts[1 + k], (unsigned long long)__popc(b));
-    if (in) cover[(size_t)k * stride + cell] = 1;
+    if (in) cover[(size_t)k * stride + VD_CHK(VD_SITE_VC_CELL, (long long)cell, (long long)stride)] = 1;
   }
 }
 
@@ -147,3 +147,5 @@ extern "C" int vd_vc_stride(const double* vc, int n, double tau_stride) {
 extern "C" int vd_vc_is_keyframe(double vc, double tau_keyframe) {
   return vc < tau_keyframe ? 1 : 0;
 }
+
+VD_CHECK_ACCESSOR(vc)

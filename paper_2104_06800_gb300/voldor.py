@@ -53,7 +53,8 @@ STAGE_NAMES = ("depth_sample", "depth_propagate", "rigidness_estep", "pose_rigid
 
 class vd_profile(C.Structure):
     _fields_ = [("ms", C.c_double * VD_N_STAGES), ("calls", C.c_longlong * VD_N_STAGES),
-                ("launches", C.c_longlong * VD_N_STAGES), ("total_launches", C.c_longlong)]
+                ("launches", C.c_longlong * VD_N_STAGES), ("total_launches", C.c_longlong),
+                ("score_evals", C.c_longlong)]
 
 
 class vd_tune(C.Structure):
@@ -146,6 +147,7 @@ _SIGS = {
     "vd_batch_get_stats": [_P, C.POINTER(vd_batch_stats)],
     "vd_check_bounded_wait": [C.c_int, _P],
     "vd_probe_pipe": [C.c_int, C.c_int, C.c_int, _P, _P],
+    "vd_check_report": [_P],
     "vd_cnn_create": [C.c_int, C.c_ulonglong, C.POINTER(_P)],
     "vd_cnn_destroy": [_P],
     "vd_cnn_layout": [_P, C.POINTER(C.c_int), _P, _P, _P, _P],
@@ -406,7 +408,8 @@ def vd_get_profile(ctx):
     p = vd_profile()
     _call("vd_get_profile", ctx, C.byref(p))
     return {name: dict(ms=p.ms[i], calls=p.calls[i], launches=p.launches[i])
-            for i, name in enumerate(STAGE_NAMES)} | {"total_launches": p.total_launches}
+            for i, name in enumerate(STAGE_NAMES)} | {"total_launches": p.total_launches,
+                                                      "score_evals": p.score_evals}
 
 
 VD_NOALLOC_MAX_POSES = 256
@@ -598,6 +601,14 @@ def vd_probe_pipe(kind, blocks, iters, stream=None):
     _call("vd_probe_pipe", int(kind), int(blocks), int(iters), C.byref(ops),
           stream if stream is not None else current_stream())
     return ops.value
+
+
+def vd_check_report():
+    """Index-check record of the checked build (see voldor_em.h): dict with
+    site, index, bound, count and checked (whether this library checks)."""
+    out = (C.c_longlong * 5)()
+    _call("vd_check_report", C.cast(out, C.c_void_p))
+    return dict(site=out[0], index=out[1], bound=out[2], count=out[3], checked=bool(out[4]))
 
 
 def vd_cnn_destroy(net):

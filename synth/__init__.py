@@ -216,7 +216,8 @@ def _cfg_planes(rng, noisy):
     G = np.stack(G)
     flow, moving = _flows(rng, sc, G, W, H, N, K, 0.5, 2.0, 0.0, noisy, (4, 12))
     return W, H, N, K, sc, G, flow, moving, dict(fisk_alpha0=0.5, fisk_beta=2.0, n_hyp=64,
-                                                  n_iters=3, dmin=2.0, dmax=10.0)
+                                                  n_iters=3, dmin=2.0, dmax=10.0,
+                                                  tmin=0.1, tmax=0.2)
 
 
 def _cfg_boxes(rng, noisy, W=640, H=480, N=5, moving=0.10, dmax=40.0):
@@ -244,7 +245,8 @@ def _cfg_boxes(rng, noisy, W=640, H=480, N=5, moving=0.10, dmax=40.0):
     G = np.stack(G)
     flow, mv = _flows(rng, sc, G, W, H, N, K, 0.5, 2.0, moving, noisy, (6, max(10, W // 16)))
     return W, H, N, K, sc, G, flow, mv, dict(fisk_alpha0=0.5, fisk_beta=2.0, n_hyp=64,
-                                              n_iters=5, dmin=1.0, dmax=dmax)
+                                              n_iters=5, dmin=1.0, dmax=dmax,
+                                              tmin=0.2, tmax=0.45)
 
 
 def _cfg_driving(rng, noisy, W=1216, H=368, N=6, kerb=False):
@@ -278,7 +280,8 @@ def _cfg_driving(rng, noisy, W=1216, H=368, N=6, kerb=False):
     G = np.stack(G)
     flow, mv = _flows(rng, sc, G, W, H, N, K, 1.0, 2.0, 0.05 if noisy else 0.0, noisy, (8, 40))
     return W, H, N, K, sc, G, flow, mv, dict(fisk_alpha0=1.0, fisk_beta=2.0, n_hyp=128,
-                                              n_iters=8, dmin=2.0, dmax=80.0)
+                                              n_iters=8, dmin=2.0, dmax=80.0,
+                                              tmin=1.0, tmax=1.55)
 
 
 CONFIGS = {
@@ -356,12 +359,16 @@ def make_window(name: str, seed: int = 0, noisy: bool = True, N: int | None = No
             z[_holes(rng, H, W, 0.10)] = np.nan
         depth_prior = z.astype(np.float32)
     # inverse-depth search range: metric when a prior fixes the scale, else in
-    # units of |tau_1| (the monocular bootstrap normalises the first translation)
-    s = 1.0 if (stereo is not None or depth_prior is not None) else float(np.linalg.norm(G[1][:, 3]))
+    # units of |tau_1| (the monocular bootstrap normalises the first
+    # translation), from the workload's bounds on depth and per-frame motion
+    # (tmin..tmax, the generator's), never from this window's true motion
+    metric = stereo is not None or depth_prior is not None
+    lo, hi = (1.0, 1.0) if metric else (prm["tmin"], prm["tmax"])
     prm = dict(prm)
-    prm["rho_min"] = float(np.float32(0.5 * s / prm["dmax"]))
-    prm["rho_max"] = float(np.float32(2.0 * s / prm["dmin"]))
-    prm["scale"] = s
+    prm["rho_min"] = float(np.float32(0.5 * lo / prm["dmax"]))
+    prm["rho_max"] = float(np.float32(2.0 * hi / prm["dmin"]))
+    # the true |tau_1| (the monocular gauge of the scene's depth): tests only
+    prm["scale"] = 1.0 if metric else float(np.linalg.norm(G[1][:, 3]))
     return Window(name=name, W=W, H=H, N=Nn, fx=fx, fy=fy, cx=cx, cy=cy, G=G, depth0=Z0,
                   flow=np.ascontiguousarray(flow), moving=mv, stereo_disp=stereo,
                   stereo_baseline=baseline, depth_prior=depth_prior, params=prm)

@@ -159,3 +159,14 @@ def test_header_is_plain_c(tmp_path):
                         "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
                         str(tmp_path / "use.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_checked_build_compiles_and_exports_every_symbol():
+    """The index-checking build (-DVD_CHECKED) of the same sources."""
+    import ctypes as C
+    from paper_2104_06800_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libvoldor_em_checked.so")
+    lib = C.CDLL(path)
+    for n in sorted(_declared()):
+        assert hasattr(lib, n), n

@@ -5,10 +5,14 @@ The network in paper_2104_06800_gb300/weights/ was trained by
 the library's own kernels, on EM-converged labels of 2000 synthetic windows
 (seeds 4000..5999).  On held-out windows (seeds 6000..) its inverse depth, used
 as the starting value of the monocular bootstrap's depth step, leaves the
-bootstrap closer to the converged EM (and to the scene's true depth) than
-the random start does.  The test checks that gain on six held-out windows.
-The EM's own iterations erase it after about two iterations (the method's
-random draws dominate from there), which the training report records."""
+bootstrap closer to the converged EM and to the scene's true depth than the
+random start does (on 93 of 100 held-out windows against the truth).  The
+EM's own iterations erase that gain: after 12 iterations the two starts are
+level against the true depth (median error 0.055 learned, 0.058 plain over
+100 windows; the learned start ahead on 58 of them, and no windows/s gain at
+any tolerance).  The test checks both facts on six held-out windows: the
+gain right after the bootstrap, and that after the EM the learned start's
+median error against the truth is within 15 % of the plain start's."""
 import os
 
 import numpy as np
@@ -27,7 +31,7 @@ def test_learned_start_beats_the_random_start():
     V.load()
     net = V.vd_cnn_create(LI.N_FLOWS, seed=1)
     V.vd_cnn_set_params(net, np.load(WEIGHTS))
-    better, gains = 0, []
+    better, gains, after = 0, [], []
     try:
         for seed in range(LI.EVAL_SEED0, LI.EVAL_SEED0 + 6):
             w = LI._make(seed)
@@ -44,14 +48,25 @@ def test_learned_start_beats_the_random_start():
                 V.vd_bootstrap(ctx)
                 V.vd_get_inv_depth(ctx, rho)
                 e_plain = LI.depth_error(rho, ref, rigid)
+                truth = (np.linalg.norm(w.G[1][:, 3]) / w.depth0).astype(np.float32)
+                V.vd_run_em(ctx, LI.MAX_ITERS)
+                V.vd_get_inv_depth(ctx, rho)
+                t_plain = LI.depth_error(rho, truth, rigid)
                 V.vd_bootstrap_learned(ctx, net)
                 V.vd_get_inv_depth(ctx, rho)
                 e_learned = LI.depth_error(rho, ref, rigid)
+                V.vd_run_em(ctx, LI.MAX_ITERS)
+                V.vd_get_inv_depth(ctx, rho)
+                after.append((t_plain, LI.depth_error(rho, truth, rigid)))
             finally:
                 V.vd_destroy(ctx)
             better += e_learned < e_plain
             gains.append(1.0 - e_learned / e_plain)
     finally:
         V.vd_cnn_destroy(net)
+    after = np.array(after)
     print("bootstrap error reduction per window:", np.round(gains, 3))
+    print(f"error vs truth after {LI.MAX_ITERS} iterations, plain / learned:", np.round(after, 3))
     assert better >= 5 and np.mean(gains) > 0.05, (better, gains)
+    m_plain, m_learned = np.median(after[:, 0]), np.median(after[:, 1])
+    assert abs(m_learned - m_plain) <= 0.15 * m_plain, (m_plain, m_learned)
