@@ -5,15 +5,16 @@
 //
 // Convolutions are implicit GEMMs on the 5th-generation tensor cores:
 // D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = (ky * 3 + kx) * C_in + c_in.
-// Activations are stored channel-group planar, [C/8][H][W][8] bf16 (16
-// bytes per pixel and group).  A tile is R image rows of 128 consecutive
-// pixels.  No im2col matrix is built: one TMA box loads the tile's halo (R
-// + 2 rows of 130 pixels of every channel group, zero outside the image)
-// into [group][row][x][8 channels]; with 16 bytes per pixel and a stride of
-// 128 B between 8-pixel core matrices this is the canonical K-major layout
-// without swizzle, so tap (ky, kx) of output row r is the same tile with
-// its start address moved by ((r + ky) * 130 + kx) * 16 bytes (LBO = the
-// group stride).  The weights, stored pre-tiled in that layout (LBO = 128 B,
+// Activations are stored pixel-major, [H][W][C] bf16 with C = 16 or 32
+// channels (32 or 64 bytes per pixel).  A tile is R image rows of 128
+// consecutive pixels.  No im2col matrix is built: one TMA box loads the
+// tile's halo (R + 2 rows of 130 pixels, every channel, zero outside the
+// image) into [row][x][C] with the 32- or 64-byte swizzle, whose rows of
+// one pixel each are the K-major swizzled operand layout (8-row groups 8
+// pixels apart), so tap (ky, kx) of output row r is the same tile with its
+// start address moved by ((r + ky) * 130 + kx) pixels, and the second 16
+// input channels by 32 bytes.  Each box row is a whole pixel and each halo
+// row one contiguous run of 130 pixels in global memory.  The weights, stored pre-tiled in that layout (LBO = 128 B,
 // SBO = 16 K bytes), arrive by one bulk copy.  One thread issues
 // R * 9 * C_in / 16 tcgen05.mma (kind::f16, bf16 x bf16 -> f32) into R
 // tensor-memory accumulators of N columns and commits them to an mbarrier;
@@ -56,6 +57,25 @@ __device__ __forceinline__ uint64_t vd_umma_desc(uint32_t saddr, uint32_t lbo, u
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Shared-memory matrix descriptor of a K-major operand in a swizzled layout
+// (rows of `row_bytes` = 32 or 64 bytes, 16-byte chunks permuted by the
+// smem address bits above the row: the layout the tensor copy writes with
+// the same swizzle): SBO = 8 rows, LBO unused (one K step fits a row),
+// swizzle mode 6 (32 B) or 4 (64 B) in bits 61-63; the base-offset field
+// (bits 49-51) carries the start's phase in the pattern when VD_SW_PHASE.
+#ifndef VD_SW_PHASE
+#define VD_SW_PHASE 0
+#endif
+__device__ __forceinline__ uint64_t vd_umma_desc_sw(uint32_t saddr, uint32_t row_bytes) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                                   // LBO (unused)
+  d |= (uint64_t)(((8u * row_bytes) >> 4) & 0x3FFFu) << 32;  // SBO
+  d |= (uint64_t)1 << 46;
+  if (VD_SW_PHASE) d |= (uint64_t)((saddr >> 7) & 7u) << 49;
+  d |= (uint64_t)(row_bytes == 64 ? 4u : 6u) << 61;
   return d;
 }
 
@@ -140,6 +160,17 @@ __device__ __forceinline__ void vd_bulk_load(uint32_t dst, const void* src, uint
 // Tiled TMA load of one box of a rank-4 tensor map at (c0, c1, c2, c3); c0
 // (the innermost coordinate) must be a multiple of 16 bytes' worth of
 // elements.
+// Tiled TMA load of one box of a rank-3 tensor map at (c0, c1, c2); c0 (the
+// innermost coordinate) must be a multiple of 16 bytes' worth of elements.
+__device__ __forceinline__ void vd_tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0,
+                                               int c1, int c2, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(vd_smem_u32(m))
+      : "memory");
+}
+
 __device__ __forceinline__ void vd_tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0,
                                                int c1, int c2, int c3, uint64_t* m) {
   asm volatile(
@@ -193,13 +224,13 @@ __device__ __forceinline__ void vd_tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ---------------------------------------------------------------------------
-// The convolution GEMM.  X (through the tensor map `xmap`): bf16 planar
-// [C_in/8][H][W][8] with C_in = K / 9 channels (a multiple of 16), dims
-// {8, W, H, C_in/8}, box {8, 130, R + 2, C_in/8}.  Wt: the N x K weights
+// The convolution GEMM.  X (through the tensor map `xmap`): bf16 [H][W][C_in]
+// with C_in = K / 9 = 16 or 32 channels, dims {C_in, W, H}, box
+// {C_in, 130, R + 2}, swizzled.  Wt: the N x K weights
 // pre-tiled (vd_tile_index).  Epilogues:
-//   EPI_RELU  out = bf16 planar [N/8][HW][8]: relu(D + bias)
+//   EPI_RELU  out = bf16 [HW][N]: relu(D + bias)
 //   EPI_LAST  out = f32 [HW][16]: D + bias for the nout real channels, 0 after
-//   EPI_DGRAD out = bf16 planar [N/8][HW][8]: D where mask (planar) > 0, else 0
+//   EPI_DGRAD out = bf16 [HW][N]: D where mask ([HW][N]) > 0, else 0
 // ---------------------------------------------------------------------------
 enum { EPI_RELU = 0, EPI_LAST = 1, EPI_DGRAD = 2 };
 
@@ -211,21 +242,26 @@ __host__ __device__ constexpr size_t vd_tile_index(int n, int k, int K) {
 
 __host__ __device__ constexpr uint32_t vd_round128(uint32_t b) { return (b + 127u) & ~127u; }
 
+__host__ __device__ constexpr uint32_t vd_round1024(uint32_t b) { return (b + 1023u) & ~1023u; }
+
 template <int K, int N, int R, int NS>
 struct VdConvShape {
-  static constexpr int CIN = K / 9, G = CIN / 8;
+  static constexpr int CIN = K / 9;
+  static constexpr uint32_t PIX = (uint32_t)CIN * 2;        // bytes of one pixel (one A row)
   static constexpr uint32_t B_BYTES = (uint32_t)N * K * 2;
-  static constexpr uint32_t GS = (uint32_t)(R + 2) * CNN_HALO_X * 16;   // one channel group
-  static constexpr uint32_t STAGE = vd_round128(G * GS);   // one halo tile (one TMA box)
-  static constexpr uint32_t A_OFF = vd_round128(B_BYTES);
+  static constexpr uint32_t BOX = (uint32_t)(R + 2) * CNN_HALO_X * PIX;   // one halo tile
+  // stages start on 1024-byte boundaries (the swizzle pattern's phase is
+  // then that of the tile's first pixel)
+  static constexpr uint32_t STAGE = vd_round1024(BOX);
+  static constexpr uint32_t A_OFF = vd_round1024(B_BYTES);
   static constexpr uint32_t ACC = (uint32_t)R * N;          // columns of one accumulator
   // tensor-memory columns: two accumulators, as a power of two >= 32
   static constexpr uint32_t NCOLS = 2 * ACC <= 32 ? 32 : 2 * ACC <= 64 ? 64 : 2 * ACC <= 128 ? 128
                                   : 2 * ACC <= 256 ? 256 : 512;
-  // shared memory: weights, NS halo stages, 128 B of alignment slack, and
+  // shared memory: weights, NS halo stages, 1024 B of alignment slack, and
   // at least enough that no more CTAs share an SM than its 512 tensor-memory
   // columns hold (228 KB per SM, 1 KB reserved per CTA)
-  static constexpr uint32_t NEED = A_OFF + NS * STAGE + 128;
+  static constexpr uint32_t NEED = A_OFF + NS * STAGE + 1024;
   static constexpr uint32_t FLOOR = 233472u / (512u / NCOLS + 1u) - 1024u + 16u;
   static constexpr uint32_t SMEM = NEED > FLOOR ? NEED : FLOOR;
 };
@@ -297,7 +333,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
   __syncthreads();
   vd_tc_fence_after();
   const uint32_t dt = tmem_base;
-  const uint32_t sB = (vd_smem_u32(smem) + 127u) & ~127u, sA = sB + S::A_OFF;
+  const uint32_t sB = (vd_smem_u32(smem) + 1023u) & ~1023u, sA = sB + S::A_OFF;
   const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (warp == 4) {
     if (lane == 0) {   // producer
@@ -311,10 +347,10 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
         }
         const int tile = blockIdx.x + i * gridDim.x;
         const int x0 = (tile % tiles_x) * CNN_TILE, y0 = (tile / tiles_x) * R;
-        vd_mbar_expect_tx(&full[s], S::G * S::GS + (i == 0 ? S::B_BYTES : 0u));
+        vd_mbar_expect_tx(&full[s], S::BOX + (i == 0 ? S::B_BYTES : 0u));
         if (i == 0) vd_bulk_load(sB, Wt, S::B_BYTES, &full[0]);
-        // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128, every group
-        vd_tma_load_4d(sA + s * S::STAGE, &xmap, 0, x0 - 1, y0 - 1, 0, &full[s]);
+        // halo rows y0 - 1 .. y0 + R, pixels x0 - 1 .. x0 + 128, every channel
+        vd_tma_load_3d(sA + s * S::STAGE, &xmap, 0, x0 - 1, y0 - 1, &full[s]);
         issued = i + 1;
       }
       // the loads in flight land before the CTA ends
@@ -340,10 +376,10 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
 #pragma unroll
           for (int t = 0; t < 9; ++t)
 #pragma unroll
-            for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (two groups) per MMA
-              const uint32_t aa = a0 + 2 * j * S::GS + ((r + t / 3) * CNN_HALO_X + t % 3) * 16;
+            for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (32 bytes) per MMA
+              const uint32_t aa = a0 + ((r + t / 3) * CNN_HALO_X + t % 3) * S::PIX + 32 * j;
               const uint32_t bb = sB + ((t * CIN + 16 * j) >> 3) * 128;
-              vd_umma_bf16(d0 + r * N, vd_umma_desc(aa, S::GS, 128), vd_umma_desc(bb, 128, K * 16),
+              vd_umma_bf16(d0 + r * N, vd_umma_desc_sw(aa, S::PIX), vd_umma_desc(bb, 128, K * 16),
                            idesc, (t | j) ? 1u : 0u);
             }
         vd_umma_commit(&empty[s]);     // the stage is free once these MMAs are done
@@ -372,7 +408,6 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
       vd_tc_fence_after();
       const int tile = blockIdx.x + i * gridDim.x;
       const int x = (tile % tiles_x) * CNN_TILE + warp * 32 + lane, y0 = (tile / tiles_x) * R;
-      const size_t HW = (size_t)Wimg * Himg;
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
         const int y = y0 + r;
@@ -403,16 +438,15 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
 #pragma unroll
             for (int c = 0; c < N; c += 8)
               *reinterpret_cast<uint4*>(mk + c) =
-                  *reinterpret_cast<const uint4*>(mask + ((c >> 3) * HW + p) * 8);
+                  *reinterpret_cast<const uint4*>(mask + p * N + c);
 #pragma unroll
             for (int c = 0; c < N; ++c)
               o[c] = __float2bfloat16_rn(__bfloat162float(mk[c]) > 0.0f ? v[c] : 0.0f);
           }
           __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(out);
 #pragma unroll
-          for (int c = 0; c < N; c += 8)   // group c / 8 of pixel p
-            *reinterpret_cast<uint4*>(dst + ((c >> 3) * HW + p) * 8) =
-                *reinterpret_cast<const uint4*>(o + c);
+          for (int c = 0; c < N; c += 8)   // channels c .. c + 7 of pixel p
+            *reinterpret_cast<uint4*>(dst + p * N + c) = *reinterpret_cast<const uint4*>(o + c);
         }
       }
       vd_tc_fence_before();
@@ -426,7 +460,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
 }
 
 // ---------------------------------------------------------------------------
-// Input planes: flow [N][H][W][2] -> bf16 planar [C0/8][H][W][8].
+// Input planes: flow [N][H][W][2] -> bf16 [H][W][C0].
 // ---------------------------------------------------------------------------
 // Geometry planes 2N .. 2N+3 (zero without a pose): the flow that the
 // rotation of T_1 alone gives pixel (u, v), and the extra flow of a point at
@@ -456,7 +490,7 @@ __global__ void k_cnn_input(const float2* __restrict__ flow, int N, int Wimg, in
       geo[3] = (y1 - y0) * (1.0f / 32.0f);
     }
   }
-  for (int g = 0; g < C0 / 8; ++g) {   // planar: group g of pixel p, 16 bytes
+  for (int g = 0; g < C0 / 8; ++g) {   // channels 8 g .. 8 g + 7 of pixel p, 16 bytes
     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -470,13 +504,13 @@ __global__ void k_cnn_input(const float2* __restrict__ flow, int N, int Wimg, in
       }
       o[k] = __float2bfloat16_rn(v);
     }
-    *reinterpret_cast<uint4*>(a0 + ((size_t)g * HW + p) * 8) = *reinterpret_cast<uint4*>(o);
+    *reinterpret_cast<uint4*>(a0 + (size_t)p * C0 + 8 * g) = *reinterpret_cast<uint4*>(o);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Heads, loss and dL/dz of the last layer (z: f32 [HW][16], channel 0 the
-// inverse depth, 1..N the rigidness of each flow; dz: bf16 planar [2][HW][8]).
+// inverse depth, 1..N the rigidness of each flow; dz: bf16 [HW][16]).
 // Per-block partial sums of the loss.
 // ---------------------------------------------------------------------------
 __global__ void k_cnn_heads(const float* __restrict__ z, int HW, int N, float rho_min,
@@ -516,8 +550,8 @@ __global__ void k_cnn_loss(const float* __restrict__ z, int HW, int N,
       o[1 + t] = __float2bfloat16_rn(wq_n * m * (s - qt) * inv_n);
     }
     l = (double)(m * (r * r + wq_n * bce));
-    *reinterpret_cast<uint4*>(dz + (size_t)p * 8) = *reinterpret_cast<uint4*>(o);   // planar
-    *reinterpret_cast<uint4*>(dz + ((size_t)HW + p) * 8) = *reinterpret_cast<uint4*>(o + 8);
+    *reinterpret_cast<uint4*>(dz + (size_t)p * 16) = *reinterpret_cast<uint4*>(o);
+    *reinterpret_cast<uint4*>(dz + (size_t)p * 16 + 8) = *reinterpret_cast<uint4*>(o + 8);
   }
   s_l[threadIdx.x] = l;
   __syncthreads();
@@ -561,7 +595,7 @@ __global__ void k_cnn_sum(const double* __restrict__ partial, int n, const int* 
 // ---------------------------------------------------------------------------
 // Weight gradient on the CUDA cores: dW[co][tap * CIN + ci] =
 // sum_p dz[p][co] X[p + offset(tap)][ci], db[co] = sum_p dz[p][co].  dz: bf16
-// planar with (at least) COUT channels; X: bf16 planar with CIN channels.
+// [HW][COUT]; X: bf16 [HW][CIN].
 // The image is cut into tiles of WG_ROWS rows x WG_COLS pixels; block b
 // takes tiles b, b + gridDim.x, ... in order.  A block stages a tile's
 // input halo and dz in shared memory; thread (co8, ci) holds dW for 8
@@ -588,7 +622,6 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
   const int tid = threadIdx.x, ci = tid % CIN, co8 = tid / CIN;
   const int tiles_x = (Wimg + WG_COLS - 1) / WG_COLS;
   const int n_tiles = tiles_x * ((Himg + WG_ROWS - 1) / WG_ROWS);
-  const size_t HW = (size_t)Wimg * Himg;
   float acc[8][9];
 #pragma unroll
   for (int c = 0; c < 8; ++c)
@@ -603,7 +636,7 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
       const int yy = y0 - 1 + px / HC, xx = x0 - 1 + px % HC;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (yy >= 0 && yy < Himg && xx >= 0 && xx < Wimg)
-        v = *reinterpret_cast<const uint4*>(X + ((size_t)g * HW + (size_t)yy * Wimg + xx) * 8);
+        v = *reinterpret_cast<const uint4*>(X + ((size_t)yy * Wimg + xx) * CIN + 8 * g);
       *reinterpret_cast<uint4*>(sX + (size_t)px * CIN + 8 * g) = v;
     }
     for (int i = tid; i < WG_ROWS * WG_COLS * (COUT / 8); i += NT) {
@@ -611,7 +644,7 @@ k_cnn_wgrad(const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict
       const int yy = y0 + px / WG_COLS, xx = x0 + px % WG_COLS;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (yy < Himg && xx < Wimg)
-        v = *reinterpret_cast<const uint4*>(dz + ((size_t)g * HW + (size_t)yy * Wimg + xx) * 8);
+        v = *reinterpret_cast<const uint4*>(dz + ((size_t)yy * Wimg + xx) * COUT + 8 * g);
       *reinterpret_cast<uint4*>(sD + (size_t)px * COUT + 8 * g) = v;
     }
     __syncthreads();
@@ -808,21 +841,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 vd_encode_tiled() {
   return fn;
 }
 
-// Tensor map of a planar bf16 image with cin channels ([cin/8][H][W][8]):
-// dims {8, W, H, cin/8}, box {8, 130, rows + 2, cin/8}, zero fill outside
-// the image.
+// Tensor map of a bf16 image with cin = 16 or 32 channels per pixel
+// ([H][W][cin]): dims {cin, W, H}, box {cin, 130, rows + 2}, zero fill
+// outside the image, 32- or 64-byte swizzle (one pixel is one swizzle row,
+// the layout vd_umma_desc_sw reads).
 static cudaError_t vd_halo_map(CUtensorMap* m, const void* X, int cin, int W, int H, int rows) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = vd_encode_tiled();
   if (!enc) return cudaErrorNotSupported;
-  if ((reinterpret_cast<uintptr_t>(X) & 15u) || cin % 16) return cudaErrorInvalidValue;
-  const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(cin / 8)};
-  const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
-  const cuuint32_t box[4] = {8, CNN_HALO_X, (cuuint32_t)rows + 2, (cuuint32_t)(cin / 8)};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(X), dims,
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) || (cin != 16 && cin != 32))
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[2] = {(cuuint64_t)cin * 2, (cuuint64_t)W * cin * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)cin, CNN_HALO_X, (cuuint32_t)rows + 2};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X), dims,
                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         cin == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -1120,12 +1155,12 @@ extern "C" vd_status vd_cnn_get_activation(vd_cnn* n, int layer, float* out, int
     return VD_OK;
   }
   const int C = n->cin[layer];
-  std::vector<__nv_bfloat16> h(HW * C);   // planar [C/8][HW][8] on the device
+  std::vector<__nv_bfloat16> h(HW * C);   // [HW][C] on the device
   VD_CU(cudaMemcpy(h.data(), n->act[layer], sizeof(__nv_bfloat16) * h.size(),
                    cudaMemcpyDeviceToHost));
   for (size_t p = 0; p < HW; ++p)
     for (int c = 0; c < C; ++c)
-      out[p * C + c] = __bfloat162float(h[((c >> 3) * HW + p) * 8 + (c & 7)]);
+      out[p * C + c] = __bfloat162float(h[p * C + c]);
   return VD_OK;
 }
 
