@@ -488,22 +488,30 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
                  const float* __restrict__ q, const float* __restrict__ prior_val,
                  const float* __restrict__ qhat, const float* __restrict__ pconf,
                  const float* __restrict__ rho_star, const float* __restrict__ e_star,
-                 float* __restrict__ rho_new, int direction, int restart) {
+                 float* __restrict__ rho_new, int direction, int restart, int s) {
   __shared__ float sPose[12 * (VD_MAX_FLOWS + 1)];
   vd_load_pose_smem<NF>(sPose, posef);
   const bool rows = (direction & 1) == 0;
   const bool rev = direction >= 2;
-  const int nchains = rows ? P.H : P.W;
-  const int L = rows ? P.W : P.H;
+  // s > 0: the chains of the coarse grid of representative pixels
+  // (min(s uc, W - 1), min(s vc, H - 1)), written to the coarse map
+  // rho_new[vc][uc] (the hierarchical scheme's global pass)
+  const int Wc = s > 0 ? (P.W + s - 1) / s : P.W, Hc = s > 0 ? (P.H + s - 1) / s : P.H;
+  const int nchains = rows ? Hc : Wc;
+  const int L = rows ? Wc : Hc;
   const int ch = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (ch >= nchains) return;          // whole warps leave together
   const int seg = (L + 31) >> 5;
   const int m0 = min(L, lane * seg), m1 = min(L, m0 + seg);
-  auto pix = [&](int m, int* u, int* v) -> size_t {
+  // position m of the chain: pixel (u, v) and index j of the inputs, and the
+  // index of the output (j itself at full resolution)
+  auto pix = [&](int m, int* u, int* v, size_t* o) -> size_t {
     const int pos = rev ? L - 1 - m : m;
-    *u = rows ? pos : ch;
-    *v = rows ? ch : pos;
+    const int uc = rows ? pos : ch, vc = rows ? ch : pos;
+    *u = s > 0 ? min(uc * s, P.W - 1) : uc;
+    *v = s > 0 ? min(vc * s, P.H - 1) : vc;
+    *o = (size_t)vc * Wc + uc;
     return (size_t)VD_CHK(VD_SITE_CHAIN, (long long)(*v) * P.W + (*u), (long long)P.W * P.H);
   };
   // phase A; the next pixel's loads are issued before this pixel's energy
@@ -511,17 +519,17 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
   float cur = 0.0f;
   VdPixLoads<NF> Ln;
   int un = 0, vn = 0;
-  size_t jn = 0;
+  size_t jn = 0, on = 0;
   if (m0 < m1) {
-    jn = pix(m0, &un, &vn);
+    jn = pix(m0, &un, &vn, &on);
     vd_pix_load<NF>(Ln, P, flow, q, prior_val, qhat, pconf, rho_star, e_star, npix, jn);
   }
   for (int m = m0; m < m1; ++m) {
     const VdPixLoads<NF> L = Ln;
     const int u = un, v = vn;
-    const size_t j = jn;
+    const size_t o = on;
     if (m + 1 < m1) {
-      jn = pix(m + 1, &un, &vn);
+      jn = pix(m + 1, &un, &vn, &on);
       vd_pix_load<NF>(Ln, P, flow, q, prior_val, qhat, pconf, rho_star, e_star, npix, jn);
     }
     if (m == m0 || (restart > 0 && m % restart == 0)) {
@@ -532,7 +540,7 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
       const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur, L.e);
       cur = (Ec < L.e) ? cur : L.own;
     }
-    rho_new[j] = cur;
+    rho_new[o] = cur;
   }
   float end = cur;                     // value carried out of the segment
   bool have_in = false;                // phase A assumed no incoming value
@@ -550,18 +558,19 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
       bool merged = false;
       for (int m = m0; m < m1; ++m) {
         int u, v;
-        const size_t j = pix(m, &u, &v);
+        size_t o;
+        const size_t j = pix(m, &u, &v, &o);
         const float own = rho_star[j];
         float nc;
         if (restart > 0 && m % restart == 0)
           nc = own;
         else
           nc = vd_prop_step<NF>(P, sPose, flow, q, prior_val, qhat, pconf, c, own, e_star[j], u, v, j);
-        if (nc == rho_new[j]) {
+        if (nc == rho_new[o]) {
           merged = true;
           break;
         }
-        rho_new[j] = nc;
+        rho_new[o] = nc;
         c = nc;
       }
       if (!merged && c != end) {
@@ -570,45 +579,6 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
       }
     }
     if (!__any_sync(0xffffffffu, changed)) break;
-  }
-}
-
-// Hierarchical scheme, global pass: chains over the coarse grid of
-// representative pixels (min(s uc, W-1), min(s vc, H-1)).
-template <int NF>
-__global__ void k_hier_coarse(DevParams P, const float* __restrict__ posef,
-                              const float2* __restrict__ flow, const float* __restrict__ q,
-                              const float* __restrict__ prior_val, const float* __restrict__ qhat,
-                              const float* __restrict__ pconf, const float* __restrict__ rho_star,
-                              const float* __restrict__ e_star, float* __restrict__ coarse,
-                              int direction, int s) {
-  __shared__ float sPose[12 * (VD_MAX_FLOWS + 1)];
-  vd_load_pose_smem<NF>(sPose, posef);
-  const int Wc = (P.W + s - 1) / s, Hc = (P.H + s - 1) / s;
-  const bool rows = (direction & 1) == 0;
-  const bool rev = direction >= 2;
-  const int nchains = rows ? Hc : Wc;
-  const int L = rows ? Wc : Hc;
-  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ch >= nchains) return;
-  const size_t npix = (size_t)P.W * P.H;
-  float cur = 0.0f;
-  for (int m = 0; m < L; ++m) {
-    const int pos = rev ? L - 1 - m : m;
-    const int uc = rows ? pos : ch;
-    const int vc = rows ? ch : pos;
-    const int u = min(uc * s, P.W - 1), v = min(vc * s, P.H - 1);
-    const size_t j = (size_t)v * P.W + u;
-    const float own = rho_star[j];
-    if (m == 0) {
-      cur = own;
-    } else {
-      VdPixel<NF> px;
-      vd_pixel_setup<NF>(px, P, sPose, u, v, q, npix, j, flow, prior_val, qhat, pconf);
-      const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur);
-      if (!(Ec < e_star[j])) cur = own;
-    }
-    coarse[(size_t)vc * Wc + uc] = cur;
   }
 }
 
@@ -700,15 +670,16 @@ cudaError_t launch_depth_propagate(vd_ctx* c, int direction, int nf) {
     const int nch = rows ? c->H : c->W;
     VD_DISPATCH_NF(nf, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                               c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
-                              c->rho_star, c->e_star, c->rho, direction, 0)));
+                              c->rho_star, c->e_star, c->rho, direction, 0, 0)));
     return cudaGetLastError();
   }
   const int s = c->prm.hier_scale;
   const int Wc = (c->W + s - 1) / s, Hc = (c->H + s - 1) / s;
   const int nchc = rows ? Hc : Wc;
-  VD_DISPATCH_NF(nf, (k_hier_coarse<NF><<<(nchc + 63) / 64, 64, 0, c->stream>>>(
+  // global pass on the coarse grid: the same segmented exact chain walk
+  VD_DISPATCH_NF(nf, (k_propagate_warp<NF><<<(nchc + 3) / 4, 128, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
-                            c->rho_star, c->e_star, c->coarse, direction, s)));
+                            c->rho_star, c->e_star, c->coarse, direction, 0, s)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 blk(32, 4);
@@ -721,7 +692,7 @@ cudaError_t launch_depth_propagate(vd_ctx* c, int direction, int nf) {
   const int nch = rows ? c->H : c->W;
   VD_DISPATCH_NF(nf, (k_propagate_warp<NF><<<(nch + 3) / 4, 128, 0, c->stream>>>(
                             c->dp, c->posef, c->flow, c->q, c->prior_val, c->qhat, c->prior_conf,
-                            c->rho_mid, c->e_mid, c->rho, direction, c->prm.hier_window)));
+                            c->rho_mid, c->e_mid, c->rho, direction, c->prm.hier_window, 0)));
   return cudaGetLastError();
 }
 
