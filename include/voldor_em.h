@@ -222,10 +222,10 @@ vd_status vd_get_profile(vd_ctx* ctx, vd_profile* out);
  *   - m must be in 1..VD_NOALLOC_MAX_POSES, else VD_ERR_ARG (see vd_last_error);
  *     n = 0 gives zero energies.
  *   - The first call on a device (with that device current) looks up the
- *     array's device address and the device's SM count; make that first call
- *     before any stream capture.  The address is kept for the life of the
- *     process: after a cudaDeviceReset of that device it is stale, and the
- *     call must not be used again in that process.
+ *     array's device address and the device's SM count with host-side CUDA
+ *     queries.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset of that device it is stale, and the call must not be
+ *     used again in that process.
  *   - All calls share the one array: calls that may overlap on the GPU (other
  *     streams, other host threads) race and must be serialised by the caller.
  *     Every scratch value a call reads is written earlier in the same call.

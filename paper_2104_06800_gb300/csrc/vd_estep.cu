@@ -226,19 +226,132 @@ k_forward_backward_warp(DevParams P, const float* __restrict__ lam, float* __res
   }
 }
 
+// The same forward-backward with the chains staged in shared memory: a
+// block takes blockDim.x / 32 adjacent chains of one flow (one warp each),
+// loads their ratios with coalesced reads (consecutive threads read
+// consecutive pixels of a row chain, or adjacent column chains at one row),
+// runs the segment scan and both walks on shared memory, and writes the
+// posteriors back the same way.  Lane k's segment sits at k * segp in its
+// chain's slot array (segp = seg rounded up to odd: the 32 lanes' walks hit
+// distinct banks; chains one float apart likewise).  The arithmetic is that
+// of k_forward_backward_warp, in the same order.
+__global__ void __launch_bounds__(256)
+k_forward_backward_staged(DevParams P, const float* __restrict__ lam, float* __restrict__ q,
+                          int direction) {
+  extern __shared__ float fb_sm[];
+  const bool rows = (direction & 1) == 0;
+  const int nchains = rows ? P.H : P.W;
+  const int L = rows ? P.W : P.H;
+  const int CB = blockDim.x >> 5;
+  const int t = blockIdx.y;
+  const int ch0 = blockIdx.x * CB;
+  const int seg = (L + 31) >> 5, segp = seg | 1;
+  const int CS = 32 * segp + 1;                   // one chain's slots
+  float* sl = fb_sm;                              // [CB][CS] ratios
+  float* sq = fb_sm + CB * CS;                    // [CB][CS] posteriors
+  const size_t npix = (size_t)P.W * P.H;
+  const float* lt = lam + (size_t)t * npix;
+  float* qt = q + (size_t)t * npix;
+  const int total = CB * L;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = rows ? idx / L : idx % CB, m = rows ? idx - c * L : idx / CB;
+    const int ch = ch0 + c;
+    if (ch < nchains)
+      sl[c * CS + (m / seg) * segp + m % seg] =
+          lt[rows ? (size_t)ch * P.W + m : (size_t)m * P.W + ch];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ch0 + w < nchains) {
+    const float* l_ = sl + w * CS;
+    float* q_ = sq + w * CS;
+    const float g = P.gamma, h = 1.0f - P.gamma;
+    const int a0 = min(L, lane * seg), b0 = min(L, a0 + seg);
+    const int first = max(a0, 1);                 // position 0 carries no matrix
+    const int o = lane * segp - a0;               // slot of position m: o + m
+    VdM2 S = {1.0f, 0.0f, 0.0f, 1.0f};
+    for (int m = first; m < b0; ++m) {
+      const float l = l_[o + m];
+      const VdM2 M = {g, h * l, h, g * l};
+      S = vd_m2_mul(S, M);
+    }
+    VdM2 X = S, Z = S;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const VdM2 Y = vd_m2_shfl_up(X, off);
+      if (lane >= off) X = vd_m2_mul(Y, X);
+      const VdM2 Yd = vd_m2_shfl_down(Z, off);
+      if (lane + off < 32) Z = vd_m2_mul(Z, Yd);
+    }
+    VdM2 Pin = vd_m2_shfl_up(X, 1);
+    VdM2 Qout = vd_m2_shfl_down(Z, 1);
+    if (lane == 0) Pin = {1.0f, 0.0f, 0.0f, 1.0f};
+    if (lane == 31) Qout = {1.0f, 0.0f, 0.0f, 1.0f};
+    if (a0 < b0) {
+      const float l0 = l_[0];
+      float f0 = fmaf(1.0f, Pin.a, l0 * Pin.c), f1 = fmaf(1.0f, Pin.b, l0 * Pin.d);
+      if (a0 == 0) {
+        const float s = 1.0f / (f0 + f1);
+        f0 *= s;
+        f1 *= s;
+        q_[0] = f1;
+      }
+      for (int m = first; m < b0; ++m) {
+        const float l = l_[o + m];
+        const float n0 = fmaf(f0, g, f1 * h);
+        const float n1 = fmaf(f0, h, f1 * g) * l;
+        const float s = 1.0f / (n0 + n1);
+        f0 = n0 * s;
+        f1 = n1 * s;
+        q_[o + m] = f1;
+      }
+      float b0v = Qout.a + Qout.b, b1v = Qout.c + Qout.d;
+      {
+        const float s = 1.0f / (b0v + b1v);
+        b0v *= s;
+        b1v *= s;
+      }
+      for (int m = b0 - 1; m >= a0; --m) {
+        if (m < b0 - 1) {
+          const float l = l_[o + m + 1];
+          const float y1 = b1v * l;
+          const float n0 = fmaf(g, b0v, h * y1);
+          const float n1 = fmaf(h, b0v, g * y1);
+          const float s = 1.0f / (n0 + n1);
+          b0v = n0 * s;
+          b1v = n1 * s;
+        }
+        const float am = q_[o + m];
+        const float num = am * b1v;
+        q_[o + m] = num / (num + (1.0f - am) * b0v);
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = rows ? idx / L : idx % CB, m = rows ? idx - c * L : idx / CB;
+    const int ch = ch0 + c;
+    if (ch < nchains)
+      qt[rows ? (size_t)ch * P.W + m : (size_t)m * P.W + ch] =
+          sq[c * CS + (m / seg) * segp + m % seg];
+  }
+}
+
 // Eq. 6: C = (sum_t q_t + q_hat) / (N + 1) with a prior, sum_t q_t / N without.
 __global__ void k_confidence(DevParams P, const float* __restrict__ q,
                              const float* __restrict__ qhat, float* __restrict__ conf) {
   const size_t npix = (size_t)P.W * P.H;
   const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= npix) return;
-  double s = 0.0;
-  for (int t = 0; t < P.N; ++t) s += (double)q[(size_t)t * npix + j];
+  // float32 sum in flow order (at most 9 terms in [0, 1]: error below 1e-6;
+  // a float64 sum costs this part's float64 pipe more than the rest)
+  float s = 0.0f;
+  for (int t = 0; t < P.N; ++t) s += q[(size_t)t * npix + j];
   if (P.prior_kind != VD_PRIOR_NONE) {
-    s += (double)qhat[j];
-    conf[j] = (float)(s / (P.N + 1));
+    s += qhat[j];
+    conf[j] = s / (float)(P.N + 1);
   } else {
-    conf[j] = (float)(s / P.N);
+    conf[j] = s / (float)P.N;
   }
 }
 
@@ -250,8 +363,21 @@ cudaError_t launch_estep(vd_ctx* c, int direction) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool rows = (direction & 1) == 0;
-  const int nwarps = (rows ? c->H : c->W) * c->N;
-  k_forward_backward_warp<<<(nwarps + 3) / 4, 128, 0, c->stream>>>(c->dp, c->lam, c->q, direction);
+  const int nch = rows ? c->H : c->W, L = rows ? c->W : c->H;
+  // chains per block of the staged kernel: 4 rows or 8 columns, fewer where
+  // their slots would pass 48 KB; chains too long for one: the unstaged one
+  const int seg = (L + 31) >> 5, segp = seg | 1;
+  const size_t per_chain = 2 * sizeof(float) * (size_t)(32 * segp + 1);
+  int cb = rows ? 4 : 8;
+  while (cb > 1 && cb * per_chain > 48 * 1024) cb >>= 1;
+  if (cb * per_chain <= 48 * 1024) {
+    k_forward_backward_staged<<<dim3((nch + cb - 1) / cb, c->N), 32 * cb, cb * per_chain,
+                                c->stream>>>(c->dp, c->lam, c->q, direction);
+  } else {
+    const int nwarps = nch * c->N;
+    k_forward_backward_warp<<<(nwarps + 3) / 4, 128, 0, c->stream>>>(c->dp, c->lam, c->q,
+                                                                      direction);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_confidence<<<(unsigned)((c->npix + 255) / 256), 256, 0, c->stream>>>(c->dp, c->q, c->qhat,
