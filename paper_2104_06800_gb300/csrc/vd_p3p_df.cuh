@@ -213,7 +213,10 @@ VD_HD VD_DF_CALL void vd_p3p_df_resultant(const VdP3Pdf& g, vd_df v, vd_df* r, v
 // precision, from the float32 estimate x0 + m: Newton steps on the factored
 // resultant inside a double-float bracket, a bisection step where Newton
 // leaves it or gains less than a halving (clustered roots converge
-// linearly); stops at a 2^-44 relative step or bracket, at most 80 steps.
+// linearly); stops at a 2^-44 relative step or bracket, or once the Newton
+// steps, below 2^-34 relative, stop halving (the resultant's double-float
+// rounding noise: on an ill-conditioned instance the steps never reach
+// 2^-44 and the bracket would otherwise be bisected down), at most 80 steps.
 VD_HD VD_DF_CALL vd_df vd_p3p_df_polish(const VdP3Pdf& g, vd_df m, float x0, float lo_f,
                                              float hi_f) {
   vd_df lo = vd_df_add(vd_df_make(lo_f), m), hi = vd_df_add(vd_df_make(hi_f), m);
@@ -232,7 +235,9 @@ VD_HD VD_DF_CALL vd_df vd_p3p_df_polish(const VdP3Pdf& g, vd_df m, float x0, flo
     bool newton = dr.hi != 0.0f;
     if (newton) {
       stp = vd_df_div(r, dr);
-      if (fabsf(stp.hi) <= tol) return vd_df_sub(x, stp);
+      if (fabsf(stp.hi) <= tol ||
+          (fabsf(stp.hi) <= 1024.0f * tol && fabsf(stp.hi) >= 0.5f * last))
+        return vd_df_sub(x, stp);
       xn = vd_df_sub(x, stp);
       newton = vd_df_gt0(vd_df_sub(xn, lo)) && vd_df_gt0(vd_df_sub(hi, xn)) &&
                fabsf(stp.hi) < 0.5f * last;
