@@ -460,8 +460,11 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
 // lane L holding the warp's sum of root 32 g + L.  Warp sums are added in
 // fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
+#ifndef VD_SCORE_PPT
+#define VD_SCORE_PPT 4
+#endif
 #undef SCORE_PPT
-#define SCORE_PPT 4
+#define SCORE_PPT VD_SCORE_PPT
 
 // One pixel's term under one root in log2 units (the caller scales by ln 2),
 // without branches.  FAST: beta = 2 and alpha1 = 0 (closed form; obs.z
