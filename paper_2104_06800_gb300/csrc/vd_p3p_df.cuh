@@ -331,8 +331,10 @@ VD_HD VD_DF_CALL void vd_df_triad(const vd_df* p, vd_df* F) {
 }
 
 // Pose (world -> camera, 3x4 row-major) of the root v; false if v gives no
-// valid triangle (v <= 0, u <= 0 or a vanishing distance).
-VD_HD VD_DF_CALL bool vd_p3p_df_pose(const VdP3Pdf& g, const vd_df* X, vd_df v, vd_df* T) {
+// valid triangle (v <= 0, u <= 0 or a vanishing distance).  Fp: the triad
+// of the world points X (vd_df_triad), the same for every root.
+VD_HD VD_DF_CALL bool vd_p3p_df_pose(const VdP3Pdf& g, const vd_df* X, const vd_df* Fp, vd_df v,
+                                      vd_df* T) {
   if (!vd_df_gt0(v)) return false;
   const vd_df one = vd_df_make(1.0f);
   const vd_df v2 = vd_df_mul(v, v);
@@ -356,8 +358,7 @@ VD_HD VD_DF_CALL bool vd_p3p_df_pose(const VdP3Pdf& g, const vd_df* X, vd_df v, 
     Q[3 + i] = vd_df_mul(s2, g.f[3 + i]);
     Q[6 + i] = vd_df_mul(s3, g.f[6 + i]);
   }
-  vd_df Fp[9], Fq[9];
-  vd_df_triad(X, Fp);
+  vd_df Fq[9];
   vd_df_triad(Q, Fq);
   for (int i = 0; i < 3; ++i)
     for (int k = 0; k < 3; ++k)
@@ -383,9 +384,11 @@ VD_HD __forceinline__ int vd_p3p_df_solve(const double* fin, const double* Xin, 
   VdP3Pdf g;
   if (!vd_p3p_df_quartic(f, X, &g, res)) return 0;
   const int nr = vd_p3p_df_roots(g, res, v);
+  vd_df Fp[9];
+  vd_df_triad(X, Fp);
   int ns = 0;
   for (int r = 0; r < nr; ++r)
-    if (vd_p3p_df_pose(g, X, v[r], T)) {
+    if (vd_p3p_df_pose(g, X, Fp, v[r], T)) {
       for (int i = 0; i < 12; ++i) poses[12 * ns + i] = vd_df_to(T[i]);
       ++ns;
     }

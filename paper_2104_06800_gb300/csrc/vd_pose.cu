@@ -396,10 +396,14 @@ k_p3p_samples(DevParams P, const double* __restrict__ G, const float2* __restric
     }
   VdP3Pdf geo;
   vd_df res[5], v[4];
+  // the world points' triad (independent of the roots: its latency overlaps
+  // the quartic's)
+  vd_df Fp[9];
+  vd_df_triad(X, Fp);
   const int nr = vd_p3p_df_quartic(f, X, &geo, res) ? vd_p3p_df_roots_warp(geo, res, v, lane) : 0;
   vd_df T[12];
   bool valid = false;
-  if (lane < 4 && lane < nr) valid = vd_p3p_df_pose(geo, X, v[lane], T);
+  if (lane < 4 && lane < nr) valid = vd_p3p_df_pose(geo, X, Fp, v[lane], T);
   float key[6] = {0, 0, 0, 0, 0, 0};
   if (valid) {
     // ordering key: rotation vector (float32 is plenty to order distinct
