@@ -564,17 +564,38 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
   int* sList = (int*)(sAcc + nwarp * 32);    // the real roots, in index order
   int* sNum = sList + M;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n = n_ptr ? *n_ptr : n_host;     // issued early: its latency overlaps the prologue
   if (wid == 0) {
-    // compact the roots that exist (slot r & 3 below its sample's root count)
-    int cnt = 0;
-    for (int base = 0; base < M; base += 32) {
-      const int r = base + lane;
-      const bool ok = r < M && (!root_count || (r & 3) < root_count[r >> 2]);
-      const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (ok) sList[cnt + __popc(m & ((1u << lane) - 1u))] = r;
-      cnt += __popc(m);
+    // compact the roots that exist (slot r & 3 below its sample's root
+    // count), in index order: every sample's count loaded at once, then a
+    // warp prefix sum per 32 samples
+    if (!root_count) {
+      for (int r = lane; r < M; r += 32) sList[r] = r;
+      if (lane == 0) *sNum = M;
+    } else {
+      const int S = M >> 2;
+      int c[VD_MAX_SAMPLES / 32];
+#pragma unroll
+      for (int k = 0; k < VD_MAX_SAMPLES / 32; ++k) {
+        const int g = 32 * k + lane;
+        c[k] = g < S ? root_count[g] : 0;
+      }
+      int base = 0;
+#pragma unroll
+      for (int k = 0; k < VD_MAX_SAMPLES / 32; ++k) {
+        if (32 * k >= S) break;                 // warp-uniform
+        int pre = c[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int up = __shfl_up_sync(0xffffffffu, pre, o);
+          if (lane >= o) pre += up;
+        }
+        const int g = 32 * k + lane;
+        for (int i = 0; i < c[k]; ++i) sList[base + pre - c[k] + i] = 4 * g + i;
+        base += __shfl_sync(0xffffffffu, pre, 31);
+      }
+      if (lane == 0) *sNum = base;
     }
-    if (lane == 0) *sNum = cnt;
   }
   for (int i = threadIdx.x; i < nwarp * 32; i += THREADS) sAcc[i] = 0.0f;
   __syncthreads();
@@ -585,7 +606,6 @@ k_pose_score(DevParams P, const float4* __restrict__ rpts, const float4* __restr
   for (int i = threadIdx.x; i < 12 * ng; i += THREADS)
     sRoot[i] = rootsf[12 * sList[g0 + i / 12] + i % 12];
   __syncthreads();
-  const int n = n_ptr ? *n_ptr : n_host;
   // contiguous pixel-block ranges of whole passes; passes go to the warps in turn
   const int per = ((n + gridDim.x - 1) / gridDim.x + PASS - 1) / PASS * PASS;
   const int beg = min(n, blockIdx.x * per);
