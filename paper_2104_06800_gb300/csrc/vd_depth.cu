@@ -478,7 +478,7 @@ __device__ __forceinline__ float vd_prop_step(const DevParams& P, const float* s
   const size_t npix = (size_t)P.W * P.H;
   VdPixel<NF> px;
   vd_pixel_setup<NF>(px, P, sPose, u, v, q, npix, j, flow, prior_val, qhat, pconf);
-  const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur, e_own);
+  const float Ec = vd_energy_full<NF>(px, P, sPose, flow, npix, cur);
   return (Ec < e_own) ? cur : own;
 }
 
@@ -537,7 +537,9 @@ k_propagate_warp(DevParams P, const float* __restrict__ posef, const float2* __r
     } else {
       VdPixel<NF> px;
       vd_pixel_from_loads<NF>(px, P, sPose, u, v, L);
-      const float Ec = vd_energy<NF>(px, P, sPose, flow, npix, cur, L.e);
+      // every gathered flow's taps in flight at once: the walk is a chain of
+      // dependent energies, so their latency, not their work, sets its pace
+      const float Ec = vd_energy_full<NF>(px, P, sPose, flow, npix, cur);
       cur = (Ec < L.e) ? cur : L.own;
     }
     rho_new[o] = cur;

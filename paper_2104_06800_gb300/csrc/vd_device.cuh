@@ -275,6 +275,58 @@ __device__ __forceinline__ float vd_flow_term(const DevParams& P, float hx, floa
   return l2;
 }
 
+// E_j(c) in full, for latency-bound callers (the chain propagation): every
+// frame's projection first, then every gathered flow's taps (all loads in
+// flight together), then the terms in the order and arithmetic of
+// vd_energy, so the value is vd_energy's without a bound.  A caller that
+// compares the result with a bound gets vd_energy's decision (an early
+// exit there returns a partial sum already at or above it).
+template <int NF>
+__device__ __forceinline__ float vd_energy_full(const VdPixel<NF>& px, const DevParams& P,
+                                                const float* __restrict__ sPose,
+                                                const float2* __restrict__ flow, size_t npix,
+                                                float c) {
+  float xs[NF], ys[NF];
+  bool fr[NF];
+#pragma unroll
+  for (int t = 0; t < NF; ++t) {   // projection into frame t + 1 (as vd_flow_term forms it)
+    const float* M = sPose + 12 * (t + 1);
+    const float hx = fmaf(c, M[9], px.ax[t]);
+    const float hy = fmaf(c, M[10], px.ay[t]);
+    const float hz = fmaf(c, M[11], px.az[t]);
+    fr[t] = hz > VD_Z_EPS;
+    const float iz = __fdividef(1.0f, hz);
+    xs[t] = hx * iz;
+    ys[t] = hy * iz;
+  }
+  float2 F[NF];
+  bool ob[NF];
+  F[0] = make_float2(px.f1x, px.f1y);
+  ob[0] = true;
+#pragma unroll
+  for (int t = 1; t < NF; ++t) {   // flow t read at the pixel's position in frame t
+    ob[t] = fr[t - 1] && vd_inside(xs[t - 1], ys[t - 1], P.W, P.H);
+    F[t] = make_float2(0.0f, 0.0f);
+    if (ob[t]) F[t] = vd_bilinear(flow + (size_t)t * npix, P.W, P.H, xs[t - 1], ys[t - 1]);
+  }
+  float E = vd_prior_energy<NF>(px, P, c);
+#pragma unroll
+  for (int t = 0; t < NF; ++t) {
+    const float xp = t == 0 ? px.u : xs[t - 1], yp = t == 0 ? px.v : ys[t - 1];
+    float l2;
+    if (ob[t] && fr[t]) {
+      const float dx = F[t].x - (xs[t] - xp);
+      const float dy = F[t].y - (ys[t] - yp);
+      const float r2 = fmaf(dx, dx, dy * dy);
+      l2 = vd_l2_flow(P, r2, fmaf(F[t].x, F[t].x, F[t].y * F[t].y));
+    } else {
+      l2 = ob[t] ? (VD_L_BEHIND / VD_LN2) : 0.0f;
+    }
+    E = fmaf(px.wl[t], l2, E);
+  }
+  return E;
+}
+
 // E_j(c): sum_t q_t l_t(c) + w_hat l_hat(c) in natural-log units.
 // Every term is non-negative, so once the partial sum reaches `bound` the
 // candidate cannot beat an energy of `bound`: the sum stops there and the
