@@ -811,30 +811,52 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   const long long INF_BITS = __double_as_longlong(INFINITY);
   long long bestE = INF_BITS;
   int bestS = 0x7fffffff;
-  for (int g = lane; g < P.S; g += 32) {
-    // the sample's lowest-energy root (ties: lower index in the sorted order)
-    const int nr = root_count[g];
-    int best = -1;
-    long long Eg = INF_BITS;
-    for (int r = 0; r < nr; ++r) {
-      const long long e = __double_as_longlong(root_energy[4 * g + r]);
-      if (best < 0 || e < Eg) {
-        Eg = e;
-        best = r;
+  // two samples per lane at a time (g and g + 32), their loads in flight
+  // together: the counts and all four energy slots (a slot without a root
+  // holds +inf), then the kept roots
+  for (int g0 = lane; g0 < P.S; g0 += 64) {
+    int nr[2];
+    long long e[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = g0 + 32 * h;
+      nr[h] = g < P.S ? root_count[g] : 0;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        e[h][r] = g < P.S ? __double_as_longlong(root_energy[4 * g + r]) : INF_BITS;
+    }
+    int best[2];
+    long long Eg[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // the sample's lowest-energy root (ties: lower index in the sorted order)
+      best[h] = -1;
+      Eg[h] = INF_BITS;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (r < nr[h] && (best[h] < 0 || e[h][r] < Eg[h])) {
+          Eg[h] = e[h][r];
+          best[h] = r;
+        }
+      if (best[h] < 0) Eg[h] = INF_BITS;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = g0 + 32 * h;
+      if (g >= P.S) continue;
+      const double* src = roots + (size_t)48 * g + 12 * (best[h] < 0 ? 0 : best[h]);
+      const float* srf = roots_r + (size_t)48 * g + 12 * (best[h] < 0 ? 0 : best[h]);
+#pragma unroll
+      for (int i = 0; i < 12; ++i) {
+        sample_pose[12 * g + i] = best[h] >= 0 ? src[i] : 0.0;
+        sT[g][i] = best[h] >= 0 ? srf[i] : 0.0f;
       }
-    }
-    const double* src = roots + (size_t)48 * g + 12 * (best < 0 ? 0 : best);
-    const float* srf = roots_r + (size_t)48 * g + 12 * (best < 0 ? 0 : best);
-    for (int i = 0; i < 12; ++i) {
-      sample_pose[12 * g + i] = best >= 0 ? src[i] : 0.0;
-      sT[g][i] = best >= 0 ? srf[i] : 0.0f;
-    }
-    if (best < 0) Eg = INF_BITS;
-    sample_energy[g] = __longlong_as_double(Eg);
-    sValid[g] = Eg < INF_BITS;
-    if (Eg < bestE) {           // g ascends per lane: ties keep the lower index
-      bestE = Eg;
-      bestS = g;
+      sample_energy[g] = __longlong_as_double(Eg[h]);
+      sValid[g] = Eg[h] < INF_BITS;
+      if (Eg[h] < bestE) {      // g ascends per lane: ties keep the lower index
+        bestE = Eg[h];
+        bestS = g;
+      }
     }
   }
   // argmin over samples (lowest energy, then lowest index): a total order, so
