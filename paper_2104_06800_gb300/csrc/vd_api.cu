@@ -233,7 +233,7 @@ extern "C" vd_status vd_destroy(vd_ctx* c) {
     return VD_ERR_STATE;
   }
   void* ptrs[] = {c->flow, c->prior_val, c->prior_rho, c->prior_conf, c->rho, c->q, c->qhat,
-                  c->conf, c->G, c->G_init, c->posef, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
+                  c->conf, c->G, c->G_init, c->posef, c->posed, c->rho_star, c->e_star, c->rho_mid, c->e_mid,
                   c->coarse, c->lam, c->flags, c->blk_counts, c->n_rigid,
                   c->rigid_idx, c->rpts, c->robs, c->roots, c->root_count, c->rootsf, c->rootsr, c->partial,
                   c->root_energy, c->score_work, c->sample_pose, c->sample_energy, c->degenerate, c->ep_partial,
@@ -302,6 +302,7 @@ extern "C" vd_status vd_create(const vd_window_desc* desc, const vd_params* para
   A(G, 12 * (N + 1));
   A(G_init, 12 * (N + 1));
   A(posef, 12 * (N + 1));
+  A(posed, 12 * (N + 1));
   A(rho_star, np);
   A(e_star, np);
   A(rho_mid, np);

@@ -368,7 +368,7 @@ k_ep_cheirality(DevParams P, const float2* __restrict__ flow, const double* __re
 // and constant-velocity guesses G_t = G_1 o G_{t-1}.
 __global__ void k_ep_finalize(DevParams P, const double* __restrict__ cand,
                               const int* __restrict__ counts, double* __restrict__ G,
-                              float* __restrict__ posef) {
+                              float* __restrict__ posef, float2* __restrict__ posed) {
   if (threadIdx.x != 0) return;
   int best = 0;
   for (int k = 1; k < 4; ++k)
@@ -392,10 +392,11 @@ __global__ void k_ep_finalize(DevParams P, const double* __restrict__ cand,
   for (int t = 0; t <= P.N; ++t) {
     const double* g = G + 12 * t;
     float* o = posef + 12 * t;
+    float2* od = posed + 12 * t;
     for (int i = 0; i < 4; ++i) {
-      o[i < 3 ? i : 9] = (float)(P.fx_d * g[i] + P.cx_d * g[8 + i]);
-      o[i < 3 ? 3 + i : 10] = (float)(P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
-      o[i < 3 ? 6 + i : 11] = (float)g[8 + i];
+      vd_store_pose_entry(o, od, i < 3 ? i : 9, P.fx_d * g[i] + P.cx_d * g[8 + i]);
+      vd_store_pose_entry(o, od, i < 3 ? 3 + i : 10, P.fy_d * g[4 + i] + P.cy_d * g[8 + i]);
+      vd_store_pose_entry(o, od, i < 3 ? 6 + i : 11, g[8 + i]);
     }
   }
 }
@@ -409,7 +410,8 @@ cudaError_t launch_eight_point(vd_ctx* c) {
   k_ep_decompose<<<1, 32, 0, c->stream>>>(c->ep_E, c->ep_cand, c->ep_count);
   k_ep_cheirality<<<c->ep_blocks, EP_THREADS, 0, c->stream>>>(c->dp, c->flow, c->ep_cand,
                                                               c->ep_count);
-  k_ep_finalize<<<1, 32, 0, c->stream>>>(c->dp, c->ep_cand, c->ep_count, c->G, c->posef);
+  k_ep_finalize<<<1, 32, 0, c->stream>>>(c->dp, c->ep_cand, c->ep_count, c->G, c->posef,
+                                      c->posed);
   return cudaGetLastError();
 }
 

@@ -33,24 +33,26 @@
 // ---------------------------------------------------------------------------
 // float K R | K tau of every frame from the float64 absolute poses.
 // ---------------------------------------------------------------------------
-__global__ void k_posef(DevParams P, const double* __restrict__ G, float* __restrict__ posef) {
+__global__ void k_posef(DevParams P, const double* __restrict__ G, float* __restrict__ posef,
+                        float2* __restrict__ posed) {
   const int t = threadIdx.x;
   if (t > P.N) return;
   const double* g = G + 12 * t;
   float* o = posef + 12 * t;
+  float2* od = posed + 12 * t;
   for (int r = 0; r < 3; ++r) {
     const double k0 = r == 0 ? P.fx_d : (r == 1 ? 0.0 : 0.0);
     const double k1 = r == 1 ? P.fy_d : 0.0;
     const double k2 = r == 0 ? P.cx_d : (r == 1 ? P.cy_d : 1.0);
     // row r of K [R | tau] = k0 * row0 + k1 * row1 + k2 * row2
     for (int c = 0; c < 3; ++c)
-      o[3 * r + c] = (float)(k0 * g[c] + k1 * g[4 + c] + k2 * g[8 + c]);
-    o[9 + r] = (float)(k0 * g[3] + k1 * g[7] + k2 * g[11]);
+      vd_store_pose_entry(o, od, 3 * r + c, k0 * g[c] + k1 * g[4 + c] + k2 * g[8 + c]);
+    vd_store_pose_entry(o, od, 9 + r, k0 * g[3] + k1 * g[7] + k2 * g[11]);
   }
 }
 
 cudaError_t launch_posef(vd_ctx* c) {
-  k_posef<<<1, 32, 0, c->stream>>>(c->dp, c->G, c->posef);
+  k_posef<<<1, 32, 0, c->stream>>>(c->dp, c->G, c->posef, c->posed);
   return cudaGetLastError();
 }
 

@@ -163,6 +163,19 @@ __device__ __forceinline__ float vd_l2_flow(const DevParams& P, float r2, float 
 }
 
 // ---------------------------------------------------------------------------
+// Entry i of a frame's rows K [R | tau] from its float64 value: float32 for
+// the depth and pose kernels, and as a double-float pair (hi, lo; hi + lo is
+// the float64 value to 48 bits) for the rigidness emissions.  Every writer
+// of the pose rows stores both.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void vd_store_pose_entry(float* __restrict__ pf, float2* __restrict__ pd,
+                                                    int i, double v) {
+  const float hi = (float)v;
+  pf[i] = hi;
+  pd[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
+// ---------------------------------------------------------------------------
 // Bilinear sample of one flow field at (x, y), which must be inside the image.
 // Taps (x0, y0)..(x0+1, y0+1) with x0 = min(floor(x), W-2).
 // ---------------------------------------------------------------------------

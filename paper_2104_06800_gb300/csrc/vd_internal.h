@@ -77,6 +77,7 @@ struct vd_ctx {
   double* G;               // [N+1][12] absolute poses
   double* G_init;          // [N+1][12] poses every bootstrap starts from (identity or vd_set_poses)
   float* posef;            // [N+1][12] float K R | K tau
+  float2* posed;           // [N+1][12] the same rows as double-float (hi, lo)
   int bootstrapped;
   int poses_set;
   int iter;                // next EM iteration index

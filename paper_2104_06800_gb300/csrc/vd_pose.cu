@@ -798,6 +798,7 @@ __global__ void __launch_bounds__(32)
 k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __restrict__ root_count,
                    const float* __restrict__ roots_r, const double* __restrict__ root_energy,
                    int t, double* __restrict__ G, float* __restrict__ posef,
+                   float2* __restrict__ posed,
                    double* __restrict__ sample_pose, double* __restrict__ sample_energy,
                    int* __restrict__ degenerate) {
   // one warp; lane l owns samples l, l + 32, ...
@@ -1059,12 +1060,14 @@ k_select_meanshift(DevParams P, const double* __restrict__ roots, const int* __r
   }
   if (lane < 12) {
     G[12 * t + lane] = o[lane];
-    // float K R | K tau of the updated pose: row lane / 4, column lane % 4
+    // K R | K tau of the updated pose: row lane / 4, column lane % 4
     const int i = lane & 3, row = lane >> 2;
     float* pf = posef + 12 * t;
-    if (row == 0) pf[i < 3 ? i : 9] = (float)(P.fx_d * o[i] + P.cx_d * o[8 + i]);
-    else if (row == 1) pf[i < 3 ? 3 + i : 10] = (float)(P.fy_d * o[4 + i] + P.cy_d * o[8 + i]);
-    else pf[i < 3 ? 6 + i : 11] = (float)o[8 + i];
+    float2* pd = posed + 12 * t;
+    if (row == 0) vd_store_pose_entry(pf, pd, i < 3 ? i : 9, P.fx_d * o[i] + P.cx_d * o[8 + i]);
+    else if (row == 1)
+      vd_store_pose_entry(pf, pd, i < 3 ? 3 + i : 10, P.fy_d * o[4 + i] + P.cy_d * o[8 + i]);
+    else vd_store_pose_entry(pf, pd, i < 3 ? 6 + i : 11, o[8 + i]);
   }
 }
 
@@ -1133,7 +1136,7 @@ cudaError_t launch_pose_frame(vd_ctx* c, uint32_t itcode, int t) {
   vd_prof_begin(c, VD_ST_SELECT);
   k_select_meanshift<<<1, 32, 0, c->stream>>>(P, c->roots, c->root_count, c->rootsr,
                                                c->root_energy, t, c->G,
-                                               c->posef, c->sample_pose + 12 * f,
+                                               c->posef, c->posed, c->sample_pose + 12 * f,
                                                c->sample_energy + f, c->degenerate);
   vd_prof_end(c, VD_ST_SELECT, 1);
   return cudaGetLastError();

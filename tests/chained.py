@@ -53,6 +53,10 @@ from gpu_common import POSE_ROT_TOL, POSE_TRANS_TOL, RIGID_TOL, tie_band
 # ~1e-6 at these sizes; the margins are ten to a hundred times that).
 BORDER_MARGIN_PX = 1e-2
 ZPLANE_MARGIN = 1e-4
+# The same for the double-float positions of the rigidness emissions (good
+# to ~1e-11 px and z to ~1e-14; again a hundred times that and more).
+BORDER_MARGIN_DF_PX = 1e-8
+ZPLANE_MARGIN_DF = 1e-10
 
 
 def pose_err(A, B):
@@ -90,6 +94,12 @@ def _lin_pos_err(c, W):
     return 2.0 ** -21 * (np.abs(np.nan_to_num(c, nan=0.0)) + W)
 
 
+def _df_pos_err(c, W):
+    """The same bound for double-float positions (48-bit products and sums,
+    one corrected division), with a wide margin."""
+    return 2.0 ** -40 * (np.abs(np.nan_to_num(c, nan=0.0)) + W)
+
+
 def _tap_gradient(F, x, y):
     """Largest difference between neighbouring bilinear taps of F around
     (x, y) (px of flow per px of position, both components)."""
@@ -115,14 +125,17 @@ def _fisk_interval(fn, rr, dr):
 MUFU_ERR = 8 * 2.0 ** -22
 
 
-def term_ranges(P, G, iu, iv, rho, p):
+def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
     """Per flow term of pixels (iu, iv) at inverse depth rho: the values a
     float32 evaluation of the same definition may give.
 
     Two effects are bounded.  Rounding: the projected positions carry a
-    few roundings (`_lin_pos_err`), which move the residual by at most the
-    position errors of x_{t-1} and x_t plus the error of x_{t-1} times the
-    flow's tap gradient there (steep at a depth edge of the flow field).
+    few roundings (`_lin_pos_err`, or `_df_pos_err` with
+    positions="df", the rigidness emissions), which move the residual by
+    at most the position errors of x_{t-1} and x_t plus the error of
+    x_{t-1} times the flow's tap gradient there (steep at a depth edge of
+    the flow field); the float32 bilinear weights, flow sample and
+    residual add a few roundings of the flow's magnitude and gradient.
     Decisions: a term whose observability (inside the image, in front of
     camera t-1) or camera-plane test at t lies within rounding of its
     threshold may take either side.
@@ -131,6 +144,10 @@ def term_ranges(P, G, iu, iv, rho, p):
     e1_hi (the rigid emission), e1 (the oracle's emission), flipped (a
     decision is within rounding) and steep (the flow changes by more than
     4 px between neighbouring taps)."""
+    if positions == "df":
+        pos_err, border, zmargin = _df_pos_err, BORDER_MARGIN_DF_PX, ZPLANE_MARGIN_DF
+    else:
+        pos_err, border, zmargin = _lin_pos_err, BORDER_MARGIN_PX, ZPLANE_MARGIN
     iu = np.asarray(iu)
     iv = np.asarray(iv)
     rho = np.asarray(rho, np.float64)
@@ -145,7 +162,7 @@ def term_ranges(P, G, iu, iv, rho, p):
         h = ogeo.project_h(P.K, G[t], r, rho)
         hz = h[..., 2]
         front = hz > ogeo.Z_EPS
-        amb_front = np.abs(hz - ogeo.Z_EPS) < ZPLANE_MARGIN
+        amb_front = np.abs(hz - ogeo.Z_EPS) < zmargin
         if t == 1:
             obs = np.ones(iu.shape, bool)
             amb_obs = np.zeros(iu.shape, bool)
@@ -157,23 +174,27 @@ def term_ranges(P, G, iu, iv, rho, p):
             with np.errstate(invalid="ignore"):
                 ins = ogeo.inside(xp, yp, W, H)
                 near = (np.minimum.reduce([np.abs(xp), np.abs(xp - (W - 1)), np.abs(yp),
-                                           np.abs(yp - (H - 1))]) < BORDER_MARGIN_PX)
-                loose = ((xp >= -BORDER_MARGIN_PX) & (xp <= W - 1 + BORDER_MARGIN_PX) &
-                         (yp >= -BORDER_MARGIN_PX) & (yp <= H - 1 + BORDER_MARGIN_PX))
+                                           np.abs(yp - (H - 1))]) < border)
+                loose = ((xp >= -border) & (xp <= W - 1 + border) &
+                         (yp >= -border) & (yp <= H - 1 + border))
             near = np.where(np.isfinite(xp) & np.isfinite(yp), near, False)
             obs = fprev & ins
-            amb_obs = (np.abs(zp - ogeo.Z_EPS) < ZPLANE_MARGIN) | (fprev & near & loose)
+            amb_obs = (np.abs(zp - ogeo.Z_EPS) < zmargin) | (fprev & near & loose)
             xs = np.clip(np.nan_to_num(xp), 0.0, W - 1)
             ys = np.clip(np.nan_to_num(yp), 0.0, H - 1)
             F = ogeo.bilinear(P.flow[t - 1], xs, ys)
-            e_prev = _lin_pos_err(xp, W) + _lin_pos_err(yp, W)
+            e_prev = pos_err(xp, W) + pos_err(yp, W)
             grad = _tap_gradient(P.flow[t - 1], xs, ys)
         hz_f = np.where(hz > ogeo.Z_EPS, hz, ogeo.Z_EPS * (1 + 1e-9))
         x = h[..., 0] / hz_f
         y = h[..., 1] / hz_f
         rr = np.hypot(F[..., 0] - (x - xp), F[..., 1] - (y - yp))
         rr = np.where(np.isfinite(rr), rr, 1e30)
-        dr = e_prev * (1.0 + grad) + _lin_pos_err(x, W) + _lin_pos_err(y, W)
+        with np.errstate(invalid="ignore"):
+            fsz = (np.abs(F).sum(-1) + np.abs(np.nan_to_num(x - xp)) +
+                   np.abs(np.nan_to_num(y - yp)))
+        dr = (e_prev * (1.0 + grad) + pos_err(x, W) + pos_err(y, W) +
+              2.0 ** -21 * (fsz + 2.0 * grad))
         alpha = p.fisk_alpha0 + p.fisk_alpha1 * np.hypot(F[..., 0], F[..., 1])
         with np.errstate(over="ignore", divide="ignore"):
             l_lo, l_hi = _fisk_interval(
@@ -357,7 +378,8 @@ def estep_stage(V, ctx, P, S, d, p, rep, label):
     """Rigidness E-step along direction d from state S (the GPU's, with the
     new depth).  Every posterior within 1e-4 of the oracle's; where one is
     not, its whole chain must lie within 1e-4 of the interval that the
-    float32 emissions of `term_ranges` allow: the posterior of a two-state
+    emissions of `term_ranges` allow (double-float positions, float32 flow
+    samples and Fisk ratios): the posterior of a two-state
     chain with gamma >= 1/2 increases with every rigid emission (a
     ferromagnetic chain), so the interval's ends are the oracle's
     forward-backward at all-lowest and at all-highest emissions."""
@@ -374,7 +396,7 @@ def estep_stage(V, ctx, P, S, d, p, rep, label):
     kinds = {"flipped": 0, "steep": 0, "other": 0}
     if (err > RIGID_TOL).any():
         iu, iv = omodel.pixel_grid(P)
-        tr = term_ranges(P, S.G, iu, iv, S.rho, p)
+        tr = term_ranges(P, S.G, iu, iv, S.rho, p, positions="df")
         for t in range(P.N):
             errc = _chain_view(err[t], d)
             chains = np.nonzero((errc > RIGID_TOL).any(1))[0]

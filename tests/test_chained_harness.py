@@ -174,6 +174,25 @@ def test_float32_ranges_hold_the_oracle_and_are_tight_off_edges():
     assert np.all(lo <= E + 1e-12) and np.all(hi >= E - 1e-12)
 
 
+def test_double_float_ranges_hold_the_oracle_and_leave_no_flips():
+    """The ranges of the rigidness emissions (double-float positions) hold
+    the oracle's emissions, decide every border and camera-plane test, and
+    are narrow enough for the 1e-4 posterior check almost everywhere."""
+    P, p = _setup()
+    S, _ = oem.bootstrap(P, p)
+    iu, iv = omodel.pixel_grid(P)
+    tr = chained.term_ranges(P, S.G, iu, iv, S.rho, p, positions="df")
+    tr32 = chained.term_ranges(P, S.G, iu, iv, S.rho, p)
+    _, e1, _ = omodel.flow_terms(P, S.G, iu, iv, S.rho, p)
+    assert np.all(tr["e1_lo"] <= e1 * (1 + 1e-12)) and np.all(tr["e1_hi"] >= e1 * (1 - 1e-12))
+    assert not tr["flipped"].any()
+    pos = e1 > 0
+    rel = (tr["e1_hi"] - tr["e1_lo"])[pos] / e1[pos]
+    rel32 = (tr32["e1_hi"] - tr32["e1_lo"])[pos] / e1[pos]
+    assert np.percentile(rel, 99) < 2e-4 and rel.max() < 1e-3
+    assert np.median(rel) * 20 < np.median(rel32)
+
+
 def test_chain_posterior_rises_with_every_rigid_emission():
     """The E-step interval check rests on this: with gamma >= 1/2 the
     posterior of every position is non-decreasing in each rigid emission."""
