@@ -574,11 +574,15 @@ static cudaError_t posef_step(vd_ctx* c) {
   return e;
 }
 
+// The pose rows (posef, posed) mirror G at every step boundary: the device
+// writers of G (the eight-point bootstrap, the mode search) store the rows
+// of what they write, and every host write of G is followed by
+// launch_posef.  So the steps below use them as they are.
+
 // One depth M-step.  boot: the monocular bootstrap's depth from X_1 alone
 // (one flow; timed with the rest of the bootstrap).
 static cudaError_t depth_step(vd_ctx* c, int iter, int direction, bool boot = false) {
-  cudaError_t e = posef_step(c);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   const int nf = boot ? 1 : c->N;
   const int st_sample = boot ? VD_ST_OTHER : VD_ST_SAMPLE;
   const int st_prop = boot ? VD_ST_OTHER : VD_ST_PROPAGATE;
@@ -600,8 +604,8 @@ static cudaError_t estep(vd_ctx* c, int direction) {
 }
 
 static cudaError_t pose_step(vd_ctx* c, int iter, int t) {
-  cudaError_t e = posef_step(c);
-  if (t > 0) return e == cudaSuccess ? launch_pose_frame(c, itcode_of(iter), t) : e;
+  cudaError_t e = cudaSuccess;
+  if (t > 0) return launch_pose_frame(c, itcode_of(iter), t);
   for (int k = 1; k <= c->N && e == cudaSuccess; ++k) e = launch_pose_frame(c, itcode_of(iter), k);
   return e;
 }

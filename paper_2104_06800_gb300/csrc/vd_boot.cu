@@ -131,13 +131,35 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
       for (int q = p; q < 9; ++q) acc[k] = ep_df_add(acc[k], ep_df_mul(wr, r[q])), ++k;
     }
   }
-  // warp and block sums in double-float, fixed order; one partial per block
+  // warp sums by a reduce-scatter over 64 slots (45 entries, zeros after):
+  // at lane bit s the upper half-lanes keep the upper half of the slots and
+  // receive their partner's copy of it, the lower ones the lower half, so
+  // that lane L ends with the warp's sums of slots 2L and 2L + 1 (62
+  // double-float additions instead of 45 x 5); then the block sum over
+  // warps.  Fixed order throughout; one partial per block.
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  {
+    vd_df r[32];
 #pragma unroll
-  for (int i = 0; i < 45; ++i) {
-    vd_df x = acc[i];
-    for (int o = 16; o > 0; o >>= 1) x = vd_df_add(x, ep_shfl_xor(x, o));
-    if (lane == 0) sW[wid][i] = x;
+    for (int i = 0; i < 32; ++i) {   // s = 16: slots i and i + 32
+      const bool upper = (lane & 16) != 0;
+      const vd_df a = acc[i];
+      const vd_df b = i + 32 < 45 ? acc[i + 32] : vd_df{0.0f, 0.0f};
+      const vd_df send = upper ? a : b;
+      r[i] = vd_df_add(upper ? b : a, ep_shfl_xor(send, 16));
+    }
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+      const bool upper = (lane & s) != 0;
+#pragma unroll
+      for (int i = 0; i < 2 * s; ++i) {
+        const vd_df send = upper ? r[i] : r[i + 2 * s];
+        const vd_df keep = upper ? r[i + 2 * s] : r[i];
+        r[i] = vd_df_add(keep, ep_shfl_xor(send, s));
+      }
+    }
+    if (2 * lane < 45) sW[wid][2 * lane] = r[0];
+    if (2 * lane + 1 < 45) sW[wid][2 * lane + 1] = r[1];
   }
   __syncthreads();
   if (threadIdx.x < 45) {
@@ -147,41 +169,12 @@ k_ep_normal(DevParams P, const float2* __restrict__ flow, const double* __restri
   }
 }
 
-// Sum the partials (fixed order) and take the eigenvector of the smallest
-// eigenvalue as E (unit Frobenius norm), by inverse iteration on the
-// symmetric positive semi-definite M shifted by 1e-14 trace(M): one warp;
-// lane 0 factors M + d I = L L^T, lanes 0..8 each solve one column of the
-// inverse, then every step x <- (M + d I)^-1 x / |x| is a 9-lane
-// matrix-vector product, until the iterate stops moving.  `warm` starts from
-// the previous round's E, else from (1, ..., 1) / 3.
-__global__ void __launch_bounds__(512)
-k_ep_solve(const float2* __restrict__ partial, int nblk, double* __restrict__ Mout,
-           double* __restrict__ Eio, int warm) {
-  __shared__ double sM[45];
-  __shared__ double sA[81];   // L (lower triangle)
-  __shared__ double sRd[9];   // 1 / L_jj
-  __shared__ double sI[81];   // (M + d I)^-1, column-major by solving lane
-  const int tid = threadIdx.x;
-  {
-    // entry e by warp e % 16 (lanes: strided blocks), double-float sums in
-    // fixed order, then one conversion to float64
-    const int lane = tid & 31, wp = tid >> 5;
-    for (int e = wp; e < 45; e += 16) {
-      vd_df s = {0.0f, 0.0f};
-      for (int b = lane; b < nblk; b += 32) {
-        const float2 x = partial[(size_t)b * 45 + e];
-        s = vd_df_add(s, vd_df_make(x.x, x.y));
-      }
-      for (int o = 16; o > 0; o >>= 1) s = vd_df_add(s, ep_shfl_xor(s, o));
-      if (lane == 0) {
-        const double d = vd_df_to(s);
-        sM[e] = d;
-        Mout[e] = d;
-      }
-    }
-  }
-  __syncthreads();
-  if (tid >= 32) return;
+// Warp 0 of k_ep_solve (tid = lane): (M + d I)^-1 of the packed upper
+// triangle sM, d = 1e-14 trace(M).  M + d I = L L^T column by column (every
+// lane forms the pivot, lanes j+1..8 the entries of column j), then lanes
+// 0..8 each solve for one column of the inverse.
+__device__ __forceinline__ void ep_inverse(const double* sM, double* sA, double* sRd, double* sI,
+                                           int tid) {
   if (tid < 9) {
     // lane q copies column q of the upper triangle into row q's lower part
     int k = 0;
@@ -229,6 +222,82 @@ k_ep_solve(const float2* __restrict__ partial, int nblk, double* __restrict__ Mo
     for (int i = 0; i < 9; ++i) sI[9 * tid + i] = y[i];
   }
   __syncwarp();
+}
+
+#ifndef EP_SQUARINGS
+#define EP_SQUARINGS 4
+#endif
+// Sum the partials (fixed order) and take the eigenvector of the smallest
+// eigenvalue as E (unit Frobenius norm), by inverse iteration on the
+// symmetric positive semi-definite M shifted by 1e-14 trace(M): warp 0
+// factors M + d I = L L^T, lanes 0..8 each solve one column of the inverse
+// B; 81 threads square B / trace(B) EP_SQUARINGS times (every squaring
+// does the work of as many steps as the last one did: 1, 2, 4, ...), the
+// start vector goes through that power once, then every step
+// x <- B x / |x| is a 9-lane matrix-vector product, until the iterate stops
+// moving.  `warm` starts from the previous round's E, else from
+// (1, ..., 1) / 3.
+__global__ void __launch_bounds__(512)
+k_ep_solve(const float2* __restrict__ partial, int nblk, double* __restrict__ Mout,
+           double* __restrict__ Eio, int warm) {
+  __shared__ double sM[45];
+  __shared__ double sA[81];   // L (lower triangle)
+  __shared__ double sRd[9];   // 1 / L_jj
+  __shared__ double sI[81];   // (M + d I)^-1, column-major by solving lane
+  __shared__ double sP[2][81];   // powers of B / trace(B)
+  const int tid = threadIdx.x;
+  {
+    // entries wp, wp + 16, wp + 32 by warp wp (lanes: strided blocks), each
+    // a double-float sum in fixed order, then one conversion to float64
+    const int lane = tid & 31, wp = tid >> 5;
+    vd_df s[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int b = lane; b < nblk; b += 32) {
+      const float2* row = partial + (size_t)b * 45;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (wp + 16 * k < 45) {
+          const float2 x = row[wp + 16 * k];
+          s[k] = vd_df_add(s[k], vd_df_make(x.x, x.y));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      for (int o = 16; o > 0; o >>= 1) s[k] = vd_df_add(s[k], ep_shfl_xor(s[k], o));
+      if (lane == 0 && wp + 16 * k < 45) {
+        const double d = vd_df_to(s[k]);
+        sM[wp + 16 * k] = d;
+        Mout[wp + 16 * k] = d;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < 32) ep_inverse(sM, sA, sRd, sI, tid);
+  __syncthreads();
+  // B / trace(B) (entries at most 1: B is positive definite), then its
+  // squares; products of entries at most 1 neither overflow nor, over
+  // EP_SQUARINGS <= 5 squarings of a unit-trace matrix, underflow the
+  // dominant part
+  if (tid < 81) {
+    double tr = 0.0;
+    for (int p = 0; p < 9; ++p) tr += sI[10 * p];
+    sP[0][tid] = sI[tid] / tr;
+  }
+#pragma unroll 1
+  for (int k = 0; k < EP_SQUARINGS; ++k) {
+    __syncthreads();
+    if (tid < 81) {
+      const double* B = sP[k & 1];
+      const int r = tid / 9, c = tid - 9 * r;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 9; ++m) acc = fma(B[9 * r + m], B[9 * m + c], acc);
+      sP[(k + 1) & 1][tid] = acc;
+    }
+  }
+  __syncthreads();
+  if (tid >= 32) return;
+  const double* Bq = sP[EP_SQUARINGS & 1];
   // lane i < 9 holds x_i
   double xi = 0.0;
   if (tid < 9) xi = warm ? Eio[tid] : 1.0 / 3.0;
@@ -239,6 +308,20 @@ k_ep_solve(const float2* __restrict__ partial, int nblk, double* __restrict__ Mo
     n2 = 1.0;
   }
   xi *= vd_rsqrt64(n2);
+  {
+    // x <- B^(2^EP_SQUARINGS) x / |.|: its sign follows x (x^T B^k x >= 0)
+    double yi = 0.0;
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      const double xm = __shfl_sync(0xffffffffu, xi, m);
+      if (tid < 9) yi = fma(Bq[9 * m + tid], xm, yi);
+    }
+    double n = yi * yi;
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    // a start orthogonal to the dominant direction (or a power that
+    // underflowed) keeps the start; the steps below then converge from it
+    if (n > 0.0 && isfinite(n)) xi = yi * vd_rsqrt64(n);
+  }
   double prev_diff = 1e300;
   for (int it = 0; it < 300; ++it) {
     double yi = 0.0;

@@ -49,10 +49,9 @@ struct EmDot2 {
   __device__ __forceinline__ vd_df get() const { return vd_two_sum(s, e); }
 };
 
-// n / d for double-float n, d (d != 0): a float quotient, then one
-// correction from the remainder n - q d.
-__device__ __forceinline__ vd_df em_df_div(vd_df n, vd_df d) {
-  const float r = 1.0f / d.hi;
+// n / d for double-float n, d (d != 0; r = 1 / d.hi rounded): a float
+// quotient, then one correction from the remainder n - q d.
+__device__ __forceinline__ vd_df em_df_div(vd_df n, vd_df d, float r) {
   const float q = __fmul_rn(n.hi, r);
   const float rem = fmaf(-q, d.lo, fmaf(-q, d.hi, n.hi) + n.lo);
   return vd_fast_two_sum(q, rem * r);
@@ -149,8 +148,9 @@ k_emission(DevParams P, const float2* __restrict__ posed, const float2* __restri
     const bool front = em_df_gt(Z, kZhi, kZlo);
     vd_df x = xp, y = yp;
     if (front) {
-      x = em_df_div(hx.get(), Z);
-      y = em_df_div(hy.get(), Z);
+      const float r = __frcp_rn(Z.hi);
+      x = em_df_div(hx.get(), Z, r);
+      y = em_df_div(hy.get(), Z, r);
     }
     bool obs;
     float2 F;
