@@ -187,6 +187,13 @@ __device__ __forceinline__ float vd_slot_candidate(const DevParams& P, uint32_t 
 #define VD_STR(x) #x
 #define VD_UNROLL(n) _Pragma(VD_STR(unroll n))
 
+// Slot of ring position i >= 0 (unsigned: no sign correction of the
+// remainder; a power-of-two ring is a mask)
+template <unsigned R>
+__device__ __forceinline__ unsigned vd_ring(int i) {
+  return (unsigned)i % R;
+}
+
 // Flows [TA, TB) of one entry; false as soon as its partial energy exceeds
 // `thr`, the entry's drop threshold (see vd_drop_threshold).
 template <int TA, int TB>
@@ -296,8 +303,8 @@ k_depth_sample_q(DevParams P, const float* __restrict__ posef, const float2* __r
   auto stage2 = [&]() {
     const int idx = h2 + lane;
     if (idx < e2) {
-      const float4 e = sR2[wq][idx % VD_KQ_R2];
-      const unsigned id = sI2[wq][idx % VD_KQ_R2];
+      const float4 e = sR2[wq][vd_ring<VD_KQ_R2>(idx)];
+      const unsigned id = sI2[wq][vd_ring<VD_KQ_R2>(idx)];
       const int p = id & 31u;
       const unsigned slot = id >> 5;
       const float thr = vd_drop_threshold(*(volatile unsigned long long*)&sBw[p], slot);
@@ -334,7 +341,7 @@ VD_UNROLL(VD_KQ_PRE_UNROLL)
         const bool keep = valid && key < bnd;
         const unsigned m = __ballot_sync(FULL, keep);
         if (keep) {
-          const int pos = (e1 + __popc(m & lt)) % VD_KQ_R1;
+          const unsigned pos = vd_ring<VD_KQ_R1>(e1 + __popc(m & lt));
           sR1[wq][pos] = make_float4(cc, Ek, f1 ? x1 : NaN, y1);
           sI1[wq][pos] = (unsigned short)(lane | (k << 5));
         }
@@ -351,8 +358,8 @@ VD_UNROLL(VD_KQ_PRE_UNROLL)
       float4 st = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       unsigned id = 0;
       if (idx < e1) {
-        st = sR1[wq][idx % VD_KQ_R1];
-        id = sI1[wq][idx % VD_KQ_R1];
+        st = sR1[wq][vd_ring<VD_KQ_R1>(idx)];
+        id = sI1[wq][vd_ring<VD_KQ_R1>(idx)];
         const int p = id & 31u;
         const unsigned slot = id >> 5;
         const float thr = vd_drop_threshold(*(volatile unsigned long long*)&sBw[p], slot);
@@ -364,7 +371,7 @@ VD_UNROLL(VD_KQ_PRE_UNROLL)
       if (T1 < NF) {
         const unsigned m = __ballot_sync(FULL, keep);
         if (keep) {
-          const int pos = (e2 + __popc(m & lt)) % VD_KQ_R2;
+          const unsigned pos = vd_ring<VD_KQ_R2>(e2 + __popc(m & lt));
           sR2[wq][pos] = st;
           sI2[wq][pos] = (unsigned short)id;
         }
