@@ -371,17 +371,24 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
         }
         vd_tc_fence_after();
         const uint32_t a0 = sA + s * S::STAGE, d0 = dt + a * S::ACC;
+        // the descriptors of the stage's first pixel and of the weights; an
+        // operand at byte offset o has the descriptor + o / 16 (the start
+        // field is the shared address / 16, 14 bits, and every address of
+        // the CTA's shared memory fits it without a carry)
+        static_assert(VD_SW_PHASE == 0, "offset descriptors need a fixed base-offset field");
+        const uint64_t dA0 = vd_umma_desc_sw(a0, S::PIX), dB0 = vd_umma_desc(sB, 128, K * 16);
 #pragma unroll 1
-        for (int r = 0; r < R; ++r)
+        for (int r = 0; r < R; ++r) {
+          const uint64_t dAr = dA0 + (uint64_t)((r * CNN_HALO_X * S::PIX) >> 4);
 #pragma unroll
           for (int t = 0; t < 9; ++t)
 #pragma unroll
             for (int j = 0; j < CIN / 16; ++j) {   // 16 input channels (32 bytes) per MMA
-              const uint32_t aa = a0 + ((r + t / 3) * CNN_HALO_X + t % 3) * S::PIX + 32 * j;
-              const uint32_t bb = sB + ((t * CIN + 16 * j) >> 3) * 128;
-              vd_umma_bf16(d0 + r * N, vd_umma_desc_sw(aa, S::PIX), vd_umma_desc(bb, 128, K * 16),
-                           idesc, (t | j) ? 1u : 0u);
+              const uint32_t oa = (((t / 3) * CNN_HALO_X + t % 3) * S::PIX + 32 * j) >> 4;
+              const uint32_t ob = (((t * CIN + 16 * j) >> 3) * 128) >> 4;
+              vd_umma_bf16(d0 + r * N, dAr + oa, dB0 + ob, idesc, (t | j) ? 1u : 0u);
             }
+        }
         vd_umma_commit(&empty[s]);     // the stage is free once these MMAs are done
         vd_umma_commit(&accfull[a]);   // and the accumulator is ready
         any = true;
