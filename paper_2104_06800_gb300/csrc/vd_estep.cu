@@ -2,7 +2,7 @@
 // along the rows or columns of every flow's rigidness map, smoothed by the
 // forward-backward algorithm, and the depth confidence map of Eq. 6.
 #include "vd_device.cuh"
-#include "vd_df64.cuh"
+#include "vd_emission_df.cuh"
 
 #define VD_DISPATCH_NF(N, KERNEL_CALL)      \
   switch (N) {                              \
@@ -17,87 +17,12 @@
     default: return cudaErrorInvalidValue;  \
   }
 
-// ---------------------------------------------------------------------------
-// Projected positions in double-float.  The posterior of a chain reacts to
-// an emission's rounding wherever the flow field is steep (a depth edge
-// moves the bilinear sample by tens of px per px of position) or a position
-// lies on an image border or the camera plane; float32 positions (~1e-3 px
-// off at 1216 px) put such entries outside 1e-4 of the exact chain, so the
-// emissions project the rays through the double-float pose rows.
-// ---------------------------------------------------------------------------
-
-// A short dot product accumulated in about twice the working precision: each
-// product's rounding error recovered with a fused multiply-add, each sum's
-// with TwoSum, all low parts and cross terms gathered in one float (the
-// compensated dot product "Dot2" of Ogita, Rump and Oishi, "Accurate sum and
-// dot product", SIAM J. Sci. Comput. 26, 2005).
-struct EmDot2 {
-  float s, e;
-  __device__ __forceinline__ explicit EmDot2(float2 z) : s(z.x), e(z.y) {}
-  __device__ __forceinline__ void add(float2 a, vd_df b) {   // a * b, both double-float
-    const vd_df p = vd_two_prod(a.x, b.hi);
-    const vd_df t = vd_two_sum(s, p.hi);
-    s = t.hi;
-    e = fmaf(a.x, b.lo, fmaf(a.y, b.hi, e + (t.lo + p.lo)));
-  }
-  __device__ __forceinline__ void add(float2 a, float b) {   // a * b, b a float
-    const vd_df p = vd_two_prod(a.x, b);
-    const vd_df t = vd_two_sum(s, p.hi);
-    s = t.hi;
-    e = fmaf(a.y, b, e + (t.lo + p.lo));
-  }
-  __device__ __forceinline__ vd_df get() const { return vd_two_sum(s, e); }
-};
-
-// n / d for double-float n, d (d != 0; r = 1 / d.hi rounded): a float
-// quotient, then one correction from the remainder n - q d.
-__device__ __forceinline__ vd_df em_df_div(vd_df n, vd_df d, float r) {
-  const float q = __fmul_rn(n.hi, r);
-  const float rem = fmaf(-q, d.lo, fmaf(-q, d.hi, n.hi) + n.lo);
-  return vd_fast_two_sum(q, rem * r);
-}
-
-// The float nearest to a - b (double-float a, b).
-__device__ __forceinline__ float em_df_diff(vd_df a, vd_df b) {
-  const vd_df s = vd_two_sum(a.hi, -b.hi);
-  return __fadd_rn(s.hi, s.lo + (a.lo - b.lo));
-}
-
-// a > b for normalised double-float values (|lo| <= ulp(hi) / 2).
-__device__ __forceinline__ bool em_df_gt(vd_df a, float bhi, float blo) {
-  return a.hi > bhi || (a.hi == bhi && a.lo > blo);
-}
-
-__device__ __forceinline__ bool em_df_inside(vd_df x, vd_df y, int W, int H) {
-  const float xm = (float)(W - 1), ym = (float)(H - 1);
-  return (x.hi > 0.0f || (x.hi == 0.0f && x.lo >= 0.0f)) &&
-         (x.hi < xm || (x.hi == xm && x.lo <= 0.0f)) &&
-         (y.hi > 0.0f || (y.hi == 0.0f && y.lo >= 0.0f)) &&
-         (y.hi < ym || (y.hi == ym && y.lo <= 0.0f));
-}
-
-// floor of a double-float value and its fractional part as a float
-__device__ __forceinline__ int em_df_floor(vd_df x, float* frac) {
-  float f = floorf(x.hi);
-  if (f == x.hi && x.lo < 0.0f) f -= 1.0f;
-  *frac = (x.hi - f) + x.lo;
-  return (int)f;
-}
-
 // Bilinear sample at an inside double-float position, the taps of
 // `vd_bilinear` (x0 = min(floor(x), W-2)).
 __device__ __forceinline__ float2 em_bilinear_df(const float2* __restrict__ F, int W, int H,
                                                  vd_df x, vd_df y) {
   float ax, ay;
-  int x0 = em_df_floor(x, &ax), y0 = em_df_floor(y, &ay);
-  if (x0 > W - 2) {   // x = W - 1 exactly: the last column with weight 1
-    ax += (float)(x0 - (W - 2));
-    x0 = W - 2;
-  }
-  if (y0 > H - 2) {
-    ay += (float)(y0 - (H - 2));
-    y0 = H - 2;
-  }
+  const int x0 = vd_em_tap(x, W, &ax), y0 = vd_em_tap(y, H, &ay);
   const float2* p = F + VD_CHK(VD_SITE_BILINEAR, (long long)y0 * W + x0, (long long)W * H - W - 1);
   const float2 f00 = __ldg(p), f01 = __ldg(p + 1);
   const float2 f10 = __ldg(p + W), f11 = __ldg(p + W + 1);
@@ -111,7 +36,8 @@ __device__ __forceinline__ float2 em_bilinear_df(const float2* __restrict__ F, i
 // depth: 1 / y for an observed term (y = P0 / p1), 0 when the point is behind
 // camera t, 1 without observation.  Also the prior's isolated posterior q_hat.
 // Positions, the camera-plane test and the image-border test in
-// double-float (above); the flow sample and the Fisk ratio in float32.
+// double-float (vd_emission_df.cuh); the flow sample and the Fisk ratio in
+// float32.
 // ---------------------------------------------------------------------------
 template <int NF>
 __global__ void __launch_bounds__(128)
@@ -128,44 +54,28 @@ k_emission(DevParams P, const float2* __restrict__ posed, const float2* __restri
   const size_t npix = (size_t)P.W * P.H;
   const size_t j = (size_t)v * P.W + u;
   const float c = rho[j];
-  // the camera plane z = 1e-6 as a double-float pair
-  constexpr float kZhi = (float)1e-6;
-  constexpr float kZlo = (float)(1e-6 - (double)kZhi);
-  const vd_df cx = vd_df_make(P.kdf[4], P.kdf[5]), cy = vd_df_make(P.kdf[6], P.kdf[7]);
-  const vd_df ifx = vd_df_make(P.kdf[8], P.kdf[9]), ify = vd_df_make(P.kdf[10], P.kdf[11]);
-  const vd_df rx = vd_df_mul(vd_df_sub(vd_df_make((float)u), cx), ifx);
-  const vd_df ry = vd_df_mul(vd_df_sub(vd_df_make((float)v), cy), ify);
+  vd_df rx, ry;
+  vd_em_ray(P.kdf, u, v, &rx, &ry);
   vd_df xp = vd_df_make((float)u), yp = vd_df_make((float)v);
   bool front_prev = true;
 #pragma unroll
   for (int t = 0; t < NF; ++t) {
-    const float2* M = sPose + 12 * (t + 1);
-    EmDot2 hx(M[2]), hy(M[5]), hz(M[8]);
-    hx.add(M[0], rx), hy.add(M[3], rx), hz.add(M[6], rx);
-    hx.add(M[1], ry), hy.add(M[4], ry), hz.add(M[7], ry);
-    hx.add(M[9], c), hy.add(M[10], c), hz.add(M[11], c);
-    const vd_df Z = hz.get();
-    const bool front = em_df_gt(Z, kZhi, kZlo);
     vd_df x = xp, y = yp;
-    if (front) {
-      const float r = __frcp_rn(Z.hi);
-      x = em_df_div(hx.get(), Z, r);
-      y = em_df_div(hy.get(), Z, r);
-    }
+    const bool front = vd_em_project(sPose + 12 * (t + 1), rx, ry, c, &x, &y);
     bool obs;
     float2 F;
     if (t == 0) {
       obs = true;
       F = __ldg(flow + j);
     } else {
-      obs = front_prev && em_df_inside(xp, yp, P.W, P.H);
+      obs = front_prev && vd_em_inside(xp, yp, P.W, P.H);
       F = make_float2(0.0f, 0.0f);
       if (obs) F = em_bilinear_df(flow + (size_t)t * npix, P.W, P.H, xp, yp);
     }
     float l;
     if (obs && front) {
-      const float dx = F.x - em_df_diff(x, xp);
-      const float dy = F.y - em_df_diff(y, yp);
+      const float dx = F.x - vd_em_diff(x, xp);
+      const float dy = F.y - vd_em_diff(y, yp);
       const float yv = vd_ratio_y(P, fmaf(dx, dx, dy * dy), fmaf(F.x, F.x, F.y * F.y));
       l = yv < 1e30f ? __frcp_rn(yv) : 0.0f;   // an overflowing (or 0 * inf) ratio: p1 / P0 = 0
     } else {

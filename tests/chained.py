@@ -54,7 +54,9 @@ from gpu_common import POSE_ROT_TOL, POSE_TRANS_TOL, RIGID_TOL, tie_band
 BORDER_MARGIN_PX = 1e-2
 ZPLANE_MARGIN = 1e-4
 # The same for the double-float positions of the rigidness emissions (good
-# to ~1e-11 px and z to ~1e-14; again a hundred times that and more).
+# to ~1e-11 px in the image and z to ~1e-14; again a hundred times that and
+# more, plus the position's own error bound, `_df_proj_err`, where it is
+# larger).
 BORDER_MARGIN_DF_PX = 1e-8
 ZPLANE_MARGIN_DF = 1e-10
 
@@ -94,10 +96,21 @@ def _lin_pos_err(c, W):
     return 2.0 ** -21 * (np.abs(np.nan_to_num(c, nan=0.0)) + W)
 
 
-def _df_pos_err(c, W):
-    """The same bound for double-float positions (48-bit products and sums,
-    one corrected division), with a wide margin."""
-    return 2.0 ** -40 * (np.abs(np.nan_to_num(c, nan=0.0)) + W)
+def _df_proj_err(h, S):
+    """Bounds on the errors of the double-float positions x = h_x / h_z,
+    y = h_y / h_z (px), given the homogeneous point h and S, the sums of the
+    absolute values of the products that form h (the projection of |R|,
+    |tau| and |r|): the compensated sums are good to a few 2^-48 S, the
+    double-float rows and rays to 2^-47, and the quotient adds the error of
+    h_z times |x|; 2^-42 leaves a wide margin.  Near the camera plane
+    (small h_z) the bound grows with 1 / h_z."""
+    with np.errstate(invalid="ignore", divide="ignore"):
+        iz = 1.0 / np.abs(h[..., 2])
+        x = np.abs(h[..., 0]) * iz
+        y = np.abs(h[..., 1]) * iz
+        ex = 2.0 ** -42 * (S[..., 0] + x * S[..., 2]) * iz
+        ey = 2.0 ** -42 * (S[..., 1] + y * S[..., 2]) * iz
+    return np.nan_to_num(ex, nan=0.0, posinf=0.0), np.nan_to_num(ey, nan=0.0, posinf=0.0)
 
 
 def _tap_gradient(F, x, y):
@@ -130,7 +143,7 @@ def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
     float32 evaluation of the same definition may give.
 
     Two effects are bounded.  Rounding: the projected positions carry a
-    few roundings (`_lin_pos_err`, or `_df_pos_err` with
+    few roundings (`_lin_pos_err`, or `_df_proj_err` with
     positions="df", the rigidness emissions), which move the residual by
     at most the position errors of x_{t-1} and x_t plus the error of
     x_{t-1} times the flow's tap gradient there (steep at a depth edge of
@@ -144,10 +157,11 @@ def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
     e1_hi (the rigid emission), e1 (the oracle's emission), flipped (a
     decision is within rounding) and steep (the flow changes by more than
     4 px between neighbouring taps)."""
-    if positions == "df":
-        pos_err, border, zmargin = _df_pos_err, BORDER_MARGIN_DF_PX, ZPLANE_MARGIN_DF
+    df = positions == "df"
+    if df:
+        border, zmargin = BORDER_MARGIN_DF_PX, ZPLANE_MARGIN_DF
     else:
-        pos_err, border, zmargin = _lin_pos_err, BORDER_MARGIN_PX, ZPLANE_MARGIN
+        border, zmargin = BORDER_MARGIN_PX, ZPLANE_MARGIN
     iu = np.asarray(iu)
     iv = np.asarray(iv)
     rho = np.asarray(rho, np.float64)
@@ -156,11 +170,17 @@ def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
     xp = iu.astype(np.float64)
     yp = iv.astype(np.float64)
     zp = np.ones(iu.shape)
+    exp_ = np.zeros(iu.shape)   # error bounds of the previous position
+    eyp = np.zeros(iu.shape)
     out = {k: [] for k in ("l_lo", "l_hi", "e1_lo", "e1_hi", "e1", "flipped", "steep")}
     big = np.inf
     for t in range(1, P.N + 1):
         h = ogeo.project_h(P.K, G[t], r, rho)
         hz = h[..., 2]
+        if df:
+            ex, ey = _df_proj_err(h, ogeo.project_h(P.K, np.abs(G[t]), np.abs(r), np.abs(rho)))
+        else:
+            ex = ey = None   # after the dehomogenisation below
         front = hz > ogeo.Z_EPS
         amb_front = np.abs(hz - ogeo.Z_EPS) < zmargin
         if t == 1:
@@ -173,28 +193,30 @@ def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
             fprev = zp > ogeo.Z_EPS
             with np.errstate(invalid="ignore"):
                 ins = ogeo.inside(xp, yp, W, H)
+                bd = border + np.maximum(exp_, eyp)
                 near = (np.minimum.reduce([np.abs(xp), np.abs(xp - (W - 1)), np.abs(yp),
-                                           np.abs(yp - (H - 1))]) < border)
-                loose = ((xp >= -border) & (xp <= W - 1 + border) &
-                         (yp >= -border) & (yp <= H - 1 + border))
+                                           np.abs(yp - (H - 1))]) < bd)
+                loose = ((xp >= -bd) & (xp <= W - 1 + bd) &
+                         (yp >= -bd) & (yp <= H - 1 + bd))
             near = np.where(np.isfinite(xp) & np.isfinite(yp), near, False)
             obs = fprev & ins
             amb_obs = (np.abs(zp - ogeo.Z_EPS) < zmargin) | (fprev & near & loose)
             xs = np.clip(np.nan_to_num(xp), 0.0, W - 1)
             ys = np.clip(np.nan_to_num(yp), 0.0, H - 1)
             F = ogeo.bilinear(P.flow[t - 1], xs, ys)
-            e_prev = pos_err(xp, W) + pos_err(yp, W)
+            e_prev = exp_ + eyp
             grad = _tap_gradient(P.flow[t - 1], xs, ys)
         hz_f = np.where(hz > ogeo.Z_EPS, hz, ogeo.Z_EPS * (1 + 1e-9))
         x = h[..., 0] / hz_f
         y = h[..., 1] / hz_f
+        if not df:
+            ex, ey = _lin_pos_err(x, W), _lin_pos_err(y, W)
         rr = np.hypot(F[..., 0] - (x - xp), F[..., 1] - (y - yp))
         rr = np.where(np.isfinite(rr), rr, 1e30)
         with np.errstate(invalid="ignore"):
             fsz = (np.abs(F).sum(-1) + np.abs(np.nan_to_num(x - xp)) +
                    np.abs(np.nan_to_num(y - yp)))
-        dr = (e_prev * (1.0 + grad) + pos_err(x, W) + pos_err(y, W) +
-              2.0 ** -21 * (fsz + 2.0 * grad))
+        dr = (e_prev * (1.0 + grad) + ex + ey + 2.0 ** -21 * (fsz + 2.0 * grad))
         alpha = p.fisk_alpha0 + p.fisk_alpha1 * np.hypot(F[..., 0], F[..., 1])
         with np.errstate(over="ignore", divide="ignore"):
             l_lo, l_hi = _fisk_interval(
@@ -226,6 +248,7 @@ def term_ranges(P, G, iu, iv, rho, p, positions="f32"):
         out["flipped"].append(amb_obs | (can_obs & amb_front))
         out["steep"].append(can_front & (grad > 4.0))
         xp, yp, zp = x, y, hz
+        exp_, eyp = ex, ey
         # positions behind the camera are not positions: NaN, as the oracle
         xp = np.where(front, xp, np.nan)
         yp = np.where(front, yp, np.nan)

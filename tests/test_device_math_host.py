@@ -18,7 +18,10 @@ def hc():
     from paper_2104_06800_gb300.build import nvcc_path
     out = os.path.join(tempfile.mkdtemp(), "libvd_hostcheck.so")
     src = os.path.join(ROOT, "tests", "native", "vd_hostcheck.cu")
-    cmd = [nvcc_path(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    # -ffp-contract=off: the host compiler must not fuse the error-free
+    # transformations' products and sums (the device code spells out its
+    # fused multiply-adds)
+    cmd = [nvcc_path(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared",
            "-gencode", "arch=compute_103a,code=sm_103a",
            "-I", os.path.join(ROOT, "paper_2104_06800_gb300", "csrc"), src, "-o", out]
     subprocess.run(cmd, check=True, capture_output=True)
@@ -32,6 +35,10 @@ def hc():
         getattr(lib, n).argtypes = [P, P]
     for n in ("hc_jacobi9", "hc_jacobi3"):
         getattr(lib, n).argtypes = [P, P, P]
+    F = C.POINTER(C.c_float)
+    lib.hc_em_project.argtypes = [F, F, C.c_int, C.c_int, C.c_float, P]
+    lib.hc_em_inside.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_int]
+    lib.hc_em_tap.argtypes = [C.c_float, C.c_float, C.c_int, F]
     return lib
 
 
@@ -180,3 +187,96 @@ def test_double_float_p3p_matches_the_oracle(hc):
     errs = np.array(errs)
     assert np.mean(errs < 1e-7) >= 0.98 and errs.max() < 1e-5
     assert np.median(errs) < 1e-11
+
+
+# ------------------------------------------------ rigidness emission positions
+def _df_pairs(a):
+    """float64 values -> interleaved float32 (hi, lo) pairs."""
+    a = np.asarray(a, np.float64).ravel()
+    hi = a.astype(np.float32)
+    lo = (a - hi.astype(np.float64)).astype(np.float32)
+    return np.ascontiguousarray(np.stack([hi, lo], -1).ravel())
+
+
+def _kdf(K):
+    fx, fy, cx, cy = K
+    return _df_pairs([fx, fy, cx, cy, 1.0 / fx, 1.0 / fy])
+
+
+def _rows(K, G):
+    """K [R | tau] as 12 float64 entries: the 3 x 3 part by rows, then the
+    last column (the library's layout of a frame's pose rows)."""
+    fx, fy, cx, cy = K
+    KM = np.array([[fx, 0, cx], [0, fy, cy], [0, 0, 1.0]])
+    A = KM @ G
+    return np.concatenate([A[:, :3].ravel(), A[:, 3]])
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def test_emission_positions_match_the_float64_projection(hc):
+    """Double-float projection and dehomogenisation against the oracle's
+    float64 ones, within the bound that the replay harness allows them
+    (`chained._df_proj_err`), and the camera-plane decision wherever z is
+    not within 1e-10 of the plane."""
+    import chained
+    rng = np.random.default_rng(7)
+    W, H = 1216, 368
+    K = (720.0, 720.0, 607.5, 183.5)
+    kdf = _kdf(K)
+    out = np.zeros(2)
+    worst = 0.0
+    n_behind = 0
+    for _ in range(40):
+        xi = np.concatenate([rng.normal(0, 0.05, 3), rng.normal(0, 0.5, 3)])
+        G = geometry.se3_exp(xi)[:3]
+        M = _df_pairs(_rows(K, G))
+        us = rng.integers(0, W, 50)
+        vs = rng.integers(0, H, 50)
+        cs = rng.uniform(0.0, 2.0, 50).astype(np.float32)
+        r = geometry.rays(W, H, K)[vs, us]
+        h = geometry.project_h(K, G, r, cs.astype(np.float64))
+        x, y, front = geometry.dehom(h)
+        ex, ey = chained._df_proj_err(h, geometry.project_h(K, np.abs(G), np.abs(r),
+                                                            cs.astype(np.float64)))
+        for i in range(50):
+            f = hc.hc_em_project(_fp(M), _fp(kdf), int(us[i]), int(vs[i]), float(cs[i]), _p(out))
+            if abs(h[i, 2] - geometry.Z_EPS) > 1e-10:
+                assert bool(f) == bool(front[i])
+            if f and front[i]:
+                for e, ref, b in ((out[0], x[i], ex[i]), (out[1], y[i], ey[i])):
+                    assert abs(e - ref) <= b, (e, ref, b)
+                    worst = max(worst, abs(e - ref) / b)
+            n_behind += int(not f)
+    assert n_behind > 0          # the camera-plane branch was exercised
+    assert worst < 0.5, worst
+
+
+def test_emission_border_and_tap_decisions_are_exact(hc):
+    """Border tests and bilinear taps decide on the exact value hi + lo."""
+    W, H = 1216, 368
+    tiny = np.float32(1e-5)
+    ins = lambda xh, xl, yh, yl: hc.hc_em_inside(xh, xl, yh, yl, W, H)
+    assert ins(W - 1, 0.0, 0.0, 0.0) == 1 and ins(0.0, 0.0, H - 1, 0.0) == 1
+    assert ins(W - 1, tiny, 5.0, 0.0) == 0 and ins(W - 1, -tiny, 5.0, 0.0) == 1
+    assert ins(0.0, -tiny, 5.0, 0.0) == 0 and ins(0.0, tiny, 5.0, 0.0) == 1
+    assert ins(5.0, 0.0, H - 1, tiny) == 0 and ins(5.0, 0.0, 0.0, -tiny) == 0
+    w = np.zeros(1, np.float32)
+    # an integer hi with a negative lo is below the integer
+    assert hc.hc_em_tap(40.0, -tiny, W, _fp(w)) == 39 and abs(w[0] - (1 - tiny)) < 1e-7
+    assert hc.hc_em_tap(40.0, tiny, W, _fp(w)) == 40 and abs(w[0] - tiny) < 1e-7
+    assert hc.hc_em_tap(0.0, 0.0, W, _fp(w)) == 0 and w[0] == 0.0
+    # the last column is reached from the tap before it with weight 1
+    assert hc.hc_em_tap(W - 1, 0.0, W, _fp(w)) == W - 2 and w[0] == 1.0
+    assert hc.hc_em_tap(W - 1, -tiny, W, _fp(w)) == W - 2 and abs(w[0] - (1 - tiny)) < 1e-7
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        x = rng.uniform(0, W - 1)
+        hi = np.float32(x)
+        lo = np.float32(x - np.float64(hi))
+        x0 = hc.hc_em_tap(hi, lo, W, _fp(w))
+        e = np.float64(hi) + np.float64(lo)
+        ref0 = min(int(np.floor(e)), W - 2)
+        assert x0 == ref0 and abs(w[0] - (e - ref0)) < 1e-6
