@@ -78,7 +78,7 @@ FP32_SCORE, MUFU_SCORE = 21, 2
 # from one ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, one launch on the kerb-side driving window); re-measure
 # when it changes.
-K1_TRAFFIC_BYTES = 34.04e6
+K1_TRAFFIC_BYTES = 34.03e6
 SM_MAX_MHZ = 2070.0
 
 
