@@ -294,14 +294,20 @@ __global__ void k_wait_probe(int polls, int* __restrict__ err) {
 // (tile = x-tile + tiles_x * row block).  Warp 4 loads halo tiles into a ring
 // of NS stages (the weights with the first); one thread of warp 5 issues a
 // tile's MMAs into one of two tensor-memory accumulators and commits them to
-// the stage's `empty` barrier and the accumulator's `full` barrier; warps
-// 0..3 (tensor-memory lanes 32 w .. 32 w + 31) run the epilogue and release
-// the accumulator.  So tile i + 1's MMAs run under tile i's epilogue and
-// the loads of the tiles after it.  Every wait is bounded; a role that gives
-// up flags the error and the abort, the others stop at their next wait, and
-// before the CTA ends the loads and MMAs it issued are waited for.
+// the stage's `empty` barrier and the accumulator's `full` barrier; the
+// other 4 * CNN_EPI_SPLIT warps run the epilogue (warp w reads tensor-memory
+// lanes 32 (w % 4) .. 32 (w % 4) + 31, the warps of one lane quarter take
+// the tile's rows in turn) and release the accumulator.  So tile i + 1's
+// MMAs run under tile i's epilogue and the loads of the tiles after it.
+// Every wait is bounded; a role that gives up flags the error and the
+// abort, the others stop at their next wait, and before the CTA ends the
+// loads and MMAs it issued are waited for.
+#ifndef CNN_EPI_SPLIT
+#define CNN_EPI_SPLIT 2
+#endif
+constexpr int CNN_CONV_THREADS = 32 * (4 * CNN_EPI_SPLIT + 2);
 template <int K, int N, int EPI, int R, int NS>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(CNN_CONV_THREADS, 1)
 k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tiles_x, int n_tiles,
           const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ bias,
           void* __restrict__ out, const __nv_bfloat16* __restrict__ mask, int nout,
@@ -324,7 +330,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
     }
     for (int a = 0; a < 2; ++a) {
       vd_mbar_init(&accfull[a], 1);
-      vd_mbar_init(&accempty[a], 4);
+      vd_mbar_init(&accempty[a], 4 * CNN_EPI_SPLIT);
     }
     vd_mbar_init(&fin, 1);
     s_abort = 0;
@@ -398,8 +404,12 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
         vd_mbar_wait_bounded(&fin, 0);
       }
     }
-  } else {   // epilogue: warp w reads accumulator lanes 32 w .. 32 w + 31
-    const uint32_t tl = dt + ((uint32_t)(warp * 32) << 16);
+  } else {   // epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31
+    // warps 0..3 take rows 0, CNN_EPI_SPLIT, ...; warps 6..9 (lane quarters
+    // 2, 3, 0, 1) rows 1, 1 + CNN_EPI_SPLIT, ...
+    static_assert(CNN_EPI_SPLIT == 1 || CNN_EPI_SPLIT == 2, "epilogue warps");
+    const int quarter = warp & 3, part = warp < 4 ? 0 : 1;
+    const uint32_t tl = dt + ((uint32_t)(quarter * 32) << 16);
     for (int i = 0; i < my_tiles; ++i) {
       const int a = i & 1;
       int ok = 0;
@@ -414,9 +424,9 @@ k_conv_tc(const __grid_constant__ CUtensorMap xmap, int Wimg, int Himg, int tile
       }
       vd_tc_fence_after();
       const int tile = blockIdx.x + i * gridDim.x;
-      const int x = (tile % tiles_x) * CNN_TILE + warp * 32 + lane, y0 = (tile / tiles_x) * R;
+      const int x = (tile % tiles_x) * CNN_TILE + quarter * 32 + lane, y0 = (tile / tiles_x) * R;
 #pragma unroll 1
-      for (int r = 0; r < R; ++r) {
+      for (int r = part; r < R; r += CNN_EPI_SPLIT) {
         const int y = y0 + r;
         if (y >= Himg) break;   // warp-uniform
         float v[N];
@@ -884,7 +894,7 @@ static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, S::SMEM);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CNN_CONV_THREADS, S::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     slots = sms * per_sm;
@@ -895,7 +905,7 @@ static cudaError_t launch_conv(const __nv_bfloat16* X, int W, int H, const __nv_
   if (reinterpret_cast<uintptr_t>(Wt) & 15u) return cudaErrorInvalidValue;
   const int tiles_x = (W + CNN_TILE - 1) / CNN_TILE;
   const int n_tiles = tiles_x * ((H + R - 1) / R);
-  kern<<<min(n_tiles, slots), 192, S::SMEM, s>>>(map, W, H, tiles_x, n_tiles, Wt, b, out, mask,
+  kern<<<min(n_tiles, slots), CNN_CONV_THREADS, S::SMEM, s>>>(map, W, H, tiles_x, n_tiles, Wt, b, out, mask,
                                                  nout, err);
   return cudaGetLastError();
 }
