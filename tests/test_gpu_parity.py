@@ -169,9 +169,10 @@ def test_energy_eval_matches_oracle(V):
                                                ("boxes640_stereo", dict(size=(90, 70), N=3), 2),
                                                ("rgbd_batch", dict(size=(77, 41), N=4), 3)])
 def test_estep_parity(V, name, kw, direction):
-    """Every posterior within 1e-4 of the oracle's; a chain with a term whose
-    observability float32 decides within rounding of a border or the camera
-    plane must match the oracle under one of that term's decisions."""
+    """Every posterior within 1e-4 of the oracle's (the emissions project in
+    double-float); a chain with a term whose observability is decided within
+    rounding of a border or the camera plane must match the oracle under one
+    of that term's decisions (none were met on these cases)."""
     win = window(name, 7, **kw)
     ctx, P, p = make_ctx(V, win)
     try:
